@@ -1,0 +1,363 @@
+"""FP64 CPU oracle for the macro-element HDG Newton step (arXiv 2507.22195).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by the smoke check and by
+the benchmark's CPU-baseline leg; never by the product path.  The C source
+``mehdg_oracle.c`` is compiled here with gcc into ``liborc.so`` (no shared
+code with the CUDA library).
+
+Mesh-level helpers below gather traces from the global trace vector, call the
+per-macro-element C routines and sum the two sides of every global face
+(eq. s32c; Algorithm 1, assembly of b-hat), then offer a monolithic
+brute-force Newton solve for tiny meshes to pin the condensation
+(eqs. R1-R6).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mehdg_oracle.c")
+_LIB = os.path.join(_HERE, "liborc.so")
+_lock = threading.Lock()
+_lib = None
+
+EC, ES, KEPES = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, portable flags)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Params(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("Re", C.c_double), ("Pr", C.c_double),
+                ("Mach", C.c_double), ("dt", C.c_double), ("viscous", C.c_int),
+                ("flux", C.c_int), ("time_term", C.c_int)]
+
+
+def params(gamma=1.4, Re=1600.0, Pr=0.71, Mach=0.1, dt=1.0, viscous=0, flux=KEPES, time_term=1):
+    return Params(gamma, Re, Pr, Mach, dt, int(viscous), int(flux), int(time_term))
+
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+_lp = C.POINTER(C.c_long)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            L.orc_gauss.argtypes = [C.c_int, _dp, _dp]
+            L.orc_gll.argtypes = [C.c_int, _dp]
+            L.orc_u_of_v.argtypes = [C.c_double, _dp, _dp]
+            L.orc_prim_of_v.argtypes = [C.c_double, _dp, _dp, _dp, _dp]
+            L.orc_A0.argtypes = [C.c_double, _dp, _dp]
+            L.orc_dudv_cs.argtypes = [C.c_double, _dp, _dp]
+            L.orc_flux_phys.argtypes = [C.c_double, _dp, _dp, _dp]
+            L.orc_flux_num.argtypes = [C.c_int, C.c_double, _dp, _dp, _dp, _dp]
+            L.orc_face_flux.argtypes = [C.POINTER(Params), _dp, _dp, _dp, _dp, _dp]
+            L.orc_visc_flux.argtypes = [C.POINTER(Params), _dp, _dp, _dp]
+            L.orc_kepes_parts.argtypes = [C.c_double, _dp, _dp, _dp, _dp, _dp, _dp]
+            L.orc_logmean.argtypes = [C.c_double, C.c_double]
+            L.orc_logmean.restype = C.c_double
+            L.orc_residual.argtypes = [C.POINTER(Params), C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp,
+                                       _dp, _dp, _dp]
+            L.orc_entropy_defect.argtypes = [C.POINTER(Params), C.c_int, C.c_int, _dp, _dp]
+            L.orc_entropy_defect.restype = C.c_double
+            L.orc_jacobian.argtypes = [C.POINTER(Params), C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp] + [_dp] * 9
+            L.orc_getrf.argtypes = [C.c_int, _dp, _ip]
+            L.orc_getrs.argtypes = [C.c_int, _dp, _ip, C.c_int, _dp]
+            L.orc_condense_blocks.argtypes = [C.c_int, C.c_long, C.c_long, C.c_long] + [_dp] * 12 + \
+                [_dp, _dp, _dp, _dp, _dp]
+            L.orc_matvec.argtypes = [C.c_long, C.c_long, _dp, _dp, _dp]
+            L.orc_dof_counts_tet.argtypes = [C.c_int, C.c_int, C.c_long, _lp, _lp]
+            L.orc_dof_counts_hex.argtypes = [C.c_int, C.c_int, C.c_long, C.c_int, _lp, _lp]
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous, (a.dtype, a.flags)
+    return a.ctypes.data_as(_dp)
+
+
+def _f(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ---------------------------------------------------------------- tables
+def gauss(n):
+    x, w = np.zeros(n), np.zeros(n)
+    assert lib().orc_gauss(n, _p(x), _p(w)) == 0
+    return x, w
+
+
+def gll(p):
+    x = np.zeros(p + 1)
+    assert lib().orc_gll(p, _p(x)) == 0
+    return x
+
+
+# ---------------------------------------------------------------- point-wise
+def u_of_v(v, gamma=1.4):
+    v = _f(v); u = np.zeros(5); lib().orc_u_of_v(gamma, _p(v), _p(u)); return u
+
+
+def prim_of_v(v, gamma=1.4):
+    v = _f(v); r, P = C.c_double(), C.c_double(); V = np.zeros(3)
+    lib().orc_prim_of_v(gamma, _p(v), C.byref(r), _p(V), C.byref(P))
+    return r.value, V, P.value
+
+
+def A0(v, gamma=1.4):
+    v = _f(v); A = np.zeros(25); lib().orc_A0(gamma, _p(v), _p(A)); return A.reshape(5, 5)
+
+
+def dudv_cs(v, gamma=1.4):
+    v = _f(v); A = np.zeros(25); lib().orc_dudv_cs(gamma, _p(v), _p(A)); return A.reshape(5, 5)
+
+
+def flux_phys(v, n, gamma=1.4):
+    v, n = _f(v), _f(n); F = np.zeros(5); lib().orc_flux_phys(gamma, _p(v), _p(n), _p(F)); return F
+
+
+def flux_num(kind, vh, v, n, gamma=1.4):
+    vh, v, n = _f(vh), _f(v), _f(n); F = np.zeros(5)
+    lib().orc_flux_num(kind, gamma, _p(vh), _p(v), _p(n), _p(F)); return F
+
+
+def face_flux(prm, vh, v, q, n):
+    vh, v, n = _f(vh), _f(v), _f(n); q = None if q is None else _f(q); F = np.zeros(5)
+    lib().orc_face_flux(C.byref(prm), _p(vh), _p(v), _p(q), _p(n), _p(F)); return F
+
+
+def visc_flux(prm, v, q):
+    v, q = _f(v), _f(q); G = np.zeros(15)
+    lib().orc_visc_flux(C.byref(prm), _p(v), _p(q), _p(G)); return G.reshape(5, 3)
+
+
+def kepes_parts(vh, v, n, gamma=1.4):
+    vh, v, n = _f(vh), _f(v), _f(n)
+    R, L, T = np.zeros(25), np.zeros(5), np.zeros(5)
+    lib().orc_kepes_parts(gamma, _p(vh), _p(v), _p(n), _p(R), _p(L), _p(T))
+    return R.reshape(5, 5), L, T
+
+
+def logmean(a, b):
+    return lib().orc_logmean(float(a), float(b))
+
+
+# ---------------------------------------------------------------- one element
+def sizes(p, m):
+    n = m * p + 1
+    Nn = n ** 3
+    return n, Nn, 5 * Nn, 15 * Nn, 30 * n * n
+
+
+def residual_K(prm, p, m, box, v, vs, vh_loc, q=None):
+    n, Nn, Nv, Nq, Nt = sizes(p, m)
+    RV, RQ, RH = np.zeros(Nv), np.zeros(Nq), np.zeros(Nt)
+    rc = lib().orc_residual(C.byref(prm), p, m, _p(_f(box)), _p(_f(v)), _p(_f(vs)),
+                            _p(_f(vh_loc)), _p(None if q is None else _f(q)), _p(RV), _p(RQ), _p(RH))
+    assert rc == 0
+    return RV, (RQ if q is not None else None), RH
+
+
+def entropy_defect_K(prm, p, m, box, v):
+    return lib().orc_entropy_defect(C.byref(prm), p, m, _p(_f(box)), _p(_f(v)))
+
+
+def jacobian_K(prm, p, m, box, v, vs, vh_loc, q=None):
+    n, Nn, Nv, Nq, Nt = sizes(p, m)
+    vis = q is not None
+    B = dict(Avv=np.zeros((Nv, Nv)), Avh=np.zeros((Nv, Nt)), Ahv=np.zeros((Nt, Nv)),
+             Ahh=np.zeros((Nt, Nt)))
+    if vis:
+        B.update(Avq=np.zeros((Nv, Nq)), Ahq=np.zeros((Nt, Nq)), Aqq=np.zeros((Nq, Nq)),
+                 Aqv=np.zeros((Nq, Nv)), Aqh=np.zeros((Nq, Nt)))
+    g = lambda k: _p(B[k]) if k in B else None
+    rc = lib().orc_jacobian(C.byref(prm), p, m, _p(_f(box)), _p(_f(v)), _p(_f(vs)), _p(_f(vh_loc)),
+                            _p(None if q is None else _f(q)),
+                            g("Avv"), g("Avh"), g("Ahv"), g("Ahh"), g("Avq"), g("Ahq"),
+                            g("Aqq"), g("Aqv"), g("Aqh"))
+    assert rc == 0
+    return B
+
+
+def getrf(A):
+    A = _f(A).copy(); N = A.shape[0]; piv = np.zeros(N, dtype=np.int32)
+    info = lib().orc_getrf(N, _p(A), piv.ctypes.data_as(_ip))
+    return A, piv, info
+
+
+def getrs(LU, piv, B):
+    B = _f(B).copy(); N = LU.shape[0]
+    nrhs = 1 if B.ndim == 1 else B.shape[1]
+    lib().orc_getrs(N, _p(LU), piv.ctypes.data_as(_ip), nrhs, _p(B))
+    return B
+
+
+def solve(A, b):
+    LU, piv, info = getrf(A)
+    assert info == 0, "singular"
+    return getrs(LU, piv, b)
+
+
+def condense_K(viscous, R, B, want_Ahat=False, dvh=None):
+    """eqs. R2-R6 for one element from its residuals R=(RV,RQ,RH) and blocks B."""
+    RV, RQ, RH = R
+    Nv, Nt = B["Avv"].shape[0], B["Avh"].shape[1]
+    Nq = B["Aqq"].shape[0] if viscous else 0
+    bhat = np.zeros(Nt)
+    Ahat = np.zeros((Nt, Nt)) if want_Ahat else None
+    dV = np.zeros(Nv) if dvh is not None else None
+    dQ = np.zeros(Nq) if (dvh is not None and viscous) else None
+    g = lambda k: _p(B[k]) if (k in B) else None
+    rc = lib().orc_condense_blocks(int(viscous), Nv, Nq, Nt, _p(_f(RV)),
+                                   _p(None if RQ is None else _f(RQ)), _p(_f(RH)),
+                                   g("Avv"), g("Avh"), g("Ahv"), g("Ahh"), g("Avq"), g("Ahq"),
+                                   g("Aqq"), g("Aqv"), g("Aqh"),
+                                   _p(bhat), _p(Ahat), _p(None if dvh is None else _f(dvh)),
+                                   _p(dV), _p(dQ))
+    assert rc == 0, rc
+    return bhat, Ahat, dV, dQ
+
+
+def dof_counts_tet(p, m, n_tet):
+    a, b = C.c_long(), C.c_long()
+    lib().orc_dof_counts_tet(p, m, n_tet, C.byref(a), C.byref(b))
+    return a.value, b.value
+
+
+def dof_counts_hex(p, m, n_macro, viscous):
+    a, b = C.c_long(), C.c_long()
+    lib().orc_dof_counts_hex(p, m, n_macro, int(viscous), C.byref(a), C.byref(b))
+    return a.value, b.value
+
+
+# ---------------------------------------------------------------- mesh level
+def gather_trace(mesh, vhat_global, K):
+    """local trace [6][5][n2] of element K from the global trace vector"""
+    return np.ascontiguousarray(vhat_global[mesh.face_gid[K]])
+
+
+def scatter_trace(mesh, local, K, out):
+    for f in range(6):
+        out[mesh.face_gid[K, f]] += local[f]
+
+
+def residual_mesh(prm, mesh, st, Ks=None):
+    """R_V [K,5,Nn], R_Q [K,5,3,Nn] or None, R_Vhat global [G,5,n2] (sum of both sides)."""
+    p, m, Nn, n2 = mesh.p, mesh.m, mesh.Nn, mesh.n2
+    Ks = range(mesh.nK) if Ks is None else Ks
+    RV = np.zeros((mesh.nK, 5, Nn))
+    RQ = np.zeros((mesh.nK, 5, 3, Nn)) if st.q is not None else None
+    RH = np.zeros((mesh.n_global_faces, 5, n2))
+    for K in Ks:
+        vh = gather_trace(mesh, st.vhat, K)
+        rv, rq, rh = residual_K(prm, p, m, mesh.boxes[K], st.v[K], st.vstar[K], vh,
+                                None if st.q is None else st.q[K])
+        RV[K] = rv.reshape(5, Nn)
+        if RQ is not None:
+            RQ[K] = rq.reshape(5, 3, Nn)
+        scatter_trace(mesh, rh.reshape(6, 5, n2), K, RH)
+    return RV, RQ, RH
+
+
+def element_system(prm, mesh, st, K):
+    p, m = mesh.p, mesh.m
+    vh = gather_trace(mesh, st.vhat, K)
+    q = None if st.q is None else st.q[K]
+    R = residual_K(prm, p, m, mesh.boxes[K], st.v[K], st.vstar[K], vh, q)
+    B = jacobian_K(prm, p, m, mesh.boxes[K], st.v[K], st.vstar[K], vh, q)
+    return R, B
+
+
+def condense_mesh(prm, mesh, st, want_Ahat=False):
+    """b-hat global (sum over elements, Algorithm 1 local contributions) and,
+    optionally, the list of local A-hat^K."""
+    n2 = mesh.n2
+    bh = np.zeros((mesh.n_global_faces, 5, n2))
+    Ahats = []
+    for K in range(mesh.nK):
+        R, B = element_system(prm, mesh, st, K)
+        b, A, _, _ = condense_K(prm.viscous, R, B, want_Ahat)
+        scatter_trace(mesh, b.reshape(6, 5, n2), K, bh)
+        Ahats.append(A)
+    return bh, Ahats
+
+
+def assemble_Ahat(mesh, Ahats):
+    G = mesh.n_global_faces * 5 * mesh.n2
+    A = np.zeros((G, G))
+    idx = lambda K: (mesh.face_gid[K][:, None] * 5 * mesh.n2 + np.arange(5 * mesh.n2)[None, :]).ravel()
+    for K, AK in enumerate(Ahats):
+        ii = idx(K)
+        A[np.ix_(ii, ii)] += AK
+    return A
+
+
+def recover_mesh(prm, mesh, st, dvh_global):
+    """eqs. R2, R6 for every element: dV [K,5,Nn], dQ [K,5,3,Nn] or None."""
+    Nn = mesh.Nn
+    dV = np.zeros((mesh.nK, 5, Nn))
+    dQ = np.zeros((mesh.nK, 5, 3, Nn)) if prm.viscous else None
+    for K in range(mesh.nK):
+        R, B = element_system(prm, mesh, st, K)
+        dvh = np.ascontiguousarray(dvh_global[mesh.face_gid[K]]).ravel()
+        _, _, v_, q_ = condense_K(prm.viscous, R, B, False, dvh)
+        dV[K] = v_.reshape(5, Nn)
+        if dQ is not None:
+            dQ[K] = q_.reshape(5, 3, Nn)
+    return dV, dQ
+
+
+def brute_force(prm, mesh, st):
+    """Monolithic Newton increment: assemble J over (Q, V, V-hat global) for all
+    elements and solve J d = -R with the oracle's GEPP (tiny meshes only)."""
+    nK, Nn, n2 = mesh.nK, mesh.Nn, mesh.n2
+    Nv, Nq, Ntg = 5 * Nn, 15 * Nn, mesh.n_global_faces * 5 * n2
+    vis = bool(prm.viscous)
+    nq_tot = nK * Nq if vis else 0
+    N = nq_tot + nK * Nv + Ntg
+    J = np.zeros((N, N))
+    R = np.zeros(N)
+    offQ = lambda K: K * Nq
+    offV = lambda K: nq_tot + K * Nv
+    offH = nq_tot + nK * Nv
+    for K in range(nK):
+        (RV, RQ, RH), B = element_system(prm, mesh, st, K)
+        iv = offV(K) + np.arange(Nv)
+        ih = (offH + mesh.face_gid[K][:, None] * 5 * n2 + np.arange(5 * n2)[None, :]).ravel()
+        R[iv] += RV
+        R[ih] += RH
+        J[np.ix_(iv, iv)] += B["Avv"]
+        J[np.ix_(iv, ih)] += B["Avh"]
+        J[np.ix_(ih, iv)] += B["Ahv"]
+        J[np.ix_(ih, ih)] += B["Ahh"]
+        if vis:
+            iq = offQ(K) + np.arange(Nq)
+            R[iq] += RQ
+            J[np.ix_(iq, iq)] += B["Aqq"]
+            J[np.ix_(iq, iv)] += B["Aqv"]
+            J[np.ix_(iq, ih)] += B["Aqh"]
+            J[np.ix_(iv, iq)] += B["Avq"]
+            J[np.ix_(ih, iq)] += B["Ahq"]
+    d = solve(J, -R)
+    dQ = d[:nq_tot].reshape(nK, 5, 3, Nn) if vis else None
+    dV = d[nq_tot:offH].reshape(nK, 5, Nn)
+    dH = d[offH:].reshape(mesh.n_global_faces, 5, n2)
+    return dQ, dV, dH

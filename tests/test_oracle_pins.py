@@ -1,0 +1,414 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test ties a part of the oracle to something other than itself: a closed
+form, an identity the paper proves, a library routine for a special case, a
+number the paper prints, or a brute-force solve.  A plausible mistake in the
+oracle (a dropped term, a sign, a transposed operand) fails at least one.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2507_22195_gb300 import inputs as I
+
+G = 1.4
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def rand_state(rng, M=0.3):
+    """random physical entropy-variable state"""
+    rho = rng.uniform(0.5, 2.0)
+    P = rng.uniform(0.4, 2.0)
+    V = rng.uniform(-M, M, 3)
+    return I.entropy_vars(np.array(rho), [np.array(c) for c in V], np.array(P)).astype(float)
+
+
+def normals():
+    out = []
+    for d in range(3):
+        for s in (-1.0, 1.0):
+            n = np.zeros(3); n[d] = s; out.append(n)
+    return out
+
+
+# ---------------------------------------------------------------- tables
+@pytest.mark.parametrize("npt", [2, 3, 4, 5, 6])
+def test_gauss_matches_library(npt):
+    x, w = oracle.gauss(npt)
+    xr, wr = np.polynomial.legendre.leggauss(npt)
+    assert np.allclose(x, xr, atol=1e-15) and np.allclose(w, wr, atol=1e-15)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_gll_are_lobatto_points(p):
+    x = oracle.gll(p)
+    assert x[0] == -1.0 and x[-1] == 1.0
+    # interior nodes are the roots of P_p'
+    dP = np.polynomial.legendre.Legendre.basis(p).deriv()
+    assert np.allclose(dP(x[1:-1]), 0.0, atol=1e-14)
+
+
+# ---------------------------------------------------------------- thermodynamics
+def test_u_of_v_inverts_eq_s222():
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        rho, P = rng.uniform(0.3, 3), rng.uniform(0.3, 3)
+        V = rng.uniform(-1, 1, 3)
+        v = I.entropy_vars(np.array(rho), [np.array(c) for c in V], np.array(P)).astype(float)
+        u = oracle.u_of_v(v)
+        E = P / (G - 1) + 0.5 * rho * V @ V
+        assert np.allclose(u, [rho, *(rho * V), E], rtol=1e-13)
+
+
+def _H_of_u(u):
+    """entropy function H = -rho s/(gamma-1), s = ln(P/rho^gamma) (eq. en)"""
+    rho = u[0]
+    P = (G - 1) * (u[4] - 0.5 * (u[1] ** 2 + u[2] ** 2 + u[3] ** 2) / rho)
+    s = np.log(P / rho ** G)
+    return -rho * s / (G - 1)
+
+
+def test_entropy_variables_are_dH_du():
+    """v = dH/du (Sec. 2.2), derivative by complex step in the test"""
+    rng = np.random.default_rng(2)
+    for _ in range(10):
+        v = rand_state(rng)
+        u = oracle.u_of_v(v)
+        g = np.zeros(5)
+        for l in range(5):
+            z = u.astype(complex); z[l] += 1e-30j
+            g[l] = _H_of_u(z).imag / 1e-30
+        assert np.allclose(g, v, rtol=1e-12, atol=1e-12)
+
+
+def test_A0_closed_form_is_du_dv_and_spd():
+    rng = np.random.default_rng(3)
+    for _ in range(10):
+        v = rand_state(rng)
+        A, J = oracle.A0(v), oracle.dudv_cs(v)
+        assert np.allclose(A, J, rtol=1e-13, atol=1e-14)
+        assert np.allclose(A, A.T)
+        assert np.linalg.eigvalsh(A).min() > 0
+
+
+def test_entropy_potential_eq_poen():
+    """Psi_n = F_n^T v - calF_n = rho V.n (eq. poen) with the entropy flux
+    calF = H V = -rho s V/(gamma-1), the flux paired with H of eq. en (the
+    printed calF = -rho s V lacks the 1/(gamma-1) of H)."""
+    rng = np.random.default_rng(4)
+    for _ in range(10):
+        v = rand_state(rng)
+        rho, V, P = oracle.prim_of_v(v)
+        s = math.log(P / rho ** G)
+        for n in normals():
+            Fn = oracle.flux_phys(v, n)
+            assert abs(Fn @ v - (-rho * s * V @ n / (G - 1)) - rho * V @ n) < 1e-13
+
+
+def test_logmean():
+    for a, b in [(1.0, 2.0), (0.3, 7.0), (1.0, 1.0 + 1e-3), (2.0, 2.0)]:
+        ref = a if a == b else (b - a) / math.log(b / a)
+        assert abs(oracle.logmean(a, b) - ref) <= 1e-15 * ref + (1e-12 if abs(a - b) < 1e-2 else 0)
+    # continuity across the series/logarithm switch (u = 1e-4 <=> zeta ~ 1.0202)
+    z = (1 + 1e-2) / (1 - 1e-2)
+    lo, hi = oracle.logmean(1.0, z * (1 - 1e-12)), oracle.logmean(1.0, z * (1 + 1e-12))
+    assert abs(hi - lo) < 1e-11
+
+
+# ---------------------------------------------------------------- fluxes
+@pytest.mark.parametrize("kind", [oracle.EC, oracle.ES, oracle.KEPES])
+def test_flux_consistency(kind):
+    """F-hat(a, a) = F(a).n"""
+    rng = np.random.default_rng(5)
+    for _ in range(5):
+        v = rand_state(rng)
+        for n in normals():
+            assert np.allclose(oracle.flux_num(kind, v, v, n), oracle.flux_phys(v, n), rtol=1e-13, atol=1e-14)
+
+
+def test_ec_symmetric_and_kep_structure():
+    rng = np.random.default_rng(6)
+    for _ in range(10):
+        a, b = rand_state(rng), rand_state(rng)
+        ra, Va, Pa = oracle.prim_of_v(a)
+        rb, Vb, Pb = oracle.prim_of_v(b)
+        for n in normals():
+            F1, F2 = oracle.flux_num(oracle.EC, a, b, n), oracle.flux_num(oracle.EC, b, a, n)
+            assert np.allclose(F1, F2, rtol=1e-14, atol=1e-15)
+            Vbar = 0.5 * (Va + Vb)
+            Pbar = 0.5 * (ra + rb) / (0.5 * (ra / Pa + rb / Pb))
+            # momentum flux = Vbar * mass flux + Pbar n (eq. KEP)
+            assert np.allclose(F1[1:4], Vbar * F1[0] + Pbar * n, rtol=1e-13, atol=1e-15)
+
+
+def _psi_n(v, n):
+    rho, V, P = oracle.prim_of_v(v)
+    return rho * V @ n
+
+
+def test_ec_condition_thm51():
+    """[[v]].F-bar - [[Psi_n]] = 0 (Thm. 5.1, eq. EC_1)"""
+    rng = np.random.default_rng(7)
+    for _ in range(50):
+        v, vh = rand_state(rng), rand_state(rng)
+        for n in normals():
+            F = oracle.flux_num(oracle.EC, vh, v, n)
+            r = (vh - v) @ F - (_psi_n(vh, n) - _psi_n(v, n))
+            assert abs(r) < 1e-13 * (1 + np.abs(vh - v).sum() * np.abs(F).sum())
+
+
+def test_kepes_entropy_production_thm52():
+    """[[v]].F-hat - [[Psi_n]] = -1/2 [[v]]^T R|L|T R^T [[v]] <= 0 (Thm. 5.2)"""
+    rng = np.random.default_rng(8)
+    for _ in range(50):
+        v, vh = rand_state(rng), rand_state(rng)
+        for n in normals():
+            F = oracle.flux_num(oracle.KEPES, vh, v, n)
+            R, L, T = oracle.kepes_parts(vh, v, n)
+            dv = vh - v
+            quad = dv @ R @ np.diag(L * T) @ R.T @ dv
+            r = dv @ F - (_psi_n(vh, n) - _psi_n(v, n))
+            assert quad >= 0
+            assert abs(r + 0.5 * quad) < 1e-12 * (1 + quad + np.abs(dv).sum() * np.abs(F).sum())
+
+
+def test_es_flux_small_jumps_dissipate():
+    """ES flux (eq. Flux_En_Inv): entropy production <= 0 for near states"""
+    rng = np.random.default_rng(9)
+    for _ in range(50):
+        v = rand_state(rng)
+        vh = v + rng.uniform(-1e-3, 1e-3, 5)
+        for n in normals():
+            F = oracle.flux_num(oracle.ES, vh, v, n)
+            r = (vh - v) @ F - (_psi_n(vh, n) - _psi_n(v, n))
+            assert r <= 1e-15
+
+
+def test_barth_scaling_at_equal_states():
+    """R T R^T = A0 at equal states (eq. KEPES4)"""
+    rng = np.random.default_rng(10)
+    for _ in range(10):
+        v = rand_state(rng)
+        for n in normals():
+            R, L, T = oracle.kepes_parts(v, v, n)
+            assert np.allclose(R @ np.diag(T) @ R.T, oracle.A0(v), rtol=1e-12, atol=1e-13)
+
+
+# ---------------------------------------------------------------- viscous
+def test_viscous_flux_dissipates_entropy_and_is_linear_in_q():
+    """sum_j q_j . G_j = -q^T K q <= 0 (eq. entropy evolution diffuse) and
+    G(v, a q1 + b q2) = a G(v,q1) + b G(v,q2)"""
+    prm = oracle.params(viscous=1, Re=100.0, Mach=0.3)
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        v = rand_state(rng)
+        q1, q2 = rng.normal(size=15), rng.normal(size=15)
+        G1, G2 = oracle.visc_flux(prm, v, q1), oracle.visc_flux(prm, v, q2)
+        assert np.sum(q1.reshape(5, 3) * G1) <= 1e-15
+        G12 = oracle.visc_flux(prm, v, 0.3 * q1 - 1.7 * q2)
+        assert np.allclose(G12, 0.3 * G1 - 1.7 * G2, rtol=1e-12, atol=1e-14)
+
+
+def test_viscous_flux_vanishes_for_rigid_rotation():
+    """tau = 0 and grad T = 0 for a rigid rotation V = w x r at constant state"""
+    prm = oracle.params(viscous=1, Re=100.0, Mach=0.3)
+    w = np.array([0.3, -0.2, 0.5])
+    rho, P = 1.2, 0.9
+    V = np.array([0.1, 0.2, -0.1])
+    gradV = np.array([[0, -w[2], w[1]], [w[2], 0, -w[0]], [-w[1], w[0], 0]])   # dV_i/dx_j
+    beta = rho / P
+    v = I.entropy_vars(np.array(rho), [np.array(c) for c in V], np.array(P)).astype(float)
+    # grad v at constant rho, P: dv1 = -beta V.gradV, dv_{2..4} = beta gradV, dv5 = 0
+    q = np.zeros((5, 3))
+    q[0] = -beta * V @ gradV
+    q[1:4] = beta * gradV
+    assert np.abs(oracle.visc_flux(prm, v, q.ravel())).max() < 1e-15
+
+
+# ---------------------------------------------------------------- residual
+@pytest.mark.parametrize("flux", [oracle.EC, oracle.ES, oracle.KEPES])
+@pytest.mark.parametrize("vis", [0, 1])
+def test_free_stream_preservation(flux, vis):
+    """P1: constant state, v-hat = v, q = 0  =>  R = 0"""
+    mesh = I.periodic_mesh(2, 2, 2)
+    st = I.make_state(mesh, "const", 0.0, 1, 2, viscous=bool(vis))
+    if vis:
+        st.q[:] = 0
+    prm = oracle.params(flux=flux, viscous=vis)
+    RV, RQ, RH = oracle.residual_mesh(prm, mesh, st)
+    assert np.abs(RV).max() < 1e-13 and np.abs(RH).max() < 1e-13
+    if vis:
+        assert np.abs(RQ).max() < 1e-13
+
+
+@pytest.mark.parametrize("flux", [oracle.EC, oracle.KEPES, oracle.ES])
+def test_discrete_entropy_identity_prop41(flux):
+    """P5: periodic Euler, time term off:
+    v^T R_V - vhat^T R_Vhat = -D_Q - sum <[[v]].F-hat - [[Psi_n]]>_Q ;
+    the last sum vanishes for EC (Thm. 5.1) and is <= 0 for KEPES/ES."""
+    mesh = I.periodic_mesh(2, 2, 2)
+    st = I.make_state(mesh, "tgv", 1e-2, 3, 4, M0=0.3)
+    prm = oracle.params(flux=flux, viscous=0, time_term=0)
+    RV, _, RH = oracle.residual_mesh(prm, mesh, st)
+    lhs = np.sum(st.v * RV) - np.sum(st.vhat * RH)
+    D = sum(oracle.entropy_defect_K(prm, 2, 2, mesh.boxes[K], st.v[K]) for K in range(mesh.nK))
+    if flux == oracle.EC:
+        assert abs(lhs + D) < 1e-12 * (abs(lhs) + abs(D) + np.abs(RV).sum() * 1e-3)
+    else:
+        assert lhs + D > 0
+
+
+def _box_moments(fun, box, npts=12):
+    """-int_K F_{k,j}(u) dV (moment with x_j) and the face integrals
+    int_dK F.n dS, int_dK x_j F.n dS, by a tensor Gauss rule of the test's own"""
+    xg, wg = np.polynomial.legendre.leggauss(npts)
+    lo, hi = np.array(box[:3]), np.array(box[3:])
+    X = [lo[d] + (hi[d] - lo[d]) * (xg + 1) / 2 for d in range(3)]
+    W = [(hi[d] - lo[d]) / 2 * wg for d in range(3)]
+    vol = np.zeros((5, 3))
+    Z, Y, Xx = np.meshgrid(X[2], X[1], X[0], indexing="ij")
+    WW = (W[2][:, None, None] * W[1][None, :, None] * W[0][None, None, :])
+    F = fun(Xx, Y, Z)                        # [5][3][...]
+    for j in range(3):
+        vol[:, j] = -np.sum(F[:, j] * WW, axis=(1, 2, 3))
+    face0 = np.zeros(5)
+    face1 = np.zeros((5, 3))
+    for d in range(3):
+        t1, t2 = [(1, 2), (0, 2), (0, 1)][d]
+        B2, B1 = np.meshgrid(X[t2], X[t1], indexing="ij")
+        Wf = W[t2][:, None] * W[t1][None, :]
+        for side, sgn in ((0, -1.0), (1, 1.0)):
+            pts = [None] * 3
+            pts[t1], pts[t2] = B1, B2
+            pts[d] = np.full_like(B1, hi[d] if side else lo[d])
+            Ff = fun(*pts)[:, d] * sgn
+            face0 += np.sum(Ff * Wf, axis=(1, 2))
+            for j in range(3):
+                face1[:, j] += np.sum(Ff * pts[j] * Wf, axis=(1, 2))
+    return vol, face0, face1
+
+
+def test_exact_vortex_truncation_converges():
+    """P6: with the exact vortex (eq. S601) on the nodes and traces of one
+    macro-element and no time term, the moments sum_a R_V[a] and
+    sum_a x_a R_V[a] (the C0 basis reproduces 1 and x) approach the exact
+    integrals int_dK F.n and -int_K F_j + int_dK x_j F.n as h -> 0."""
+    p = 3
+    box = [3.5, 3.5, 3.5, 6.5, 6.5, 6.5]
+
+    def Fexact(x, y, z):
+        rho, V, P = I.vortex_prim(x, y, z)
+        E = P / (G - 1) + 0.5 * rho * (V[0] ** 2 + V[1] ** 2 + V[2] ** 2)
+        F = np.zeros((5, 3) + np.shape(x))
+        for j in range(3):
+            F[0, j] = rho * V[j]
+            for i in range(3):
+                F[1 + i, j] = rho * V[i] * V[j] + (P if i == j else 0)
+            F[4, j] = V[j] * (E + P)
+        return F
+
+    vol, f0, f1 = _box_moments(Fexact, box, npts=20)
+    errs = []
+    for m in (1, 2, 4):
+        mesh = I.Mesh(p, m, np.array([box]), np.arange(6).reshape(1, 6), 6)
+        st = I.make_state(mesh, "vortex", 0.0, 1, 2)
+        prm = oracle.params(flux=oracle.KEPES, time_term=0)
+        RV, _, _ = oracle.residual_mesh(prm, mesh, st)
+        X, Y, Z = I.node_coords(mesh, 0)
+        m0 = RV[0].sum(axis=1)
+        m1 = np.stack([RV[0] @ X, RV[0] @ Y, RV[0] @ Z], axis=1)
+        errs.append((np.abs(m0 - f0).max() / np.abs(f0).max(),
+                     np.abs(m1 - (vol + f1)).max() / np.abs(vol + f1).max()))
+    errs = np.array(errs)
+    rates = np.log2(errs[:-1] / errs[1:])
+    assert errs[-1].max() < 1e-5, errs
+    assert rates.min() >= p, (errs, rates)
+
+
+def test_rq_linear_and_mass_block():
+    """P10: R_Q is linear in (q, v, vhat); A_qq = I_15 (x) M with M SPD,
+    1^T M 1 = |K|; A_qv 1 = boundary term (int d_d phi_a = oint n_d phi_a)."""
+    p, m = 2, 1
+    mesh = I.periodic_mesh(1, p, m, 0.0, 1.3)
+    st = I.make_state(mesh, "tgv", 1e-2, 3, 4, viscous=True, M0=0.3)
+    prm = oracle.params(viscous=1, Re=100.0, Mach=0.3)
+    vh = oracle.gather_trace(mesh, st.vhat, 0)
+    B = oracle.jacobian_K(prm, p, m, mesh.boxes[0], st.v[0], st.vstar[0], vh, st.q[0])
+    Nn = mesh.Nn
+    Aqq = B["Aqq"]
+    M = Aqq[:Nn, :Nn]
+    assert np.allclose(Aqq, np.kron(np.eye(15), M))
+    assert np.allclose(M, M.T) and np.linalg.eigvalsh(M).min() > 0
+    assert abs(M.sum() - 1.3 ** 3) < 1e-13
+    _, RQ0, _ = oracle.residual_K(prm, p, m, mesh.boxes[0], st.v[0], st.vstar[0], vh, st.q[0])
+    lin = Aqq @ st.q[0].ravel() + B["Aqv"] @ st.v[0].ravel() + B["Aqh"] @ vh.ravel()
+    assert np.allclose(RQ0, lin, rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("flux", [oracle.EC, oracle.ES])
+@pytest.mark.parametrize("vis", [0, 1])
+def test_jacobian_matches_central_differences(flux, vis):
+    """P8: complex-step Jacobian blocks vs central differences (step 1e-6)"""
+    p, m = 2, 1
+    mesh = I.periodic_mesh(2, p, m)
+    st = I.make_state(mesh, "tgv", 1e-2, 5, 6, viscous=bool(vis), M0=0.3)
+    prm = oracle.params(flux=flux, viscous=vis, Re=100.0, Mach=0.3)
+    K = 3
+    vh = oracle.gather_trace(mesh, st.vhat, K)
+    q = None if st.q is None else st.q[K]
+    B = oracle.jacobian_K(prm, p, m, mesh.boxes[K], st.v[K], st.vstar[K], vh, q)
+    rng = np.random.default_rng(0)
+    dv, dh = rng.uniform(-1, 1, st.v[K].shape), rng.uniform(-1, 1, vh.shape)
+    dq = None if q is None else rng.uniform(-1, 1, q.shape)
+    eps = 1e-6
+
+    def R(s):
+        return oracle.residual_K(prm, p, m, mesh.boxes[K], st.v[K] + s * dv, st.vstar[K], vh + s * dh,
+                                 None if q is None else q + s * dq)
+    Rp, Rm = R(eps), R(-eps)
+    jV = B["Avv"] @ dv.ravel() + B["Avh"] @ dh.ravel() + (B["Avq"] @ dq.ravel() if vis else 0)
+    jH = B["Ahv"] @ dv.ravel() + B["Ahh"] @ dh.ravel() + (B["Ahq"] @ dq.ravel() if vis else 0)
+    for fd, j in (((Rp[0] - Rm[0]) / (2 * eps), jV), ((Rp[2] - Rm[2]) / (2 * eps), jH)):
+        assert np.linalg.norm(fd - j) / np.linalg.norm(j) < 5e-9
+
+
+@pytest.mark.parametrize("mp", [(1, 1), (1, 2), (2, 1)])
+@pytest.mark.parametrize("vis", [0, 1])
+def test_condensation_matches_monolithic_brute_force(mp, vis):
+    """P7: condense (R3, R5) -> dense global solve -> recover (R2, R6) equals
+    the monolithic GEPP solve of the full Newton system on 2^3 elements"""
+    m, p = mp
+    mesh = I.periodic_mesh(2, p, m)
+    st = I.make_state(mesh, "tgv", 1e-2, 5, 6, viscous=bool(vis), M0=0.3)
+    prm = oracle.params(flux=oracle.ES if vis else oracle.KEPES, viscous=vis, Re=100.0, Mach=0.3)
+    dQ, dV, dH = oracle.brute_force(prm, mesh, st)
+    bh, Ahats = oracle.condense_mesh(prm, mesh, st, want_Ahat=True)
+    A = oracle.assemble_Ahat(mesh, Ahats)
+    x = oracle.solve(A, bh.ravel()).reshape(dH.shape)
+    dV2, dQ2 = oracle.recover_mesh(prm, mesh, st, x)
+    e = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)
+    assert e(x, dH) < 1e-10 and e(dV2, dV) < 1e-10
+    if vis:
+        assert e(dQ2, dQ) < 1e-10
+
+
+def test_getrf_matches_library_solve():
+    rng = np.random.default_rng(12)
+    A = rng.normal(size=(60, 60)); b = rng.normal(size=60)
+    x = oracle.solve(A, b)
+    assert np.allclose(x, np.linalg.solve(A, b), rtol=1e-11)
+    LU, piv, info = oracle.getrf(A)
+    assert piv[0] == int(np.argmax(np.abs(A[:, 0])))
+
+
+def test_dof_tables():
+    """P9: counting reproduces Tables Inv_TGV_DOF / TGV_DOF"""
+    rows = json.load(open(os.path.join(HERE, "golden", "dof_tables.json")))["rows"]
+    for r in rows:
+        for m in (1, 2):
+            loc, glo = oracle.dof_counts_tet(r["p"], m, r["N_ele"])
+            assert loc == r[f"m{m}_local"] and glo == r[f"m{m}_global"], (r, m, loc, glo)
