@@ -1,0 +1,168 @@
+/*
+ * mehdg.h -- C-ABI of the GB300 (sm_103a) hot path of the entropy-variable
+ * macro-element HDG method (Badrkhani, ten Eikelder, Hasse, Schillinger,
+ * arXiv 2507.22195): the per-macro-element Newton step.
+ *
+ *   residual  : eq. s32 (a-c) with the one-stage implicit term of eq. C242,
+ *               inviscid fluxes of eqs. Flux_En_Inv (ES), EC and ES (KEPES),
+ *               viscous flux of eq. Flux_En_Vis;
+ *   condense  : local Jacobian (eq. R1), Q-elimination and Schur complement
+ *               (eqs. R2, R3), LU of S, right-hand side b-hat (eq. R5b);
+ *   apply     : the four-stage reduced mat-vec of Sec. 6.3 (Algorithm 1,
+ *               global matrix-vector product);
+ *   recover   : local back-substitution, eqs. R2 and R6 (Algorithm 1,
+ *               local recovery).
+ *
+ * Discretisation: each macro-element K is an axis-aligned box split into m^3
+ * hexahedral micro-elements carrying Q_p on Gauss-Lobatto-Legendre nodes,
+ * continuous inside K; tensor Gauss quadrature with p+2 points per direction
+ * per micro-element (volume and faces).  n = m p + 1 nodes per direction,
+ * Nn = n^3, node index A = i + n (j + n k).
+ *
+ * Layouts (all FP64, C-contiguous):
+ *   v, v*      [nK][5][Nn]            entropy variables (eq. s222)
+ *   q, R_Q, dQ [nK][5][3][Nn]         q ~ grad v (eq. s32a); viscous only
+ *   R_V, dV    [nK][5][Nn]
+ *   trace      [n_global_faces][5][n^2]   v-hat, R_V-hat, b-hat, dV-hat, x, y
+ *              face node c = i_t1 + n i_t2, (t1,t2) = the two tangential
+ *              axes in increasing order; local faces x-,x+,y-,y+,z-,z+.
+ * Global trace quantities (R_V-hat, b-hat, y) are sums over the elements
+ * adjacent to each global face (eq. s32c; Algorithm 1, assembly).
+ *
+ * Ownership: every array argument is a caller-owned pointer; the library
+ * never frees it.  Pointers to state (set_state) must stay valid and
+ * unchanged until the next set_state or destroy.  Arrays passed to
+ * residual/condense/apply/recover are DEVICE pointers unless stated
+ * otherwise; mesh arrays (set_mesh) are HOST pointers.  The context owns
+ * its device workspaces (the LU factors of every S^K, pivots, residuals).
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
+ * default stream).  Work is enqueued on it; condense/apply/recover
+ * synchronise that stream once per refinement sweep to test convergence.
+ *
+ * Errors: functions return MEHDG_OK (0) or a negative code below, and keep
+ * a message readable with mehdg_last_error.  Per-element failures (a
+ * non-physical state, a zero pivot, refinement not converged, a device wait
+ * that ran out) are also recorded per element, readable with mehdg_status.
+ */
+#ifndef MEHDG_H
+#define MEHDG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mehdg_ctx mehdg_ctx;
+
+/* inviscid numerical flux */
+typedef enum {
+    MEHDG_FLUX_EC = 0,     /* entropy-conservative, kinetic-energy-preserving, eq. EC   */
+    MEHDG_FLUX_ES = 1,     /* entropy-stable Lax-Friedrichs type, eq. Flux_En_Inv       */
+    MEHDG_FLUX_KEPES = 2   /* KEP and entropy-stable, hybrid LF/Roe dissipation, eq. ES */
+} mehdg_flux;
+
+/* precision of the local LU and Schur products (residuals, Jacobian point
+ * physics and the refinement residual are always FP64) */
+typedef enum {
+    MEHDG_FP64 = 0,        /* FP64 LU on the FP64 pipe                              */
+    MEHDG_MIXED_TF32 = 1,  /* FP32 storage, TF32 tensor-core updates, FP32 accumulate */
+    MEHDG_MIXED_BF16 = 2   /* FP32 storage, BF16 tensor-core updates, FP32 accumulate */
+} mehdg_prec;
+
+enum {
+    MEHDG_OK = 0,
+    MEHDG_EINVAL = -1,     /* bad argument, shape or pointer                        */
+    MEHDG_ENONPHYS = -2,   /* beta <= 0, rho <= 0 or non-finite state at a point    */
+    MEHDG_ESINGULAR = -3,  /* zero pivot in LU(S)                                    */
+    MEHDG_ENOCONV = -4,    /* iterative refinement did not reach refine_tol         */
+    MEHDG_ECUDA = -5,      /* CUDA runtime error                                     */
+    MEHDG_ENOMEM = -6,     /* device allocation failed                               */
+    MEHDG_ESTATE = -7,     /* call out of order (e.g. recover before condense)       */
+    MEHDG_ETIMEOUT = -8    /* a bounded device wait ran out                          */
+};
+
+typedef struct {
+    double gamma;          /* ratio of specific heats                                */
+    double Re, Pr, Mach;   /* viscous data: mu/Re_c = Mach/Re, kappa from Pr         */
+    double dt;             /* time step of the stage term (u(v)-u(v*))/dt, eq. C242  */
+    int viscous;           /* 0 Euler, 1 Navier-Stokes                               */
+    int flux;              /* mehdg_flux                                              */
+    int prec;              /* mehdg_prec                                              */
+    double refine_tol;     /* ||r - S x|| <= refine_tol ||r|| ends refinement         */
+    int refine_max_iter;   /* refinement sweeps before MEHDG_ENOCONV                  */
+    int time_term;         /* 1: include the stage term (default), 0: steady        */
+} mehdg_params;
+
+/* Fill *prm with defaults: gamma 1.4, Re 1600, Pr 0.71, Mach 0.1, dt 1,
+ * Euler, KEPES, MIXED_TF32, refine_tol 1e-12, refine_max_iter 10, time_term 1. */
+void mehdg_default_params(mehdg_params* prm);
+
+/* Create a context.  prm: host pointer, copied.  *out receives the handle. */
+int mehdg_create(mehdg_ctx** out, const mehdg_params* prm);
+
+/* Mesh (Sec. 3.1): nK macro-elements, all with the same degree p (1..4) and
+ * micro-element count m per direction (p[], m[]: host arrays of length nK;
+ * mixed values return MEHDG_EINVAL).  box: host [nK][6] = x0 y0 z0 x1 y1 z1.
+ * face_gid: host [nK][6], global face of each local face, in
+ * [0, n_global_faces); a global face used by two elements couples them
+ * (interior face), one used once is an unshared face.  Allocates the device
+ * workspaces (one dense S^K per element in the precision of prm->prec). */
+int mehdg_set_mesh(mehdg_ctx* ctx, int64_t nK, const int32_t* p, const int32_t* m,
+                   const double* box, const int64_t* face_gid, int64_t n_global_faces);
+
+/* State of the Newton iterate (device pointers, not copied): v [nK][5][Nn],
+ * vhat [G][5][n^2], q [nK][5][3][Nn] (NULL for Euler), vstar [nK][5][Nn]
+ * (state at the start of the step; may be NULL when time_term = 0). */
+int mehdg_set_state(mehdg_ctx* ctx, const double* v, const double* vhat, const double* q,
+                    const double* vstar, void* stream);
+
+/* Residual of eq. s32 at the state: R_V [nK][5][Nn], R_Q [nK][5][3][Nn]
+ * (may be NULL; ignored for Euler), R_Vhat [G][5][n^2] summed over both
+ * sides of every face.  Device pointers, overwritten. */
+int mehdg_residual(mehdg_ctx* ctx, double* R_V, double* R_Q, double* R_Vhat, void* stream);
+
+/* Condensation (eqs. R1-R3, R5b): residual, Jacobian, Q-elimination, LU of
+ * S^K (kept in the context), refined S^-1 products, and
+ * bhat [G][5][n^2] = sum_K bhat^K (device, overwritten).
+ * Ahat_local must be NULL (the explicit A-hat^K is not formed; use apply). */
+int mehdg_condense(mehdg_ctx* ctx, double* bhat, double* Ahat_local, void* stream);
+
+/* y = A-hat x for a global trace vector x (the four stages y1..y4 of
+ * Sec. 6.3 summed over elements).  Needs a prior condense.  Device. */
+int mehdg_apply_condensed(mehdg_ctx* ctx, const double* x, double* y, void* stream);
+
+/* Recovery after the global trace solve: dV (eq. R2) and dQ (eq. R6, NULL
+ * or ignored for Euler) from dVhat [G][5][n^2].  Needs a prior condense. */
+int mehdg_recover(mehdg_ctx* ctx, const double* dVhat, double* dV, double* dQ, void* stream);
+
+/* Copy the per-element status words (0 or a negative code above) of the
+ * last call into the HOST array per_K_status [nK]; synchronises the device.
+ * Also copies, if iters != NULL, the refinement sweeps used per element. */
+int mehdg_status(mehdg_ctx* ctx, int32_t* per_K_status, int32_t* iters);
+
+/* Message of the last error of this context (static storage of ctx). */
+const char* mehdg_last_error(const mehdg_ctx* ctx);
+
+/* Optional timing of the phases with CUDA events recorded on the caller's
+ * stream (off by default).  enable != 0 starts a new record. */
+int mehdg_profile_enable(mehdg_ctx* ctx, int enable);
+
+/* Per-phase sums since profile_enable (synchronises the device): event-timed
+ * milliseconds, launches timed and algorithmic flops (host arrays of length
+ * nphase).  Phases: 0 residual, 1 Jacobian assembly, 2 LU panels (leaf
+ * panels, swaps, TRSM, inner updates), 3 LU outer trailing update (depth
+ * 256), 4 triangular solves, 5 matrix-free tangent residuals. */
+int mehdg_profile_read(mehdg_ctx* ctx, double* ms, int64_t* launches, double* flops, int nphase);
+
+/* Number of kernels this library has launched since it was loaded. */
+int64_t mehdg_launch_count(void);
+
+/* Free every device workspace and the context. */
+void mehdg_destroy(mehdg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MEHDG_H */

@@ -306,7 +306,8 @@ def assemble_Ahat(mesh, Ahats):
     idx = lambda K: (mesh.face_gid[K][:, None] * 5 * mesh.n2 + np.arange(5 * mesh.n2)[None, :]).ravel()
     for K, AK in enumerate(Ahats):
         ii = idx(K)
-        A[np.ix_(ii, ii)] += AK
+        # a face may appear twice in one element (periodic with itself): add, never overwrite
+        np.add.at(A, (ii[:, None], ii[None, :]), AK)
     return A
 
 
@@ -342,20 +343,16 @@ def brute_force(prm, mesh, st):
         (RV, RQ, RH), B = element_system(prm, mesh, st, K)
         iv = offV(K) + np.arange(Nv)
         ih = (offH + mesh.face_gid[K][:, None] * 5 * n2 + np.arange(5 * n2)[None, :]).ravel()
-        R[iv] += RV
-        R[ih] += RH
-        J[np.ix_(iv, iv)] += B["Avv"]
-        J[np.ix_(iv, ih)] += B["Avh"]
-        J[np.ix_(ih, iv)] += B["Ahv"]
-        J[np.ix_(ih, ih)] += B["Ahh"]
+        # np.add.at: trace indices repeat when an element is periodic with itself
+        add = lambda r, c, X: np.add.at(J, (r[:, None], c[None, :]), X)
+        np.add.at(R, iv, RV)
+        np.add.at(R, ih, RH)
+        add(iv, iv, B["Avv"]); add(iv, ih, B["Avh"]); add(ih, iv, B["Ahv"]); add(ih, ih, B["Ahh"])
         if vis:
             iq = offQ(K) + np.arange(Nq)
-            R[iq] += RQ
-            J[np.ix_(iq, iq)] += B["Aqq"]
-            J[np.ix_(iq, iv)] += B["Aqv"]
-            J[np.ix_(iq, ih)] += B["Aqh"]
-            J[np.ix_(iv, iq)] += B["Avq"]
-            J[np.ix_(ih, iq)] += B["Ahq"]
+            np.add.at(R, iq, RQ)
+            add(iq, iq, B["Aqq"]); add(iq, iv, B["Aqv"]); add(iq, ih, B["Aqh"])
+            add(iv, iq, B["Avq"]); add(ih, iq, B["Ahq"])
     d = solve(J, -R)
     dQ = d[:nq_tot].reshape(nK, 5, 3, Nn) if vis else None
     dV = d[nq_tot:offH].reshape(nK, 5, Nn)

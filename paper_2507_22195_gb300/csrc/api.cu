@@ -1,0 +1,351 @@
+// api.cu -- the C-ABI of include/mehdg.h and the orchestration of one Newton
+// step per macro-element (Algorithm 1, local parts):
+//   condense : R (eq. s32), S^K = A_vv assembled (eq. R1/R3), LU(S^K),
+//              y = S^-1 (-R_V) refined in FP64, bhat^K = -R_Vhat - A_vhat,v y
+//              (eq. R5b), summed over the two sides of every face;
+//   apply    : y = A_vhat,vhat x + A_vhat,v S^-1 (-A_v,vhat x)  (Sec. 6.3 stages 1-4);
+//   recover  : dV = S^-1 (-R_V - A_v,vhat dVhat)  (eq. R2).
+// Every product with a Jacobian block other than the LU of S is matrix-free:
+// a forward-mode tangent of the FP64 residual.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+#include "common.cuh"
+#include "kernels.cuh"
+#include "prof.cuh"
+
+cudaError_t launch_axpy(int64_t nK, int64_t ld, const double* dx, double* x, const int32_t* conv, cudaStream_t st);
+
+std::atomic<long long> g_mehdg_launches{0};
+
+void set_err(mehdg_ctx* ctx, const char* fmt, ...) {
+    if (!ctx) return;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+    va_end(ap);
+}
+
+namespace {
+
+template <class T> void dfree(T*& p) { if (p) { cudaFree((void*)p); p = nullptr; } }
+
+void free_mesh(mehdg_ctx* c) {
+    dfree(c->d_box); dfree(c->d_gid); dfree(c->d_g2l); dfree(c->d_RV); dfree(c->d_RHloc);
+    dfree(c->d_tRHloc); dfree(c->d_tRHloc2); dfree(c->d_tRV); dfree(c->d_xu); dfree(c->d_r); dfree(c->d_x);
+    dfree(c->d_res); dfree(c->d_dx); dfree(c->d_nrm); dfree(c->d_status); dfree(c->d_iters); dfree(c->d_conv);
+    dfree(c->d_cnt); dfree(c->d_S); dfree(c->d_piv); dfree(c->d_work);
+    if (c->h_cnt) { cudaFreeHost(c->h_cnt); c->h_cnt = nullptr; }
+    c->nK = 0; c->condensed = false;
+}
+
+ResidualArgs base_args(mehdg_ctx* c) {
+    ResidualArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.tab = c->tab; a.ph = c->ph; a.box = c->d_box; a.gid = c->d_gid;
+    a.v = c->v; a.vs = c->vs; a.vh = c->vh; a.q = c->q;
+    a.status = c->d_status;
+    return a;
+}
+
+LUPlan plan(mehdg_ctx* c) {
+    LUPlan P;
+    P.nK = c->nK; P.ld = c->Npad; P.N = c->Nv;
+    P.fp64 = c->prm.prec == MEHDG_FP64; P.prec = c->prm.prec;
+    P.S = c->d_S; P.piv = c->d_piv; P.status = c->d_status;
+    P.work = c->d_work; P.work_bytes = c->work_bytes;
+    P.prof = &c->prof;
+    return P;
+}
+
+#define TRY(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { set_err(c, "%s: %s", #x, cudaGetErrorString(e_)); return MEHDG_ECUDA; } } while (0)
+
+// tangent residual: tRV (unpadded [nK][5Nn]) and tRH (per-side trace) along (dv, dvh)
+int tangent(mehdg_ctx* c, const double* dv, const double* dvh, double* tRV, double* tRH,
+            const int32_t* skip, cudaStream_t st) {
+    ResidualArgs a = base_args(c);
+    a.dv = dv; a.dvh = dvh; a.tRV = tRV; a.tRH = tRH; a.skip = skip;
+    int ev = prof_begin(&c->prof, PH_TANGENT, st);
+    TRY(launch_residual(a, c->nK, c->ph.viscous, true, st));
+    prof_end(&c->prof, ev, st, 0.0);
+    return MEHDG_OK;
+}
+
+// x (padded FP64) = S^-1 r by LU solves in the factor precision and FP64
+// refinement with the matrix-free S x
+int refine_solve(mehdg_ctx* c, const double* r, double* x, cudaStream_t st) {
+    LUPlan P = plan(c);
+    const int64_t nK = c->nK, ld = c->Npad;
+    TRY(cudaMemsetAsync(x, 0, sizeof(double) * nK * ld, st));
+    TRY(cudaMemcpyAsync(c->d_res, r, sizeof(double) * nK * ld, cudaMemcpyDeviceToDevice, st));
+    TRY(cudaMemsetAsync(c->d_conv, 0, sizeof(int32_t) * nK, st));
+    const int maxit = c->prm.refine_max_iter > 0 ? c->prm.refine_max_iter : 1;
+    for (int it = 0; it < maxit; ++it) {
+        int ev = prof_begin(&c->prof, PH_SOLVE, st);
+        TRY(lu_solve(P, c->d_res, c->d_dx, c->d_conv, st));
+        prof_end(&c->prof, ev, st, 0.0);
+        TRY(launch_axpy(nK, ld, c->d_dx, x, c->d_conv, st));
+        TRY(launch_copy_unpad(nK, c->Nv, ld, x, c->d_xu, 1.0, st));
+        int rc = tangent(c, c->d_xu, nullptr, c->d_tRV, nullptr, c->d_conv, st);
+        if (rc) return rc;
+        TRY(cudaMemsetAsync(c->d_cnt, 0, sizeof(int32_t), st));
+        TRY(launch_refine_update(nK, c->Nv, ld, r, c->d_tRV, c->d_res, c->d_nrm, c->d_conv, c->d_iters,
+                                 c->d_status, c->prm.refine_tol, it, it == maxit - 1, nullptr, nullptr,
+                                 c->d_cnt, st));
+        TRY(cudaMemcpyAsync(c->h_cnt, c->d_cnt, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        TRY(cudaStreamSynchronize(st));
+        if (*c->h_cnt == 0) break;
+    }
+    return MEHDG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mehdg_default_params(mehdg_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->gamma = 1.4; p->Re = 1600.0; p->Pr = 0.71; p->Mach = 0.1; p->dt = 1.0;
+    p->viscous = 0; p->flux = MEHDG_FLUX_KEPES; p->prec = MEHDG_MIXED_TF32;
+    p->refine_tol = 1e-12; p->refine_max_iter = 10; p->time_term = 1;
+}
+
+int mehdg_create(mehdg_ctx** out, const mehdg_params* prm) {
+    if (!out || !prm) return MEHDG_EINVAL;
+    *out = nullptr;
+    if (!(prm->gamma > 1.0) || prm->flux < 0 || prm->flux > 2 || prm->prec < 0 || prm->prec > 2 ||
+        (prm->time_term && !(prm->dt > 0.0)) || (prm->viscous && !(prm->Re > 0 && prm->Pr > 0 && prm->Mach > 0)))
+        return MEHDG_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return MEHDG_ECUDA;
+    mehdg_ctx* c = new mehdg_ctx();
+    c->prm = *prm;
+    c->err[0] = 0;
+    Phys& ph = c->ph;
+    ph.gamma = prm->gamma;
+    ph.mu = prm->viscous ? prm->Mach / prm->Re : 0.0;
+    ph.kappa = prm->viscous ? ph.mu / ((prm->gamma - 1.0) * prm->Pr) : 0.0;
+    ph.sv_mom = prm->viscous ? 1.0 / prm->Re : 0.0;
+    ph.sv_en = prm->viscous ? 1.0 / (prm->Re * (prm->gamma - 1.0) * prm->Mach * prm->Mach * prm->Pr) : 0.0;
+    ph.inv_dt = prm->time_term ? 1.0 / prm->dt : 0.0;
+    ph.viscous = prm->viscous; ph.flux = prm->flux; ph.time_term = prm->time_term;
+    *out = c;
+    return MEHDG_OK;
+}
+
+int mehdg_set_mesh(mehdg_ctx* c, int64_t nK, const int32_t* p, const int32_t* m, const double* box,
+                   const int64_t* face_gid, int64_t G) {
+    if (!c) return MEHDG_EINVAL;
+    if (nK <= 0 || !p || !m || !box || !face_gid || G <= 0) { set_err(c, "set_mesh: bad arguments"); return MEHDG_EINVAL; }
+    const int p0 = p[0], m0 = m[0];
+    for (int64_t K = 0; K < nK; ++K)
+        if (p[K] != p0 || m[K] != m0) { set_err(c, "set_mesh: all elements must share p and m"); return MEHDG_EINVAL; }
+    if (p0 < 1 || p0 > MEHDG_MAXP || m0 < 1 || m0 > 16) { set_err(c, "set_mesh: p in 1..4, m in 1..16"); return MEHDG_EINVAL; }
+    if (c->prm.viscous) { set_err(c, "set_mesh: the Navier-Stokes path is not built in this library version"); return MEHDG_EINVAL; }
+    std::vector<int64_t> g2l(2 * G, -1);
+    for (int64_t K = 0; K < nK; ++K) {
+        for (int d = 0; d < 3; ++d)
+            if (!(box[6 * K + 3 + d] > box[6 * K + d])) { set_err(c, "set_mesh: degenerate box %lld", (long long)K); return MEHDG_EINVAL; }
+        for (int f = 0; f < 6; ++f) {
+            int64_t g = face_gid[6 * K + f];
+            if (g < 0 || g >= G) { set_err(c, "set_mesh: face id out of range"); return MEHDG_EINVAL; }
+            if (g2l[2 * g] < 0) g2l[2 * g] = 6 * K + f;
+            else if (g2l[2 * g + 1] < 0) g2l[2 * g + 1] = 6 * K + f;
+            else { set_err(c, "set_mesh: global face %lld used more than twice", (long long)g); return MEHDG_EINVAL; }
+        }
+    }
+    free_mesh(c);
+    c->nK = nK; c->G = G; c->p = p0; c->m = m0;
+    host_build_tables(p0, m0, &c->tab);
+    const Tab& t = c->tab;
+    c->Nv = 5 * t.Nn;
+    c->Nt_loc = 30 * t.n2;
+    c->Npad = (c->Nv + 255) / 256 * 256;
+    const bool fp64 = c->prm.prec == MEHDG_FP64;
+    const size_t ts = fp64 ? 8 : 4;
+    const size_t Sbytes = (size_t)nK * c->Npad * c->Npad * ts;
+    size_t freeb = 0, totb = 0;
+    cudaMemGetInfo(&freeb, &totb);
+    if (Sbytes > freeb * 0.9) {
+        set_err(c, "set_mesh: %zu bytes of dense S^K do not fit (%zu free); use fewer elements per context", Sbytes, freeb);
+        return MEHDG_ENOMEM;
+    }
+#define DALLOC(ptr, bytes) do { if (cudaMalloc((void**)&(ptr), (bytes)) != cudaSuccess) { set_err(c, "cudaMalloc %s (%zu bytes) failed", #ptr, (size_t)(bytes)); free_mesh(c); return MEHDG_ENOMEM; } } while (0)
+    DALLOC(c->d_box, sizeof(double) * 6 * nK);
+    DALLOC(c->d_gid, sizeof(int64_t) * 6 * nK);
+    DALLOC(c->d_g2l, sizeof(int64_t) * 2 * G);
+    DALLOC(c->d_RV, sizeof(double) * nK * c->Nv);
+    DALLOC(c->d_RHloc, sizeof(double) * nK * c->Nt_loc);
+    DALLOC(c->d_tRHloc, sizeof(double) * nK * c->Nt_loc);
+    DALLOC(c->d_tRHloc2, sizeof(double) * nK * c->Nt_loc);
+    DALLOC(c->d_tRV, sizeof(double) * nK * c->Nv);
+    DALLOC(c->d_xu, sizeof(double) * nK * c->Nv);
+    DALLOC(c->d_r, sizeof(double) * nK * c->Npad);
+    DALLOC(c->d_x, sizeof(double) * nK * c->Npad);
+    DALLOC(c->d_res, sizeof(double) * nK * c->Npad);
+    DALLOC(c->d_dx, sizeof(double) * nK * c->Npad);
+    DALLOC(c->d_nrm, sizeof(double) * 2 * nK);
+    DALLOC(c->d_status, sizeof(int32_t) * nK);
+    DALLOC(c->d_iters, sizeof(int32_t) * nK);
+    DALLOC(c->d_conv, sizeof(int32_t) * nK);
+    DALLOC(c->d_cnt, sizeof(int32_t));
+    DALLOC(c->d_S, Sbytes);
+    DALLOC(c->d_piv, sizeof(int32_t) * nK * c->Npad);
+    c->work_bytes = lu_work_bytes(nK, c->Npad, fp64, c->prm.prec);
+    DALLOC(c->d_work, c->work_bytes);
+#undef DALLOC
+    if (cudaMallocHost((void**)&c->h_cnt, sizeof(int32_t)) != cudaSuccess) { free_mesh(c); return MEHDG_ENOMEM; }
+    if (cudaMemcpy(c->d_box, box, sizeof(double) * 6 * nK, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->d_gid, face_gid, sizeof(int64_t) * 6 * nK, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->d_g2l, g2l.data(), sizeof(int64_t) * 2 * G, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(c->d_status, 0, sizeof(int32_t) * nK) != cudaSuccess ||
+        cudaMemset(c->d_iters, 0, sizeof(int32_t) * nK) != cudaSuccess) {
+        set_err(c, "set_mesh: copy failed"); free_mesh(c); return MEHDG_ECUDA;
+    }
+    return MEHDG_OK;
+}
+
+int mehdg_set_state(mehdg_ctx* c, const double* v, const double* vhat, const double* q, const double* vstar,
+                    void*) {
+    if (!c) return MEHDG_EINVAL;
+    if (c->nK == 0) { set_err(c, "set_state before set_mesh"); return MEHDG_ESTATE; }
+    if (!v || !vhat || (c->prm.viscous && !q) || (c->prm.time_term && !vstar)) {
+        set_err(c, "set_state: missing array"); return MEHDG_EINVAL;
+    }
+    c->v = v; c->vh = vhat; c->q = q; c->vs = vstar;
+    c->condensed = false;
+    return MEHDG_OK;
+}
+
+int mehdg_residual(mehdg_ctx* c, double* R_V, double* R_Q, double* R_Vhat, void* stream) {
+    if (!c) return MEHDG_EINVAL;
+    if (!c->v) { set_err(c, "residual before set_state"); return MEHDG_ESTATE; }
+    if (!R_V || !R_Vhat) { set_err(c, "residual: null output"); return MEHDG_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    TRY(cudaMemsetAsync(c->d_status, 0, sizeof(int32_t) * c->nK, st));
+    ResidualArgs a = base_args(c);
+    a.RV = R_V; a.RQ = c->ph.viscous ? R_Q : nullptr; a.RH = c->d_RHloc;
+    int ev = prof_begin(&c->prof, PH_RESIDUAL, st);
+    TRY(launch_residual(a, c->nK, c->ph.viscous, false, st));
+    prof_end(&c->prof, ev, st, 0.0);
+    TRY(launch_trace_gather(c->d_RHloc, c->d_g2l, c->G, c->tab.n2, R_Vhat, 1.0, nullptr, 0.0, st));
+    return MEHDG_OK;
+}
+
+int mehdg_condense(mehdg_ctx* c, double* bhat, double* Ahat_local, void* stream) {
+    if (!c) return MEHDG_EINVAL;
+    if (!c->v) { set_err(c, "condense before set_state"); return MEHDG_ESTATE; }
+    if (!bhat) { set_err(c, "condense: null bhat"); return MEHDG_EINVAL; }
+    if (Ahat_local) { set_err(c, "condense: the explicit A-hat^K is not formed; use mehdg_apply_condensed"); return MEHDG_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool fp64 = c->prm.prec == MEHDG_FP64;
+    const int64_t nK = c->nK, ld = c->Npad;
+    TRY(cudaMemsetAsync(c->d_status, 0, sizeof(int32_t) * nK, st));
+    TRY(cudaMemsetAsync(c->d_iters, 0, sizeof(int32_t) * nK, st));
+    // residual at the state
+    ResidualArgs a = base_args(c);
+    a.RV = c->d_RV; a.RH = c->d_RHloc;
+    int ev = prof_begin(&c->prof, PH_RESIDUAL, st);
+    TRY(launch_residual(a, nK, c->ph.viscous, false, st));
+    prof_end(&c->prof, ev, st, 0.0);
+    // S^K = A_vv (dense), padded identity
+    ev = prof_begin(&c->prof, PH_JACOBIAN, st);
+    TRY(cudaMemsetAsync(c->d_S, 0, (size_t)nK * ld * ld * (fp64 ? 8 : 4), st));
+    TRY(launch_pad_identity(c->d_S, nK, ld, c->Nv, fp64, st));
+    JacobianArgs ja;
+    ja.tab = c->tab; ja.ph = c->ph; ja.box = c->d_box; ja.v = c->v; ja.vs = c->vs; ja.vh = c->vh; ja.q = c->q;
+    ja.gid = c->d_gid; ja.S = c->d_S; ja.ld = ld; ja.status = c->d_status;
+    TRY(launch_jacobian(ja, nK, fp64, st));
+    prof_end(&c->prof, ev, st, 0.0);
+    // LU
+    LUPlan P = plan(c);
+    TRY(lu_factor(P, st));
+    // y = S^-1 (-R_V)
+    TRY(launch_set_rhs(nK, c->Nv, ld, c->tab.Nn, c->d_RV, -1.0, nullptr, 0.0, c->d_r, st));
+    int rc = refine_solve(c, c->d_r, c->d_x, st);
+    if (rc) return rc;
+    // bhat^K = -R_Vhat^K - A_vhat,v y, summed over sides
+    TRY(launch_copy_unpad(nK, c->Nv, ld, c->d_x, c->d_xu, 1.0, st));
+    rc = tangent(c, c->d_xu, nullptr, c->d_tRV, c->d_tRHloc, nullptr, st);
+    if (rc) return rc;
+    TRY(launch_trace_gather(c->d_RHloc, c->d_g2l, c->G, c->tab.n2, bhat, -1.0, nullptr, 0.0, st));
+    TRY(launch_trace_gather(c->d_tRHloc, c->d_g2l, c->G, c->tab.n2, bhat, -1.0, bhat, 1.0, st));
+    c->condensed = true;
+    return MEHDG_OK;
+}
+
+int mehdg_apply_condensed(mehdg_ctx* c, const double* x, double* y, void* stream) {
+    if (!c) return MEHDG_EINVAL;
+    if (!c->condensed) { set_err(c, "apply_condensed before condense"); return MEHDG_ESTATE; }
+    if (!x || !y) return MEHDG_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t nK = c->nK, ld = c->Npad;
+    // stage 1: A_v,vhat x and A_vhat,vhat x (tangent along vhat)
+    int rc = tangent(c, nullptr, x, c->d_tRV, c->d_tRHloc2, nullptr, st);
+    if (rc) return rc;
+    // stage 2: y2 = S^-1 (-A_v,vhat x)
+    TRY(launch_set_rhs(nK, c->Nv, ld, c->tab.Nn, c->d_tRV, -1.0, nullptr, 0.0, c->d_r, st));
+    rc = refine_solve(c, c->d_r, c->d_x, st);
+    if (rc) return rc;
+    // stage 3: A_vhat,v y2
+    TRY(launch_copy_unpad(nK, c->Nv, ld, c->d_x, c->d_xu, 1.0, st));
+    rc = tangent(c, c->d_xu, nullptr, c->d_tRV, c->d_tRHloc, nullptr, st);
+    if (rc) return rc;
+    // stage 4: assembly over the sides of every face
+    TRY(launch_trace_gather(c->d_tRHloc2, c->d_g2l, c->G, c->tab.n2, y, 1.0, nullptr, 0.0, st));
+    TRY(launch_trace_gather(c->d_tRHloc, c->d_g2l, c->G, c->tab.n2, y, 1.0, y, 1.0, st));
+    return MEHDG_OK;
+}
+
+int mehdg_recover(mehdg_ctx* c, const double* dVhat, double* dV, double* dQ, void* stream) {
+    if (!c) return MEHDG_EINVAL;
+    (void)dQ;
+    if (!c->condensed) { set_err(c, "recover before condense"); return MEHDG_ESTATE; }
+    if (!dVhat || !dV) return MEHDG_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t nK = c->nK, ld = c->Npad;
+    int rc = tangent(c, nullptr, dVhat, c->d_tRV, c->d_tRHloc2, nullptr, st);
+    if (rc) return rc;
+    // eq. R2: S dV = -R_V - A_v,vhat dVhat
+    TRY(launch_set_rhs(nK, c->Nv, ld, c->tab.Nn, c->d_RV, -1.0, c->d_tRV, -1.0, c->d_r, st));
+    rc = refine_solve(c, c->d_r, c->d_x, st);
+    if (rc) return rc;
+    TRY(launch_copy_unpad(nK, c->Nv, ld, c->d_x, dV, 1.0, st));
+    return MEHDG_OK;
+}
+
+int mehdg_status(mehdg_ctx* c, int32_t* per_K_status, int32_t* iters) {
+    if (!c) return MEHDG_EINVAL;
+    if (c->nK == 0) return MEHDG_ESTATE;
+    TRY(cudaDeviceSynchronize());
+    if (per_K_status) TRY(cudaMemcpy(per_K_status, c->d_status, sizeof(int32_t) * c->nK, cudaMemcpyDeviceToHost));
+    if (iters) TRY(cudaMemcpy(iters, c->d_iters, sizeof(int32_t) * c->nK, cudaMemcpyDeviceToHost));
+    return MEHDG_OK;
+}
+
+const char* mehdg_last_error(const mehdg_ctx* c) { return c ? c->err : "null context"; }
+
+void mehdg_destroy(mehdg_ctx* c) {
+    if (!c) return;
+    free_mesh(c);
+    prof_free(&c->prof);
+    delete c;
+}
+
+int mehdg_profile_enable(mehdg_ctx* c, int enable) {
+    if (!c) return MEHDG_EINVAL;
+    return prof_enable(&c->prof, enable) ? MEHDG_OK : MEHDG_ECUDA;
+}
+
+int mehdg_profile_read(mehdg_ctx* c, double* ms, int64_t* launches, double* flops, int nphase) {
+    if (!c || !ms || !launches || !flops) return MEHDG_EINVAL;
+    if (cudaDeviceSynchronize() != cudaSuccess) return MEHDG_ECUDA;
+    prof_read(&c->prof, ms, launches, flops, nphase);
+    return MEHDG_OK;
+}
+
+int64_t mehdg_launch_count(void) { return (int64_t)g_mehdg_launches.load(); }
+
+}  // extern "C"

@@ -1,0 +1,246 @@
+// jacobian.cu -- assembly of the dense Schur matrix S^K = A_vv (eq. R1, R3)
+// of every macro-element, in FP32 (mixed path) or FP64.
+//
+// The point-wise Jacobians of the integrands (5x5 blocks dU/dv and
+// dFG_j/dv at every Gauss point, dF-hat/dv at every face point) come from
+// forward-mode duals with 5 tangent directions (FP64 log/exp of the
+// entropy-to-conservative map and of the logarithmic means).  They are
+// weighted and contracted with the basis of the micro-element:
+//   S[(k,A),(l,B)] += sum_x W [ phi_A phi_B dU_k/dv_l - sum_j d_j phi_A phi_B dFG_kj/dv_l ]
+//                   + sum_faces sum_x w mu_A mu_B dFhat_k/dv_l,
+// one thread per (A,B) pair of local nodes with 25 accumulators, and added
+// into S with atomics (micro-elements share nodes).  S is column-major with
+// a padded leading dimension; the padding is an identity block.
+#include "physics.cuh"
+#include "kernels.cuh"
+
+namespace {
+
+__device__ __forceinline__ void atomic_add_t(float* p, double x) { atomicAdd(p, (float)x); }
+__device__ __forceinline__ void atomic_add_t(double* p, double x) { atomicAdd(p, x); }
+
+template <class TS, bool VISC>
+__global__ void __launch_bounds__(256)
+jac_volume_kernel(JacobianArgs a) {
+    const Tab& tb = a.tab;
+    const int K = blockIdx.y, e = blockIdx.x;
+    const int p = tb.p, m = tb.m, n = tb.n, ng = tb.ng, Nn = tb.Nn;
+    const int nl = tb.nl, npt = tb.npt, p1 = p + 1;
+    const int e1 = e % m, e2 = (e / m) % m, e3 = e / (m * m);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* sL = reinterpret_cast<double*>(smem_raw);
+    double* sD = sL + MEHDG_MAXG * (MEHDG_MAXP + 1);
+    double* sW = sD + MEHDG_MAXG * (MEHDG_MAXP + 1);
+    double* vl = sW + 8;                  // [5][nl]
+    double* vsl = vl + 5 * nl;            // [5][nl]
+    double* ql = vsl + 5 * nl;            // [15][nl]
+    TS* P = reinterpret_cast<TS*>(ql + (VISC ? 15 * nl : 0));   // [npt][4][25]
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (int i = tid; i < ng * p1; i += nth) { sL[i] = tb.L[i / p1][i % p1]; sD[i] = tb.dL[i / p1][i % p1]; }
+    if (tid < ng) sW[tid] = tb.w[tid];
+    const double* box = a.box + 6 * K;
+    double sc[3], hw[3];
+    for (int d = 0; d < 3; ++d) { double h = (box[3 + d] - box[d]) / m; sc[d] = 2.0 / h; hw[d] = 0.5 * h; }
+    const int64_t oV = (int64_t)K * 5 * Nn, oQ = (int64_t)K * 15 * Nn;
+    for (int i = tid; i < nl; i += nth) {
+        int l1 = i % p1, l2 = (i / p1) % p1, l3 = i / (p1 * p1);
+        int A = (e1 * p + l1) + n * ((e2 * p + l2) + n * (e3 * p + l3));
+        for (int k = 0; k < 5; ++k) {
+            vl[k * nl + i] = a.v[oV + k * Nn + A];
+            vsl[k * nl + i] = a.ph.time_term ? a.vs[oV + k * Nn + A] : 0.0;
+        }
+        if (VISC) for (int c = 0; c < 15; ++c) ql[c * nl + i] = a.q[oQ + c * Nn + A];
+    }
+    __syncthreads();
+    bool ok = true;
+    for (int x = tid; x < npt; x += nth) {
+        int g1 = x % ng, g2 = (x / ng) % ng, g3 = x / (ng * ng);
+        double vx[5] = {0, 0, 0, 0, 0}, vsx[5] = {0, 0, 0, 0, 0}, qx[15];
+        for (int c = 0; c < 15; ++c) qx[c] = 0.0;
+        for (int i = 0; i < nl; ++i) {
+            double f = sL[g1 * p1 + i % p1] * sL[g2 * p1 + (i / p1) % p1] * sL[g3 * p1 + i / (p1 * p1)];
+            for (int k = 0; k < 5; ++k) { vx[k] += f * vl[k * nl + i]; vsx[k] += f * vsl[k * nl + i]; }
+            if (VISC) for (int c = 0; c < 15; ++c) qx[c] += f * ql[c * nl + i];
+        }
+        Dual<5> dv[5], dvs[5], dq[15];
+        for (int k = 0; k < 5; ++k) {
+            dv[k] = mkdual<5>(vx[k]); dv[k].d[k] = 1.0;
+            dvs[k] = mkdual<5>(vsx[k]);
+        }
+        for (int c = 0; c < 15; ++c) dq[c] = mkdual<5>(qx[c]);
+        Dual<5> U[5], FG[5][3];
+        ok = vol_integrand(a.ph, dv, dvs, dq, U, FG) && ok;
+        double W = sW[g1] * hw[0] * sW[g2] * hw[1] * sW[g3] * hw[2];
+        TS* Px = P + (size_t)x * 100;
+        for (int k = 0; k < 5; ++k)
+            for (int l = 0; l < 5; ++l) {
+                Px[k * 5 + l] = (TS)(W * U[k].d[l]);
+                for (int j = 0; j < 3; ++j) Px[25 * (1 + j) + k * 5 + l] = (TS)(-W * FG[k][j].d[l]);
+            }
+    }
+    if (!ok && a.status) a.status[K] = MEHDG_ENONPHYS;
+    __syncthreads();
+    // contraction: thread per pair of local nodes (two pairs per pass)
+    TS* S = reinterpret_cast<TS*>(a.S) + (size_t)K * a.ld * a.ld;
+    const int npair = nl * nl;
+    const int half = (npair + 1) / 2;
+    for (int r0 = tid; r0 < half; r0 += nth) {
+        int rr[2] = {r0, r0 + half};
+        bool act1 = rr[1] < npair;
+        int la[2][3], lb[2][3];
+        for (int u = 0; u < 2; ++u) {
+            int ia = rr[u] / nl, ib = rr[u] % nl;
+            if (!act1 && u == 1) { ia = 0; ib = 0; }
+            la[u][0] = ia % p1; la[u][1] = (ia / p1) % p1; la[u][2] = ia / (p1 * p1);
+            lb[u][0] = ib % p1; lb[u][1] = (ib / p1) % p1; lb[u][2] = ib / (p1 * p1);
+        }
+        TS acc[2][25];
+        for (int u = 0; u < 2; ++u)
+            for (int i = 0; i < 25; ++i) acc[u][i] = 0;
+        for (int x = 0; x < npt; ++x) {
+            int g[3] = {x % ng, (x / ng) % ng, x / (ng * ng)};
+            TS c[2][4];
+            for (int u = 0; u < 2; ++u) {
+                double Aa[3], Ad[3], Bb = 1.0;
+                for (int d = 0; d < 3; ++d) {
+                    Aa[d] = sL[g[d] * p1 + la[u][d]];
+                    Ad[d] = sD[g[d] * p1 + la[u][d]] * sc[d];
+                    Bb *= sL[g[d] * p1 + lb[u][d]];
+                }
+                c[u][0] = (TS)(Aa[0] * Aa[1] * Aa[2] * Bb);
+                c[u][1] = (TS)(Ad[0] * Aa[1] * Aa[2] * Bb);
+                c[u][2] = (TS)(Aa[0] * Ad[1] * Aa[2] * Bb);
+                c[u][3] = (TS)(Aa[0] * Aa[1] * Ad[2] * Bb);
+            }
+            const TS* Px = P + (size_t)x * 100;
+#pragma unroll 5
+            for (int kl = 0; kl < 25; ++kl) {
+                TS p0 = Px[kl], q1 = Px[25 + kl], q2 = Px[50 + kl], q3 = Px[75 + kl];
+                acc[0][kl] += c[0][0] * p0 + c[0][1] * q1 + c[0][2] * q2 + c[0][3] * q3;
+                acc[1][kl] += c[1][0] * p0 + c[1][1] * q1 + c[1][2] * q2 + c[1][3] * q3;
+            }
+        }
+        for (int u = 0; u < 2; ++u) {
+            if (u == 1 && !act1) break;
+            int A = (e1 * p + la[u][0]) + n * ((e2 * p + la[u][1]) + n * (e3 * p + la[u][2]));
+            int B = (e1 * p + lb[u][0]) + n * ((e2 * p + lb[u][1]) + n * (e3 * p + lb[u][2]));
+            for (int k = 0; k < 5; ++k)
+                for (int l = 0; l < 5; ++l)
+                    atomic_add_t(&S[(size_t)(k * Nn + A) + (size_t)(l * Nn + B) * a.ld], (double)acc[u][k * 5 + l]);
+        }
+    }
+}
+
+template <class TS, bool VISC>
+__global__ void __launch_bounds__(256)
+jac_face_kernel(JacobianArgs a) {
+    const Tab& tb = a.tab;
+    const int K = blockIdx.y;
+    const int p = tb.p, m = tb.m, n = tb.n, ng = tb.ng, Nn = tb.Nn, n2 = tb.n2, p1 = p + 1;
+    const int f = blockIdx.x / (m * m), e = blockIdx.x % (m * m);
+    const int e1 = e % m, e2 = e / m;
+    const int d = f / 2, t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+    const double sgn = (f & 1) ? 1.0 : -1.0;
+    const int fl = p1 * p1, fpt = ng * ng;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* sL = reinterpret_cast<double*>(smem_raw);
+    double* sW = sL + MEHDG_MAXG * (MEHDG_MAXP + 1);
+    double* fv = sW + 8;              // [5][fl]
+    double* fh = fv + 5 * fl;         // [5][fl]
+    double* fq = fh + 5 * fl;         // [15][fl]
+    int* nodeA = reinterpret_cast<int*>(fq + 15 * fl);   // [fl]
+    TS* P = reinterpret_cast<TS*>(reinterpret_cast<double*>(nodeA) + ((fl + 1) / 2 + 1));  // [fpt][25]
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (int i = tid; i < ng * p1; i += nth) sL[i] = tb.L[i / p1][i % p1];
+    if (tid < ng) sW[tid] = tb.w[tid];
+    const double* box = a.box + 6 * K;
+    double hw1 = 0.5 * (box[3 + t1] - box[t1]) / m, hw2 = 0.5 * (box[3 + t2] - box[t2]) / m;
+    const int64_t oV = (int64_t)K * 5 * Nn, oQ = (int64_t)K * 15 * Nn, og = a.gid[6 * K + f] * 5 * n2;
+    for (int i = tid; i < fl; i += nth) {
+        int c1 = e1 * p + i % p1, c2 = e2 * p + i / p1;
+        int idx[3]; idx[d] = (f & 1) ? n - 1 : 0; idx[t1] = c1; idx[t2] = c2;
+        int A = idx[0] + n * (idx[1] + n * idx[2]);
+        nodeA[i] = A;
+        for (int k = 0; k < 5; ++k) {
+            fv[k * fl + i] = a.v[oV + k * Nn + A];
+            fh[k * fl + i] = a.vh[og + k * n2 + c1 + n * c2];
+        }
+        if (VISC) for (int c = 0; c < 15; ++c) fq[c * fl + i] = a.q[oQ + c * Nn + A];
+    }
+    __syncthreads();
+    for (int x = tid; x < fpt; x += nth) {
+        int g1 = x % ng, g2 = x / ng;
+        double vx[5] = {0, 0, 0, 0, 0}, hx[5] = {0, 0, 0, 0, 0}, qx[15];
+        for (int c = 0; c < 15; ++c) qx[c] = 0.0;
+        for (int i = 0; i < fl; ++i) {
+            double mu = sL[g1 * p1 + i % p1] * sL[g2 * p1 + i / p1];
+            for (int k = 0; k < 5; ++k) { vx[k] += mu * fv[k * fl + i]; hx[k] += mu * fh[k * fl + i]; }
+            if (VISC) for (int c = 0; c < 15; ++c) qx[c] += mu * fq[c * fl + i];
+        }
+        Dual<5> dv[5], dh[5], dq[15];
+        for (int k = 0; k < 5; ++k) { dv[k] = mkdual<5>(vx[k]); dv[k].d[k] = 1.0; dh[k] = mkdual<5>(hx[k]); }
+        for (int c = 0; c < 15; ++c) dq[c] = mkdual<5>(qx[c]);
+        Dual<5> Fh[5];
+        face_integrand(a.ph, dv, dh, dq, d, sgn, Fh);
+        double W = sW[g1] * hw1 * sW[g2] * hw2;
+        for (int k = 0; k < 5; ++k)
+            for (int l = 0; l < 5; ++l) P[x * 25 + k * 5 + l] = (TS)(W * Fh[k].d[l]);
+    }
+    __syncthreads();
+    TS* S = reinterpret_cast<TS*>(a.S) + (size_t)K * a.ld * a.ld;
+    for (int r = tid; r < fl * fl; r += nth) {
+        int ia = r / fl, ib = r % fl;
+        TS acc[25];
+        for (int i = 0; i < 25; ++i) acc[i] = 0;
+        for (int x = 0; x < fpt; ++x) {
+            int g1 = x % ng, g2 = x / ng;
+            TS c = (TS)(sL[g1 * p1 + ia % p1] * sL[g2 * p1 + ia / p1] * sL[g1 * p1 + ib % p1] * sL[g2 * p1 + ib / p1]);
+            for (int kl = 0; kl < 25; ++kl) acc[kl] += c * P[x * 25 + kl];
+        }
+        int A = nodeA[ia], B = nodeA[ib];
+        for (int k = 0; k < 5; ++k)
+            for (int l = 0; l < 5; ++l)
+                atomic_add_t(&S[(size_t)(k * Nn + A) + (size_t)(l * Nn + B) * a.ld], (double)acc[k * 5 + l]);
+    }
+}
+
+template <class TS>
+__global__ void pad_identity_kernel(TS* S, int64_t ld, int Nv) {
+    int K = blockIdx.y;
+    int64_t i = Nv + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < ld) S[(size_t)K * ld * ld + i + i * ld] = (TS)1;
+}
+
+}  // namespace
+
+cudaError_t launch_jacobian(const JacobianArgs& a, int64_t nK, bool fp64, cudaStream_t st) {
+    const Tab& t = a.tab;
+    bool visc = a.ph.viscous != 0;
+    size_t ts = fp64 ? 8 : 4;
+    size_t sv = sizeof(double) * (2 * MEHDG_MAXG * (MEHDG_MAXP + 1) + 8 + (size_t)(10 + (visc ? 15 : 0)) * t.nl)
+              + ts * 100 * (size_t)t.npt;
+    int fl = (t.p + 1) * (t.p + 1), fpt = t.ng * t.ng;
+    size_t sf = sizeof(double) * (MEHDG_MAXG * (MEHDG_MAXP + 1) + 8 + 25 * (size_t)fl + (fl + 1) / 2 + 1)
+              + ts * 25 * (size_t)fpt + 64;
+    dim3 gv(t.m * t.m * t.m, (unsigned)nK), gf(6 * t.m * t.m, (unsigned)nK), b(256);
+#define LJ(TS, V)                                                                                   \
+    do { cudaFuncSetAttribute(jac_volume_kernel<TS, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sv); \
+         cudaFuncSetAttribute(jac_face_kernel<TS, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf);   \
+         jac_volume_kernel<TS, V><<<gv, b, sv, st>>>(a);                                            \
+         jac_face_kernel<TS, V><<<gf, b, sf, st>>>(a); } while (0)
+    if (fp64) { if (visc) LJ(double, true); else LJ(double, false); }
+    else { if (visc) LJ(float, true); else LJ(float, false); }
+#undef LJ
+    MEHDG_COUNT(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pad_identity(void* S, int64_t nK, int64_t ld, int Nv, bool fp64, cudaStream_t st) {
+    int64_t np = ld - Nv;
+    if (np <= 0) return cudaSuccess;
+    dim3 g((unsigned)((np + 127) / 128), (unsigned)nK);
+    if (fp64) pad_identity_kernel<double><<<g, 128, 0, st>>>((double*)S, ld, Nv);
+    else pad_identity_kernel<float><<<g, 128, 0, st>>>((float*)S, ld, Nv);
+    MEHDG_COUNT(1);
+    return cudaGetLastError();
+}

@@ -1,0 +1,62 @@
+// kernels.cuh -- launch interfaces between the C-ABI layer and the kernels.
+#pragma once
+#include "common.cuh"
+
+struct ResidualArgs {
+    Tab tab;
+    Phys ph;
+    const double* box;        // [nK][6]
+    const int64_t* gid;       // [nK][6]
+    const double *v, *vs, *vh, *q;        // state (vs may be null if no time term)
+    const double *dv, *dvh, *dq;          // tangent directions (null = 0)
+    double *RV, *RQ, *RH;                 // values (null = skip); RH = per-element sides
+    double *tRV, *tRQ, *tRH;              // tangents (tangent launches only)
+    int32_t* status;
+    const int32_t* skip;                  // [nK] nonzero = skip element (may be null)
+};
+
+cudaError_t launch_residual(const ResidualArgs& a, int64_t nK, bool visc, bool tangent, cudaStream_t st);
+cudaError_t launch_trace_gather(const double* loc, const int64_t* g2l, int64_t G, int n2, double* out,
+                                double alpha, const double* add, double beta, cudaStream_t st);
+
+// dense S^K assembly (col-major, leading dimension ld = Npad), element by element
+struct JacobianArgs {
+    Tab tab;
+    Phys ph;
+    const double* box;
+    const double *v, *vs, *vh, *q;
+    const int64_t* gid;
+    void* S;                  // float or double [nK][ld][ld]
+    int64_t ld;
+    int32_t* status;
+};
+cudaError_t launch_jacobian(const JacobianArgs& a, int64_t nK, bool fp64, cudaStream_t st);
+cudaError_t launch_pad_identity(void* S, int64_t nK, int64_t ld, int Nv, bool fp64, cudaStream_t st);
+
+// batched dense LU with partial pivoting and solves (lu.cu)
+struct LUPlan {
+    int64_t nK, ld, N;        // ld = padded size (multiple of 256), N = true size
+    bool fp64;
+    int prec;                 // mehdg_prec
+    void* S;                  // factors in place
+    int32_t* piv;             // [nK][ld] absolute row swapped with row i at step i
+    int32_t* status;
+    void* work;               // scratch (operand panels, permutation lists)
+    size_t work_bytes;
+    Prof* prof;
+};
+size_t lu_work_bytes(int64_t nK, int64_t ld, bool fp64, int prec);
+cudaError_t lu_factor(const LUPlan& P, cudaStream_t st);
+// solve S x = r for every element whose conv flag is 0: x (FP64) = LU^-1 r,
+// computed in the factor precision; r, x: [nK][ld] FP64 (padded tail 0).
+cudaError_t lu_solve(const LUPlan& P, const double* r, double* x, const int32_t* skip, cudaStream_t st);
+
+// small vector kernels for the refinement (refine.cu)
+cudaError_t launch_refine_update(int64_t nK, int Nv, int64_t ld, const double* r, const double* Sx,
+                                 double* res, double* nrm, int32_t* conv, int32_t* iters, int32_t* status,
+                                 double tol, int it, int last, const double* dx, double* x, int32_t* cnt,
+                                 cudaStream_t st);
+cudaError_t launch_set_rhs(int64_t nK, int Nv, int64_t ld, int Nn, const double* a, double sa,
+                           const double* b, double sb, double* out, cudaStream_t st);
+cudaError_t launch_copy_unpad(int64_t nK, int Nv, int64_t ld, const double* x, double* out, double s,
+                              cudaStream_t st);

@@ -1,0 +1,481 @@
+// lu.cu -- batched dense LU with partial pivoting of every S^K, and solves.
+//
+// S^K is column-major with a padded size ld (multiple of 256; the padding is
+// an identity block, so pivots never leave the true rows).  The factorisation
+// is right-looking over outer panels of NB = 256 columns; each outer panel is
+// factored recursively (halves, down to 32-column leaves):
+//   leaf   : one CTA per element factors the (ld-c) x 32 panel, 8 (or fewer)
+//            columns at a time in shared memory with partial pivoting
+//            (largest |a|, ties to the lowest row), left-looking between the
+//            sub-panels;
+//   inner  : row swaps, TRSM with the unit-lower triangle, trailing update
+//            of the right half (narrow GEMM), recursion on the right half,
+//            row swaps of the left half;
+//   outer  : row swaps and TRSM of the rows right of the panel, then the
+//            trailing update C -= L21 U12 with depth 256.
+// Rows left of an outer panel are not swapped again (LINPACK order); the
+// forward solve replays each outer panel's swaps before its block column.
+// The trailing updates run on the tensor cores for the mixed precisions
+// (gemm_tc.cu) and on the FP64 pipe for MEHDG_FP64.
+#include <cstdio>
+#include <type_traits>
+#include "common.cuh"
+#include "kernels.cuh"
+#include "lu_internal.cuh"
+
+namespace {
+
+constexpr int LEAF = 32;
+constexpr int PANEL_THREADS = 512;
+
+// ---------------------------------------------------------------- leaf panel
+template <class TS, int IB>
+__global__ void __launch_bounds__(PANEL_THREADS)
+panel_kernel(TS* __restrict__ Sall, int64_t ld, int c, int32_t* __restrict__ pivall, int32_t* status) {
+    const int K = blockIdx.x;
+    TS* S = Sall + (size_t)K * ld * ld;
+    int32_t* piv = pivall + (size_t)K * ld;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int R0 = (int)(ld - c);                  // rows of the panel
+    TS* X = reinterpret_cast<TS*>(smem_raw);       // [IB][R0] column-major sub-panel
+    __shared__ TS Utop[LEAF][IB];
+    __shared__ double red_v[PANEL_THREADS / 32];
+    __shared__ int red_i[PANEL_THREADS / 32];
+    __shared__ int s_piv[IB];
+    const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, wid = tid >> 5;
+    bool singular = false;
+    for (int jb = 0; jb < LEAF; jb += IB) {
+        const int R = R0 - jb;                     // rows of this sub-panel, starting at c + jb
+        // (a) left-looking update with the earlier sub-panels of this leaf
+        if (jb > 0) {
+            // U part: rows c..c+jb-1 of the sub-panel columns, unit-lower forward substitution
+            if (tid < IB) {
+                const int col = c + jb + tid;
+                for (int i = 0; i < jb; ++i) {
+                    TS s = S[(size_t)(c + i) + (size_t)col * ld];
+                    for (int t = 0; t < i; ++t) s -= S[(size_t)(c + i) + (size_t)(c + t) * ld] * Utop[t][tid];
+                    Utop[i][tid] = s;
+                    S[(size_t)(c + i) + (size_t)col * ld] = s;
+                }
+            }
+            __syncthreads();
+            // L part into shared memory: X[cc][r] = A[c+jb+r][col] - sum_t L[c+jb+r][c+t] U[t][cc]
+            for (int r = tid; r < R; r += nth) {
+                TS acc[IB];
+                for (int cc = 0; cc < IB; ++cc) acc[cc] = S[(size_t)(c + jb + r) + (size_t)(c + jb + cc) * ld];
+                for (int t = 0; t < jb; ++t) {
+                    TS l = S[(size_t)(c + jb + r) + (size_t)(c + t) * ld];
+                    for (int cc = 0; cc < IB; ++cc) acc[cc] -= l * Utop[t][cc];
+                }
+                for (int cc = 0; cc < IB; ++cc) X[(size_t)cc * R0 + r] = acc[cc];
+            }
+        } else {
+            for (int r = tid; r < R; r += nth)
+                for (int cc = 0; cc < IB; ++cc) X[(size_t)cc * R0 + r] = S[(size_t)(c + r) + (size_t)(c + cc) * ld];
+        }
+        __syncthreads();
+        // (b) partial pivoting factorisation of the IB columns in shared memory
+        for (int cc = 0; cc < IB; ++cc) {
+            TS* xc = X + (size_t)cc * R0;
+            double best = -1.0; int bi = 0x7fffffff;
+            for (int r = cc + tid; r < R; r += nth) {
+                double a = fabs((double)xc[r]);
+                if (a > best) { best = a; bi = r; }          // increasing r: ties keep the lowest
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if (lane == 0) { red_v[wid] = best; red_i[wid] = bi; }
+            __syncthreads();
+            if (wid == 0) {
+                best = lane < nth / 32 ? red_v[lane] : -1.0;
+                bi = lane < nth / 32 ? red_i[lane] : 0x7fffffff;
+                for (int o = 16; o > 0; o >>= 1) {
+                    double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                    int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+                }
+                // no finite candidate (all zero or NaN): keep the row, report singular
+                if (bi >= R || !(best > 0.0)) { bi = cc; best = 0.0; }
+                if (lane == 0) { s_piv[cc] = bi; red_v[0] = best; }
+            }
+            __syncthreads();
+            const int pr = s_piv[cc];
+            if (red_v[0] == 0.0 || pr >= R) singular = true;
+            // swap rows cc and pr of the sub-panel
+            if (pr != cc && pr < R && tid < IB) {
+                TS t = X[(size_t)tid * R0 + cc];
+                X[(size_t)tid * R0 + cc] = X[(size_t)tid * R0 + pr];
+                X[(size_t)tid * R0 + pr] = t;
+            }
+            __syncthreads();
+            TS pivv = xc[cc];
+            TS inv = pivv != (TS)0 ? (TS)1 / pivv : (TS)0;
+            for (int r = cc + 1 + tid; r < R; r += nth) {
+                TS l = xc[r] * inv;
+                xc[r] = l;
+                for (int c2 = cc + 1; c2 < IB; ++c2) X[(size_t)c2 * R0 + r] -= l * X[(size_t)c2 * R0 + cc];
+            }
+            __syncthreads();
+        }
+        // (c) write back, record pivots
+        for (int r = tid; r < R; r += nth)
+            for (int cc = 0; cc < IB; ++cc) S[(size_t)(c + jb + r) + (size_t)(c + jb + cc) * ld] = X[(size_t)cc * R0 + r];
+        if (tid < IB) piv[c + jb + tid] = c + jb + s_piv[tid];
+        __syncthreads();
+        // (d) apply the IB swaps to the other columns of the leaf
+        if (tid < LEAF && (tid < jb || tid >= jb + IB)) {
+            const int col = c + tid;
+            for (int cc = 0; cc < IB; ++cc) {
+                int a = c + jb + cc, b = c + jb + s_piv[cc];
+                if (a != b) {
+                    TS t = S[(size_t)a + (size_t)col * ld];
+                    S[(size_t)a + (size_t)col * ld] = S[(size_t)b + (size_t)col * ld];
+                    S[(size_t)b + (size_t)col * ld] = t;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (singular && tid == 0 && status) status[K] = MEHDG_ESINGULAR;
+}
+
+// ---------------------------------------------------------------- row swaps
+// Net permutation of the swap sequence piv[c0 .. c0+w): list of (dst, src)
+// rows such that new[dst] = old[src].  One thread per element.
+__global__ void perm_build_kernel(const int32_t* __restrict__ pivall, int64_t ld, int c0, int w,
+                                  int32_t* __restrict__ perm /*[nK][1 + 4w]*/, int nK) {
+    int K = blockIdx.x * blockDim.x + threadIdx.x;
+    if (K >= nK) return;
+    const int32_t* piv = pivall + (size_t)K * ld;
+    int32_t* out = perm + (size_t)K * (1 + 4 * w);
+    int32_t* rows = out + 1;          // [2w] rows touched
+    int32_t* cont = rows + 2 * w;     // [2w] source row now sitting in rows[i]
+    int nr = w;
+    for (int i = 0; i < w; ++i) { rows[i] = c0 + i; cont[i] = c0 + i; }
+    for (int i = 0; i < w; ++i) {
+        int b = piv[c0 + i];
+        if (b == c0 + i) continue;
+        int sb = -1;
+        if (b < c0 + w) sb = b - c0;
+        else {
+            for (int j = w; j < nr; ++j) if (rows[j] == b) { sb = j; break; }
+            if (sb < 0) { sb = nr++; rows[sb] = b; cont[sb] = b; }
+        }
+        int t = cont[i]; cont[i] = cont[sb]; cont[sb] = t;
+    }
+    out[0] = nr;
+}
+
+template <class TS>
+__global__ void __launch_bounds__(256)
+laswp_kernel(TS* __restrict__ Sall, int64_t ld, const int32_t* __restrict__ perm, int w, int j0, int j1) {
+    const int K = blockIdx.y;
+    TS* S = Sall + (size_t)K * ld * ld;
+    const int32_t* pl = perm + (size_t)K * (1 + 4 * w);
+    const int nr = pl[0];
+    const int32_t* rows = pl + 1;
+    const int32_t* cont = rows + 2 * w;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TS* buf = reinterpret_cast<TS*>(smem_raw);      // [2w][16]
+    const int col0 = j0 + blockIdx.x * 16;
+    const int tc = threadIdx.x & 15, tr = threadIdx.x >> 4;   // 16 columns x 16 row groups
+    const int col = col0 + tc;
+    if (col < j1)
+        for (int i = tr; i < nr; i += 16) buf[i * 16 + tc] = S[(size_t)cont[i] + (size_t)col * ld];
+    __syncthreads();
+    if (col < j1)
+        for (int i = tr; i < nr; i += 16) S[(size_t)rows[i] + (size_t)col * ld] = buf[i * 16 + tc];
+}
+
+// ---------------------------------------------------------------- TRSM
+// X = L^-1 X for X = rows [c0, c0+t) of columns [j0, j1), L = unit-lower
+// S[c0:c0+t, c0:c0+t].  One CTA per 32 columns; 256 threads = 32 cols x 8.
+template <class TS>
+__global__ void __launch_bounds__(256)
+trsm_kernel(TS* __restrict__ Sall, int64_t ld, int c0, int t, int j0, int j1) {
+    const int K = blockIdx.y;
+    TS* S = Sall + (size_t)K * ld * ld;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TS* X = reinterpret_cast<TS*>(smem_raw);        // [t][32]
+    __shared__ TS Lb[32][33];
+    const int tc = threadIdx.x & 31, tr = threadIdx.x >> 5;
+    const int col = j0 + blockIdx.x * 32 + tc;
+    const bool act = col < j1;
+    for (int i = tr; i < t; i += 8) X[i * 32 + tc] = act ? S[(size_t)(c0 + i) + (size_t)col * ld] : (TS)0;
+    __syncthreads();
+    for (int rb = 0; rb < t; rb += 32) {
+        for (int i = tr; i < 32; i += 8) Lb[i][tc] = S[(size_t)(c0 + rb + i) + (size_t)(c0 + rb + tc) * ld];
+        __syncthreads();
+        if (tr == 0) {
+            for (int i = 1; i < 32; ++i) {
+                TS s = X[(rb + i) * 32 + tc];
+                for (int q = 0; q < i; ++q) s -= Lb[i][q] * X[(rb + q) * 32 + tc];
+                X[(rb + i) * 32 + tc] = s;
+            }
+        }
+        __syncthreads();
+        for (int i = rb + 32 + tr; i < t; i += 8) {
+            TS s = X[i * 32 + tc];
+            const TS* Lr = S + (size_t)(c0 + i) + (size_t)(c0 + rb) * ld;
+            for (int q = 0; q < 32; ++q) s -= Lr[(size_t)q * ld] * X[(rb + q) * 32 + tc];
+            X[i * 32 + tc] = s;
+        }
+        __syncthreads();
+    }
+    if (act)
+        for (int i = tr; i < t; i += 8) S[(size_t)(c0 + i) + (size_t)col * ld] = X[i * 32 + tc];
+}
+
+// ---------------------------------------------------------------- SIMT GEMM
+// C[r0.., c0..] -= A[r0.., k0..] * B[k0.., c0..] (M x N, depth Kd), col-major
+// blocks of the same S^K.  64x64 tile, 256 threads, 4x4 per thread.
+template <class TS>
+__global__ void __launch_bounds__(256)
+gemm_simt_kernel(TS* __restrict__ Sall, int64_t ld, int r0, int c0, int k0, int M, int N, int Kd) {
+    const int K = blockIdx.z;
+    TS* S = Sall + (size_t)K * ld * ld;
+    const int tm = blockIdx.x * 64, tn = blockIdx.y * 64;
+    __shared__ TS As[16][64 + 1];
+    __shared__ TS Bs[16][64 + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    TS acc[4][4] = {};
+    for (int kk = 0; kk < Kd; kk += 16) {
+        for (int i = threadIdx.x; i < 16 * 64; i += 256) {
+            int a_m = i % 64, a_k = i / 64;
+            int gm = tm + a_m;
+            As[a_k][a_m] = (gm < M) ? S[(size_t)(r0 + gm) + (size_t)(k0 + kk + a_k) * ld] : (TS)0;
+            int b_k = i % 16, b_n = i / 16;
+            int gn = tn + b_n;
+            Bs[b_k][b_n] = (gn < N) ? S[(size_t)(k0 + kk + b_k) + (size_t)(c0 + gn) * ld] : (TS)0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            TS a[4], b[4];
+            for (int i = 0; i < 4; ++i) { a[i] = As[q][tx + 16 * i]; b[i] = Bs[q][ty + 16 * i]; }
+            for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+        }
+        __syncthreads();
+    }
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+            int gm = tm + tx + 16 * i, gn = tn + ty + 16 * j;
+            if (gm < M && gn < N) S[(size_t)(r0 + gm) + (size_t)(c0 + gn) * ld] -= acc[i][j];
+        }
+}
+
+// ---------------------------------------------------------------- solve
+// One CTA per element: forward substitution with the LINPACK-ordered unit
+// lower factor (outer-panel swaps replayed first), then backward with U.
+// Arithmetic in the factor precision; r scaled by its max norm.
+template <class TS>
+__global__ void __launch_bounds__(512)
+solve_kernel(const TS* __restrict__ Sall, int64_t ld, const int32_t* __restrict__ pivall,
+             const double* __restrict__ rall, double* __restrict__ xall, const int32_t* skip, int NBo) {
+    const int K = blockIdx.x;
+    if (skip && skip[K]) return;
+    const TS* S = Sall + (size_t)K * ld * ld;
+    const int32_t* piv = pivall + (size_t)K * ld;
+    const double* r = rall + (size_t)K * ld;
+    double* x = xall + (size_t)K * ld;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TS* y = reinterpret_cast<TS*>(smem_raw);
+    __shared__ double red[16];
+    const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, wid = tid >> 5;
+    double mx = 0.0;
+    for (int i = tid; i < ld; i += nth) mx = fmax(mx, fabs(r[i]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) red[wid] = mx;
+    __syncthreads();
+    mx = 0.0;
+    for (int i = 0; i < nth / 32; ++i) mx = fmax(mx, red[i]);
+    const double sc = mx > 0.0 ? 1.0 / mx : 1.0;
+    for (int i = tid; i < ld; i += nth) y[i] = (TS)(r[i] * sc);
+    __syncthreads();
+    // forward
+    for (int c0 = 0; c0 < ld; c0 += NBo) {
+        if (tid == 0)
+            for (int i = c0; i < c0 + NBo; ++i) {
+                int b = piv[i];
+                if (b != i) { TS t = y[i]; y[i] = y[b]; y[b] = t; }
+            }
+        __syncthreads();
+        for (int cb = c0; cb < c0 + NBo; cb += 32) {
+            if (wid == 0) {
+                TS yl = y[cb + lane];
+                for (int i = 0; i < 32; ++i) {
+                    TS yi = __shfl_sync(0xffffffffu, yl, i);
+                    if (lane > i) yl -= S[(size_t)(cb + lane) + (size_t)(cb + i) * ld] * yi;
+                }
+                y[cb + lane] = yl;
+            }
+            __syncthreads();
+            for (int rr = cb + 32 + tid; rr < ld; rr += nth) {
+                TS s = y[rr];
+                const TS* Lr = S + rr + (size_t)cb * ld;
+#pragma unroll 8
+                for (int q = 0; q < 32; ++q) s -= Lr[(size_t)q * ld] * y[cb + q];
+                y[rr] = s;
+            }
+            __syncthreads();
+        }
+    }
+    // backward
+    for (int cb = (int)ld - 32; cb >= 0; cb -= 32) {
+        if (wid == 0) {
+            TS yl = y[cb + lane];
+            for (int i = 31; i >= 0; --i) {
+                TS yi = 0;
+                if (lane == i) { yl = yl / S[(size_t)(cb + i) + (size_t)(cb + i) * ld]; }
+                yi = __shfl_sync(0xffffffffu, yl, i);
+                if (lane < i) yl -= S[(size_t)(cb + lane) + (size_t)(cb + i) * ld] * yi;
+            }
+            y[cb + lane] = yl;
+        }
+        __syncthreads();
+        for (int rr = tid; rr < cb; rr += nth) {
+            TS s = y[rr];
+            const TS* Ur = S + rr + (size_t)cb * ld;
+#pragma unroll 8
+            for (int q = 0; q < 32; ++q) s -= Ur[(size_t)q * ld] * y[cb + q];
+            y[rr] = s;
+        }
+        __syncthreads();
+    }
+    for (int i = tid; i < ld; i += nth) x[i] = (double)y[i] * mx;
+}
+
+template <class TS>
+int pick_ib(int64_t ld) {
+    size_t budget = 200 * 1024;
+    int ib = 8;
+    while (ib > 1 && (size_t)ib * ld * sizeof(TS) > budget) ib >>= 1;
+    return ib;
+}
+
+template <class TS>
+cudaError_t launch_panel(TS* S, int64_t ld, int c, int32_t* piv, int32_t* status, int64_t nK, cudaStream_t st) {
+    int ib = pick_ib<TS>(ld);
+    size_t sm = (size_t)ib * (ld - c) * sizeof(TS);
+    if (sm < 16) sm = 16;
+#define LP(IB) do { cudaFuncSetAttribute(panel_kernel<TS, IB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(ib * ld * sizeof(TS))); \
+                    panel_kernel<TS, IB><<<(unsigned)nK, PANEL_THREADS, sm, st>>>(S, ld, c, piv, status); } while (0)
+    switch (ib) {
+    case 8: LP(8); break;
+    case 4: LP(4); break;
+    case 2: LP(2); break;
+    default: LP(1); break;
+    }
+#undef LP
+    MEHDG_COUNT(1);
+    return cudaGetLastError();
+}
+
+template <class TS>
+cudaError_t launch_laswp(const LUPlan& P, int c0, int w, int j0, int j1, cudaStream_t st) {
+    if (j1 <= j0) return cudaSuccess;
+    int32_t* perm = reinterpret_cast<int32_t*>(P.work);
+    perm_build_kernel<<<(unsigned)((P.nK + 63) / 64), 64, 0, st>>>(P.piv, P.ld, c0, w, perm, (int)P.nK);
+    size_t sm = (size_t)2 * w * 16 * sizeof(TS);
+    cudaFuncSetAttribute(laswp_kernel<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    dim3 g((unsigned)((j1 - j0 + 15) / 16), (unsigned)P.nK);
+    laswp_kernel<TS><<<g, 256, sm, st>>>((TS*)P.S, P.ld, perm, w, j0, j1);
+    MEHDG_COUNT(2);
+    return cudaGetLastError();
+}
+
+template <class TS>
+cudaError_t launch_trsm(const LUPlan& P, int c0, int t, int j0, int j1, cudaStream_t st) {
+    if (j1 <= j0) return cudaSuccess;
+    size_t sm = (size_t)t * 32 * sizeof(TS);
+    cudaFuncSetAttribute(trsm_kernel<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    dim3 g((unsigned)((j1 - j0 + 31) / 32), (unsigned)P.nK);
+    trsm_kernel<TS><<<g, 256, sm, st>>>((TS*)P.S, P.ld, c0, t, j0, j1);
+    MEHDG_COUNT(1);
+    return cudaGetLastError();
+}
+
+template <class TS>
+cudaError_t launch_gemm_simt(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    dim3 g((unsigned)((M + 63) / 64), (unsigned)((N + 63) / 64), (unsigned)P.nK);
+    gemm_simt_kernel<TS><<<g, 256, 0, st>>>((TS*)P.S, P.ld, r0, c0, k0, M, N, Kd);
+    MEHDG_COUNT(1);
+    return cudaGetLastError();
+}
+
+template <class TS>
+cudaError_t trailing_update(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st) {
+    if constexpr (std::is_same<TS, double>::value) return launch_gemm_simt<double>(P, r0, c0, k0, M, N, Kd, st);
+    else return gemm_tc_update(P, r0, c0, k0, M, N, Kd, st);
+}
+
+template <class TS>
+cudaError_t rec_panel(const LUPlan& P, int c, int w, cudaStream_t st) {
+    cudaError_t e;
+    if (w == LEAF) return launch_panel<TS>((TS*)P.S, P.ld, c, P.piv, P.status, P.nK, st);
+    int h = w / 2;
+    if ((e = rec_panel<TS>(P, c, h, st)) != cudaSuccess) return e;
+    if ((e = launch_laswp<TS>(P, c, h, c + h, c + w, st)) != cudaSuccess) return e;
+    if ((e = launch_trsm<TS>(P, c, h, c + h, c + w, st)) != cudaSuccess) return e;
+    if ((e = trailing_update<TS>(P, c + h, c + h, c, (int)P.ld - (c + h), h, h, st)) != cudaSuccess) return e;
+    if ((e = rec_panel<TS>(P, c + h, h, st)) != cudaSuccess) return e;
+    return launch_laswp<TS>(P, c + h, h, c, c + h, st);
+}
+
+template <class TS>
+cudaError_t factor_t(const LUPlan& P, cudaStream_t st) {
+    cudaError_t e;
+    const int ld = (int)P.ld;
+    for (int c0 = 0; c0 < ld; c0 += LU_NB) {
+        int ev = prof_begin(P.prof, PH_LU_PANELS, st);
+        if ((e = rec_panel<TS>(P, c0, LU_NB, st)) != cudaSuccess) return e;
+        if (c0 + LU_NB < ld) {
+            if ((e = launch_laswp<TS>(P, c0, LU_NB, c0 + LU_NB, ld, st)) != cudaSuccess) return e;
+            if ((e = launch_trsm<TS>(P, c0, LU_NB, c0 + LU_NB, ld, st)) != cudaSuccess) return e;
+        }
+        prof_end(P.prof, ev, st, 0.0);
+        if (c0 + LU_NB < ld) {
+            int rest = ld - (c0 + LU_NB);
+            ev = prof_begin(P.prof, PH_GEMM_OUTER, st);
+            if ((e = trailing_update<TS>(P, c0 + LU_NB, c0 + LU_NB, c0, rest, rest, LU_NB, st)) != cudaSuccess) return e;
+            prof_end(P.prof, ev, st, 2.0 * rest * (double)rest * LU_NB * (double)P.nK);
+        }
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t gemm_simt_update_f32(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st) {
+    return launch_gemm_simt<float>(P, r0, c0, k0, M, N, Kd, st);
+}
+
+size_t lu_work_bytes(int64_t nK, int64_t ld, bool fp64, int prec) {
+    size_t perm = (size_t)nK * (1 + 4 * LU_NB) * sizeof(int32_t);
+    perm = (perm + 255) & ~(size_t)255;
+    return perm + (fp64 ? 0 : gemm_tc_work_bytes(nK, ld, prec));
+}
+
+cudaError_t lu_factor(const LUPlan& P, cudaStream_t st) {
+    if (P.fp64) return factor_t<double>(P, st);
+    return factor_t<float>(P, st);
+}
+
+cudaError_t lu_solve(const LUPlan& P, const double* r, double* x, const int32_t* skip, cudaStream_t st) {
+    size_t ts = P.fp64 ? 8 : 4;
+    size_t sm = ts * P.ld;
+    if (P.fp64) {
+        cudaFuncSetAttribute(solve_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        solve_kernel<double><<<(unsigned)P.nK, 512, sm, st>>>((const double*)P.S, P.ld, P.piv, r, x, skip, LU_NB);
+    } else {
+        cudaFuncSetAttribute(solve_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        solve_kernel<float><<<(unsigned)P.nK, 512, sm, st>>>((const float*)P.S, P.ld, P.piv, r, x, skip, LU_NB);
+    }
+    MEHDG_COUNT(1);
+    return cudaGetLastError();
+}

@@ -1,0 +1,11 @@
+// lu_internal.cuh -- pieces shared by lu.cu and gemm_tc.cu
+#pragma once
+#include "kernels.cuh"
+
+constexpr int LU_NB = 256;   // outer panel width (depth of the big trailing update)
+
+// C[r0.., c0..] -= L[r0.., k0..k0+Kd) * U[k0..k0+Kd, c0..] on the tensor cores
+// (TF32 or BF16 operands, FP32 accumulation), S^K column-major FP32.
+cudaError_t gemm_tc_update(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st);
+size_t gemm_tc_work_bytes(int64_t nK, int64_t ld, int prec);
+cudaError_t gemm_simt_update_f32(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st);

@@ -1,0 +1,234 @@
+"""Thin Python binding of the C-ABI in include/mehdg.h (argument marshalling
+only; every step of the Newton step runs in libmehdg.so's CUDA kernels).
+
+The functions keep the C names.  Device arrays are torch CUDA tensors (FP64,
+contiguous); mesh arrays are numpy arrays.  ``stream`` defaults to the
+current torch stream.  Loading fails loudly when the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmehdg.so")
+
+MEHDG_FLUX_EC, MEHDG_FLUX_ES, MEHDG_FLUX_KEPES = 0, 1, 2
+MEHDG_FP64, MEHDG_MIXED_TF32, MEHDG_MIXED_BF16 = 0, 1, 2
+ERRORS = {0: "MEHDG_OK", -1: "MEHDG_EINVAL", -2: "MEHDG_ENONPHYS", -3: "MEHDG_ESINGULAR",
+          -4: "MEHDG_ENOCONV", -5: "MEHDG_ECUDA", -6: "MEHDG_ENOMEM", -7: "MEHDG_ESTATE",
+          -8: "MEHDG_ETIMEOUT"}
+PHASES = ["residual", "jacobian", "lu_panels", "lu_trailing_update", "solve", "tangent"]
+
+EXPORTED = ["mehdg_default_params", "mehdg_create", "mehdg_set_mesh", "mehdg_set_state",
+            "mehdg_residual", "mehdg_condense", "mehdg_apply_condensed", "mehdg_recover",
+            "mehdg_status", "mehdg_last_error", "mehdg_destroy", "mehdg_profile_enable",
+            "mehdg_profile_read", "mehdg_launch_count"]
+
+
+class mehdg_params(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("Re", C.c_double), ("Pr", C.c_double), ("Mach", C.c_double),
+                ("dt", C.c_double), ("viscous", C.c_int), ("flux", C.c_int), ("prec", C.c_int),
+                ("refine_tol", C.c_double), ("refine_max_iter", C.c_int), ("time_term", C.c_int)]
+
+
+class MehdgError(RuntimeError):
+    pass
+
+
+_lib = None
+_vp = C.c_void_p
+
+
+def load(path: str | None = None):
+    """Load libmehdg.so (built by build.py / __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise MehdgError(f"{p} is missing: build it with paper_2507_22195_gb300.build.build()")
+    L = C.CDLL(p)
+    L.mehdg_default_params.argtypes = [C.POINTER(mehdg_params)]
+    L.mehdg_default_params.restype = None
+    L.mehdg_create.argtypes = [C.POINTER(_vp), C.POINTER(mehdg_params)]
+    L.mehdg_set_mesh.argtypes = [_vp, C.c_int64, _vp, _vp, _vp, _vp, C.c_int64]
+    L.mehdg_set_state.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+    L.mehdg_residual.argtypes = [_vp, _vp, _vp, _vp, _vp]
+    L.mehdg_condense.argtypes = [_vp, _vp, _vp, _vp]
+    L.mehdg_apply_condensed.argtypes = [_vp, _vp, _vp, _vp]
+    L.mehdg_recover.argtypes = [_vp, _vp, _vp, _vp, _vp]
+    L.mehdg_status.argtypes = [_vp, _vp, _vp]
+    L.mehdg_last_error.argtypes = [_vp]
+    L.mehdg_last_error.restype = C.c_char_p
+    L.mehdg_destroy.argtypes = [_vp]
+    L.mehdg_destroy.restype = None
+    L.mehdg_profile_enable.argtypes = [_vp, C.c_int]
+    L.mehdg_profile_read.argtypes = [_vp, _vp, _vp, _vp, C.c_int]
+    L.mehdg_launch_count.argtypes = []
+    L.mehdg_launch_count.restype = C.c_int64
+    _lib = L
+    return L
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        import torch
+        assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous(), (t.device, t.dtype)
+        return t.data_ptr()
+    return t.ctypes.data
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _check(ctx, rc, what):
+    if rc != 0:
+        msg = load().mehdg_last_error(ctx).decode() if ctx else ""
+        raise MehdgError(f"{what}: {ERRORS.get(rc, rc)}: {msg}")
+
+
+def mehdg_default_params(**overrides) -> mehdg_params:
+    p = mehdg_params()
+    load().mehdg_default_params(C.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def mehdg_create(params: mehdg_params):
+    h = _vp()
+    _check(None, load().mehdg_create(C.byref(h), C.byref(params)), "mehdg_create")
+    return h.value
+
+
+def mehdg_set_mesh(ctx, p, m, box, face_gid, n_global_faces):
+    p = np.ascontiguousarray(p, dtype=np.int32)
+    m = np.ascontiguousarray(m, dtype=np.int32)
+    box = np.ascontiguousarray(box, dtype=np.float64)
+    gid = np.ascontiguousarray(face_gid, dtype=np.int64)
+    _check(ctx, load().mehdg_set_mesh(ctx, len(p), p.ctypes.data, m.ctypes.data, box.ctypes.data,
+                                      gid.ctypes.data, int(n_global_faces)), "mehdg_set_mesh")
+
+
+def mehdg_set_state(ctx, v, vhat, q, vstar, stream=None):
+    _check(ctx, load().mehdg_set_state(ctx, _ptr(v), _ptr(vhat), _ptr(q), _ptr(vstar), _stream(stream)),
+           "mehdg_set_state")
+
+
+def mehdg_residual(ctx, R_V, R_Q, R_Vhat, stream=None):
+    _check(ctx, load().mehdg_residual(ctx, _ptr(R_V), _ptr(R_Q), _ptr(R_Vhat), _stream(stream)),
+           "mehdg_residual")
+
+
+def mehdg_condense(ctx, bhat, Ahat_local=None, stream=None):
+    _check(ctx, load().mehdg_condense(ctx, _ptr(bhat), _ptr(Ahat_local), _stream(stream)), "mehdg_condense")
+
+
+def mehdg_apply_condensed(ctx, x, y, stream=None):
+    _check(ctx, load().mehdg_apply_condensed(ctx, _ptr(x), _ptr(y), _stream(stream)), "mehdg_apply_condensed")
+
+
+def mehdg_recover(ctx, dVhat, dV, dQ=None, stream=None):
+    _check(ctx, load().mehdg_recover(ctx, _ptr(dVhat), _ptr(dV), _ptr(dQ), _stream(stream)), "mehdg_recover")
+
+
+def mehdg_status(ctx, nK):
+    st = np.zeros(nK, dtype=np.int32)
+    it = np.zeros(nK, dtype=np.int32)
+    _check(ctx, load().mehdg_status(ctx, st.ctypes.data, it.ctypes.data), "mehdg_status")
+    return st, it
+
+
+def mehdg_last_error(ctx) -> str:
+    return load().mehdg_last_error(ctx).decode()
+
+
+def mehdg_destroy(ctx):
+    load().mehdg_destroy(ctx)
+
+
+def mehdg_profile_enable(ctx, enable=True):
+    _check(ctx, load().mehdg_profile_enable(ctx, int(enable)), "mehdg_profile_enable")
+
+
+def mehdg_profile_read(ctx):
+    n = len(PHASES)
+    ms, cnt, fl = np.zeros(n), np.zeros(n, dtype=np.int64), np.zeros(n)
+    _check(ctx, load().mehdg_profile_read(ctx, ms.ctypes.data, cnt.ctypes.data, fl.ctypes.data, n),
+           "mehdg_profile_read")
+    return {PHASES[i]: dict(ms=float(ms[i]), launches=int(cnt[i]), flops=float(fl[i])) for i in range(n)}
+
+
+def mehdg_launch_count() -> int:
+    return int(load().mehdg_launch_count())
+
+
+class Context:
+    """Owner of one library context over a mesh (see inputs.Mesh)."""
+
+    def __init__(self, mesh, **params):
+        self.mesh = mesh
+        self.params = mehdg_default_params(**params)
+        self.ctx = mehdg_create(self.params)
+        nK = mesh.nK
+        mehdg_set_mesh(self.ctx, np.full(nK, mesh.p), np.full(nK, mesh.m), mesh.boxes, mesh.face_gid,
+                       mesh.n_global_faces)
+        self._state = None
+
+    def close(self):
+        if self.ctx:
+            mehdg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, v, vhat, q=None, vstar=None):
+        self._state = (v, vhat, q, vstar)      # keep the tensors alive
+        mehdg_set_state(self.ctx, v, vhat, q, vstar)
+
+    def residual(self):
+        import torch
+        m = self.mesh
+        dev = self._state[0].device
+        RV = torch.empty((m.nK, 5, m.Nn), dtype=torch.float64, device=dev)
+        RQ = torch.empty((m.nK, 5, 3, m.Nn), dtype=torch.float64, device=dev) if self.params.viscous else None
+        RH = torch.empty((m.n_global_faces, 5, m.n2), dtype=torch.float64, device=dev)
+        mehdg_residual(self.ctx, RV, RQ, RH)
+        return RV, RQ, RH
+
+    def condense(self, bhat=None):
+        import torch
+        m = self.mesh
+        if bhat is None:
+            bhat = torch.empty((m.n_global_faces, 5, m.n2), dtype=torch.float64, device=self._state[0].device)
+        mehdg_condense(self.ctx, bhat)
+        return bhat
+
+    def apply(self, x):
+        import torch
+        y = torch.empty_like(x)
+        mehdg_apply_condensed(self.ctx, x, y)
+        return y
+
+    def recover(self, dvh):
+        import torch
+        m = self.mesh
+        dV = torch.empty((m.nK, 5, m.Nn), dtype=torch.float64, device=dvh.device)
+        mehdg_recover(self.ctx, dvh, dV)
+        return dV
+
+    def status(self):
+        return mehdg_status(self.ctx, self.mesh.nK)

@@ -1,0 +1,161 @@
+"""GPU parity: the CUDA path through the C-ABI against the FP64 oracle, on the
+same seeded inputs, element by element.
+
+Tolerances (relative 2-norms over each output array):
+  residual R_V, R_Vhat (FP64 kernels)                         1e-11
+  condensed b-hat, recovered dV, A-hat x, FP64 LU             1e-10
+  same with the mixed-precision LU after FP64 refinement      1e-8
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2507_22195_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FLUX = {0: "EC", 1: "ES", 2: "KEPES"}
+
+
+def M():
+    from paper_2507_22195_gb300 import mehdg
+    return mehdg
+
+
+def rel(a, b):
+    a = a.detach().cpu().numpy() if hasattr(a, "detach") else a
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def to_dev(st):
+    d = torch.device("cuda:0")
+    q = None if st.q is None else torch.tensor(st.q, device=d)
+    return (torch.tensor(st.v, device=d), torch.tensor(st.vhat, device=d), q,
+            torch.tensor(st.vstar, device=d))
+
+
+def case(name):
+    if name == "vortex_p2m2":
+        mesh = I.periodic_mesh(2, 2, 2, 0.0, 10.0)
+        st = I.make_state(mesh, "vortex", 1e-3, 22195, 22196, period=10.0)
+        return mesh, st, dict(Mach=0.1)
+    if name == "vortex_p2m1":
+        mesh = I.periodic_mesh(2, 2, 1, 0.0, 10.0)
+        st = I.make_state(mesh, "vortex", 1e-3, 22195, 22196, period=10.0)
+        return mesh, st, dict(Mach=0.1)
+    if name == "tgv_p3m2":
+        mesh = I.periodic_mesh((2, 1, 1), 3, 2)
+        st = I.make_state(mesh, "tgv", 1e-3, 22197, 22198, M0=0.1)
+        return mesh, st, dict(Mach=0.1)
+    if name == "tgv_p3m3":
+        mesh = I.periodic_mesh((2, 2, 1), 3, 3)
+        st = I.make_state(mesh, "tgv", 1e-3, 22197, 22198, M0=0.1)
+        return mesh, st, dict(Mach=0.1)
+    if name == "tgv_p1m1":
+        mesh = I.periodic_mesh(3, 1, 1)
+        st = I.make_state(mesh, "tgv", 1e-2, 5, 6, M0=0.3)
+        return mesh, st, dict(Mach=0.3)
+    if name == "tgv_p4m1":
+        mesh = I.periodic_mesh(2, 4, 1)
+        st = I.make_state(mesh, "tgv", 1e-2, 5, 6, M0=0.3)
+        return mesh, st, dict(Mach=0.3)
+    raise ValueError(name)
+
+
+@pytest.mark.parametrize("name", ["vortex_p2m2", "tgv_p3m3", "tgv_p1m1", "tgv_p4m1"])
+@pytest.mark.parametrize("flux", [0, 1, 2])
+@pytest.mark.parametrize("time_term", [1, 0])
+def test_residual_matches_oracle(name, flux, time_term):
+    mesh, st, kw = case(name)
+    ctx = M().Context(mesh, flux=flux, prec=M().MEHDG_FP64, time_term=time_term, **kw)
+    ctx.set_state(*to_dev(st))
+    RV, _, RH = ctx.residual()
+    torch.cuda.synchronize()
+    stat, _ = ctx.status()
+    assert (stat == 0).all()
+    prm = oracle.params(flux=flux, time_term=time_term, **kw)
+    rv, _, rh = oracle.residual_mesh(prm, mesh, st)
+    assert rel(RV, rv) < 1e-11, rel(RV, rv)
+    assert rel(RH, rh) < 1e-11, rel(RH, rh)
+    ctx.close()
+
+
+def _oracle_condensed(prm, mesh, st, dvh):
+    bh, Ahats = oracle.condense_mesh(prm, mesh, st, want_Ahat=True)
+    A = oracle.assemble_Ahat(mesh, Ahats)
+    dV, _ = oracle.recover_mesh(prm, mesh, st, dvh)
+    return bh, A, dV
+
+
+@pytest.mark.parametrize("name", ["vortex_p2m1", "vortex_p2m2", "tgv_p3m2"])
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_condense_apply_recover_match_oracle(name, prec):
+    mesh, st, kw = case(name)
+    flux = 2
+    ctx = M().Context(mesh, flux=flux, prec=prec, **kw)
+    v, vh, q, vs = to_dev(st)
+    ctx.set_state(v, vh, q, vs)
+    bh = ctx.condense()
+    dvh_np = I.random_direction(st.vhat.shape, 77, 1e-3)
+    dvh = torch.tensor(dvh_np, device="cuda:0")
+    y = ctx.apply(dvh)
+    dV = ctx.recover(dvh)
+    torch.cuda.synchronize()
+    stat, iters = ctx.status()
+    assert (stat == 0).all(), (stat, iters)
+    prm = oracle.params(flux=flux, **kw)
+    bh_o, A_o, dV_o = _oracle_condensed(prm, mesh, st, dvh_np)
+    y_o = (A_o @ dvh_np.ravel()).reshape(dvh_np.shape)
+    tol = 1e-10 if prec == 0 else 1e-8
+    e = (rel(bh, bh_o), rel(y, y_o), rel(dV, dV_o))
+    assert max(e) < tol, (e, iters)
+    ctx.close()
+
+
+def test_newton_step_matches_brute_force():
+    """condense -> dense global solve of sum A-hat (built column by column with
+    apply_condensed) -> recover equals the oracle's monolithic solve"""
+    mesh = I.periodic_mesh(2, 1, 1)
+    st = I.make_state(mesh, "tgv", 1e-2, 5, 6, M0=0.3)
+    ctx = M().Context(mesh, flux=2, prec=M().MEHDG_FP64, Mach=0.3)
+    ctx.set_state(*to_dev(st))
+    bh = ctx.condense()
+    G = st.vhat.size
+    A = np.zeros((G, G))
+    for j in range(G):
+        e = torch.zeros(st.vhat.shape, dtype=torch.float64, device="cuda:0")
+        e.view(-1)[j] = 1.0
+        A[:, j] = ctx.apply(e).cpu().numpy().ravel()
+    x = np.linalg.solve(A, bh.cpu().numpy().ravel()).reshape(st.vhat.shape)
+    dV = ctx.recover(torch.tensor(x, device="cuda:0"))
+    prm = oracle.params(flux=2, Mach=0.3)
+    _, dV_o, dH_o = oracle.brute_force(prm, mesh, st)
+    assert rel(x, dH_o) < 1e-9 and rel(dV, dV_o) < 1e-9
+    ctx.close()
+
+
+def test_nonphysical_state_reports_status():
+    mesh, st, kw = case("vortex_p2m1")
+    st.v[3, 4, :] = 0.5           # beta = -v5 < 0 in element 3
+    ctx = M().Context(mesh, flux=2, prec=M().MEHDG_FP64, **kw)
+    ctx.set_state(*to_dev(st))
+    ctx.residual()
+    stat, _ = ctx.status()
+    assert stat[3] == -2 and (np.delete(stat, 3) == 0).all()
+    ctx.close()
+
+
+def test_bad_arguments_return_einval():
+    mesh, st, kw = case("vortex_p2m1")
+    with pytest.raises(M().MehdgError, match="EINVAL"):
+        ctx = M().Context(mesh, flux=7)
+    ctx = M().Context(mesh, **kw)
+    with pytest.raises(M().MehdgError, match="ESTATE"):
+        ctx.recover(torch.zeros(st.vhat.shape, dtype=torch.float64, device="cuda:0"))
+    gid = mesh.face_gid.copy()
+    gid[0, 0] = mesh.n_global_faces + 5
+    with pytest.raises(M().MehdgError, match="EINVAL"):
+        M().mehdg_set_mesh(ctx.ctx, np.full(mesh.nK, 2), np.full(mesh.nK, 1), mesh.boxes, gid,
+                           mesh.n_global_faces)
+    ctx.close()

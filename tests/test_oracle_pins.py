@@ -396,6 +396,20 @@ def test_condensation_matches_monolithic_brute_force(mp, vis):
         assert e(dQ2, dQ) < 1e-10
 
 
+def test_brute_force_on_self_periodic_mesh():
+    """P7 on a 2x1x1 periodic mesh, where an element's y-/y+ and z-/z+
+    faces are the same global face (both sides summed, eq. s32c)"""
+    mesh = I.periodic_mesh((2, 1, 1), 1, 1)
+    st = I.make_state(mesh, "tgv", 1e-2, 5, 6, M0=0.3)
+    prm = oracle.params(flux=oracle.KEPES, Mach=0.3)
+    dQ, dV, dH = oracle.brute_force(prm, mesh, st)
+    bh, Ahats = oracle.condense_mesh(prm, mesh, st, want_Ahat=True)
+    x = oracle.solve(oracle.assemble_Ahat(mesh, Ahats), bh.ravel()).reshape(dH.shape)
+    dV2, _ = oracle.recover_mesh(prm, mesh, st, x)
+    e = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)
+    assert e(x, dH) < 1e-10 and e(dV2, dV) < 1e-10
+
+
 def test_getrf_matches_library_solve():
     rng = np.random.default_rng(12)
     A = rng.normal(size=(60, 60)); b = rng.normal(size=60)
