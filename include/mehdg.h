@@ -48,6 +48,7 @@
 #ifndef MEHDG_H
 #define MEHDG_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -158,6 +159,18 @@ int mehdg_profile_read(mehdg_ctx* ctx, double* ms, int64_t* launches, double* fl
 
 /* Number of kernels this library has launched since it was loaded. */
 int64_t mehdg_launch_count(void);
+
+/* Diagnostics: one tensor-core trailing update of the mixed-precision LU,
+ *   S[r0+i, c0+j] -= sum_k S[r0+i, k0+k] S[k0+k, c0+j]  (i<M, j<N, k<Kd),
+ * on nK column-major FP32 matrices S [nK][ld][ld] (device), with operands
+ * rounded to TF32 (prec 1) or BF16 (prec 2) and FP32 accumulation; the
+ * Schur-complement update step of the LU of S^K (eq. R3 factorisation).
+ * M, N, Kd and the offsets are multiples of 32; work: device scratch of
+ * mehdg_test_trailing_work_bytes(nK, ld) bytes.  Returns MEHDG_OK or
+ * MEHDG_ECUDA. */
+int mehdg_test_trailing_update(int64_t nK, int64_t ld, float* S, int r0, int c0, int k0, int M, int N,
+                               int Kd, int prec, void* work, void* stream);
+size_t mehdg_test_trailing_work_bytes(int64_t nK, int64_t ld);
 
 /* Free every device workspace and the context. */
 void mehdg_destroy(mehdg_ctx* ctx);

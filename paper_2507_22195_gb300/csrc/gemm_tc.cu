@@ -1,7 +1,360 @@
-// gemm_tc.cu -- trailing update of the mixed-precision LU (placeholder: SIMT FP32)
+// gemm_tc.cu -- trailing update of the mixed-precision LU on the 5th-generation
+// tensor cores (tcgen05, sm_103a):
+//     C[r0+i, c0+j] -= sum_k L[r0+i, k0+k] U[k0+k, c0+j],   i < M, j < N, k < Kd
+// on the column-major FP32 S^K of every element (batched over elements).
+//
+// 1. pack: L (M x Kd) and U (Kd x N) are copied into K-major operand panels
+//    in the operand type (TF32 rounded to nearest, or BF16), zero-padded in K
+//    to whole 128-byte rows;
+// 2. MMA: one CTA per 128 x BN tile of C (BN = 128, or 32/64 for narrow
+//    updates).  Warp 0 (one lane) streams 128-byte K-chunks of both panels
+//    into a shared-memory ring with TMA (128B swizzle, mbarrier transaction
+//    counts); warp 1 (one lane) issues tcgen05.mma (kind::tf32 or
+//    kind::f16) accumulating in TMEM and releases each ring slot with
+//    tcgen05.commit; warp 2 owns the TMEM allocation;
+// 3. epilogue: the four warps read their 32 TMEM lanes (rows) with
+//    tcgen05.ld.32x32b and subtract from C in place (32 consecutive rows per
+//    warp and column: coalesced 128-byte accesses).
+// Every mbarrier wait is bounded; on timeout the element's status becomes
+// MEHDG_ETIMEOUT, the epilogue is skipped and TMEM is still released.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cstring>
 #include "lu_internal.cuh"
 
-cudaError_t gemm_tc_update(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st) {
-    return gemm_simt_update_f32(P, r0, c0, k0, M, N, Kd, st);
+namespace {
+
+constexpr int TM = 128;           // rows of a C tile (TMEM lanes)
+constexpr int CHUNK_BYTES = 128;  // K bytes per TMA box / swizzle row
+constexpr int STAGES = 2;
+
+__device__ __forceinline__ uint32_t s_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t cnt) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s_addr(b)), "r"(cnt) : "memory");
 }
-size_t gemm_tc_work_bytes(int64_t, int64_t, int) { return 0; }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s_addr(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok) : "r"(s_addr(b)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// bounded wait (about a second at most); false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+    for (uint32_t i = 0; i < (1u << 23); ++i) {
+        if (mbar_try(b, parity)) return true;
+        if (i > 32) __nanosleep(64);
+    }
+    return false;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
+        ::"r"(s_addr(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(s_addr(bar)), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+// shared-memory matrix descriptor: K-major, 128B swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1u << 16;                 // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024u >> 4) << 32;       // stride byte offset
+    d |= (uint64_t)1u << 46;                 // descriptor version
+    d |= (uint64_t)2u << 61;                 // 128-byte swizzle
+    return d;
+}
+// instruction descriptor: D = F32, A/B format, K-major A and B, N>>3, M>>4
+__host__ __device__ constexpr uint32_t idesc(int M, int N, uint32_t fmt) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+template <bool BF16>
+__device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    if constexpr (BF16)
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                     ::"r"(d), "l"(a), "l"(b), "r"(id), "r"(acc));
+    else
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                     " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                     ::"r"(d), "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(s_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <int BN, bool BF16>
+__global__ void __launch_bounds__(128)
+tc_update_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                 float* __restrict__ Sall, int64_t ld, int r0, int c0, int M, int N, int nchunk, int tiles_m,
+                 int32_t* status) {
+    constexpr int A_BYTES = TM * CHUNK_BYTES;
+    constexpr int B_BYTES = BN * CHUNK_BYTES;
+    constexpr int CHUNK_K = BF16 ? 64 : 32;
+    constexpr uint32_t ID = idesc(TM, BN, BF16 ? 1u : 2u);
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* sA = smem;
+    unsigned char* sB = smem + STAGES * A_BYTES;
+    __shared__ uint64_t full[STAGES], empty[STAGES], done;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_fail;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int K = blockIdx.y, tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        mbar_init(&done, 1);
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(s_addr(&tmem_slot)), "r"((uint32_t)BN) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // producer: TMA ring
+        for (int c = 0; c < nchunk; ++c) {
+            const int s = c % STAGES;
+            if (c >= STAGES && !mbar_wait(&empty[s], ((c / STAGES) - 1) & 1)) { s_fail = 1; break; }
+            mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
+            tma_load_3d(sA + s * A_BYTES, &mapA, &full[s], c * CHUNK_K, tm * TM, K);
+            tma_load_3d(sB + s * B_BYTES, &mapB, &full[s], c * CHUNK_K, tn * BN, K);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        for (int c = 0; c < nchunk; ++c) {
+            const int s = c % STAGES;
+            if (!mbar_wait(&full[s], (c / STAGES) & 1)) { s_fail = 1; break; }
+            tc_fence_after();
+            const uint64_t da = sdesc(s_addr(sA + s * A_BYTES));
+            const uint64_t db = sdesc(s_addr(sB + s * B_BYTES));
+#pragma unroll
+            for (int j = 0; j < CHUNK_BYTES / 32; ++j)      // 32 bytes of K per instruction
+                umma<BF16>(tmem, da + (uint64_t)(j * 2), db + (uint64_t)(j * 2), ID, (c | j) != 0);
+            umma_commit(&empty[s]);
+        }
+        umma_commit(&done);
+    }
+    __syncwarp();
+    // epilogue: the C values do not depend on the MMA, so the first 32-column
+    // chunk is fetched before waiting for it and each next chunk while the
+    // current one is written (32 independent loads in flight per thread)
+    float* S = Sall + (size_t)K * ld * ld;
+    const int row = tm * TM + warp * 32 + lane;
+    const bool rok = row < M;
+    float* Crow = S + (size_t)(r0 + row) + (size_t)c0 * ld;
+    float cv[32], cn[32];
+    {
+        const int col0 = tn * BN;
+        if (rok && col0 < N) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) cv[j] = __ldcs(Crow + (size_t)(col0 + j) * ld);
+        }
+    }
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(&done, 0));   // warp-uniform
+    tc_fence_after();
+    if (ok && !s_fail) {
+#pragma unroll 1
+        for (int cc = 0; cc < BN; cc += 32) {
+            const int col0 = tn * BN + cc;
+            const bool has_next = cc + 32 < BN && col0 + 32 < N;
+            if (rok && has_next) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) cn[j] = __ldcs(Crow + (size_t)(col0 + 32 + j) * ld);
+            }
+            uint32_t r[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc, r);
+            if (rok && col0 < N) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) __stcs(Crow + (size_t)(col0 + j) * ld, cv[j] - __uint_as_float(r[j]));
+            }
+#pragma unroll
+            for (int j = 0; j < 32; ++j) cv[j] = cn[j];
+        }
+    } else if (threadIdx.x == 0 && status) {
+        status[K] = MEHDG_ETIMEOUT;
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 2) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------- packing
+// A panel: Ap[K][m][k] = L[r0+m][k0+k] (k < Kd, else 0); 32x32 transposes.
+template <bool BF16>
+__global__ void pack_A_kernel(const float* __restrict__ Sall, int64_t ld, int r0, int k0, int M, int Kd, int Kp,
+                              void* __restrict__ out) {
+    const int K = blockIdx.z;
+    const float* S = Sall + (size_t)K * ld * ld;
+    __shared__ float t[32][33];
+    const int m0 = blockIdx.x * 32, kk0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;     // 32 x 8
+    for (int i = ty; i < 32; i += 8) {
+        int k = kk0 + i, m = m0 + tx;
+        t[i][tx] = (k < Kd && m < M) ? S[(size_t)(r0 + m) + (size_t)(k0 + k) * ld] : 0.f;
+    }
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+        int m = m0 + i, k = kk0 + tx;
+        if (m < M && k < Kp) {
+            size_t o = ((size_t)K * M + m) * Kp + k;
+            float x = t[tx][i];
+            if constexpr (BF16) reinterpret_cast<__nv_bfloat16*>(out)[o] = __float2bfloat16_rn(x);
+            else {
+                uint32_t y;
+                asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
+                reinterpret_cast<uint32_t*>(out)[o] = y;
+            }
+        }
+    }
+}
+// B panel: Bp[K][n][k] = U[k0+k][c0+n] (contiguous in k on both sides)
+template <bool BF16>
+__global__ void pack_B_kernel(const float* __restrict__ Sall, int64_t ld, int k0, int c0, int N, int Kd, int Kp,
+                              void* __restrict__ out) {
+    const int K = blockIdx.z;
+    const float* S = Sall + (size_t)K * ld * ld;
+    const int n = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (n >= N) return;
+    for (int k = threadIdx.x & 31; k < Kp; k += 32) {
+        float x = k < Kd ? S[(size_t)(k0 + k) + (size_t)(c0 + n) * ld] : 0.f;
+        size_t o = ((size_t)K * N + n) * Kp + k;
+        if constexpr (BF16) reinterpret_cast<__nv_bfloat16*>(out)[o] = __float2bfloat16_rn(x);
+        else {
+            uint32_t y;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
+            reinterpret_cast<uint32_t*>(out)[o] = y;
+        }
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+bool encoder() {
+    if (g_encode) return true;
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+        return false;
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    return true;
+}
+
+// 3-D map over packed panels [nK][rows][Kp], box = 128 bytes of K x box_rows
+bool make_map(CUtensorMap* map, void* base, bool bf16, int Kp, int rows, int64_t nK, int box_rows) {
+    const int es = bf16 ? 2 : 4;
+    cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)nK};
+    cuuint64_t strides[2] = {(cuuint64_t)Kp * es, (cuuint64_t)Kp * es * rows};
+    cuuint32_t box[3] = {(cuuint32_t)(CHUNK_BYTES / es), (cuuint32_t)box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = g_encode(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base,
+                          dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+size_t perm_bytes(int64_t nK) {
+    size_t b = (size_t)nK * (1 + 4 * LU_NB) * sizeof(int32_t);
+    return (b + 255) & ~(size_t)255;
+}
+
+template <int BN, bool BF16>
+cudaError_t launch_tc(const CUtensorMap& a, const CUtensorMap& b, const LUPlan& P, int r0, int c0, int M, int N,
+                      int nchunk, cudaStream_t st) {
+    const int tiles_m = (M + TM - 1) / TM, tiles_n = (N + BN - 1) / BN;
+    const size_t sm = STAGES * (size_t)(TM + BN) * CHUNK_BYTES + 1024;
+    cudaFuncSetAttribute(tc_update_kernel<BN, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    dim3 g((unsigned)(tiles_m * tiles_n), (unsigned)P.nK);
+    tc_update_kernel<BN, BF16><<<g, 128, sm, st>>>(a, b, (float*)P.S, P.ld, r0, c0, M, N, nchunk, tiles_m, P.status);
+    MEHDG_COUNT(1);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t gemm_tc_work_bytes(int64_t nK, int64_t ld, int prec) {
+    (void)prec;
+    // two panels of at most ld x 256 FP32 per element, each 256-byte aligned
+    size_t pan = (size_t)nK * ld * LU_NB * 4;
+    pan = (pan + 255) & ~(size_t)255;
+    return 2 * pan;
+}
+
+cudaError_t gemm_tc_update(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    if (M < TM) return gemm_simt_update_f32(P, r0, c0, k0, M, N, Kd, st);   // a few tiny inner updates
+    if (!encoder()) return cudaErrorNotSupported;
+    const bool bf16 = P.prec == MEHDG_MIXED_BF16;
+    const int es = bf16 ? 2 : 4;
+    const int chunk_k = CHUNK_BYTES / es;
+    const int Kp = (Kd + chunk_k - 1) / chunk_k * chunk_k;
+    const int nchunk = Kp / chunk_k;
+    unsigned char* w = reinterpret_cast<unsigned char*>(P.work) + perm_bytes(P.nK);
+    size_t pan = ((size_t)P.nK * P.ld * LU_NB * 4 + 255) & ~(size_t)255;
+    void* Ap = w;
+    void* Bp = w + pan;
+    // pack
+    {
+        dim3 g((unsigned)((M + 31) / 32), (unsigned)((Kp + 31) / 32), (unsigned)P.nK);
+        if (bf16) pack_A_kernel<true><<<g, 256, 0, st>>>((const float*)P.S, P.ld, r0, k0, M, Kd, Kp, Ap);
+        else pack_A_kernel<false><<<g, 256, 0, st>>>((const float*)P.S, P.ld, r0, k0, M, Kd, Kp, Ap);
+        dim3 gb((unsigned)((N + 7) / 8), 1, (unsigned)P.nK);
+        if (bf16) pack_B_kernel<true><<<gb, 256, 0, st>>>((const float*)P.S, P.ld, k0, c0, N, Kd, Kp, Bp);
+        else pack_B_kernel<false><<<gb, 256, 0, st>>>((const float*)P.S, P.ld, k0, c0, N, Kd, Kp, Bp);
+        MEHDG_COUNT(2);
+    }
+    const int BN = N >= 128 ? 128 : (N >= 64 ? 64 : 32);
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, Ap, bf16, Kp, M, P.nK, TM) || !make_map(&mb, Bp, bf16, Kp, N, P.nK, BN))
+        return cudaErrorInvalidValue;
+#define LT(BNV) (bf16 ? launch_tc<BNV, true>(ma, mb, P, r0, c0, M, N, nchunk, st) \
+                      : launch_tc<BNV, false>(ma, mb, P, r0, c0, M, N, nchunk, st))
+    if (BN == 128) return LT(128);
+    if (BN == 64) return LT(64);
+    return LT(32);
+#undef LT
+}
+
+// test hook: one trailing update on caller-owned FP32 column-major matrices
+extern "C" int mehdg_test_trailing_update(int64_t nK, int64_t ld, float* S, int r0, int c0, int k0, int M, int N,
+                                          int Kd, int prec, void* work, void* stream) {
+    LUPlan P;
+    std::memset(&P, 0, sizeof(P));
+    P.nK = nK; P.ld = ld; P.N = ld; P.fp64 = false; P.prec = prec; P.S = S; P.work = work;
+    cudaError_t e = gemm_tc_update(P, r0, c0, k0, M, N, Kd, (cudaStream_t)stream);
+    return e == cudaSuccess ? MEHDG_OK : MEHDG_ECUDA;
+}
+
+extern "C" size_t mehdg_test_trailing_work_bytes(int64_t nK, int64_t ld) {
+    return perm_bytes(nK) + gemm_tc_work_bytes(nK, ld, 1);
+}

@@ -145,28 +145,45 @@ panel_kernel(TS* __restrict__ Sall, int64_t ld, int c, int32_t* __restrict__ piv
 // ---------------------------------------------------------------- row swaps
 // Net permutation of the swap sequence piv[c0 .. c0+w): list of (dst, src)
 // rows such that new[dst] = old[src].  One thread per element.
-__global__ void perm_build_kernel(const int32_t* __restrict__ pivall, int64_t ld, int c0, int w,
-                                  int32_t* __restrict__ perm /*[nK][1 + 4w]*/, int nK) {
-    int K = blockIdx.x * blockDim.x + threadIdx.x;
+// One warp per element: rows/cont live in shared memory, the search for a
+// row below the block is done by the 32 lanes at once.
+__global__ void __launch_bounds__(128)
+perm_build_kernel(const int32_t* __restrict__ pivall, int64_t ld, int c0, int w,
+                  int32_t* __restrict__ perm /*[nK][1 + 4w]*/, int nK) {
+    extern __shared__ int32_t sp[];               // per warp: rows[2w], cont[2w]
+    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int K = blockIdx.x * 4 + wl;
     if (K >= nK) return;
     const int32_t* piv = pivall + (size_t)K * ld;
-    int32_t* out = perm + (size_t)K * (1 + 4 * w);
-    int32_t* rows = out + 1;          // [2w] rows touched
-    int32_t* cont = rows + 2 * w;     // [2w] source row now sitting in rows[i]
+    int32_t* rows = sp + wl * 4 * w;
+    int32_t* cont = rows + 2 * w;
+    for (int i = lane; i < w; i += 32) { rows[i] = c0 + i; cont[i] = c0 + i; }
+    __syncwarp();
     int nr = w;
-    for (int i = 0; i < w; ++i) { rows[i] = c0 + i; cont[i] = c0 + i; }
     for (int i = 0; i < w; ++i) {
-        int b = piv[c0 + i];
+        const int b = piv[c0 + i];
         if (b == c0 + i) continue;
-        int sb = -1;
+        int sb;
         if (b < c0 + w) sb = b - c0;
         else {
-            for (int j = w; j < nr; ++j) if (rows[j] == b) { sb = j; break; }
-            if (sb < 0) { sb = nr++; rows[sb] = b; cont[sb] = b; }
+            sb = -1;
+            for (int j0 = w; j0 < nr && sb < 0; j0 += 32) {
+                int j = j0 + lane;
+                unsigned hit = __ballot_sync(0xffffffffu, j < nr && rows[j] == b);
+                if (hit) sb = j0 + __ffs(hit) - 1;
+            }
+            if (sb < 0) {
+                sb = nr++;
+                if (lane == 0) { rows[sb] = b; cont[sb] = b; }
+            }
         }
-        int t = cont[i]; cont[i] = cont[sb]; cont[sb] = t;
+        __syncwarp();
+        if (lane == 0) { int t = cont[i]; cont[i] = cont[sb]; cont[sb] = t; }
+        __syncwarp();
     }
-    out[0] = nr;
+    int32_t* out = perm + (size_t)K * (1 + 4 * w);
+    for (int i = lane; i < nr; i += 32) { out[1 + i] = rows[i]; out[1 + 2 * w + i] = cont[i]; }
+    if (lane == 0) out[0] = nr;
 }
 
 template <class TS>
@@ -379,7 +396,8 @@ template <class TS>
 cudaError_t launch_laswp(const LUPlan& P, int c0, int w, int j0, int j1, cudaStream_t st) {
     if (j1 <= j0) return cudaSuccess;
     int32_t* perm = reinterpret_cast<int32_t*>(P.work);
-    perm_build_kernel<<<(unsigned)((P.nK + 63) / 64), 64, 0, st>>>(P.piv, P.ld, c0, w, perm, (int)P.nK);
+    perm_build_kernel<<<(unsigned)((P.nK + 3) / 4), 128, 4 * 4 * w * sizeof(int32_t), st>>>(P.piv, P.ld, c0, w,
+                                                                                           perm, (int)P.nK);
     size_t sm = (size_t)2 * w * 16 * sizeof(TS);
     cudaFuncSetAttribute(laswp_kernel<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     dim3 g((unsigned)((j1 - j0 + 15) / 16), (unsigned)P.nK);

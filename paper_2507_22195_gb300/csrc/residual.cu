@@ -1,16 +1,15 @@
 // residual.cu -- FP64 residual of eq. s32 (with the stage term of eq. C242)
 // for every macro-element, and its forward-mode tangent.
 //
-// One CTA per macro-element.  The CTA walks the m^3 micro-elements and the
-// 6 m^2 micro-faces in turn; per micro-element it stages the local nodal
-// state in shared memory, evaluates the state and the point physics at the
-// (p+2)^3 Gauss points (one thread per point), stores the weighted
-// integrands in shared memory and then tests them against the local basis
-// (one thread per local node and component), accumulating straight into the
-// element's rows of R_V / R_Q in HBM (the CTA owns them, so the sums are
-// deterministic).  The face pass does the same with the two-point fluxes and
-// also writes the element's side of the trace residual; a second kernel sums
-// the two sides of every global face (eq. s32c).
+// Volume pass: one CTA per (micro-element, macro-element).  The CTA stages
+// the local nodal state in shared memory, evaluates the state and the point
+// physics at the (p+2)^3 Gauss points (one thread per point), stores the
+// weighted integrands in shared memory, tests them against the local basis
+// (one thread per local node and component) and adds the result into the
+// element's rows of R_V / R_Q with FP64 atomics (micro-elements share nodes).
+// Face pass: one CTA per (micro-face, macro-element) with the two-point
+// fluxes; it adds into R_V and into the element's side of the trace residual.
+// A third kernel sums the two sides of every global face (eq. s32c).
 //
 // With T = Dual<1> the same code returns R and dR[dv, dvh, dq], the
 // directional derivative used by the refinement residual r - S x, the
@@ -30,32 +29,35 @@ __device__ __forceinline__ double tan0(const Dual<1>& x) { return x.d[0]; }
 
 template <class T>
 __device__ __forceinline__ void acc_out(double* out, double* tout, int64_t i, const T& x) {
-    if (out) out[i] += val(x);
-    if (tout) tout[i] += tan0(x);
+    if (out) atomicAdd(out + i, val(x));
+    if (tout) atomicAdd(tout + i, tan0(x));
 }
 
-struct Geo {
-    double sc[3];      // 2/h per direction
-    double hw[3];      // h/2 per direction
-};
+__device__ __forceinline__ void load_tables(const Tab& tb, double* sL, double* sD, double* sW) {
+    const int p1 = tb.p + 1;
+    for (int i = threadIdx.x; i < tb.ng * p1; i += blockDim.x) {
+        sL[i] = tb.L[i / p1][i % p1];
+        sD[i] = tb.dL[i / p1][i % p1];
+    }
+    if (threadIdx.x < tb.ng) sW[threadIdx.x] = tb.w[threadIdx.x];
+}
 
 }  // namespace
 
 template <class T, bool VISC>
-__global__ void __launch_bounds__(256)
-residual_kernel(ResidualArgs a) {
+__global__ void __launch_bounds__(128)
+residual_volume_kernel(ResidualArgs a) {
     const Tab& tb = a.tab;
-    const int K = blockIdx.x;
+    const int K = blockIdx.y, e = blockIdx.x;
     if (a.skip && a.skip[K]) return;
-    const int p = tb.p, m = tb.m, n = tb.n, ng = tb.ng, Nn = tb.Nn, n2 = tb.n2;
-    const int nl = tb.nl, npt = tb.npt;
-    const int p1 = p + 1;
+    const int p = tb.p, m = tb.m, n = tb.n, ng = tb.ng, Nn = tb.Nn;
+    const int nl = tb.nl, npt = tb.npt, p1 = p + 1;
+    const int e1 = e % m, e2 = (e / m) % m, e3 = e / (m * m);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* sL = reinterpret_cast<double*>(smem_raw);         // [ng][p1]
     double* sD = sL + MEHDG_MAXG * (MEHDG_MAXP + 1);          // [ng][p1]
     double* sW = sD + MEHDG_MAXG * (MEHDG_MAXP + 1);          // [ng]
     T* base = reinterpret_cast<T*>(sW + 8);
-    // volume layout
     T* vl = base;                 // [5][nl]
     T* vsl = vl + 5 * nl;         // [5][nl]
     T* ql = vsl + 5 * nl;         // [15][nl]
@@ -64,179 +66,163 @@ residual_kernel(ResidualArgs a) {
     T* pq = pf + 15 * npt;        // [15][npt]
     T* pv = pq + (VISC ? 15 * npt : 0);  // [5][npt]
     const int tid = threadIdx.x, nth = blockDim.x;
-
-    for (int i = tid; i < ng * p1; i += nth) {
-        sL[i] = tb.L[i / p1][i % p1];
-        sD[i] = tb.dL[i / p1][i % p1];
-    }
-    if (tid < ng) sW[tid] = tb.w[tid];
-
-    Geo geo;
+    load_tables(tb, sL, sD, sW);
+    const Phys& ph = a.ph;
     const double* box = a.box + 6 * K;
-    for (int d = 0; d < 3; ++d) {
-        double h = (box[3 + d] - box[d]) / m;
-        geo.sc[d] = 2.0 / h; geo.hw[d] = 0.5 * h;
-    }
-    const int64_t oV = (int64_t)K * 5 * Nn, oQ = (int64_t)K * 15 * Nn, oH = (int64_t)K * 30 * n2;
-    // zero this element's outputs
-    for (int i = tid; i < 5 * Nn; i += nth) {
-        if (a.RV) a.RV[oV + i] = 0.0;
-        if (a.tRV) a.tRV[oV + i] = 0.0;
-    }
-    if (VISC) for (int i = tid; i < 15 * Nn; i += nth) {
-        if (a.RQ) a.RQ[oQ + i] = 0.0;
-        if (a.tRQ) a.tRQ[oQ + i] = 0.0;
-    }
-    for (int i = tid; i < 30 * n2; i += nth) {
-        if (a.RH) a.RH[oH + i] = 0.0;
-        if (a.tRH) a.tRH[oH + i] = 0.0;
+    double sc[3], hw[3];
+    for (int d = 0; d < 3; ++d) { double h = (box[3 + d] - box[d]) / m; sc[d] = 2.0 / h; hw[d] = 0.5 * h; }
+    const int64_t oV = (int64_t)K * 5 * Nn, oQ = (int64_t)K * 15 * Nn;
+
+    for (int i = tid; i < nl; i += nth) {
+        int l1 = i % p1, l2 = (i / p1) % p1, l3 = i / (p1 * p1);
+        int A = (e1 * p + l1) + n * ((e2 * p + l2) + n * (e3 * p + l3));
+        for (int k = 0; k < 5; ++k) {
+            vl[k * nl + i] = load_t<T>(a.v, a.dv, oV + k * Nn + A);
+            if (ph.time_term) vsl[k * nl + i] = load_t<T>(a.vs, nullptr, oV + k * Nn + A);
+        }
+        if (VISC)
+            for (int c = 0; c < 15; ++c) ql[c * nl + i] = load_t<T>(a.q, a.dq, oQ + c * Nn + A);
     }
     __syncthreads();
     bool ok = true;
-    const Phys& ph = a.ph;
-
-    // ------------------------------------------------------------ volume
-    for (int e = 0; e < m * m * m; ++e) {
-        const int e1 = e % m, e2 = (e / m) % m, e3 = e / (m * m);
-        for (int i = tid; i < nl; i += nth) {
+    for (int x = tid; x < npt; x += nth) {
+        int g1 = x % ng, g2 = (x / ng) % ng, g3 = x / (ng * ng);
+        T vx[5], vsx[5], qx[15];
+        for (int k = 0; k < 5; ++k) { vx[k] = cst<T>(0.0); vsx[k] = cst<T>(0.0); }
+        if (VISC) for (int c = 0; c < 15; ++c) qx[c] = cst<T>(0.0);
+        for (int i = 0; i < nl; ++i) {
             int l1 = i % p1, l2 = (i / p1) % p1, l3 = i / (p1 * p1);
-            int A = (e1 * p + l1) + n * ((e2 * p + l2) + n * (e3 * p + l3));
+            double f = sL[g1 * p1 + l1] * sL[g2 * p1 + l2] * sL[g3 * p1 + l3];
             for (int k = 0; k < 5; ++k) {
-                vl[k * nl + i] = load_t<T>(a.v, a.dv, oV + k * Nn + A);
-                if (ph.time_term) vsl[k * nl + i] = load_t<T>(a.vs, nullptr, oV + k * Nn + A);
+                vx[k] += vl[k * nl + i] * f;
+                if (ph.time_term) vsx[k] += vsl[k * nl + i] * f;
             }
-            if (VISC)
-                for (int c = 0; c < 15; ++c) ql[c * nl + i] = load_t<T>(a.q, a.dq, oQ + c * Nn + A);
+            if (VISC) for (int c = 0; c < 15; ++c) qx[c] += ql[c * nl + i] * f;
         }
-        __syncthreads();
-        for (int x = tid; x < npt; x += nth) {
-            int g1 = x % ng, g2 = (x / ng) % ng, g3 = x / (ng * ng);
-            T vx[5], vsx[5], qx[15];
-            for (int k = 0; k < 5; ++k) { vx[k] = cst<T>(0.0); vsx[k] = cst<T>(0.0); }
-            if (VISC) for (int c = 0; c < 15; ++c) qx[c] = cst<T>(0.0);
-            for (int i = 0; i < nl; ++i) {
-                int l1 = i % p1, l2 = (i / p1) % p1, l3 = i / (p1 * p1);
-                double ph_ = sL[g1 * p1 + l1] * sL[g2 * p1 + l2] * sL[g3 * p1 + l3];
-                for (int k = 0; k < 5; ++k) {
-                    vx[k] += vl[k * nl + i] * ph_;
-                    if (ph.time_term) vsx[k] += vsl[k * nl + i] * ph_;
-                }
-                if (VISC) for (int c = 0; c < 15; ++c) qx[c] += ql[c * nl + i] * ph_;
-            }
-            T U[5], FG[5][3];
-            ok = vol_integrand(ph, vx, vsx, qx, U, FG) && ok;
-            double W = sW[g1] * geo.hw[0] * sW[g2] * geo.hw[1] * sW[g3] * geo.hw[2];
-            for (int k = 0; k < 5; ++k) {
-                pu[k * npt + x] = U[k] * W;
-                for (int j = 0; j < 3; ++j) pf[(k * 3 + j) * npt + x] = FG[k][j] * W;
-            }
-            if (VISC) {
-                for (int c = 0; c < 15; ++c) pq[c * npt + x] = qx[c] * W;
-                for (int k = 0; k < 5; ++k) pv[k * npt + x] = vx[k] * W;
-            }
+        T U[5], FG[5][3];
+        ok = vol_integrand(ph, vx, vsx, qx, U, FG) && ok;
+        double W = sW[g1] * hw[0] * sW[g2] * hw[1] * sW[g3] * hw[2];
+        for (int k = 0; k < 5; ++k) {
+            pu[k * npt + x] = U[k] * W;
+            for (int j = 0; j < 3; ++j) pf[(k * 3 + j) * npt + x] = FG[k][j] * W;
         }
-        __syncthreads();
-        const int nrow = VISC ? nl * 20 : nl * 5;
-        for (int r = tid; r < nrow; r += nth) {
-            int i = r % nl, kk = r / nl;          // kk < 5: R_V row; else R_Q row (k,d) = kk-5
-            int l1 = i % p1, l2 = (i / p1) % p1, l3 = i / (p1 * p1);
-            int A = (e1 * p + l1) + n * ((e2 * p + l2) + n * (e3 * p + l3));
-            T s = cst<T>(0.0);
-            if (kk < 5) {
-                for (int x = 0; x < npt; ++x) {
-                    int g1 = x % ng, g2 = (x / ng) % ng, g3 = x / (ng * ng);
-                    double a1 = sL[g1 * p1 + l1], a2 = sL[g2 * p1 + l2], a3 = sL[g3 * p1 + l3];
-                    double d1 = sD[g1 * p1 + l1] * geo.sc[0], d2 = sD[g2 * p1 + l2] * geo.sc[1],
-                           d3 = sD[g3 * p1 + l3] * geo.sc[2];
-                    s += pu[kk * npt + x] * (a1 * a2 * a3);
-                    s -= pf[(kk * 3 + 0) * npt + x] * (d1 * a2 * a3);
-                    s -= pf[(kk * 3 + 1) * npt + x] * (a1 * d2 * a3);
-                    s -= pf[(kk * 3 + 2) * npt + x] * (a1 * a2 * d3);
-                }
-                acc_out(a.RV, a.tRV, oV + kk * Nn + A, s);
-            } else if (VISC) {
-                int c = kk - 5, k = c / 3, d = c % 3;
-                for (int x = 0; x < npt; ++x) {
-                    int g1 = x % ng, g2 = (x / ng) % ng, g3 = x / (ng * ng);
-                    double a1 = sL[g1 * p1 + l1], a2 = sL[g2 * p1 + l2], a3 = sL[g3 * p1 + l3];
-                    double dd = d == 0 ? sD[g1 * p1 + l1] * geo.sc[0] * a2 * a3
-                              : d == 1 ? a1 * sD[g2 * p1 + l2] * geo.sc[1] * a3
-                                       : a1 * a2 * sD[g3 * p1 + l3] * geo.sc[2];
-                    s += pq[c * npt + x] * (a1 * a2 * a3) + pv[k * npt + x] * dd;
-                }
-                acc_out(a.RQ, a.tRQ, oQ + c * Nn + A, s);
-            }
-        }
-        __syncthreads();
-    }
-
-    // ------------------------------------------------------------ faces
-    const int fl = p1 * p1, fpt = ng * ng;
-    T* fv = base;                  // [5][fl]
-    T* fh = fv + 5 * fl;           // [5][fl]
-    T* fq = fh + 5 * fl;           // [15][fl]
-    T* pF = fq + (VISC ? 15 * fl : 0);    // [5][fpt]
-    T* pH = pF + 5 * fpt;          // [5][fpt]  W vh (for R_Q)
-    for (int f = 0; f < 6; ++f) {
-        const int d = f / 2;
-        const double sgn = (f & 1) ? 1.0 : -1.0;
-        const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
-        const int64_t og = a.gid[6 * K + f] * 5 * n2;
-        for (int e = 0; e < m * m; ++e) {
-            const int e1 = e % m, e2 = e / m;
-            for (int i = tid; i < fl; i += nth) {
-                int l1 = i % p1, l2 = i / p1;
-                int c1 = e1 * p + l1, c2 = e2 * p + l2;
-                int idx[3]; idx[d] = (f & 1) ? n - 1 : 0; idx[t1] = c1; idx[t2] = c2;
-                int A = idx[0] + n * (idx[1] + n * idx[2]);
-                int c = c1 + n * c2;
-                for (int k = 0; k < 5; ++k) {
-                    fv[k * fl + i] = load_t<T>(a.v, a.dv, oV + k * Nn + A);
-                    fh[k * fl + i] = load_t<T>(a.vh, a.dvh, og + k * n2 + c);
-                }
-                if (VISC)
-                    for (int cc = 0; cc < 15; ++cc) fq[cc * fl + i] = load_t<T>(a.q, a.dq, oQ + cc * Nn + A);
-            }
-            __syncthreads();
-            for (int x = tid; x < fpt; x += nth) {
-                int g1 = x % ng, g2 = x / ng;
-                T vx[5], hx[5], qx[15];
-                for (int k = 0; k < 5; ++k) { vx[k] = cst<T>(0.0); hx[k] = cst<T>(0.0); }
-                if (VISC) for (int cc = 0; cc < 15; ++cc) qx[cc] = cst<T>(0.0);
-                for (int i = 0; i < fl; ++i) {
-                    double mu = sL[g1 * p1 + (i % p1)] * sL[g2 * p1 + (i / p1)];
-                    for (int k = 0; k < 5; ++k) { vx[k] += fv[k * fl + i] * mu; hx[k] += fh[k * fl + i] * mu; }
-                    if (VISC) for (int cc = 0; cc < 15; ++cc) qx[cc] += fq[cc * fl + i] * mu;
-                }
-                T Fh[5];
-                ok = face_integrand(ph, vx, hx, qx, d, sgn, Fh) && ok;
-                double W = sW[g1] * geo.hw[t1] * sW[g2] * geo.hw[t2];
-                for (int k = 0; k < 5; ++k) {
-                    pF[k * fpt + x] = Fh[k] * W;
-                    if (VISC) pH[k * fpt + x] = hx[k] * (W * sgn);
-                }
-            }
-            __syncthreads();
-            for (int r = tid; r < fl * 5; r += nth) {
-                int i = r % fl, k = r / fl;
-                int l1 = i % p1, l2 = i / p1;
-                int c1 = e1 * p + l1, c2 = e2 * p + l2;
-                int idx[3]; idx[d] = (f & 1) ? n - 1 : 0; idx[t1] = c1; idx[t2] = c2;
-                int A = idx[0] + n * (idx[1] + n * idx[2]);
-                T s = cst<T>(0.0), sq = cst<T>(0.0);
-                for (int x = 0; x < fpt; ++x) {
-                    double mu = sL[(x % ng) * p1 + l1] * sL[(x / ng) * p1 + l2];
-                    s += pF[k * fpt + x] * mu;
-                    if (VISC) sq += pH[k * fpt + x] * mu;
-                }
-                acc_out(a.RV, a.tRV, oV + k * Nn + A, s);
-                acc_out(a.RH, a.tRH, oH + (f * 5 + k) * n2 + c1 + n * c2, s);
-                if (VISC) acc_out(a.RQ, a.tRQ, oQ + (k * 3 + d) * Nn + A, -sq);
-            }
-            __syncthreads();
+        if (VISC) {
+            for (int c = 0; c < 15; ++c) pq[c * npt + x] = qx[c] * W;
+            for (int k = 0; k < 5; ++k) pv[k * npt + x] = vx[k] * W;
         }
     }
     if (!ok && a.status) a.status[K] = MEHDG_ENONPHYS;
+    __syncthreads();
+    const int nrow = VISC ? nl * 20 : nl * 5;
+    for (int r = tid; r < nrow; r += nth) {
+        int i = r % nl, kk = r / nl;          // kk < 5: R_V row; else R_Q row (k,d) = kk-5
+        int l1 = i % p1, l2 = (i / p1) % p1, l3 = i / (p1 * p1);
+        int A = (e1 * p + l1) + n * ((e2 * p + l2) + n * (e3 * p + l3));
+        T s = cst<T>(0.0);
+        if (kk < 5) {
+            for (int x = 0; x < npt; ++x) {
+                int g1 = x % ng, g2 = (x / ng) % ng, g3 = x / (ng * ng);
+                double a1 = sL[g1 * p1 + l1], a2 = sL[g2 * p1 + l2], a3 = sL[g3 * p1 + l3];
+                double d1 = sD[g1 * p1 + l1] * sc[0], d2 = sD[g2 * p1 + l2] * sc[1], d3 = sD[g3 * p1 + l3] * sc[2];
+                s += pu[kk * npt + x] * (a1 * a2 * a3);
+                s -= pf[(kk * 3 + 0) * npt + x] * (d1 * a2 * a3);
+                s -= pf[(kk * 3 + 1) * npt + x] * (a1 * d2 * a3);
+                s -= pf[(kk * 3 + 2) * npt + x] * (a1 * a2 * d3);
+            }
+            acc_out(a.RV, a.tRV, oV + kk * Nn + A, s);
+        } else if (VISC) {
+            int c = kk - 5, k = c / 3, d = c % 3;
+            for (int x = 0; x < npt; ++x) {
+                int g1 = x % ng, g2 = (x / ng) % ng, g3 = x / (ng * ng);
+                double a1 = sL[g1 * p1 + l1], a2 = sL[g2 * p1 + l2], a3 = sL[g3 * p1 + l3];
+                double dd = d == 0 ? sD[g1 * p1 + l1] * sc[0] * a2 * a3
+                          : d == 1 ? a1 * sD[g2 * p1 + l2] * sc[1] * a3
+                                   : a1 * a2 * sD[g3 * p1 + l3] * sc[2];
+                s += pq[c * npt + x] * (a1 * a2 * a3) + pv[k * npt + x] * dd;
+            }
+            acc_out(a.RQ, a.tRQ, oQ + c * Nn + A, s);
+        }
+    }
+}
+
+template <class T, bool VISC>
+__global__ void __launch_bounds__(128)
+residual_face_kernel(ResidualArgs a) {
+    const Tab& tb = a.tab;
+    const int K = blockIdx.y;
+    if (a.skip && a.skip[K]) return;
+    const int p = tb.p, m = tb.m, n = tb.n, ng = tb.ng, Nn = tb.Nn, n2 = tb.n2, p1 = p + 1;
+    const int f = blockIdx.x / (m * m), e = blockIdx.x % (m * m);
+    const int e1 = e % m, e2 = e / m;
+    const int d = f / 2;
+    const double sgn = (f & 1) ? 1.0 : -1.0;
+    const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+    const int fl = p1 * p1, fpt = ng * ng;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* sL = reinterpret_cast<double*>(smem_raw);
+    double* sD = sL + MEHDG_MAXG * (MEHDG_MAXP + 1);
+    double* sW = sD + MEHDG_MAXG * (MEHDG_MAXP + 1);
+    T* fv = reinterpret_cast<T*>(sW + 8);   // [5][fl]
+    T* fh = fv + 5 * fl;           // [5][fl]
+    T* fq = fh + 5 * fl;           // [15][fl]
+    T* pF = fq + (VISC ? 15 * fl : 0);    // [5][fpt]
+    T* pH = pF + 5 * fpt;          // [5][fpt]  W n_d vh (for R_Q)
+    const int tid = threadIdx.x, nth = blockDim.x;
+    load_tables(tb, sL, sD, sW);
+    const Phys& ph = a.ph;
+    const double* box = a.box + 6 * K;
+    const double hw1 = 0.5 * (box[3 + t1] - box[t1]) / m, hw2 = 0.5 * (box[3 + t2] - box[t2]) / m;
+    const int64_t oV = (int64_t)K * 5 * Nn, oQ = (int64_t)K * 15 * Nn, oH = (int64_t)K * 30 * n2;
+    const int64_t og = a.gid[6 * K + f] * 5 * n2;
+    for (int i = tid; i < fl; i += nth) {
+        int c1 = e1 * p + i % p1, c2 = e2 * p + i / p1;
+        int idx[3]; idx[d] = (f & 1) ? n - 1 : 0; idx[t1] = c1; idx[t2] = c2;
+        int A = idx[0] + n * (idx[1] + n * idx[2]);
+        for (int k = 0; k < 5; ++k) {
+            fv[k * fl + i] = load_t<T>(a.v, a.dv, oV + k * Nn + A);
+            fh[k * fl + i] = load_t<T>(a.vh, a.dvh, og + k * n2 + c1 + n * c2);
+        }
+        if (VISC)
+            for (int cc = 0; cc < 15; ++cc) fq[cc * fl + i] = load_t<T>(a.q, a.dq, oQ + cc * Nn + A);
+    }
+    __syncthreads();
+    bool ok = true;
+    for (int x = tid; x < fpt; x += nth) {
+        int g1 = x % ng, g2 = x / ng;
+        T vx[5], hx[5], qx[15];
+        for (int k = 0; k < 5; ++k) { vx[k] = cst<T>(0.0); hx[k] = cst<T>(0.0); }
+        if (VISC) for (int cc = 0; cc < 15; ++cc) qx[cc] = cst<T>(0.0);
+        for (int i = 0; i < fl; ++i) {
+            double mu = sL[g1 * p1 + (i % p1)] * sL[g2 * p1 + (i / p1)];
+            for (int k = 0; k < 5; ++k) { vx[k] += fv[k * fl + i] * mu; hx[k] += fh[k * fl + i] * mu; }
+            if (VISC) for (int cc = 0; cc < 15; ++cc) qx[cc] += fq[cc * fl + i] * mu;
+        }
+        T Fh[5];
+        ok = face_integrand(ph, vx, hx, qx, d, sgn, Fh) && ok;
+        double W = sW[g1] * hw1 * sW[g2] * hw2;
+        for (int k = 0; k < 5; ++k) {
+            pF[k * fpt + x] = Fh[k] * W;
+            if (VISC) pH[k * fpt + x] = hx[k] * (W * sgn);
+        }
+    }
+    if (!ok && a.status) a.status[K] = MEHDG_ENONPHYS;
+    __syncthreads();
+    for (int r = tid; r < fl * 5; r += nth) {
+        int i = r % fl, k = r / fl;
+        int l1 = i % p1, l2 = i / p1;
+        int c1 = e1 * p + l1, c2 = e2 * p + l2;
+        int idx[3]; idx[d] = (f & 1) ? n - 1 : 0; idx[t1] = c1; idx[t2] = c2;
+        int A = idx[0] + n * (idx[1] + n * idx[2]);
+        T s = cst<T>(0.0), sq = cst<T>(0.0);
+        for (int x = 0; x < fpt; ++x) {
+            double mu = sL[(x % ng) * p1 + l1] * sL[(x / ng) * p1 + l2];
+            s += pF[k * fpt + x] * mu;
+            if (VISC) sq += pH[k * fpt + x] * mu;
+        }
+        acc_out(a.RV, a.tRV, oV + k * Nn + A, s);
+        acc_out(a.RH, a.tRH, oH + (f * 5 + k) * n2 + c1 + n * c2, s);
+        if (VISC) acc_out(a.RQ, a.tRQ, oQ + (k * 3 + d) * Nn + A, -sq);
+    }
 }
 
 // sum the (one or two) element sides of every global face
@@ -257,25 +243,59 @@ __global__ void trace_gather_kernel(const double* __restrict__ loc, const int64_
     out[i] = o;
 }
 
-size_t residual_smem_bytes(const Tab& t, bool visc, bool tangent) {
-    size_t ts = tangent ? sizeof(Dual<1>) : sizeof(double);
-    size_t head = sizeof(double) * (2 * MEHDG_MAXG * (MEHDG_MAXP + 1) + 8);
-    size_t vol = (size_t)(10 + (visc ? 15 : 0)) * t.nl + (size_t)(20 + (visc ? 20 : 0)) * t.npt;
-    int fl = (t.p + 1) * (t.p + 1), fpt = t.ng * t.ng;
-    size_t fac = (size_t)(10 + (visc ? 15 : 0)) * fl + 10 * (size_t)fpt;
-    return head + ts * (vol > fac ? vol : fac);
+// zero the outputs of the elements that are not skipped
+__global__ void zero_outputs_kernel(double* a, double* b, int64_t per, const int32_t* skip) {
+    const int K = blockIdx.y;
+    if (skip && skip[K]) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < per; i += (int64_t)gridDim.x * blockDim.x) {
+        if (a) a[(size_t)K * per + i] = 0.0;
+        if (b) b[(size_t)K * per + i] = 0.0;
+    }
 }
 
+namespace {
+
+size_t head_bytes() { return sizeof(double) * (2 * MEHDG_MAXG * (MEHDG_MAXP + 1) + 8); }
+
+size_t volume_smem_bytes(const Tab& t, bool visc, size_t ts) {
+    size_t n = (size_t)(10 + (visc ? 15 : 0)) * t.nl + (size_t)(20 + (visc ? 20 : 0)) * t.npt;
+    return head_bytes() + ts * n;
+}
+
+size_t face_smem_bytes(const Tab& t, bool visc, size_t ts) {
+    int fl = (t.p + 1) * (t.p + 1), fpt = t.ng * t.ng;
+    size_t n = (size_t)(10 + (visc ? 15 : 0)) * fl + 10 * (size_t)fpt;
+    return head_bytes() + ts * n;
+}
+
+cudaError_t zero(double* a, double* b, int64_t per, int64_t nK, const int32_t* skip, cudaStream_t st) {
+    if (!a && !b) return cudaSuccess;
+    dim3 g((unsigned)((per + 255) / 256 < 64 ? (per + 255) / 256 : 64), (unsigned)nK);
+    zero_outputs_kernel<<<g, 256, 0, st>>>(a, b, per, skip);
+    MEHDG_COUNT(1);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
 cudaError_t launch_residual(const ResidualArgs& a, int64_t nK, bool visc, bool tangent, cudaStream_t st) {
-    size_t sm = residual_smem_bytes(a.tab, visc, tangent);
-    dim3 grid((unsigned)nK), block(256);
-#define LAUNCH_RES(T, V)                                                                      \
-    do { cudaFuncSetAttribute(residual_kernel<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
-         residual_kernel<T, V><<<grid, block, sm, st>>>(a); } while (0)
+    const Tab& t = a.tab;
+    cudaError_t e;
+    if ((e = zero(a.RV, a.tRV, 5LL * t.Nn, nK, a.skip, st)) != cudaSuccess) return e;
+    if (visc && (e = zero(a.RQ, a.tRQ, 15LL * t.Nn, nK, a.skip, st)) != cudaSuccess) return e;
+    if ((e = zero(a.RH, a.tRH, 30LL * t.n2, nK, a.skip, st)) != cudaSuccess) return e;
+    size_t ts = tangent ? sizeof(Dual<1>) : sizeof(double);
+    size_t sv = volume_smem_bytes(t, visc, ts), sf = face_smem_bytes(t, visc, ts);
+    dim3 gv((unsigned)(t.m * t.m * t.m), (unsigned)nK), gf((unsigned)(6 * t.m * t.m), (unsigned)nK), b(128);
+#define LAUNCH_RES(T, V)                                                                                 \
+    do { cudaFuncSetAttribute(residual_volume_kernel<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sv); \
+         cudaFuncSetAttribute(residual_face_kernel<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf);   \
+         residual_volume_kernel<T, V><<<gv, b, sv, st>>>(a);                                             \
+         residual_face_kernel<T, V><<<gf, b, sf, st>>>(a); } while (0)
     if (tangent) { if (visc) LAUNCH_RES(Dual<1>, true); else LAUNCH_RES(Dual<1>, false); }
     else { if (visc) LAUNCH_RES(double, true); else LAUNCH_RES(double, false); }
 #undef LAUNCH_RES
-    MEHDG_COUNT(1);
+    MEHDG_COUNT(2);
     return cudaGetLastError();
 }
 

@@ -25,7 +25,8 @@ PHASES = ["residual", "jacobian", "lu_panels", "lu_trailing_update", "solve", "t
 EXPORTED = ["mehdg_default_params", "mehdg_create", "mehdg_set_mesh", "mehdg_set_state",
             "mehdg_residual", "mehdg_condense", "mehdg_apply_condensed", "mehdg_recover",
             "mehdg_status", "mehdg_last_error", "mehdg_destroy", "mehdg_profile_enable",
-            "mehdg_profile_read", "mehdg_launch_count"]
+            "mehdg_profile_read", "mehdg_launch_count", "mehdg_test_trailing_update",
+            "mehdg_test_trailing_work_bytes"]
 
 
 class mehdg_params(C.Structure):
@@ -69,6 +70,10 @@ def load(path: str | None = None):
     L.mehdg_profile_read.argtypes = [_vp, _vp, _vp, _vp, C.c_int]
     L.mehdg_launch_count.argtypes = []
     L.mehdg_launch_count.restype = C.c_int64
+    L.mehdg_test_trailing_update.argtypes = [C.c_int64, C.c_int64, _vp, C.c_int, C.c_int, C.c_int, C.c_int,
+                                             C.c_int, C.c_int, C.c_int, _vp, _vp]
+    L.mehdg_test_trailing_work_bytes.argtypes = [C.c_int64, C.c_int64]
+    L.mehdg_test_trailing_work_bytes.restype = C.c_size_t
     _lib = L
     return L
 
@@ -166,6 +171,20 @@ def mehdg_profile_read(ctx):
     _check(ctx, load().mehdg_profile_read(ctx, ms.ctypes.data, cnt.ctypes.data, fl.ctypes.data, n),
            "mehdg_profile_read")
     return {PHASES[i]: dict(ms=float(ms[i]), launches=int(cnt[i]), flops=float(fl[i])) for i in range(n)}
+
+
+def mehdg_test_trailing_update(S, r0, c0, k0, M, N, Kd, prec, work=None, stream=None):
+    """S: torch float32 CUDA tensor [nK][ld][ld] holding column-major matrices
+    (element [K][j][i] is row i, column j)."""
+    import torch
+    assert S.is_cuda and S.dtype == torch.float32 and S.is_contiguous()
+    nK, ld = S.shape[0], S.shape[1]
+    if work is None:
+        nb = load().mehdg_test_trailing_work_bytes(nK, ld)
+        work = torch.empty(nb, dtype=torch.uint8, device=S.device)
+    _check(None, load().mehdg_test_trailing_update(nK, ld, S.data_ptr(), r0, c0, k0, M, N, Kd, prec,
+                                                   work.data_ptr(), _stream(stream)),
+           "mehdg_test_trailing_update")
 
 
 def mehdg_launch_count() -> int:
