@@ -148,6 +148,29 @@ def reference_main(a):
 
 
 # ---------------------------------------------------------------- GPU arm
+def once_main(a):
+    """Workload setup, `warmup` condenses and one more, nothing timed: the
+    command the ncu summaries under profiles/ are taken with."""
+    import numpy as np
+    import torch
+    from paper_2507_22195_gb300 import inputs as I
+    from paper_2507_22195_gb300 import mehdg as M
+    mesh = I.periodic_mesh(a.nk, 3, 3)
+    st = I.make_state(mesh, "tgv", 1e-3, 22197, 22198, M0=0.1)
+    dev = torch.device("cuda:0")
+    v, vh, vs = (torch.tensor(x, device=dev) for x in (st.v, st.vhat, st.vstar))
+    ctx = M.Context(mesh, flux=M.MEHDG_FLUX_KEPES, prec=PREC[a.prec], Mach=0.1)
+    ctx.set_state(v, vh, None, vs)
+    for _ in range(a.warmup + 1):
+        ctx.condense()
+    torch.cuda.synchronize()
+    stat, iters = ctx.status()
+    print(json.dumps({"once": True, "nK": mesh.nK, "prec": a.prec, "status_ok": bool((stat == 0).all()),
+                      "refine_iters": sorted(set(int(x) for x in iters)), "launches": M.mehdg_launch_count()}))
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -159,9 +182,12 @@ def main():
     ap.add_argument("--fp64-sample", type=int, default=2, help="nk of the FP64 comparison mesh (nk^3 elements)")
     ap.add_argument("--cpu-sample", type=int, default=-1, help="elements for the CPU oracle baseline (-1: one per core)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--once", action="store_true", help="one condense after --warmup ones, no timing (for profilers)")
     a = ap.parse_args()
     if a.impl == "reference":
         return reference_main(a)
+    if a.once:
+        return once_main(a)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -102,7 +102,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-template <int BN, bool BF16>
+// STORE = false: C -= A B^T (trailing update); STORE = true: C = A B^T
+// (triangular solve through the inverse of the diagonal block).
+template <int BN, bool BF16, bool STORE>
 __global__ void __launch_bounds__(128)
 tc_update_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                  float* __restrict__ Sall, int64_t ld, int r0, int c0, int M, int N, int nchunk, int tiles_m,
@@ -170,7 +172,9 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
     const bool rok = row < M;
     float* Crow = S + (size_t)(r0 + row) + (size_t)c0 * ld;
     float cv[32], cn[32];
-    {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) { cv[j] = 0.f; cn[j] = 0.f; }
+    if (!STORE) {
         const int col0 = tn * BN;
         if (rok && col0 < N) {
 #pragma unroll
@@ -184,7 +188,7 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
         for (int cc = 0; cc < BN; cc += 32) {
             const int col0 = tn * BN + cc;
             const bool has_next = cc + 32 < BN && col0 + 32 < N;
-            if (rok && has_next) {
+            if (!STORE && rok && has_next) {
 #pragma unroll
                 for (int j = 0; j < 32; ++j) cn[j] = __ldcs(Crow + (size_t)(col0 + 32 + j) * ld);
             }
@@ -192,7 +196,8 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc, r);
             if (rok && col0 < N) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) __stcs(Crow + (size_t)(col0 + j) * ld, cv[j] - __uint_as_float(r[j]));
+                for (int j = 0; j < 32; ++j)
+                    __stcs(Crow + (size_t)(col0 + j) * ld, STORE ? __uint_as_float(r[j]) : cv[j] - __uint_as_float(r[j]));
             }
 #pragma unroll
             for (int j = 0; j < 32; ++j) cv[j] = cn[j];
@@ -288,19 +293,93 @@ size_t perm_bytes(int64_t nK) {
     return (b + 255) & ~(size_t)255;
 }
 
-template <int BN, bool BF16>
+template <int BN, bool BF16, bool STORE = false>
 cudaError_t launch_tc(const CUtensorMap& a, const CUtensorMap& b, const LUPlan& P, int r0, int c0, int M, int N,
                       int nchunk, cudaStream_t st) {
     const int tiles_m = (M + TM - 1) / TM, tiles_n = (N + BN - 1) / BN;
     const size_t sm = STAGES * (size_t)(TM + BN) * CHUNK_BYTES + 1024;
-    cudaFuncSetAttribute(tc_update_kernel<BN, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(tc_update_kernel<BN, BF16, STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     dim3 g((unsigned)(tiles_m * tiles_n), (unsigned)P.nK);
-    tc_update_kernel<BN, BF16><<<g, 128, sm, st>>>(a, b, (float*)P.S, P.ld, r0, c0, M, N, nchunk, tiles_m, P.status);
+    tc_update_kernel<BN, BF16, STORE><<<g, 128, sm, st>>>(a, b, (float*)P.S, P.ld, r0, c0, M, N, nchunk, tiles_m,
+                                                          P.status);
     MEHDG_COUNT(1);
     return cudaGetLastError();
 }
 
+// Inverse X = L^-1 of the unit-lower 256 x 256 diagonal block L of every
+// element, written as the K-major operand panel Ap[K][m][k] = X[m][k] (TF32
+// rounded or BF16).  One CTA per (32-column block of X, element): the block
+// column of L X = I is solved by column-oriented forward substitution, 32
+// columns x 8 row groups, with the columns of L staged in shared memory.
+template <bool BF16>
+__global__ void __launch_bounds__(256)
+trtri256_kernel(const float* __restrict__ Sall, int64_t ld, int c0, void* __restrict__ Ap) {
+    constexpr int T = 256;
+    const int K = blockIdx.y, b = blockIdx.x;
+    const float* S = Sall + (size_t)K * ld * ld;
+    __shared__ float X[T][33];
+    __shared__ float Lc[T];
+    const int tc = threadIdx.x & 31, tr = threadIdx.x >> 5;
+    const int col = 32 * b + tc;
+    for (int i = tr; i < T; i += 8) X[i][tc] = (i == col) ? 1.f : 0.f;
+    __syncthreads();
+    for (int t = 32 * b; t < T - 1; ++t) {
+        for (int i = t + 1 + threadIdx.x; i < T; i += 256) Lc[i] = S[(size_t)(c0 + i) + (size_t)(c0 + t) * ld];
+        __syncthreads();
+        const float xt = X[t][tc];
+        for (int i = t + 1 + tr; i < T; i += 8) X[i][tc] -= Lc[i] * xt;
+        __syncthreads();
+    }
+    for (int m = tr; m < T; m += 8) {
+        const size_t o = ((size_t)K * T + m) * T + 32 * b + tc;
+        const float x = X[m][tc];
+        if constexpr (BF16) reinterpret_cast<__nv_bfloat16*>(Ap)[o] = __float2bfloat16_rn(x);
+        else {
+            uint32_t y;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
+            reinterpret_cast<uint32_t*>(Ap)[o] = y;
+        }
+    }
+}
+
 }  // namespace
+
+// Rows [c0, c0+256) of the columns [j0, j1): U12 = L11^-1 A12 on the tensor
+// cores, through the explicit inverse of the unit-lower block L11.
+cudaError_t gemm_tc_trsm256(const LUPlan& P, int c0, int j0, int j1, cudaStream_t st) {
+    const int N = j1 - j0, Kd = LU_NB;
+    if (N <= 0) return cudaSuccess;
+    if (!encoder()) return cudaErrorNotSupported;
+    // TF32 in both mixed modes: the inverse of L11 amplifies operand rounding,
+    // and BF16 here leaves the factors too inexact for the FP64 refinement
+    const bool bf16 = false;
+    const int es = bf16 ? 2 : 4;
+    const int chunk_k = CHUNK_BYTES / es;
+    const int nchunk = Kd / chunk_k;
+    unsigned char* w = reinterpret_cast<unsigned char*>(P.work) + perm_bytes(P.nK);
+    size_t pan = ((size_t)P.nK * P.ld * LU_NB * 4 + 255) & ~(size_t)255;
+    void* Ap = w;
+    void* Bp = w + pan;
+    {
+        dim3 gt(LU_NB / 32, (unsigned)P.nK);
+        if (bf16) trtri256_kernel<true><<<gt, 256, 0, st>>>((const float*)P.S, P.ld, c0, Ap);
+        else trtri256_kernel<false><<<gt, 256, 0, st>>>((const float*)P.S, P.ld, c0, Ap);
+    }
+    dim3 gb((unsigned)((N + 7) / 8), 1, (unsigned)P.nK);
+    if (bf16) pack_B_kernel<true><<<gb, 256, 0, st>>>((const float*)P.S, P.ld, c0, j0, N, Kd, Kd, Bp);
+    else pack_B_kernel<false><<<gb, 256, 0, st>>>((const float*)P.S, P.ld, c0, j0, N, Kd, Kd, Bp);
+    MEHDG_COUNT(2);
+    const int BN = N >= 128 ? 128 : (N >= 64 ? 64 : 32);
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, Ap, bf16, Kd, 256, P.nK, TM) || !make_map(&mb, Bp, bf16, Kd, N, P.nK, BN))
+        return cudaErrorInvalidValue;
+#define LS(BNV) (bf16 ? launch_tc<BNV, true, true>(ma, mb, P, c0, j0, 256, N, nchunk, st) \
+                      : launch_tc<BNV, false, true>(ma, mb, P, c0, j0, 256, N, nchunk, st))
+    if (BN == 128) return LS(128);
+    if (BN == 64) return LS(64);
+    return LS(32);
+#undef LS
+}
 
 size_t gemm_tc_work_bytes(int64_t nK, int64_t ld, int prec) {
     (void)prec;

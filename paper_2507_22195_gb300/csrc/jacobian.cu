@@ -1,4 +1,4 @@
-// jacobian.cu -- assembly of the dense Schur matrix S^K = A_vv (eq. R1, R3)
+// jacobian.cu -- assembly of the dense Schur matrix S^K = A_vv (eqs. R1, R3)
 // of every macro-element, in FP32 (mixed path) or FP64.
 //
 // The point-wise Jacobians of the integrands (5x5 blocks dU/dv and
@@ -7,10 +7,16 @@
 // entropy-to-conservative map and of the logarithmic means).  They are
 // weighted and contracted with the basis of the micro-element:
 //   S[(k,A),(l,B)] += sum_x W [ phi_A phi_B dU_k/dv_l - sum_j d_j phi_A phi_B dFG_kj/dv_l ]
-//                   + sum_faces sum_x w mu_A mu_B dFhat_k/dv_l,
-// one thread per (A,B) pair of local nodes with 25 accumulators, and added
-// into S with atomics (micro-elements share nodes).  S is column-major with
-// a padded leading dimension; the padding is an identity block.
+//                   + sum_faces sum_x w mu_A mu_B dFhat_k/dv_l.
+// Volume contraction by sum factorisation over the three tensor directions
+// (test/trial pair tables per direction; about 2.9M FMA per micro-element at
+// p = 3 instead of 51M pair by pair), per (k,l) block; the pair-by-pair form
+// remains for the case whose staging does not fit in shared memory (FP64,
+// p = 4).  Results are added into S with atomics (micro-elements share
+// nodes).  Unknowns are ordered node-major, row (A, k) = 5 A + k, so the
+// partial pivoting (which mostly exchanges components of one node) stays
+// inside a block of rows.  S is column-major with a padded leading
+// dimension; the padding is an identity block.
 #include "physics.cuh"
 #include "kernels.cuh"
 
@@ -19,28 +25,18 @@ namespace {
 __device__ __forceinline__ void atomic_add_t(float* p, double x) { atomicAdd(p, (float)x); }
 __device__ __forceinline__ void atomic_add_t(double* p, double x) { atomicAdd(p, x); }
 
+constexpr int HEAD_DOUBLES = 2 * MEHDG_MAXG * (MEHDG_MAXP + 1) + 8;
+
+// Stage the local state of micro-element (e1,e2,e3) of element K and write
+// the weighted point Jacobians P[x][alpha][k*5+l] (alpha 0: W dU/dv; alpha
+// 1..3: -W dFG_j/dv).  vl/vsl/ql: shared scratch.
 template <class TS, bool VISC>
-__global__ void __launch_bounds__(256)
-jac_volume_kernel(JacobianArgs a) {
+__device__ void volume_point_jacobians(const JacobianArgs& a, int K, int e1, int e2, int e3, const double* sL,
+                                       const double* sW, const double* hw, double* vl, double* vsl, double* ql,
+                                       TS* P) {
     const Tab& tb = a.tab;
-    const int K = blockIdx.y, e = blockIdx.x;
-    const int p = tb.p, m = tb.m, n = tb.n, ng = tb.ng, Nn = tb.Nn;
-    const int nl = tb.nl, npt = tb.npt, p1 = p + 1;
-    const int e1 = e % m, e2 = (e / m) % m, e3 = e / (m * m);
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    double* sL = reinterpret_cast<double*>(smem_raw);
-    double* sD = sL + MEHDG_MAXG * (MEHDG_MAXP + 1);
-    double* sW = sD + MEHDG_MAXG * (MEHDG_MAXP + 1);
-    double* vl = sW + 8;                  // [5][nl]
-    double* vsl = vl + 5 * nl;            // [5][nl]
-    double* ql = vsl + 5 * nl;            // [15][nl]
-    TS* P = reinterpret_cast<TS*>(ql + (VISC ? 15 * nl : 0));   // [npt][4][25]
+    const int p = tb.p, n = tb.n, ng = tb.ng, Nn = tb.Nn, nl = tb.nl, npt = tb.npt, p1 = p + 1;
     const int tid = threadIdx.x, nth = blockDim.x;
-    for (int i = tid; i < ng * p1; i += nth) { sL[i] = tb.L[i / p1][i % p1]; sD[i] = tb.dL[i / p1][i % p1]; }
-    if (tid < ng) sW[tid] = tb.w[tid];
-    const double* box = a.box + 6 * K;
-    double sc[3], hw[3];
-    for (int d = 0; d < 3; ++d) { double h = (box[3 + d] - box[d]) / m; sc[d] = 2.0 / h; hw[d] = 0.5 * h; }
     const int64_t oV = (int64_t)K * 5 * Nn, oQ = (int64_t)K * 15 * Nn;
     for (int i = tid; i < nl; i += nth) {
         int l1 = i % p1, l2 = (i / p1) % p1, l3 = i / (p1 * p1);
@@ -80,57 +76,149 @@ jac_volume_kernel(JacobianArgs a) {
     }
     if (!ok && a.status) a.status[K] = MEHDG_ENONPHYS;
     __syncthreads();
-    // contraction: thread per pair of local nodes (two pairs per pass)
+}
+
+__device__ __forceinline__ void geometry(const JacobianArgs& a, int K, double* sc, double* hw) {
+    const double* box = a.box + 6 * K;
+    for (int d = 0; d < 3; ++d) { double h = (box[3 + d] - box[d]) / a.tab.m; sc[d] = 2.0 / h; hw[d] = 0.5 * h; }
+}
+
+__device__ __forceinline__ void load_tables(const Tab& tb, double* sL, double* sD, double* sW) {
+    const int p1 = tb.p + 1;
+    for (int i = threadIdx.x; i < tb.ng * p1; i += blockDim.x) { sL[i] = tb.L[i / p1][i % p1]; sD[i] = tb.dL[i / p1][i % p1]; }
+    if (threadIdx.x < tb.ng) sW[threadIdx.x] = tb.w[threadIdx.x];
+}
+
+// ---------------------------------------------------------------- sum factorised
+template <class TS, bool VISC>
+__global__ void __launch_bounds__(256)
+jac_volume_sf_kernel(JacobianArgs a) {
+    const Tab& tb = a.tab;
+    const int K = blockIdx.y, e = blockIdx.x;
+    const int p = tb.p, m = tb.m, n = tb.n, ng = tb.ng, nl = tb.nl, npt = tb.npt, p1 = p + 1;
+    const int PP = p1 * p1, G2 = ng * ng;
+    const int e1 = e % m, e2 = (e / m) % m, e3 = e / (m * m);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* sL = reinterpret_cast<double*>(smem_raw);
+    double* sD = sL + MEHDG_MAXG * (MEHDG_MAXP + 1);
+    double* sW = sD + MEHDG_MAXG * (MEHDG_MAXP + 1);
+    TS* Mt = reinterpret_cast<TS*>(sW + 8);                 // [3][2][ng][PP] pair tables
+    TS* P = Mt + 6 * MEHDG_MAXG * (MEHDG_MAXP + 1) * (MEHDG_MAXP + 1);   // [npt][100]
+    unsigned char* uni = reinterpret_cast<unsigned char*>(P + (size_t)npt * 100);
+    double* vl = reinterpret_cast<double*>(uni);            // phase 1: nodal state
+    double* vsl = vl + 5 * nl;
+    double* ql = vsl + 5 * nl;
+    TS* H1 = reinterpret_cast<TS*>(uni);                     // phase 2: [4][PP][G2]
+    TS* H2 = H1 + 4 * PP * G2;                               // [4][PP][PP][ng]
+    const int tid = threadIdx.x, nth = blockDim.x;
+    load_tables(tb, sL, sD, sW);
+    double sc[3], hw[3];
+    geometry(a, K, sc, hw);
+    __syncthreads();
+    // pair tables: Mt[d][tau][g][a*p1+b] = (tau ? dphi_a : phi_a)(g) phi_b(g), direction d
+    for (int i = tid; i < 6 * ng * PP; i += nth) {
+        int ab = i % PP, g = (i / PP) % ng, dt = i / (PP * ng), d = dt >> 1, tau = dt & 1;
+        int aa = ab / p1, bb = ab % p1;
+        double t = tau ? sD[g * p1 + aa] * sc[d] : sL[g * p1 + aa];
+        Mt[i] = (TS)(t * sL[g * p1 + bb]);
+    }
+    volume_point_jacobians<TS, VISC>(a, K, e1, e2, e3, sL, sW, hw, vl, vsl, ql, P);
     TS* S = reinterpret_cast<TS*>(a.S) + (size_t)K * a.ld * a.ld;
-    const int npair = nl * nl;
-    const int half = (npair + 1) / 2;
-    for (int r0 = tid; r0 < half; r0 += nth) {
-        int rr[2] = {r0, r0 + half};
-        bool act1 = rr[1] < npair;
-        int la[2][3], lb[2][3];
-        for (int u = 0; u < 2; ++u) {
-            int ia = rr[u] / nl, ib = rr[u] % nl;
-            if (!act1 && u == 1) { ia = 0; ib = 0; }
-            la[u][0] = ia % p1; la[u][1] = (ia / p1) % p1; la[u][2] = ia / (p1 * p1);
-            lb[u][0] = ib % p1; lb[u][1] = (ib / p1) % p1; lb[u][2] = ib / (p1 * p1);
+    const TS* M1 = Mt;                       // direction x: tau=0 at [0], tau=1 at [ng*PP]
+    const TS* M2 = Mt + 2 * ng * PP;
+    const TS* M3 = Mt + 4 * ng * PP;
+    for (int kl = 0; kl < 25; ++kl) {
+        // stage 1: contract g1
+        for (int i = tid; i < 4 * PP * G2; i += nth) {
+            int g23 = i % G2, ab1 = (i / G2) % PP, al = i / (G2 * PP);
+            const TS* Mx = M1 + (al == 1 ? ng * PP : 0);
+            TS s = 0;
+            for (int g1 = 0; g1 < ng; ++g1) s += Mx[g1 * PP + ab1] * P[(size_t)(g1 + ng * g23) * 100 + 25 * al + kl];
+            H1[i] = s;
         }
-        TS acc[2][25];
-        for (int u = 0; u < 2; ++u)
-            for (int i = 0; i < 25; ++i) acc[u][i] = 0;
-        for (int x = 0; x < npt; ++x) {
-            int g[3] = {x % ng, (x / ng) % ng, x / (ng * ng)};
-            TS c[2][4];
-            for (int u = 0; u < 2; ++u) {
-                double Aa[3], Ad[3], Bb = 1.0;
-                for (int d = 0; d < 3; ++d) {
-                    Aa[d] = sL[g[d] * p1 + la[u][d]];
-                    Ad[d] = sD[g[d] * p1 + la[u][d]] * sc[d];
-                    Bb *= sL[g[d] * p1 + lb[u][d]];
-                }
-                c[u][0] = (TS)(Aa[0] * Aa[1] * Aa[2] * Bb);
-                c[u][1] = (TS)(Ad[0] * Aa[1] * Aa[2] * Bb);
-                c[u][2] = (TS)(Aa[0] * Ad[1] * Aa[2] * Bb);
-                c[u][3] = (TS)(Aa[0] * Aa[1] * Ad[2] * Bb);
+        __syncthreads();
+        // stage 2: contract g2
+        for (int i = tid; i < 4 * PP * PP * ng; i += nth) {
+            int g3 = i % ng, ab2 = (i / ng) % PP, ab1 = (i / (ng * PP)) % PP, al = i / (ng * PP * PP);
+            const TS* My = M2 + (al == 2 ? ng * PP : 0);
+            const TS* h = H1 + ((size_t)al * PP + ab1) * G2 + ng * g3;
+            TS s = 0;
+            for (int g2 = 0; g2 < ng; ++g2) s += My[g2 * PP + ab2] * h[g2];
+            H2[i] = s;
+        }
+        __syncthreads();
+        // stage 3: contract g3, sum the four integrand parts, add into S
+        const int k = kl / 5, l = kl % 5;
+        for (int i = tid; i < PP * PP * PP; i += nth) {
+            int ab3 = i % PP, ab2 = (i / PP) % PP, ab1 = i / (PP * PP);
+            TS s = 0;
+            for (int al = 0; al < 4; ++al) {
+                const TS* Mz = M3 + (al == 3 ? ng * PP : 0);
+                const TS* h = H2 + (((size_t)al * PP + ab1) * PP + ab2) * ng;
+                for (int g3 = 0; g3 < ng; ++g3) s += Mz[g3 * PP + ab3] * h[g3];
             }
-            const TS* Px = P + (size_t)x * 100;
-#pragma unroll 5
-            for (int kl = 0; kl < 25; ++kl) {
-                TS p0 = Px[kl], q1 = Px[25 + kl], q2 = Px[50 + kl], q3 = Px[75 + kl];
-                acc[0][kl] += c[0][0] * p0 + c[0][1] * q1 + c[0][2] * q2 + c[0][3] * q3;
-                acc[1][kl] += c[1][0] * p0 + c[1][1] * q1 + c[1][2] * q2 + c[1][3] * q3;
-            }
+            int a1 = ab1 / p1, b1 = ab1 % p1, a2 = ab2 / p1, b2 = ab2 % p1, a3 = ab3 / p1, b3 = ab3 % p1;
+            int A = (e1 * p + a1) + n * ((e2 * p + a2) + n * (e3 * p + a3));
+            int B = (e1 * p + b1) + n * ((e2 * p + b2) + n * (e3 * p + b3));
+            atomic_add_t(&S[(size_t)(A * 5 + k) + (size_t)(B * 5 + l) * a.ld], (double)s);
         }
-        for (int u = 0; u < 2; ++u) {
-            if (u == 1 && !act1) break;
-            int A = (e1 * p + la[u][0]) + n * ((e2 * p + la[u][1]) + n * (e3 * p + la[u][2]));
-            int B = (e1 * p + lb[u][0]) + n * ((e2 * p + lb[u][1]) + n * (e3 * p + lb[u][2]));
-            for (int k = 0; k < 5; ++k)
-                for (int l = 0; l < 5; ++l)
-                    atomic_add_t(&S[(size_t)(k * Nn + A) + (size_t)(l * Nn + B) * a.ld], (double)acc[u][k * 5 + l]);
-        }
+        __syncthreads();
     }
 }
 
+// ---------------------------------------------------------------- pair by pair
+template <class TS, bool VISC>
+__global__ void __launch_bounds__(256)
+jac_volume_kernel(JacobianArgs a) {
+    const Tab& tb = a.tab;
+    const int K = blockIdx.y, e = blockIdx.x;
+    const int p = tb.p, m = tb.m, n = tb.n, ng = tb.ng, nl = tb.nl, npt = tb.npt, p1 = p + 1;
+    const int e1 = e % m, e2 = (e / m) % m, e3 = e / (m * m);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* sL = reinterpret_cast<double*>(smem_raw);
+    double* sD = sL + MEHDG_MAXG * (MEHDG_MAXP + 1);
+    double* sW = sD + MEHDG_MAXG * (MEHDG_MAXP + 1);
+    double* vl = sW + 8;                  // [5][nl]
+    double* vsl = vl + 5 * nl;            // [5][nl]
+    double* ql = vsl + 5 * nl;            // [15][nl]
+    TS* P = reinterpret_cast<TS*>(ql + (VISC ? 15 * nl : 0));   // [npt][4][25]
+    const int tid = threadIdx.x, nth = blockDim.x;
+    load_tables(tb, sL, sD, sW);
+    double sc[3], hw[3];
+    geometry(a, K, sc, hw);
+    __syncthreads();
+    volume_point_jacobians<TS, VISC>(a, K, e1, e2, e3, sL, sW, hw, vl, vsl, ql, P);
+    TS* S = reinterpret_cast<TS*>(a.S) + (size_t)K * a.ld * a.ld;
+    const int npair = nl * nl;
+    for (int r = tid; r < npair; r += nth) {
+        int ia = r / nl, ib = r % nl;
+        int la[3] = {ia % p1, (ia / p1) % p1, ia / (p1 * p1)};
+        int lb[3] = {ib % p1, (ib / p1) % p1, ib / (p1 * p1)};
+        TS acc[25];
+        for (int i = 0; i < 25; ++i) acc[i] = 0;
+        for (int x = 0; x < npt; ++x) {
+            int g[3] = {x % ng, (x / ng) % ng, x / (ng * ng)};
+            double Aa[3], Ad[3], Bb = 1.0;
+            for (int d = 0; d < 3; ++d) {
+                Aa[d] = sL[g[d] * p1 + la[d]];
+                Ad[d] = sD[g[d] * p1 + la[d]] * sc[d];
+                Bb *= sL[g[d] * p1 + lb[d]];
+            }
+            TS c0 = (TS)(Aa[0] * Aa[1] * Aa[2] * Bb), c1 = (TS)(Ad[0] * Aa[1] * Aa[2] * Bb);
+            TS c2 = (TS)(Aa[0] * Ad[1] * Aa[2] * Bb), c3 = (TS)(Aa[0] * Aa[1] * Ad[2] * Bb);
+            const TS* Px = P + (size_t)x * 100;
+            for (int kl = 0; kl < 25; ++kl)
+                acc[kl] += c0 * Px[kl] + c1 * Px[25 + kl] + c2 * Px[50 + kl] + c3 * Px[75 + kl];
+        }
+        int A = (e1 * p + la[0]) + n * ((e2 * p + la[1]) + n * (e3 * p + la[2]));
+        int B = (e1 * p + lb[0]) + n * ((e2 * p + lb[1]) + n * (e3 * p + lb[2]));
+        for (int k = 0; k < 5; ++k)
+            for (int l = 0; l < 5; ++l)
+                atomic_add_t(&S[(size_t)(A * 5 + k) + (size_t)(B * 5 + l) * a.ld], (double)acc[k * 5 + l]);
+    }
+}
+
+// ---------------------------------------------------------------- faces
 template <class TS, bool VISC>
 __global__ void __launch_bounds__(256)
 jac_face_kernel(JacobianArgs a) {
@@ -200,7 +288,7 @@ jac_face_kernel(JacobianArgs a) {
         int A = nodeA[ia], B = nodeA[ib];
         for (int k = 0; k < 5; ++k)
             for (int l = 0; l < 5; ++l)
-                atomic_add_t(&S[(size_t)(k * Nn + A) + (size_t)(l * Nn + B) * a.ld], (double)acc[k * 5 + l]);
+                atomic_add_t(&S[(size_t)(A * 5 + k) + (size_t)(B * 5 + l) * a.ld], (double)acc[k * 5 + l]);
     }
 }
 
@@ -211,22 +299,40 @@ __global__ void pad_identity_kernel(TS* S, int64_t ld, int Nv) {
     if (i < ld) S[(size_t)K * ld * ld + i + i * ld] = (TS)1;
 }
 
+size_t sf_smem_bytes(const Tab& t, bool visc, size_t ts) {
+    const size_t PP = (size_t)(t.p + 1) * (t.p + 1), G2 = (size_t)t.ng * t.ng;
+    size_t head = sizeof(double) * HEAD_DOUBLES;
+    size_t tables = ts * 6 * MEHDG_MAXG * (MEHDG_MAXP + 1) * (MEHDG_MAXP + 1);
+    size_t P = ts * 100 * (size_t)t.npt;
+    size_t state = sizeof(double) * (size_t)(10 + (visc ? 15 : 0)) * t.nl;
+    size_t hbuf = ts * (4 * PP * G2 + 4 * PP * PP * t.ng);
+    return head + tables + P + (state > hbuf ? state : hbuf) + 16;
+}
+
 }  // namespace
 
 cudaError_t launch_jacobian(const JacobianArgs& a, int64_t nK, bool fp64, cudaStream_t st) {
     const Tab& t = a.tab;
     bool visc = a.ph.viscous != 0;
     size_t ts = fp64 ? 8 : 4;
-    size_t sv = sizeof(double) * (2 * MEHDG_MAXG * (MEHDG_MAXP + 1) + 8 + (size_t)(10 + (visc ? 15 : 0)) * t.nl)
-              + ts * 100 * (size_t)t.npt;
+    size_t ssf = sf_smem_bytes(t, visc, ts);
+    const bool use_sf = ssf <= 220 * 1024;
+    size_t sv = use_sf ? ssf
+                       : sizeof(double) * (HEAD_DOUBLES + (size_t)(10 + (visc ? 15 : 0)) * t.nl)
+                             + ts * 100 * (size_t)t.npt;
     int fl = (t.p + 1) * (t.p + 1), fpt = t.ng * t.ng;
     size_t sf = sizeof(double) * (MEHDG_MAXG * (MEHDG_MAXP + 1) + 8 + 25 * (size_t)fl + (fl + 1) / 2 + 1)
               + ts * 25 * (size_t)fpt + 64;
     dim3 gv(t.m * t.m * t.m, (unsigned)nK), gf(6 * t.m * t.m, (unsigned)nK), b(256);
-#define LJ(TS, V)                                                                                   \
-    do { cudaFuncSetAttribute(jac_volume_kernel<TS, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sv); \
-         cudaFuncSetAttribute(jac_face_kernel<TS, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf);   \
-         jac_volume_kernel<TS, V><<<gv, b, sv, st>>>(a);                                            \
+#define LJ(TS, V)                                                                                        \
+    do { if (use_sf) {                                                                                   \
+             cudaFuncSetAttribute(jac_volume_sf_kernel<TS, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sv); \
+             jac_volume_sf_kernel<TS, V><<<gv, b, sv, st>>>(a);                                          \
+         } else {                                                                                        \
+             cudaFuncSetAttribute(jac_volume_kernel<TS, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sv); \
+             jac_volume_kernel<TS, V><<<gv, b, sv, st>>>(a);                                             \
+         }                                                                                               \
+         cudaFuncSetAttribute(jac_face_kernel<TS, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf); \
          jac_face_kernel<TS, V><<<gf, b, sf, st>>>(a); } while (0)
     if (fp64) { if (visc) LJ(double, true); else LJ(double, false); }
     else { if (visc) LJ(float, true); else LJ(float, false); }

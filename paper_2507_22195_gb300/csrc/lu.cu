@@ -143,10 +143,11 @@ panel_kernel(TS* __restrict__ Sall, int64_t ld, int c, int32_t* __restrict__ piv
 }
 
 // ---------------------------------------------------------------- row swaps
-// Net permutation of the swap sequence piv[c0 .. c0+w): list of (dst, src)
-// rows such that new[dst] = old[src].  One thread per element.
-// One warp per element: rows/cont live in shared memory, the search for a
-// row below the block is done by the 32 lanes at once.
+// Net permutation of the swap sequence piv[c0 .. c0+w): slots 0..w-1 are the
+// rows c0..c0+w-1, further slots the rows below the block that take part;
+// after the sequence, slot i holds the old content of slot cont[i].  One warp
+// per element: rows/cont live in shared memory, the search for a row below
+// the block is done by the 32 lanes at once.
 __global__ void __launch_bounds__(128)
 perm_build_kernel(const int32_t* __restrict__ pivall, int64_t ld, int c0, int w,
                   int32_t* __restrict__ perm /*[nK][1 + 4w]*/, int nK) {
@@ -157,7 +158,7 @@ perm_build_kernel(const int32_t* __restrict__ pivall, int64_t ld, int c0, int w,
     const int32_t* piv = pivall + (size_t)K * ld;
     int32_t* rows = sp + wl * 4 * w;
     int32_t* cont = rows + 2 * w;
-    for (int i = lane; i < w; i += 32) { rows[i] = c0 + i; cont[i] = c0 + i; }
+    for (int i = lane; i < w; i += 32) { rows[i] = c0 + i; cont[i] = i; }
     __syncwarp();
     int nr = w;
     for (int i = 0; i < w; ++i) {
@@ -174,7 +175,7 @@ perm_build_kernel(const int32_t* __restrict__ pivall, int64_t ld, int c0, int w,
             }
             if (sb < 0) {
                 sb = nr++;
-                if (lane == 0) { rows[sb] = b; cont[sb] = b; }
+                if (lane == 0) { rows[sb] = b; cont[sb] = sb; }
             }
         }
         __syncwarp();
@@ -186,6 +187,8 @@ perm_build_kernel(const int32_t* __restrict__ pivall, int64_t ld, int c0, int w,
     if (lane == 0) out[0] = nr;
 }
 
+// Row exchanges of the columns [j0, j1): new row rows[i] = old row rows[cont[i]].
+// One warp per column; the block rows [c0, c0+w) are read contiguously.
 template <class TS>
 __global__ void __launch_bounds__(256)
 laswp_kernel(TS* __restrict__ Sall, int64_t ld, const int32_t* __restrict__ perm, int w, int j0, int j1) {
@@ -196,15 +199,17 @@ laswp_kernel(TS* __restrict__ Sall, int64_t ld, const int32_t* __restrict__ perm
     const int32_t* rows = pl + 1;
     const int32_t* cont = rows + 2 * w;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    TS* buf = reinterpret_cast<TS*>(smem_raw);      // [2w][16]
-    const int col0 = j0 + blockIdx.x * 16;
-    const int tc = threadIdx.x & 15, tr = threadIdx.x >> 4;   // 16 columns x 16 row groups
-    const int col = col0 + tc;
-    if (col < j1)
-        for (int i = tr; i < nr; i += 16) buf[i * 16 + tc] = S[(size_t)cont[i] + (size_t)col * ld];
-    __syncthreads();
-    if (col < j1)
-        for (int i = tr; i < nr; i += 16) S[(size_t)rows[i] + (size_t)col * ld] = buf[i * 16 + tc];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    TS* buf = reinterpret_cast<TS*>(smem_raw) + (size_t)warp * 2 * w;
+    const int col = j0 + blockIdx.x * 8 + warp;
+    if (col >= j1) return;
+    TS* Sc = S + (size_t)col * ld;
+    for (int i = lane; i < nr; i += 32) buf[i] = Sc[rows[i]];
+    __syncwarp();
+    for (int i = lane; i < nr; i += 32) {
+        const int src = cont[i];
+        if (src != i) Sc[rows[i]] = buf[src];
+    }
 }
 
 // ---------------------------------------------------------------- TRSM
@@ -398,9 +403,9 @@ cudaError_t launch_laswp(const LUPlan& P, int c0, int w, int j0, int j1, cudaStr
     int32_t* perm = reinterpret_cast<int32_t*>(P.work);
     perm_build_kernel<<<(unsigned)((P.nK + 3) / 4), 128, 4 * 4 * w * sizeof(int32_t), st>>>(P.piv, P.ld, c0, w,
                                                                                            perm, (int)P.nK);
-    size_t sm = (size_t)2 * w * 16 * sizeof(TS);
+    size_t sm = (size_t)8 * 2 * w * sizeof(TS);
     cudaFuncSetAttribute(laswp_kernel<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    dim3 g((unsigned)((j1 - j0 + 15) / 16), (unsigned)P.nK);
+    dim3 g((unsigned)((j1 - j0 + 7) / 8), (unsigned)P.nK);
     laswp_kernel<TS><<<g, 256, sm, st>>>((TS*)P.S, P.ld, perm, w, j0, j1);
     MEHDG_COUNT(2);
     return cudaGetLastError();
@@ -454,7 +459,9 @@ cudaError_t factor_t(const LUPlan& P, cudaStream_t st) {
         if ((e = rec_panel<TS>(P, c0, LU_NB, st)) != cudaSuccess) return e;
         if (c0 + LU_NB < ld) {
             if ((e = launch_laswp<TS>(P, c0, LU_NB, c0 + LU_NB, ld, st)) != cudaSuccess) return e;
-            if ((e = launch_trsm<TS>(P, c0, LU_NB, c0 + LU_NB, ld, st)) != cudaSuccess) return e;
+            if constexpr (std::is_same<TS, double>::value) e = launch_trsm<TS>(P, c0, LU_NB, c0 + LU_NB, ld, st);
+            else e = gemm_tc_trsm256(P, c0, c0 + LU_NB, ld, st);
+            if (e != cudaSuccess) return e;
         }
         prof_end(P.prof, ev, st, 0.0);
         if (c0 + LU_NB < ld) {

@@ -8,4 +8,7 @@ constexpr int LU_NB = 256;   // outer panel width (depth of the big trailing upd
 // (TF32 or BF16 operands, FP32 accumulation), S^K column-major FP32.
 cudaError_t gemm_tc_update(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st);
 size_t gemm_tc_work_bytes(int64_t nK, int64_t ld, int prec);
+// rows [c0, c0+256) of the columns [j0, j1) := L11^-1 (same rows), on the
+// tensor cores through the explicit inverse of the unit-lower block L11
+cudaError_t gemm_tc_trsm256(const LUPlan& P, int c0, int j0, int j1, cudaStream_t st);
 cudaError_t gemm_simt_update_f32(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st);

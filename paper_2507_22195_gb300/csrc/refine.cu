@@ -2,45 +2,51 @@
 //   x_{i+1} = x_i + LU^-1 (r - S x_i),  S x evaluated matrix-free in FP64
 // (forward-mode tangent of the residual), stopped per element when
 // ||r - S x|| <= tol ||r|| (2-norms over the element's unknowns).
+// The LU works on node-major vectors (entry 5 A + k, padded to ld); the
+// residual kernels use the component-major layout [5][Nn] of the C-ABI.
 #include "kernels.cuh"
 
 namespace {
 
-// out[K][i] = sa a[K][i] + sb b[K][i] for i < Nv (a, b with stride Nv), 0 for padding
-__global__ void set_rhs_kernel(int Nv, int64_t ld, const double* a, double sa, const double* b, double sb,
+// out[K][5A+k] = sa a[K][k Nn + A] + sb b[K][k Nn + A]; 0 in the padding
+__global__ void set_rhs_kernel(int Nn, int64_t ld, const double* a, double sa, const double* b, double sb,
                                double* out) {
     int K = blockIdx.y;
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= ld) return;
     double v = 0.0;
+    const int Nv = 5 * Nn;
     if (i < Nv) {
-        if (a) v += sa * a[(size_t)K * Nv + i];
-        if (b) v += sb * b[(size_t)K * Nv + i];
+        const int64_t j = (i % 5) * Nn + i / 5;
+        if (a) v += sa * a[(size_t)K * Nv + j];
+        if (b) v += sb * b[(size_t)K * Nv + j];
     }
     out[(size_t)K * ld + i] = v;
 }
 
-// out[K][i] = s x[K][i] for i < Nv (strip the padding)
-__global__ void copy_unpad_kernel(int Nv, int64_t ld, const double* x, double* out, double s) {
+// out[K][k Nn + A] = s x[K][5A+k]
+__global__ void copy_unpad_kernel(int Nn, int64_t ld, const double* x, double* out, double s) {
     int K = blockIdx.y;
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= Nv) return;
-    out[(size_t)K * Nv + i] = s * x[(size_t)K * ld + i];
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int Nv = 5 * Nn;
+    if (j >= Nv) return;
+    const int64_t i = (j % Nn) * 5 + j / Nn;
+    out[(size_t)K * Nv + j] = s * x[(size_t)K * ld + i];
 }
 
-// per element: x += dx (if not converged before this sweep); res = r - Sx;
-// convergence test; count unconverged elements
+// per element: res = r - Sx; convergence test; count unconverged elements
 __global__ void __launch_bounds__(256)
-refine_update_kernel(int Nv, int64_t ld, const double* r, const double* Sx, double* res, double* nrm,
+refine_update_kernel(int Nn, int64_t ld, const double* r, const double* Sx, double* res, double* nrm,
                      int32_t* conv, int32_t* iters, int32_t* status, double tol, int it, int last,
                      int32_t* cnt) {
     int K = blockIdx.x;
     if (conv[K]) return;
+    const int Nv = 5 * Nn;
     __shared__ double red[2][8];
     double s_r = 0.0, s_e = 0.0;
     for (int i = threadIdx.x; i < Nv; i += blockDim.x) {
         double rv = r[(size_t)K * ld + i];
-        double e = rv - Sx[(size_t)K * Nv + i];
+        double e = rv - Sx[(size_t)K * Nv + (i % 5) * Nn + i / 5];
         res[(size_t)K * ld + i] = e;
         s_r += rv * rv; s_e += e * e;
     }
@@ -72,10 +78,11 @@ __global__ void axpy_kernel(int64_t ld, const double* dx, double* x, const int32
 
 }  // namespace
 
-cudaError_t launch_set_rhs(int64_t nK, int Nv, int64_t ld, int, const double* a, double sa, const double* b,
+cudaError_t launch_set_rhs(int64_t nK, int Nv, int64_t ld, int Nn, const double* a, double sa, const double* b,
                            double sb, double* out, cudaStream_t st) {
+    (void)Nv;
     dim3 g((unsigned)((ld + 255) / 256), (unsigned)nK);
-    set_rhs_kernel<<<g, 256, 0, st>>>(Nv, ld, a, sa, b, sb, out);
+    set_rhs_kernel<<<g, 256, 0, st>>>(Nn, ld, a, sa, b, sb, out);
     MEHDG_COUNT(1);
     return cudaGetLastError();
 }
@@ -83,7 +90,7 @@ cudaError_t launch_set_rhs(int64_t nK, int Nv, int64_t ld, int, const double* a,
 cudaError_t launch_copy_unpad(int64_t nK, int Nv, int64_t ld, const double* x, double* out, double s,
                               cudaStream_t st) {
     dim3 g((unsigned)((Nv + 255) / 256), (unsigned)nK);
-    copy_unpad_kernel<<<g, 256, 0, st>>>(Nv, ld, x, out, s);
+    copy_unpad_kernel<<<g, 256, 0, st>>>(Nv / 5, ld, x, out, s);
     MEHDG_COUNT(1);
     return cudaGetLastError();
 }
@@ -99,7 +106,7 @@ cudaError_t launch_refine_update(int64_t nK, int Nv, int64_t ld, const double* r
                                  double* res, double* nrm, int32_t* conv, int32_t* iters, int32_t* status,
                                  double tol, int it, int last, const double*, double*, int32_t* cnt,
                                  cudaStream_t st) {
-    refine_update_kernel<<<(unsigned)nK, 256, 0, st>>>(Nv, ld, r, Sx, res, nrm, conv, iters, status, tol, it,
+    refine_update_kernel<<<(unsigned)nK, 256, 0, st>>>(Nv / 5, ld, r, Sx, res, nrm, conv, iters, status, tol, it,
                                                          last, cnt);
     MEHDG_COUNT(1);
     return cudaGetLastError();

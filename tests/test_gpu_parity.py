@@ -93,7 +93,8 @@ def _oracle_condensed(prm, mesh, st, dvh):
 def test_condense_apply_recover_match_oracle(name, prec):
     mesh, st, kw = case(name)
     flux = 2
-    ctx = M().Context(mesh, flux=flux, prec=prec, **kw)
+    # the BF16 factors contract the refinement error more slowly: more sweeps
+    ctx = M().Context(mesh, flux=flux, prec=prec, refine_max_iter=40 if prec == 2 else 10, **kw)
     v, vh, q, vs = to_dev(st)
     ctx.set_state(v, vh, q, vs)
     bh = ctx.condense()
