@@ -160,6 +160,26 @@ int mehdg_profile_read(mehdg_ctx* ctx, double* ms, int64_t* launches, double* fl
 /* Number of kernels this library has launched since it was loaded. */
 int64_t mehdg_launch_count(void);
 
+/* Residual without any device allocation (the paper has no counterpart; it
+ * exists for callers that must not allocate device memory after start-up,
+ * e.g. a host application whose own pool allocator owns the whole GPU, where
+ * a stray cudaMalloc fails or breaks its accounting, or a real-time loop
+ * that forbids allocation).  Same result as mehdg_residual, but no context:
+ * prm (host), p, m, and DEVICE arrays box [nK][6], face_gid [nK][6],
+ * v, vhat, q (NULL for Euler), vstar, R_V, R_Q (NULL for Euler), R_Vhat in
+ * the layouts above.  Its scratch is one static device array of 24 MiB per
+ * GPU, held until the process exits; the call needs
+ * nK * 30 n^2 doubles + 2 n_global_faces int64 (+ alignment) of it and
+ * returns MEHDG_EINVAL (message on stderr) when that does not fit.  The
+ * first call made on a device looks up the array's device address (once per
+ * device).  Calls share the array: calls that overlap on the GPU race.  The
+ * call synchronises `stream` once, after checking the face ids on the device
+ * and before the residual kernels read with them. */
+int mehdg_residual_static(const mehdg_params* prm, int64_t nK, int p, int m, const double* box,
+                          const int64_t* face_gid, int64_t n_global_faces, const double* v,
+                          const double* vhat, const double* q, const double* vstar, double* R_V,
+                          double* R_Q, double* R_Vhat, void* stream);
+
 /* Diagnostics: one tensor-core trailing update of the mixed-precision LU,
  *   S[r0+i, c0+j] -= sum_k S[r0+i, k0+k] S[k0+k, c0+j]  (i<M, j<N, k<Kd),
  * on nK column-major FP32 matrices S [nK][ld][ld] (device), with operands

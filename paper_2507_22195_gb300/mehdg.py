@@ -26,7 +26,7 @@ EXPORTED = ["mehdg_default_params", "mehdg_create", "mehdg_set_mesh", "mehdg_set
             "mehdg_residual", "mehdg_condense", "mehdg_apply_condensed", "mehdg_recover",
             "mehdg_status", "mehdg_last_error", "mehdg_destroy", "mehdg_profile_enable",
             "mehdg_profile_read", "mehdg_launch_count", "mehdg_test_trailing_update",
-            "mehdg_test_trailing_work_bytes"]
+            "mehdg_test_trailing_work_bytes", "mehdg_residual_static"]
 
 
 class mehdg_params(C.Structure):
@@ -74,6 +74,8 @@ def load(path: str | None = None):
                                              C.c_int, C.c_int, C.c_int, _vp, _vp]
     L.mehdg_test_trailing_work_bytes.argtypes = [C.c_int64, C.c_int64]
     L.mehdg_test_trailing_work_bytes.restype = C.c_size_t
+    L.mehdg_residual_static.argtypes = [C.POINTER(mehdg_params), C.c_int64, C.c_int, C.c_int, _vp, _vp,
+                                        C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
     _lib = L
     return L
 
@@ -185,6 +187,19 @@ def mehdg_test_trailing_update(S, r0, c0, k0, M, N, Kd, prec, work=None, stream=
     _check(None, load().mehdg_test_trailing_update(nK, ld, S.data_ptr(), r0, c0, k0, M, N, Kd, prec,
                                                    work.data_ptr(), _stream(stream)),
            "mehdg_test_trailing_update")
+
+
+def mehdg_residual_static(params, p, m, box, face_gid, n_global_faces, v, vhat, q, vstar, R_V, R_Q, R_Vhat,
+                          stream=None):
+    """Allocation-free residual: every array is a caller-owned CUDA tensor
+    (box float64 [nK,6], face_gid int64 [nK,6], the rest float64)."""
+    import torch
+    assert box.is_cuda and box.dtype == torch.float64 and face_gid.is_cuda and face_gid.dtype == torch.int64
+    nK = box.shape[0]
+    rc = load().mehdg_residual_static(C.byref(params), nK, p, m, box.data_ptr(), face_gid.data_ptr(),
+                                      int(n_global_faces), _ptr(v), _ptr(vhat), _ptr(q), _ptr(vstar), _ptr(R_V),
+                                      _ptr(R_Q), _ptr(R_Vhat), _stream(stream))
+    _check(None, rc, "mehdg_residual_static")
 
 
 def mehdg_launch_count() -> int:
