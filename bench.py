@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 METRIC = "macro-elements condensed/sec at p=3 (mixed vs FP64 GPU), err vs FP64 oracle"
 UNIT = "macro-elements/s"
 WORKLOAD = "inviscid Taylor-Green vortex, 8^3 macro-elements x 3^3 micro-elements, p=3, KEPES, one Newton-step condensation"
-PREC = {"tf32": 1, "bf16": 2, "fp64": 0}
+PREC = {"tf32": 1, "bf16": 2, "fp64": 0, "tf32x3": 3, "bf16x3": 4}
 
 
 def peaks():
@@ -177,7 +177,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="tf32", choices=list(PREC))
+    ap.add_argument("--prec", default="bf16x3", choices=list(PREC))
     ap.add_argument("--nk", type=int, default=8)
     ap.add_argument("--fp64-sample", type=int, default=2, help="nk of the FP64 comparison mesh (nk^3 elements)")
     ap.add_argument("--cpu-sample", type=int, default=-1, help="elements for the CPU oracle baseline (-1: one per core)")
@@ -333,7 +333,9 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
-            "dtype": {"tf32": "tf32 (f32 accumulate) + f64", "bf16": "bf16 (f32 accumulate) + f64", "fp64": "f64"}[a.prec],
+            "dtype": {"tf32": "tf32 (f32 accumulate) + f64", "bf16": "bf16 (f32 accumulate) + f64",
+                      "tf32x3": "split tf32 x3 (f32 accumulate) + f64", "bf16x3": "split bf16 x3 (f32 accumulate) + f64",
+                      "fp64": "f64"}[a.prec],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "global_batch": mesh.nK, "seq_len": None,
                        "parallelism": f"dp{world}" if world > 1 else "none", "nK": mesh.nK, "p": 3, "m": 3,

@@ -69,7 +69,11 @@ typedef enum {
 typedef enum {
     MEHDG_FP64 = 0,        /* FP64 LU on the FP64 pipe                              */
     MEHDG_MIXED_TF32 = 1,  /* FP32 storage, TF32 tensor-core updates, FP32 accumulate */
-    MEHDG_MIXED_BF16 = 2   /* FP32 storage, BF16 tensor-core updates, FP32 accumulate */
+    MEHDG_MIXED_BF16 = 2,  /* FP32 storage, BF16 tensor-core updates, FP32 accumulate */
+    /* split precision: each product a b taken as a_hi b_hi + a_hi b_lo + a_lo b_hi
+     * (hi = round(a), lo = round(a - hi)) on the tensor cores, FP32 accumulate */
+    MEHDG_MIXED_TF32X3 = 3,
+    MEHDG_MIXED_BF16X3 = 4
 } mehdg_prec;
 
 enum {

@@ -115,7 +115,7 @@ void mehdg_default_params(mehdg_params* p) {
 int mehdg_create(mehdg_ctx** out, const mehdg_params* prm) {
     if (!out || !prm) return MEHDG_EINVAL;
     *out = nullptr;
-    if (!(prm->gamma > 1.0) || prm->flux < 0 || prm->flux > 2 || prm->prec < 0 || prm->prec > 2 ||
+    if (!(prm->gamma > 1.0) || prm->flux < 0 || prm->flux > 2 || prm->prec < 0 || prm->prec > 4 ||
         (prm->time_term && !(prm->dt > 0.0)) || (prm->viscous && !(prm->Re > 0 && prm->Pr > 0 && prm->Mach > 0)))
         return MEHDG_EINVAL;
     int ndev = 0;

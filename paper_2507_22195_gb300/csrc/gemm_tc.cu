@@ -214,10 +214,42 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
 }
 
 // ---------------------------------------------------------------- packing
-// A panel: Ap[K][m][k] = L[r0+m][k0+k] (k < Kd, else 0); 32x32 transposes.
+// Operand rounding: TF32 (round to nearest on 10 mantissa bits, kept in FP32
+// storage) or BF16.  With split precision a product a b is taken as
+// a_hi b_hi + a_hi b_lo + a_lo b_hi (hi = round(x), lo = round(x - hi)): the
+// A panel holds the three K-segments [hi | hi | lo] and the B panel
+// [hi | lo | hi], so one GEMM over the tripled depth gives the sum.
+__device__ __forceinline__ float tf32_rn(float x) {
+    uint32_t y;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
+    return __uint_as_float(y);
+}
+template <bool BF16>
+__device__ __forceinline__ float op_round(float x) {
+    if constexpr (BF16) return __bfloat162float(__float2bfloat16_rn(x));
+    else return tf32_rn(x);
+}
+template <bool BF16>
+__device__ __forceinline__ void op_store(void* out, size_t o, float x) {
+    if constexpr (BF16) reinterpret_cast<__nv_bfloat16*>(out)[o] = __float2bfloat16_rn(x);
+    else reinterpret_cast<float*>(out)[o] = x;     // already TF32-rounded
+}
+// write x into the nseg K-segments of row `row` (segment pattern sel: A = hi,hi,lo; B = hi,lo,hi)
+template <bool BF16, bool IS_A>
+__device__ __forceinline__ void op_put(void* out, size_t row_base, int Kp, int k, int nseg, float x) {
+    const float hi = op_round<BF16>(x);
+    op_store<BF16>(out, row_base + k, hi);
+    if (nseg == 3) {
+        const float lo = op_round<BF16>(x - hi);
+        op_store<BF16>(out, row_base + Kp + k, IS_A ? hi : lo);
+        op_store<BF16>(out, row_base + 2 * (size_t)Kp + k, IS_A ? lo : hi);
+    }
+}
+
+// A panel: Ap[K][m][seg*Kp + k] = L[r0+m][k0+k] (k < Kd, else 0); 32x32 transposes.
 template <bool BF16>
 __global__ void pack_A_kernel(const float* __restrict__ Sall, int64_t ld, int r0, int k0, int M, int Kd, int Kp,
-                              void* __restrict__ out) {
+                              int nseg, void* __restrict__ out) {
     const int K = blockIdx.z;
     const float* S = Sall + (size_t)K * ld * ld;
     __shared__ float t[32][33];
@@ -230,35 +262,21 @@ __global__ void pack_A_kernel(const float* __restrict__ Sall, int64_t ld, int r0
     __syncthreads();
     for (int i = ty; i < 32; i += 8) {
         int m = m0 + i, k = kk0 + tx;
-        if (m < M && k < Kp) {
-            size_t o = ((size_t)K * M + m) * Kp + k;
-            float x = t[tx][i];
-            if constexpr (BF16) reinterpret_cast<__nv_bfloat16*>(out)[o] = __float2bfloat16_rn(x);
-            else {
-                uint32_t y;
-                asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
-                reinterpret_cast<uint32_t*>(out)[o] = y;
-            }
-        }
+        if (m < M && k < Kp)
+            op_put<BF16, true>(out, ((size_t)K * M + m) * (size_t)(nseg * Kp), Kp, k, nseg, t[tx][i]);
     }
 }
-// B panel: Bp[K][n][k] = U[k0+k][c0+n] (contiguous in k on both sides)
+// B panel: Bp[K][n][seg*Kp + k] = U[k0+k][c0+n] (contiguous in k on both sides)
 template <bool BF16>
 __global__ void pack_B_kernel(const float* __restrict__ Sall, int64_t ld, int k0, int c0, int N, int Kd, int Kp,
-                              void* __restrict__ out) {
+                              int nseg, void* __restrict__ out) {
     const int K = blockIdx.z;
     const float* S = Sall + (size_t)K * ld * ld;
     const int n = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (n >= N) return;
     for (int k = threadIdx.x & 31; k < Kp; k += 32) {
         float x = k < Kd ? S[(size_t)(k0 + k) + (size_t)(c0 + n) * ld] : 0.f;
-        size_t o = ((size_t)K * N + n) * Kp + k;
-        if constexpr (BF16) reinterpret_cast<__nv_bfloat16*>(out)[o] = __float2bfloat16_rn(x);
-        else {
-            uint32_t y;
-            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
-            reinterpret_cast<uint32_t*>(out)[o] = y;
-        }
+        op_put<BF16, false>(out, ((size_t)K * N + n) * (size_t)(nseg * Kp), Kp, k, nseg, x);
     }
 }
 
@@ -293,6 +311,12 @@ size_t perm_bytes(int64_t nK) {
     return (b + 255) & ~(size_t)255;
 }
 
+// one operand panel: ld rows x (3 segments x 256) FP32 per element
+size_t panel_bytes(int64_t nK, int64_t ld) {
+    size_t b = (size_t)nK * ld * 3 * LU_NB * 4;
+    return (b + 255) & ~(size_t)255;
+}
+
 template <int BN, bool BF16, bool STORE = false>
 cudaError_t launch_tc(const CUtensorMap& a, const CUtensorMap& b, const LUPlan& P, int r0, int c0, int M, int N,
                       int nchunk, cudaStream_t st) {
@@ -313,7 +337,7 @@ cudaError_t launch_tc(const CUtensorMap& a, const CUtensorMap& b, const LUPlan& 
 // columns x 8 row groups, with the columns of L staged in shared memory.
 template <bool BF16>
 __global__ void __launch_bounds__(256)
-trtri256_kernel(const float* __restrict__ Sall, int64_t ld, int c0, void* __restrict__ Ap) {
+trtri256_kernel(const float* __restrict__ Sall, int64_t ld, int c0, int nseg, void* __restrict__ Ap) {
     constexpr int T = 256;
     const int K = blockIdx.y, b = blockIdx.x;
     const float* S = Sall + (size_t)K * ld * ld;
@@ -330,16 +354,8 @@ trtri256_kernel(const float* __restrict__ Sall, int64_t ld, int c0, void* __rest
         for (int i = t + 1 + tr; i < T; i += 8) X[i][tc] -= Lc[i] * xt;
         __syncthreads();
     }
-    for (int m = tr; m < T; m += 8) {
-        const size_t o = ((size_t)K * T + m) * T + 32 * b + tc;
-        const float x = X[m][tc];
-        if constexpr (BF16) reinterpret_cast<__nv_bfloat16*>(Ap)[o] = __float2bfloat16_rn(x);
-        else {
-            uint32_t y;
-            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
-            reinterpret_cast<uint32_t*>(Ap)[o] = y;
-        }
-    }
+    for (int m = tr; m < T; m += 8)
+        op_put<BF16, true>(Ap, ((size_t)K * T + m) * (size_t)(nseg * T), T, 32 * b + tc, nseg, X[m][tc]);
 }
 
 }  // namespace
@@ -350,28 +366,28 @@ cudaError_t gemm_tc_trsm256(const LUPlan& P, int c0, int j0, int j1, cudaStream_
     const int N = j1 - j0, Kd = LU_NB;
     if (N <= 0) return cudaSuccess;
     if (!encoder()) return cudaErrorNotSupported;
-    // TF32 in both mixed modes: the inverse of L11 amplifies operand rounding,
-    // and BF16 here leaves the factors too inexact for the FP64 refinement
+    // split TF32 in every mixed mode: the explicit inverse of L11 amplifies
+    // operand rounding, and one-pass TF32 or BF16 here leaves the factors too
+    // inexact for the FP64 refinement
     const bool bf16 = false;
+    const int nseg = 3;
     const int es = bf16 ? 2 : 4;
     const int chunk_k = CHUNK_BYTES / es;
-    const int nchunk = Kd / chunk_k;
+    const int nchunk = nseg * Kd / chunk_k;
     unsigned char* w = reinterpret_cast<unsigned char*>(P.work) + perm_bytes(P.nK);
-    size_t pan = ((size_t)P.nK * P.ld * LU_NB * 4 + 255) & ~(size_t)255;
+    const size_t pan = panel_bytes(P.nK, P.ld);
     void* Ap = w;
     void* Bp = w + pan;
     {
         dim3 gt(LU_NB / 32, (unsigned)P.nK);
-        if (bf16) trtri256_kernel<true><<<gt, 256, 0, st>>>((const float*)P.S, P.ld, c0, Ap);
-        else trtri256_kernel<false><<<gt, 256, 0, st>>>((const float*)P.S, P.ld, c0, Ap);
+        trtri256_kernel<false><<<gt, 256, 0, st>>>((const float*)P.S, P.ld, c0, nseg, Ap);
     }
     dim3 gb((unsigned)((N + 7) / 8), 1, (unsigned)P.nK);
-    if (bf16) pack_B_kernel<true><<<gb, 256, 0, st>>>((const float*)P.S, P.ld, c0, j0, N, Kd, Kd, Bp);
-    else pack_B_kernel<false><<<gb, 256, 0, st>>>((const float*)P.S, P.ld, c0, j0, N, Kd, Kd, Bp);
+    pack_B_kernel<false><<<gb, 256, 0, st>>>((const float*)P.S, P.ld, c0, j0, N, Kd, Kd, nseg, Bp);
     MEHDG_COUNT(2);
     const int BN = N >= 128 ? 128 : (N >= 64 ? 64 : 32);
     CUtensorMap ma, mb;
-    if (!make_map(&ma, Ap, bf16, Kd, 256, P.nK, TM) || !make_map(&mb, Bp, bf16, Kd, N, P.nK, BN))
+    if (!make_map(&ma, Ap, bf16, nseg * Kd, 256, P.nK, TM) || !make_map(&mb, Bp, bf16, nseg * Kd, N, P.nK, BN))
         return cudaErrorInvalidValue;
 #define LS(BNV) (bf16 ? launch_tc<BNV, true, true>(ma, mb, P, c0, j0, 256, N, nchunk, st) \
                       : launch_tc<BNV, false, true>(ma, mb, P, c0, j0, 256, N, nchunk, st))
@@ -383,38 +399,37 @@ cudaError_t gemm_tc_trsm256(const LUPlan& P, int c0, int j0, int j1, cudaStream_
 
 size_t gemm_tc_work_bytes(int64_t nK, int64_t ld, int prec) {
     (void)prec;
-    // two panels of at most ld x 256 FP32 per element, each 256-byte aligned
-    size_t pan = (size_t)nK * ld * LU_NB * 4;
-    pan = (pan + 255) & ~(size_t)255;
-    return 2 * pan;
+    // two panels of at most ld x (3 x 256) FP32 per element (split precision)
+    return 2 * panel_bytes(nK, ld);
 }
 
 cudaError_t gemm_tc_update(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st) {
     if (M <= 0 || N <= 0) return cudaSuccess;
     if (M < TM) return gemm_simt_update_f32(P, r0, c0, k0, M, N, Kd, st);   // a few tiny inner updates
     if (!encoder()) return cudaErrorNotSupported;
-    const bool bf16 = P.prec == MEHDG_MIXED_BF16;
+    const bool bf16 = P.prec == MEHDG_MIXED_BF16 || P.prec == MEHDG_MIXED_BF16X3;
+    const int nseg = (P.prec == MEHDG_MIXED_TF32X3 || P.prec == MEHDG_MIXED_BF16X3) ? 3 : 1;
     const int es = bf16 ? 2 : 4;
     const int chunk_k = CHUNK_BYTES / es;
     const int Kp = (Kd + chunk_k - 1) / chunk_k * chunk_k;
-    const int nchunk = Kp / chunk_k;
+    const int nchunk = nseg * Kp / chunk_k;
     unsigned char* w = reinterpret_cast<unsigned char*>(P.work) + perm_bytes(P.nK);
-    size_t pan = ((size_t)P.nK * P.ld * LU_NB * 4 + 255) & ~(size_t)255;
+    const size_t pan = panel_bytes(P.nK, P.ld);
     void* Ap = w;
     void* Bp = w + pan;
     // pack
     {
         dim3 g((unsigned)((M + 31) / 32), (unsigned)((Kp + 31) / 32), (unsigned)P.nK);
-        if (bf16) pack_A_kernel<true><<<g, 256, 0, st>>>((const float*)P.S, P.ld, r0, k0, M, Kd, Kp, Ap);
-        else pack_A_kernel<false><<<g, 256, 0, st>>>((const float*)P.S, P.ld, r0, k0, M, Kd, Kp, Ap);
+        if (bf16) pack_A_kernel<true><<<g, 256, 0, st>>>((const float*)P.S, P.ld, r0, k0, M, Kd, Kp, nseg, Ap);
+        else pack_A_kernel<false><<<g, 256, 0, st>>>((const float*)P.S, P.ld, r0, k0, M, Kd, Kp, nseg, Ap);
         dim3 gb((unsigned)((N + 7) / 8), 1, (unsigned)P.nK);
-        if (bf16) pack_B_kernel<true><<<gb, 256, 0, st>>>((const float*)P.S, P.ld, k0, c0, N, Kd, Kp, Bp);
-        else pack_B_kernel<false><<<gb, 256, 0, st>>>((const float*)P.S, P.ld, k0, c0, N, Kd, Kp, Bp);
+        if (bf16) pack_B_kernel<true><<<gb, 256, 0, st>>>((const float*)P.S, P.ld, k0, c0, N, Kd, Kp, nseg, Bp);
+        else pack_B_kernel<false><<<gb, 256, 0, st>>>((const float*)P.S, P.ld, k0, c0, N, Kd, Kp, nseg, Bp);
         MEHDG_COUNT(2);
     }
     const int BN = N >= 128 ? 128 : (N >= 64 ? 64 : 32);
     CUtensorMap ma, mb;
-    if (!make_map(&ma, Ap, bf16, Kp, M, P.nK, TM) || !make_map(&mb, Bp, bf16, Kp, N, P.nK, BN))
+    if (!make_map(&ma, Ap, bf16, nseg * Kp, M, P.nK, TM) || !make_map(&mb, Bp, bf16, nseg * Kp, N, P.nK, BN))
         return cudaErrorInvalidValue;
 #define LT(BNV) (bf16 ? launch_tc<BNV, true>(ma, mb, P, r0, c0, M, N, nchunk, st) \
                       : launch_tc<BNV, false>(ma, mb, P, r0, c0, M, N, nchunk, st))

@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmehdg.so")
 
 MEHDG_FLUX_EC, MEHDG_FLUX_ES, MEHDG_FLUX_KEPES = 0, 1, 2
-MEHDG_FP64, MEHDG_MIXED_TF32, MEHDG_MIXED_BF16 = 0, 1, 2
+MEHDG_FP64, MEHDG_MIXED_TF32, MEHDG_MIXED_BF16, MEHDG_MIXED_TF32X3, MEHDG_MIXED_BF16X3 = 0, 1, 2, 3, 4
 ERRORS = {0: "MEHDG_OK", -1: "MEHDG_EINVAL", -2: "MEHDG_ENONPHYS", -3: "MEHDG_ESINGULAR",
           -4: "MEHDG_ENOCONV", -5: "MEHDG_ECUDA", -6: "MEHDG_ENOMEM", -7: "MEHDG_ESTATE",
           -8: "MEHDG_ETIMEOUT"}

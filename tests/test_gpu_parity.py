@@ -89,7 +89,7 @@ def _oracle_condensed(prm, mesh, st, dvh):
 
 
 @pytest.mark.parametrize("name", ["vortex_p2m1", "vortex_p2m2", "tgv_p3m2"])
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3, 4])
 def test_condense_apply_recover_match_oracle(name, prec):
     mesh, st, kw = case(name)
     flux = 2
