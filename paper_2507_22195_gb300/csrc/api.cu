@@ -1,12 +1,17 @@
 // api.cu -- the C-ABI of include/mehdg.h and the orchestration of one Newton
-// step per macro-element (Algorithm 1, local parts):
-//   condense : R (eq. s32), S^K = A_vv assembled (eq. R1/R3), LU(S^K),
-//              y = S^-1 (-R_V) refined in FP64, bhat^K = -R_Vhat - A_vhat,v y
+// step per macro-element (Algorithm 1, local parts; eqs. R1-R6):
+//   condense : R (eq. s32); z = A_qq^-1 R_Q; S^K = A_vv - A_vq A_qq^-1 A_qv
+//              (eqs. R1, R3); LU(S^K); y = S^-1 (-R_V + A_vq z) refined in FP64;
+//              bhat^K = -R_Vhat + A_vhat,q z + (-A_vhat,v + A_vhat,q C) y
 //              (eq. R5b), summed over the two sides of every face;
-//   apply    : y = A_vhat,vhat x + A_vhat,v S^-1 (-A_v,vhat x)  (Sec. 6.3 stages 1-4);
-//   recover  : dV = S^-1 (-R_V - A_v,vhat dVhat)  (eq. R2).
+//   apply    : y = (A_vhat,vhat - A_vhat,q C_t) x + (A_vhat,v - A_vhat,q C) S^-1
+//              (-A_v,vhat + A_vq C_t) x  (Sec. 6.3 stages 1-4);
+//   recover  : dV = S^-1 (-R_V + A_vq z - (A_v,vhat - A_vq C_t) dVhat)  (eq. R2),
+//              dQ = -z - C dV - C_t dVhat  (eq. R6),
+// with C = A_qq^-1 A_qv and C_t = A_qq^-1 A_qvhat (Euler: no q, no z, C, C_t).
 // Every product with a Jacobian block other than the LU of S is matrix-free:
-// a forward-mode tangent of the FP64 residual.
+// a forward-mode tangent of the FP64 residual along (dv, dvhat, dq), with
+// the q-direction built by the line operators of qproj.cu.
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -36,6 +41,7 @@ void free_mesh(mehdg_ctx* c) {
     dfree(c->d_tRHloc); dfree(c->d_tRHloc2); dfree(c->d_tRV); dfree(c->d_xu); dfree(c->d_r); dfree(c->d_x);
     dfree(c->d_res); dfree(c->d_dx); dfree(c->d_nrm); dfree(c->d_status); dfree(c->d_iters); dfree(c->d_conv);
     dfree(c->d_cnt); dfree(c->d_S); dfree(c->d_piv); dfree(c->d_work);
+    dfree(c->d_RQ); dfree(c->d_z); dfree(c->d_dq); dfree(c->d_qt1); dfree(c->d_qt2); dfree(c->d_Minv); dfree(c->d_C1);
     if (c->h_cnt) { cudaFreeHost(c->h_cnt); c->h_cnt = nullptr; }
     c->nK = 0; c->condensed = false;
 }
@@ -47,6 +53,13 @@ ResidualArgs base_args(mehdg_ctx* c) {
     a.v = c->v; a.vs = c->vs; a.vh = c->vh; a.q = c->q;
     a.status = c->d_status;
     return a;
+}
+
+QProjArgs qargs(mehdg_ctx* c) {
+    QProjArgs q;
+    q.tab = c->tab; q.box = c->d_box; q.gid = c->d_gid; q.Minv = c->d_Minv; q.C1 = c->d_C1;
+    q.tmp1 = c->d_qt1; q.tmp2 = c->d_qt2;
+    return q;
 }
 
 LUPlan plan(mehdg_ctx* c) {
@@ -61,15 +74,33 @@ LUPlan plan(mehdg_ctx* c) {
 
 #define TRY(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { set_err(c, "%s: %s", #x, cudaGetErrorString(e_)); return MEHDG_ECUDA; } } while (0)
 
-// tangent residual: tRV (unpadded [nK][5Nn]) and tRH (per-side trace) along (dv, dvh)
-int tangent(mehdg_ctx* c, const double* dv, const double* dvh, double* tRV, double* tRH,
+bool viscous(const mehdg_ctx* c) { return c->ph.viscous != 0; }
+
+// q-direction: out = alpha A_qq^-1 R_Q + beta C x + gamma C_t xh (viscous only)
+int qproj(mehdg_ctx* c, double alpha, const double* x, double beta, const double* xh, double gamma, double* out,
+          const int32_t* skip, cudaStream_t st) {
+    TRY(launch_qproj(qargs(c), c->nK, alpha != 0.0 ? c->d_RQ : nullptr, alpha, x, beta, xh, gamma, out, skip, st));
+    return MEHDG_OK;
+}
+
+// tangent residual along (dv, dvh, dq): tRV ([nK][5][Nn]) and tRH (per-side trace)
+int tangent(mehdg_ctx* c, const double* dv, const double* dvh, const double* dq, double* tRV, double* tRH,
             const int32_t* skip, cudaStream_t st) {
     ResidualArgs a = base_args(c);
-    a.dv = dv; a.dvh = dvh; a.tRV = tRV; a.tRH = tRH; a.skip = skip;
+    a.dv = dv; a.dvh = dvh; a.dq = viscous(c) ? dq : nullptr; a.tRV = tRV; a.tRH = tRH; a.skip = skip;
     int ev = prof_begin(&c->prof, PH_TANGENT, st);
-    TRY(launch_residual(a, c->nK, c->ph.viscous, true, st));
+    TRY(launch_residual(a, c->nK, viscous(c), true, st));
     prof_end(&c->prof, ev, st, 0.0);
     return MEHDG_OK;
+}
+
+// S x = A_vv x - A_vq C x, matrix-free: tangent along (dv = x, dq = -C x)
+int apply_S(mehdg_ctx* c, const double* xu, double* out, const int32_t* skip, cudaStream_t st) {
+    if (viscous(c)) {
+        int rc = qproj(c, 0.0, xu, -1.0, nullptr, 0.0, c->d_dq, skip, st);
+        if (rc) return rc;
+    }
+    return tangent(c, xu, nullptr, c->d_dq, out, nullptr, skip, st);
 }
 
 // x (padded FP64) = S^-1 r by LU solves in the factor precision and FP64
@@ -87,7 +118,7 @@ int refine_solve(mehdg_ctx* c, const double* r, double* x, cudaStream_t st) {
         prof_end(&c->prof, ev, st, 0.0);
         TRY(launch_axpy(nK, ld, c->d_dx, x, c->d_conv, st));
         TRY(launch_copy_unpad(nK, c->Nv, ld, x, c->d_xu, 1.0, st));
-        int rc = tangent(c, c->d_xu, nullptr, c->d_tRV, nullptr, c->d_conv, st);
+        int rc = apply_S(c, c->d_xu, c->d_tRV, c->d_conv, st);
         if (rc) return rc;
         TRY(cudaMemsetAsync(c->d_cnt, 0, sizeof(int32_t), st));
         TRY(launch_refine_update(nK, c->Nv, ld, r, c->d_tRV, c->d_res, c->d_nrm, c->d_conv, c->d_iters,
@@ -143,7 +174,9 @@ int mehdg_set_mesh(mehdg_ctx* c, int64_t nK, const int32_t* p, const int32_t* m,
     for (int64_t K = 0; K < nK; ++K)
         if (p[K] != p0 || m[K] != m0) { set_err(c, "set_mesh: all elements must share p and m"); return MEHDG_EINVAL; }
     if (p0 < 1 || p0 > MEHDG_MAXP || m0 < 1 || m0 > 16) { set_err(c, "set_mesh: p in 1..4, m in 1..16"); return MEHDG_EINVAL; }
-    if (c->prm.viscous) { set_err(c, "set_mesh: the Navier-Stokes path is not built in this library version"); return MEHDG_EINVAL; }
+    if (c->prm.viscous && c->prm.prec == MEHDG_FP64 && p0 > 3) {
+        set_err(c, "set_mesh: the FP64 viscous Jacobian supports p <= 3"); return MEHDG_EINVAL;
+    }
     std::vector<int64_t> g2l(2 * G, -1);
     for (int64_t K = 0; K < nK; ++K) {
         for (int d = 0; d < 3; ++d)
@@ -164,6 +197,7 @@ int mehdg_set_mesh(mehdg_ctx* c, int64_t nK, const int32_t* p, const int32_t* m,
     c->Nt_loc = 30 * t.n2;
     c->Npad = (c->Nv + 255) / 256 * 256;
     const bool fp64 = c->prm.prec == MEHDG_FP64;
+    const bool vis = c->prm.viscous != 0;
     const size_t ts = fp64 ? 8 : 4;
     const size_t Sbytes = (size_t)nK * c->Npad * c->Npad * ts;
     size_t freeb = 0, totb = 0;
@@ -191,6 +225,12 @@ int mehdg_set_mesh(mehdg_ctx* c, int64_t nK, const int32_t* p, const int32_t* m,
     DALLOC(c->d_iters, sizeof(int32_t) * nK);
     DALLOC(c->d_conv, sizeof(int32_t) * nK);
     DALLOC(c->d_cnt, sizeof(int32_t));
+    if (vis) {
+        const size_t qb = sizeof(double) * nK * 15 * (size_t)t.Nn;
+        DALLOC(c->d_RQ, qb); DALLOC(c->d_z, qb); DALLOC(c->d_dq, qb); DALLOC(c->d_qt1, qb); DALLOC(c->d_qt2, qb);
+        DALLOC(c->d_Minv, sizeof(double) * t.n * t.n);
+        DALLOC(c->d_C1, sizeof(double) * t.n * t.n);
+    }
     DALLOC(c->d_S, Sbytes);
     DALLOC(c->d_piv, sizeof(int32_t) * nK * c->Npad);
     c->work_bytes = lu_work_bytes(nK, c->Npad, fp64, c->prm.prec);
@@ -203,6 +243,14 @@ int mehdg_set_mesh(mehdg_ctx* c, int64_t nK, const int32_t* p, const int32_t* m,
         cudaMemset(c->d_status, 0, sizeof(int32_t) * nK) != cudaSuccess ||
         cudaMemset(c->d_iters, 0, sizeof(int32_t) * nK) != cudaSuccess) {
         set_err(c, "set_mesh: copy failed"); free_mesh(c); return MEHDG_ECUDA;
+    }
+    if (vis) {
+        std::vector<double> Minv(t.n * t.n), C1(t.n * t.n);
+        host_build_qtables(t, Minv.data(), C1.data());
+        if (cudaMemcpy(c->d_Minv, Minv.data(), sizeof(double) * t.n * t.n, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(c->d_C1, C1.data(), sizeof(double) * t.n * t.n, cudaMemcpyHostToDevice) != cudaSuccess) {
+            set_err(c, "set_mesh: copy failed"); free_mesh(c); return MEHDG_ECUDA;
+        }
     }
     return MEHDG_OK;
 }
@@ -226,9 +274,9 @@ int mehdg_residual(mehdg_ctx* c, double* R_V, double* R_Q, double* R_Vhat, void*
     cudaStream_t st = (cudaStream_t)stream;
     TRY(cudaMemsetAsync(c->d_status, 0, sizeof(int32_t) * c->nK, st));
     ResidualArgs a = base_args(c);
-    a.RV = R_V; a.RQ = c->ph.viscous ? R_Q : nullptr; a.RH = c->d_RHloc;
+    a.RV = R_V; a.RQ = viscous(c) ? R_Q : nullptr; a.RH = c->d_RHloc;
     int ev = prof_begin(&c->prof, PH_RESIDUAL, st);
-    TRY(launch_residual(a, c->nK, c->ph.viscous, false, st));
+    TRY(launch_residual(a, c->nK, viscous(c), false, st));
     prof_end(&c->prof, ev, st, 0.0);
     TRY(launch_trace_gather(c->d_RHloc, c->d_g2l, c->G, c->tab.n2, R_Vhat, 1.0, nullptr, 0.0, st));
     return MEHDG_OK;
@@ -241,35 +289,43 @@ int mehdg_condense(mehdg_ctx* c, double* bhat, double* Ahat_local, void* stream)
     if (Ahat_local) { set_err(c, "condense: the explicit A-hat^K is not formed; use mehdg_apply_condensed"); return MEHDG_EINVAL; }
     cudaStream_t st = (cudaStream_t)stream;
     const bool fp64 = c->prm.prec == MEHDG_FP64;
+    const bool vis = viscous(c);
     const int64_t nK = c->nK, ld = c->Npad;
     TRY(cudaMemsetAsync(c->d_status, 0, sizeof(int32_t) * nK, st));
     TRY(cudaMemsetAsync(c->d_iters, 0, sizeof(int32_t) * nK, st));
     // residual at the state
     ResidualArgs a = base_args(c);
-    a.RV = c->d_RV; a.RH = c->d_RHloc;
+    a.RV = c->d_RV; a.RH = c->d_RHloc; a.RQ = vis ? c->d_RQ : nullptr;
     int ev = prof_begin(&c->prof, PH_RESIDUAL, st);
-    TRY(launch_residual(a, nK, c->ph.viscous, false, st));
+    TRY(launch_residual(a, nK, vis, false, st));
     prof_end(&c->prof, ev, st, 0.0);
-    // S^K = A_vv (dense), padded identity
+    // z = A_qq^-1 R_Q
+    int rc;
+    if (vis && (rc = qproj(c, 1.0, nullptr, 0.0, nullptr, 0.0, c->d_z, nullptr, st))) return rc;
+    // S^K = A_vv - A_vq C (dense), padded identity
     ev = prof_begin(&c->prof, PH_JACOBIAN, st);
     TRY(cudaMemsetAsync(c->d_S, 0, (size_t)nK * ld * ld * (fp64 ? 8 : 4), st));
     TRY(launch_pad_identity(c->d_S, nK, ld, c->Nv, fp64, st));
     JacobianArgs ja;
     ja.tab = c->tab; ja.ph = c->ph; ja.box = c->d_box; ja.v = c->v; ja.vs = c->vs; ja.vh = c->vh; ja.q = c->q;
-    ja.gid = c->d_gid; ja.S = c->d_S; ja.ld = ld; ja.status = c->d_status;
+    ja.gid = c->d_gid; ja.S = c->d_S; ja.ld = ld; ja.status = c->d_status; ja.C1 = c->d_C1;
     TRY(launch_jacobian(ja, nK, fp64, st));
     prof_end(&c->prof, ev, st, 0.0);
     // LU
     LUPlan P = plan(c);
     TRY(lu_factor(P, st));
-    // y = S^-1 (-R_V)
-    TRY(launch_set_rhs(nK, c->Nv, ld, c->tab.Nn, c->d_RV, -1.0, nullptr, 0.0, c->d_r, st));
-    int rc = refine_solve(c, c->d_r, c->d_x, st);
-    if (rc) return rc;
-    // bhat^K = -R_Vhat^K - A_vhat,v y, summed over sides
+    // y = S^-1 (-R_V + A_vq z)
+    if (vis) {
+        if ((rc = tangent(c, nullptr, nullptr, c->d_z, c->d_tRV, nullptr, nullptr, st))) return rc;
+        TRY(launch_set_rhs(nK, c->Nv, ld, c->tab.Nn, c->d_RV, -1.0, c->d_tRV, 1.0, c->d_r, st));
+    } else {
+        TRY(launch_set_rhs(nK, c->Nv, ld, c->tab.Nn, c->d_RV, -1.0, nullptr, 0.0, c->d_r, st));
+    }
+    if ((rc = refine_solve(c, c->d_r, c->d_x, st))) return rc;
+    // bhat^K = -R_Vhat^K - dR_Vhat[dv = y, dq = -C y - z], summed over sides
     TRY(launch_copy_unpad(nK, c->Nv, ld, c->d_x, c->d_xu, 1.0, st));
-    rc = tangent(c, c->d_xu, nullptr, c->d_tRV, c->d_tRHloc, nullptr, st);
-    if (rc) return rc;
+    if (vis && (rc = qproj(c, -1.0, c->d_xu, -1.0, nullptr, 0.0, c->d_dq, nullptr, st))) return rc;
+    if ((rc = tangent(c, c->d_xu, nullptr, c->d_dq, c->d_tRV, c->d_tRHloc, nullptr, st))) return rc;
     TRY(launch_trace_gather(c->d_RHloc, c->d_g2l, c->G, c->tab.n2, bhat, -1.0, nullptr, 0.0, st));
     TRY(launch_trace_gather(c->d_tRHloc, c->d_g2l, c->G, c->tab.n2, bhat, -1.0, bhat, 1.0, st));
     c->condensed = true;
@@ -281,38 +337,39 @@ int mehdg_apply_condensed(mehdg_ctx* c, const double* x, double* y, void* stream
     if (!c->condensed) { set_err(c, "apply_condensed before condense"); return MEHDG_ESTATE; }
     if (!x || !y) return MEHDG_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
+    const bool vis = viscous(c);
     const int64_t nK = c->nK, ld = c->Npad;
-    // stage 1: A_v,vhat x and A_vhat,vhat x (tangent along vhat)
-    int rc = tangent(c, nullptr, x, c->d_tRV, c->d_tRHloc2, nullptr, st);
-    if (rc) return rc;
-    // stage 2: y2 = S^-1 (-A_v,vhat x)
+    int rc;
+    // stage 1: y1 = -dR_V[dvhat = x, dq = -C_t x]
+    if (vis && (rc = qproj(c, 0.0, nullptr, 0.0, x, -1.0, c->d_dq, nullptr, st))) return rc;
+    if ((rc = tangent(c, nullptr, x, c->d_dq, c->d_tRV, nullptr, nullptr, st))) return rc;
+    // stage 2: y2 = S^-1 y1
     TRY(launch_set_rhs(nK, c->Nv, ld, c->tab.Nn, c->d_tRV, -1.0, nullptr, 0.0, c->d_r, st));
-    rc = refine_solve(c, c->d_r, c->d_x, st);
-    if (rc) return rc;
-    // stage 3: A_vhat,v y2
+    if ((rc = refine_solve(c, c->d_r, c->d_x, st))) return rc;
+    // stages 3-4: y = dR_Vhat[dv = y2, dvhat = x, dq = -C y2 - C_t x], summed over sides
     TRY(launch_copy_unpad(nK, c->Nv, ld, c->d_x, c->d_xu, 1.0, st));
-    rc = tangent(c, c->d_xu, nullptr, c->d_tRV, c->d_tRHloc, nullptr, st);
-    if (rc) return rc;
-    // stage 4: assembly over the sides of every face
-    TRY(launch_trace_gather(c->d_tRHloc2, c->d_g2l, c->G, c->tab.n2, y, 1.0, nullptr, 0.0, st));
-    TRY(launch_trace_gather(c->d_tRHloc, c->d_g2l, c->G, c->tab.n2, y, 1.0, y, 1.0, st));
+    if (vis && (rc = qproj(c, 0.0, c->d_xu, -1.0, x, -1.0, c->d_dq, nullptr, st))) return rc;
+    if ((rc = tangent(c, c->d_xu, x, c->d_dq, c->d_tRV, c->d_tRHloc, nullptr, st))) return rc;
+    TRY(launch_trace_gather(c->d_tRHloc, c->d_g2l, c->G, c->tab.n2, y, 1.0, nullptr, 0.0, st));
     return MEHDG_OK;
 }
 
 int mehdg_recover(mehdg_ctx* c, const double* dVhat, double* dV, double* dQ, void* stream) {
     if (!c) return MEHDG_EINVAL;
-    (void)dQ;
     if (!c->condensed) { set_err(c, "recover before condense"); return MEHDG_ESTATE; }
-    if (!dVhat || !dV) return MEHDG_EINVAL;
+    if (!dVhat || !dV || (viscous(c) && !dQ)) return MEHDG_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
+    const bool vis = viscous(c);
     const int64_t nK = c->nK, ld = c->Npad;
-    int rc = tangent(c, nullptr, dVhat, c->d_tRV, c->d_tRHloc2, nullptr, st);
-    if (rc) return rc;
-    // eq. R2: S dV = -R_V - A_v,vhat dVhat
+    int rc;
+    // eq. R2: S dV = -R_V - dR_V[dvhat = dVhat, dq = -z - C_t dVhat]
+    if (vis && (rc = qproj(c, -1.0, nullptr, 0.0, dVhat, -1.0, c->d_dq, nullptr, st))) return rc;
+    if ((rc = tangent(c, nullptr, dVhat, c->d_dq, c->d_tRV, nullptr, nullptr, st))) return rc;
     TRY(launch_set_rhs(nK, c->Nv, ld, c->tab.Nn, c->d_RV, -1.0, c->d_tRV, -1.0, c->d_r, st));
-    rc = refine_solve(c, c->d_r, c->d_x, st);
-    if (rc) return rc;
+    if ((rc = refine_solve(c, c->d_r, c->d_x, st))) return rc;
     TRY(launch_copy_unpad(nK, c->Nv, ld, c->d_x, dV, 1.0, st));
+    // eq. R6: dQ = -z - C dV - C_t dVhat
+    if (vis && (rc = qproj(c, -1.0, dV, -1.0, dVhat, -1.0, dQ, nullptr, st))) return rc;
     return MEHDG_OK;
 }
 

@@ -160,6 +160,12 @@ struct mehdg_ctx {
     double* d_tRHloc2 = nullptr;        // second tangent trace buffer
     double* d_tRV = nullptr;            // tangent of R_V
     double* d_xu = nullptr;             // [nK][5][Nn] unpadded solution (tangent direction)
+    // viscous: gradient-equation data, q-shaped [nK][15][Nn]
+    double* d_RQ = nullptr;             // R_Q at the condensed state
+    double* d_z = nullptr;              // A_qq^-1 R_Q
+    double* d_dq = nullptr;             // q-direction of a tangent
+    double *d_qt1 = nullptr, *d_qt2 = nullptr;   // line-operator scratch
+    double *d_Minv = nullptr, *d_C1 = nullptr;   // [n][n] 1-D tables
     double* d_r = nullptr;              // [nK][Npad] FP64 right-hand side
     double* d_x = nullptr;              // [nK][Npad] FP64 solution
     double* d_res = nullptr;            // [nK][Npad] FP64 refinement residual

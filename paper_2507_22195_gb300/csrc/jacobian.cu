@@ -292,6 +292,222 @@ jac_face_kernel(JacobianArgs a) {
     }
 }
 
+// ---------------------------------------------------------------- viscous: -A_vq C
+// Q-elimination term of S = A_vv - A_vq A_qq^-1 A_qv (eq. R3).  A_qq = I x M
+// with M a tensor product of 1-D mass matrices, so C = A_qq^-1 A_qv acts on
+// the q-component (l, d) along the d-lines only: C = (2/h_d) C1_ref (x) I.
+// Per micro-element and direction d, the block
+//   E[(a,k),(c,l)] = sum_x W d_j phi_a phi_c dG_kj/dq_ld      (= -A_vq, q-direction d)
+// is sum-factorised as for A_vv and then multiplied by C along d:
+//   S[(a,k),(b,l)] += sum_{c_d} E[(a,k),(c_d,b_perp)] (2/h_d) C1_ref[c_d][b_d],
+// b_d running over the whole d-line of the macro-element.
+template <class TS>
+__global__ void __launch_bounds__(256)
+jac_visc_q_volume_kernel(JacobianArgs a, const double* __restrict__ C1) {
+    const Tab& tb = a.tab;
+    const int K = blockIdx.y, e = blockIdx.x;
+    const int p = tb.p, m = tb.m, n = tb.n, ng = tb.ng, Nn = tb.Nn, nl = tb.nl, npt = tb.npt, p1 = p + 1;
+    const int PP = p1 * p1, G2 = ng * ng;
+    const int eo[3] = {(e % m) * p, ((e / m) % m) * p, (e / (m * m)) * p};
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* sL = reinterpret_cast<double*>(smem_raw);
+    double* sD = sL + MEHDG_MAXG * (MEHDG_MAXP + 1);
+    double* sW = sD + MEHDG_MAXG * (MEHDG_MAXP + 1);
+    double* C1s = sW + 8;                                    // [n][n]
+    double* vl = C1s + n * n;                                // [5][nl]
+    double* vx = vl + 5 * nl;                                // [npt][5]
+    TS* Mt = reinterpret_cast<TS*>(vx + 5 * npt);            // [3][2][ng][PP]
+    TS* P = Mt + 6 * ng * PP;                                // [npt][100]
+    TS* H1 = P + (size_t)npt * 100;                          // [4][PP][G2]
+    TS* H2 = H1 + 4 * PP * G2;                               // [4][PP][PP][ng]
+    TS* E = H2 + 4 * PP * PP * ng;                           // [PP^3]
+    const int tid = threadIdx.x, nth = blockDim.x;
+    load_tables(tb, sL, sD, sW);
+    double sc[3], hw[3];
+    geometry(a, K, sc, hw);
+    for (int i = tid; i < n * n; i += nth) C1s[i] = C1[i];
+    const int64_t oV = (int64_t)K * 5 * Nn;
+    for (int i = tid; i < nl; i += nth) {
+        int A = (eo[0] + i % p1) + n * ((eo[1] + (i / p1) % p1) + n * (eo[2] + i / (p1 * p1)));
+        for (int k = 0; k < 5; ++k) vl[k * nl + i] = a.v[oV + k * Nn + A];
+    }
+    __syncthreads();
+    for (int i = tid; i < 6 * ng * PP; i += nth) {
+        int ab = i % PP, g = (i / PP) % ng, dt = i / (PP * ng), d = dt >> 1, tau = dt & 1;
+        int aa = ab / p1, bb = ab % p1;
+        double t = tau ? sD[g * p1 + aa] * sc[d] : sL[g * p1 + aa];
+        Mt[i] = (TS)(t * sL[g * p1 + bb]);
+    }
+    for (int x = tid; x < npt; x += nth) {
+        int g1 = x % ng, g2 = (x / ng) % ng, g3 = x / (ng * ng);
+        double s5[5] = {0, 0, 0, 0, 0};
+        for (int i = 0; i < nl; ++i) {
+            double f = sL[g1 * p1 + i % p1] * sL[g2 * p1 + (i / p1) % p1] * sL[g3 * p1 + i / (p1 * p1)];
+            for (int k = 0; k < 5; ++k) s5[k] += f * vl[k * nl + i];
+        }
+        for (int k = 0; k < 5; ++k) vx[x * 5 + k] = s5[k];
+    }
+    __syncthreads();
+    TS* S = reinterpret_cast<TS*>(a.S) + (size_t)K * a.ld * a.ld;
+    const TS* M1 = Mt;
+    const TS* M2 = Mt + 2 * ng * PP;
+    const TS* M3 = Mt + 4 * ng * PP;
+    for (int d = 0; d < 3; ++d) {
+        // point blocks P[x][1+j][k*5+l] = W dG_kj/dq_ld (G is linear in q)
+        for (int x = tid; x < npt; x += nth) {
+            int g1 = x % ng, g2 = (x / ng) % ng, g3 = x / (ng * ng);
+            Dual<15> v15[5], q15[15], G[5][3];
+            for (int k = 0; k < 5; ++k) v15[k] = mkdual<15>(vx[x * 5 + k]);
+            for (int c = 0; c < 15; ++c) { q15[c] = mkdual<15>(0.0); q15[c].d[c] = 1.0; }
+            visc_flux(v15, q15, a.ph, G);
+            double W = sW[g1] * hw[0] * sW[g2] * hw[1] * sW[g3] * hw[2];
+            TS* Px = P + (size_t)x * 100;
+            for (int kl = 0; kl < 25; ++kl) Px[kl] = (TS)0;
+            for (int j = 0; j < 3; ++j)
+                for (int k = 0; k < 5; ++k)
+                    for (int l = 0; l < 5; ++l) Px[25 * (1 + j) + k * 5 + l] = (TS)(W * G[k][j].d[l * 3 + d]);
+        }
+        __syncthreads();
+        const double cs = sc[d];        // 2/h_d
+        for (int kl = 0; kl < 25; ++kl) {
+            for (int i = tid; i < 4 * PP * G2; i += nth) {
+                int g23 = i % G2, ab1 = (i / G2) % PP, al = i / (G2 * PP);
+                const TS* Mx = M1 + (al == 1 ? ng * PP : 0);
+                TS s = 0;
+                if (al) for (int g1 = 0; g1 < ng; ++g1) s += Mx[g1 * PP + ab1] * P[(size_t)(g1 + ng * g23) * 100 + 25 * al + kl];
+                H1[i] = s;
+            }
+            __syncthreads();
+            for (int i = tid; i < 4 * PP * PP * ng; i += nth) {
+                int g3 = i % ng, ab2 = (i / ng) % PP, ab1 = (i / (ng * PP)) % PP, al = i / (ng * PP * PP);
+                const TS* My = M2 + (al == 2 ? ng * PP : 0);
+                const TS* h = H1 + ((size_t)al * PP + ab1) * G2 + ng * g3;
+                TS s = 0;
+                if (al) for (int g2 = 0; g2 < ng; ++g2) s += My[g2 * PP + ab2] * h[g2];
+                H2[i] = s;
+            }
+            __syncthreads();
+            for (int i = tid; i < PP * PP * PP; i += nth) {
+                int ab3 = i % PP, ab2 = (i / PP) % PP, ab1 = i / (PP * PP);
+                TS s = 0;
+                for (int al = 1; al < 4; ++al) {
+                    const TS* Mz = M3 + (al == 3 ? ng * PP : 0);
+                    const TS* h = H2 + (((size_t)al * PP + ab1) * PP + ab2) * ng;
+                    for (int g3 = 0; g3 < ng; ++g3) s += Mz[g3 * PP + ab3] * h[g3];
+                }
+                E[i] = s;
+            }
+            __syncthreads();
+            // multiply by C along d and add into S: (a, c_perp, b_d)
+            const int k = kl / 5, l = kl % 5;
+            const int dA = d == 0 ? 1 : 0, dB = d == 2 ? 1 : 2;       // the two other directions
+            for (int i = tid; i < nl * PP * n; i += nth) {
+                int bd = i % n, cp = (i / n) % PP, ia = i / (n * PP);
+                int la[3] = {ia % p1, (ia / p1) % p1, ia / (p1 * p1)};
+                int lc[3];
+                lc[dA] = cp % p1; lc[dB] = cp / p1;
+                double s = 0.0;
+                for (int cd = 0; cd <= p; ++cd) {
+                    lc[d] = cd;
+                    int ab1 = la[0] * p1 + lc[0], ab2 = la[1] * p1 + lc[1], ab3 = la[2] * p1 + lc[2];
+                    s += (double)E[(ab1 * PP + ab2) * PP + ab3] * C1s[(eo[d] + cd) * n + bd];
+                }
+                int A = (eo[0] + la[0]) + n * ((eo[1] + la[1]) + n * (eo[2] + la[2]));
+                int bc[3] = {eo[0] + lc[0], eo[1] + lc[1], eo[2] + lc[2]};
+                bc[d] = bd;
+                int B = bc[0] + n * (bc[1] + n * bc[2]);
+                atomic_add_t(&S[(size_t)(A * 5 + k) + (size_t)(B * 5 + l) * a.ld], s * cs);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// face part of -A_vq C: G-hat = G(vhat, q).n depends on the interior q at the
+// face points, A_vq(face) = sum_x w mu_a dGhat_k/dq_ld phi_c (face nodes c),
+// multiplied by C along d (the normal line for d = the face direction).
+template <class TS>
+__global__ void __launch_bounds__(256)
+jac_visc_q_face_kernel(JacobianArgs a, const double* __restrict__ C1) {
+    const Tab& tb = a.tab;
+    const int K = blockIdx.y;
+    const int p = tb.p, m = tb.m, n = tb.n, ng = tb.ng, n2 = tb.n2, p1 = p + 1;
+    const int f = blockIdx.x / (m * m), e = blockIdx.x % (m * m);
+    const int e1 = e % m, e2 = e / m;
+    const int df = f / 2, t1 = df == 0 ? 1 : 0, t2 = df == 2 ? 1 : 2;
+    const double sgn = (f & 1) ? 1.0 : -1.0;
+    const int iface = (f & 1) ? n - 1 : 0;
+    const int fl = p1 * p1, fpt = ng * ng;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* sL = reinterpret_cast<double*>(smem_raw);
+    double* sW = sL + MEHDG_MAXG * (MEHDG_MAXP + 1);
+    double* C1s = sW + 8;             // [n][n]
+    double* fh = C1s + n * n;         // [5][fl]
+    TS* PF = reinterpret_cast<TS*>(fh + 5 * fl);   // [fpt][3][25]
+    TS* E = PF + (size_t)fpt * 75;                  // [fl][fl]
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (int i = tid; i < ng * p1; i += nth) sL[i] = tb.L[i / p1][i % p1];
+    if (tid < ng) sW[tid] = tb.w[tid];
+    for (int i = tid; i < n * n; i += nth) C1s[i] = C1[i];
+    const double* box = a.box + 6 * K;
+    double h[3];
+    for (int d = 0; d < 3; ++d) h[d] = (box[3 + d] - box[d]) / m;
+    const double hw1 = 0.5 * h[t1], hw2 = 0.5 * h[t2];
+    const int64_t og = a.gid[6 * K + f] * 5 * n2;
+    for (int i = tid; i < fl; i += nth) {
+        int c1 = e1 * p + i % p1, c2 = e2 * p + i / p1;
+        for (int k = 0; k < 5; ++k) fh[k * fl + i] = a.vh[og + k * n2 + c1 + n * c2];
+    }
+    __syncthreads();
+    for (int x = tid; x < fpt; x += nth) {
+        int g1 = x % ng, g2 = x / ng;
+        Dual<15> v15[5], q15[15], G[5][3];
+        for (int k = 0; k < 5; ++k) {
+            double s = 0.0;
+            for (int i = 0; i < fl; ++i) s += sL[g1 * p1 + i % p1] * sL[g2 * p1 + i / p1] * fh[k * fl + i];
+            v15[k] = mkdual<15>(s);
+        }
+        for (int c = 0; c < 15; ++c) { q15[c] = mkdual<15>(0.0); q15[c].d[c] = 1.0; }
+        visc_flux(v15, q15, a.ph, G);
+        const double W = sW[g1] * hw1 * sW[g2] * hw2 * sgn;
+        for (int d = 0; d < 3; ++d)
+            for (int k = 0; k < 5; ++k)
+                for (int l = 0; l < 5; ++l) PF[(size_t)x * 75 + d * 25 + k * 5 + l] = (TS)(W * G[k][df].d[l * 3 + d]);
+    }
+    __syncthreads();
+    TS* S = reinterpret_cast<TS*>(a.S) + (size_t)K * a.ld * a.ld;
+    for (int d = 0; d < 3; ++d) {
+        const double cs = 2.0 / h[d];
+        for (int kl = 0; kl < 25; ++kl) {
+            for (int r = tid; r < fl * fl; r += nth) {
+                int ia = r / fl, ic = r % fl;
+                TS s = 0;
+                for (int x = 0; x < fpt; ++x) {
+                    int g1 = x % ng, g2 = x / ng;
+                    s += (TS)(sL[g1 * p1 + ia % p1] * sL[g2 * p1 + ia / p1] * sL[g1 * p1 + ic % p1] *
+                              sL[g2 * p1 + ic / p1]) * PF[(size_t)x * 75 + d * 25 + kl];
+                }
+                E[r] = s;
+            }
+            __syncthreads();
+            const int k = kl / 5, l = kl % 5;
+            for (int i = tid; i < fl * fl * n; i += nth) {
+                int bd = i % n, ic = (i / n) % fl, ia = i / (n * fl);
+                int ca[3], cc[3];
+                ca[df] = iface; ca[t1] = e1 * p + ia % p1; ca[t2] = e2 * p + ia / p1;
+                cc[df] = iface; cc[t1] = e1 * p + ic % p1; cc[t2] = e2 * p + ic / p1;
+                const int cd = cc[d];
+                cc[d] = bd;
+                int A = ca[0] + n * (ca[1] + n * ca[2]);
+                int B = cc[0] + n * (cc[1] + n * cc[2]);
+                atomic_add_t(&S[(size_t)(A * 5 + k) + (size_t)(B * 5 + l) * a.ld],
+                             -(double)E[ic + fl * ia] * C1s[cd * n + bd] * cs);
+            }
+            __syncthreads();
+        }
+    }
+}
+
 template <class TS>
 __global__ void pad_identity_kernel(TS* S, int64_t ld, int Nv) {
     int K = blockIdx.y;
@@ -338,6 +554,22 @@ cudaError_t launch_jacobian(const JacobianArgs& a, int64_t nK, bool fp64, cudaSt
     else { if (visc) LJ(float, true); else LJ(float, false); }
 #undef LJ
     MEHDG_COUNT(2);
+    if (visc) {
+        const size_t PP = (size_t)(t.p + 1) * (t.p + 1), G2 = (size_t)t.ng * t.ng;
+        size_t sq = sizeof(double) * (HEAD_DOUBLES + (size_t)t.n * t.n + 5 * (size_t)t.nl + 5 * (size_t)t.npt)
+                  + ts * (6 * (size_t)t.ng * PP + 100 * (size_t)t.npt + 4 * PP * G2 + 4 * PP * PP * t.ng + PP * PP * PP) + 16;
+        size_t sqf = sizeof(double) * (MEHDG_MAXG * (MEHDG_MAXP + 1) + 8 + (size_t)t.n * t.n + 5 * (size_t)fl)
+                   + ts * (75 * (size_t)fpt + (size_t)fl * fl) + 16;
+        if (sq > 227 * 1024) return cudaErrorInvalidValue;      // FP64 at p = 4: not supported
+#define LQ(TS)                                                                                          \
+        do { cudaFuncSetAttribute(jac_visc_q_volume_kernel<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sq); \
+             cudaFuncSetAttribute(jac_visc_q_face_kernel<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sqf); \
+             jac_visc_q_volume_kernel<TS><<<gv, b, sq, st>>>(a, a.C1);                                 \
+             jac_visc_q_face_kernel<TS><<<gf, b, sqf, st>>>(a, a.C1); } while (0)
+        if (fp64) LQ(double); else LQ(float);
+#undef LQ
+        MEHDG_COUNT(2);
+    }
     return cudaGetLastError();
 }
 

@@ -19,6 +19,20 @@ cudaError_t launch_residual(const ResidualArgs& a, int64_t nK, bool visc, bool t
 cudaError_t launch_trace_gather(const double* loc, const int64_t* g2l, int64_t G, int n2, double* out,
                                 double alpha, const double* add, double beta, cudaStream_t st);
 
+// gradient-equation line operators (qproj.cu), q-shaped outputs [nK][15][Nn]:
+// out = alpha A_qq^-1 Rq + beta A_qq^-1 A_qv x + gamma A_qq^-1 A_qvhat xh
+struct QProjArgs {
+    Tab tab;
+    const double* box;
+    const int64_t* gid;
+    const double* Minv;       // [n][n] M1_ref^-1
+    const double* C1;         // [n][n] M1_ref^-1 G1_ref
+    double *tmp1, *tmp2;      // [nK][15][Nn] scratch
+};
+cudaError_t launch_qproj(const QProjArgs& q, int64_t nK, const double* Rq, double alpha, const double* x, double beta,
+                         const double* xh, double gamma, double* out, const int32_t* skip, cudaStream_t st);
+void host_build_qtables(const Tab& t, double* Minv_ref, double* C1_ref);
+
 // dense S^K assembly (col-major, leading dimension ld = Npad), element by element
 struct JacobianArgs {
     Tab tab;
@@ -29,6 +43,7 @@ struct JacobianArgs {
     void* S;                  // float or double [nK][ld][ld]
     int64_t ld;
     int32_t* status;
+    const double* C1;         // [n][n] M1_ref^-1 G1_ref (viscous only)
 };
 cudaError_t launch_jacobian(const JacobianArgs& a, int64_t nK, bool fp64, cudaStream_t st);
 cudaError_t launch_pad_identity(void* S, int64_t nK, int64_t ld, int Nv, bool fp64, cudaStream_t st);

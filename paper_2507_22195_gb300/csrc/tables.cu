@@ -8,6 +8,8 @@
 // the barycentric form.
 #include <cmath>
 #include <cstring>
+#include <utility>
+#include <vector>
 #include "common.cuh"
 
 namespace {
@@ -102,4 +104,46 @@ void host_build_tables(int p, int m, Tab* t) {
             t->dL[g][l] = Ll * (S1 - 1.0 / (z - xi[l]));
         }
     }
+}
+
+// 1-D operators of the gradient equation (eq. s32a) on the macro grid of one
+// direction, for a reference micro-interval of length 2 (physical operators:
+// M1 = (h/2) M1_ref, G1 = G1_ref):
+//   M1_ref[a][b] = sum_e sum_g w_g phi_a phi_b,  G1_ref[a][b] = sum_e sum_g w_g phi_b dphi_a/dxi
+// Outputs (n x n, row-major): Minv_ref = M1_ref^-1 and C1_ref = M1_ref^-1 G1_ref,
+// so that A_qq^-1 A_qv acts along the d-lines as (2/h_d) C1_ref.
+void host_build_qtables(const Tab& t, double* Minv_ref, double* C1_ref) {
+    const int n = t.n, p = t.p, m = t.m;
+    std::vector<double> M(n * n, 0.0), G(n * n, 0.0), A(n * 2 * n, 0.0);
+    for (int e = 0; e < m; ++e)
+        for (int g = 0; g < t.ng; ++g)
+            for (int la = 0; la <= p; ++la)
+                for (int lb = 0; lb <= p; ++lb) {
+                    int a = e * p + la, b = e * p + lb;
+                    M[a * n + b] += t.w[g] * t.L[g][la] * t.L[g][lb];
+                    G[a * n + b] += t.w[g] * t.L[g][lb] * t.dL[g][la];
+                }
+    // Gauss-Jordan with partial pivoting on [M | I]
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) { A[i * 2 * n + j] = M[i * n + j]; A[i * 2 * n + n + j] = (i == j); }
+    for (int c = 0; c < n; ++c) {
+        int r = c;
+        for (int i = c + 1; i < n; ++i) if (std::fabs(A[i * 2 * n + c]) > std::fabs(A[r * 2 * n + c])) r = i;
+        if (r != c) for (int j = 0; j < 2 * n; ++j) std::swap(A[c * 2 * n + j], A[r * 2 * n + j]);
+        double inv = 1.0 / A[c * 2 * n + c];
+        for (int j = 0; j < 2 * n; ++j) A[c * 2 * n + j] *= inv;
+        for (int i = 0; i < n; ++i) {
+            if (i == c) continue;
+            double f = A[i * 2 * n + c];
+            if (f != 0.0) for (int j = 0; j < 2 * n; ++j) A[i * 2 * n + j] -= f * A[c * 2 * n + j];
+        }
+    }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) Minv_ref[i * n + j] = A[i * 2 * n + n + j];
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < n; ++k) s += Minv_ref[i * n + k] * G[k * n + j];
+            C1_ref[i * n + j] = s;
+        }
 }

@@ -257,12 +257,13 @@ class Context:
         mehdg_apply_condensed(self.ctx, x, y)
         return y
 
-    def recover(self, dvh):
+    def recover(self, dvh, with_dQ=False):
         import torch
         m = self.mesh
         dV = torch.empty((m.nK, 5, m.Nn), dtype=torch.float64, device=dvh.device)
-        mehdg_recover(self.ctx, dvh, dV)
-        return dV
+        dQ = torch.empty((m.nK, 5, 3, m.Nn), dtype=torch.float64, device=dvh.device) if self.params.viscous else None
+        mehdg_recover(self.ctx, dvh, dV, dQ)
+        return (dV, dQ) if with_dQ else dV
 
     def status(self):
         return mehdg_status(self.ctx, self.mesh.nK)

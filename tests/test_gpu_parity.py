@@ -160,3 +160,51 @@ def test_bad_arguments_return_einval():
         M().mehdg_set_mesh(ctx.ctx, np.full(mesh.nK, 2), np.full(mesh.nK, 1), mesh.boxes, gid,
                            mesh.n_global_faces)
     ctx.close()
+
+
+# ---------------------------------------------------------------- viscous
+def vcase(name):
+    p, m = {"p2m1": (2, 1), "p2m2": (2, 2), "p3m1": (3, 1), "p1m2": (1, 2)}[name]
+    mesh = I.periodic_mesh((2, 1, 1), p, m)
+    st = I.make_state(mesh, "tgv", 1e-2, 5, 6, viscous=True, M0=0.3)
+    return mesh, st, dict(Mach=0.3, Re=100.0, viscous=1)
+
+
+@pytest.mark.parametrize("name", ["p2m1", "p2m2", "p3m1"])
+@pytest.mark.parametrize("flux", [1, 2])
+def test_viscous_residual_matches_oracle(name, flux):
+    mesh, st, kw = vcase(name)
+    ctx = M().Context(mesh, flux=flux, prec=M().MEHDG_FP64, **kw)
+    ctx.set_state(*to_dev(st))
+    RV, RQ, RH = ctx.residual()
+    torch.cuda.synchronize()
+    prm = oracle.params(flux=flux, **kw)
+    rv, rq, rh = oracle.residual_mesh(prm, mesh, st)
+    for a, b in ((RV, rv), (RQ, rq), (RH, rh)):
+        assert rel(a, b) < 1e-11, rel(a, b)
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", ["p2m1", "p2m2", "p3m1", "p1m2"])
+@pytest.mark.parametrize("prec", [0, 3, 4])
+def test_viscous_condense_apply_recover_match_oracle(name, prec):
+    """Q-elimination (eqs. R2, R3, R5, R6) against the oracle's literal blocks"""
+    mesh, st, kw = vcase(name)
+    ctx = M().Context(mesh, flux=1, prec=prec, **kw)
+    ctx.set_state(*to_dev(st))
+    bh = ctx.condense()
+    dvh_np = I.random_direction(st.vhat.shape, 78, 1e-3)
+    dvh = torch.tensor(dvh_np, device="cuda:0")
+    y = ctx.apply(dvh)
+    dV, dQ = ctx.recover(dvh, with_dQ=True)
+    torch.cuda.synchronize()
+    stat, iters = ctx.status()
+    assert (stat == 0).all(), (stat, iters)
+    prm = oracle.params(flux=1, **kw)
+    bh_o, A_o, _ = _oracle_condensed(prm, mesh, st, dvh_np)
+    dV_o, dQ_o = oracle.recover_mesh(prm, mesh, st, dvh_np)
+    y_o = (A_o @ dvh_np.ravel()).reshape(dvh_np.shape)
+    tol = 1e-10 if prec == 0 else 1e-8
+    e = (rel(bh, bh_o), rel(y, y_o), rel(dV, dV_o), rel(dQ, dQ_o))
+    assert max(e) < tol, (e, iters)
+    ctx.close()
