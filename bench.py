@@ -1,16 +1,19 @@
 """Benchmark: macro-elements condensed per second (one Newton step of the
 entropy-variable macro-element HDG method, arXiv 2507.22195).
 
-Workload (one "step"): inviscid Taylor-Green vortex, Mach 0.1, periodic
-[0, 2 pi]^3, 8^3 macro-elements of 3^3 micro-elements, p = 3 (N_v = 5000
-unknowns per element), KEPES flux, stage term with dt = 1: residual, dense
-Jacobian S^K, batched LU, FP64-refined S^-1 R_V and b-hat, for all 512
-elements (mehdg_condense).  Inputs are resident in HBM; the dense S^K of the
-512 elements (53.7 GB FP32) is far larger than L2, so nothing is cached
+Default workload (one "step"): inviscid Taylor-Green vortex, Mach 0.1,
+periodic [0, 2 pi]^3, 8^3 macro-elements of 3^3 micro-elements, p = 3 (N_v =
+5000 unknowns per element), KEPES flux, stage term with dt = 1: residual,
+dense Jacobian S^K, batched LU, FP64-refined S^-1 R_V and b-hat, for all
+512 elements (mehdg_condense).  Inputs are resident in HBM; the dense S^K of
+the 512 elements (53.7 GB FP32) is far larger than L2, so nothing is cached
 between steps.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec tf32|bf16|fp64]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16x3|tf32x3|tf32|bf16|fp64]
+  python bench.py --workload tgv_viscous [--block B]   # B^3 block of the 16^3 x 4^3 viscous TGV
+  python bench.py --workload vortex                    # 2^3 x 2^3 isentropic vortex, p = 2
   python bench.py --impl reference     # the FP64 CPU oracle on the host cores
+  python bench.py --once               # one condense, untimed (for profilers)
 
 Under torchrun every rank condenses its own copy of the workload (weak
 scaling, no collective on the data path); rank 0 prints one JSON line.
@@ -19,7 +22,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import multiprocessing as mp
 import os
 import statistics
@@ -33,8 +35,17 @@ sys.path.insert(0, ROOT)
 
 METRIC = "macro-elements condensed/sec at p=3 (mixed vs FP64 GPU), err vs FP64 oracle"
 UNIT = "macro-elements/s"
-WORKLOAD = "inviscid Taylor-Green vortex, 8^3 macro-elements x 3^3 micro-elements, p=3, KEPES, one Newton-step condensation"
+WORKLOADS = {
+    "tgv_inviscid": "inviscid Taylor-Green vortex, 8^3 macro-elements x 3^3 micro-elements, p=3, KEPES, "
+                    "one Newton-step condensation",
+    "tgv_viscous": "viscous Taylor-Green vortex Re=1600, block of the 16^3 x 4^3 mesh, p=3, ES, "
+                   "one Newton-step condensation (Q-elimination)",
+    "vortex": "isentropic vortex, 2^3 macro-elements x 2^3 micro-elements, p=2, ES, one Newton-step condensation",
+}
 PREC = {"tf32": 1, "bf16": 2, "fp64": 0, "tf32x3": 3, "bf16x3": 4}
+DTYPE = {"tf32": "tf32 (f32 accumulate) + f64", "bf16": "bf16 (f32 accumulate) + f64",
+         "tf32x3": "split tf32 x3 (f32 accumulate) + f64", "bf16x3": "split bf16 x3 (f32 accumulate) + f64",
+         "fp64": "f64"}
 
 
 def peaks():
@@ -94,6 +105,26 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ---------------------------------------------------------------- workloads
+def workload(name, nk=8, block=4):
+    """(mesh, state, library params) of a named workload"""
+    from paper_2507_22195_gb300 import inputs as I
+    if name == "tgv_inviscid":
+        mesh = I.periodic_mesh(nk, 3, 3)
+        st = I.make_state(mesh, "tgv", 1e-3, 22197, 22198, M0=0.1)
+        return mesh, st, dict(flux=2, Mach=0.1, Re=1600.0, Pr=0.71, viscous=0)
+    if name == "tgv_viscous":
+        full = I.periodic_mesh(16, 3, 4)
+        mesh = I.sub_mesh(full, I.block_elements(16, block))
+        st = I.make_state(mesh, "tgv", 1e-3, 22201, 22202, viscous=True, M0=0.1)
+        return mesh, st, dict(flux=1, Mach=0.1, Re=1600.0, Pr=0.71, viscous=1)
+    if name == "vortex":
+        mesh = I.periodic_mesh(2, 2, 2, 0.0, 10.0)
+        st = I.make_state(mesh, "vortex", 1e-3, 22195, 22196, period=10.0)
+        return mesh, st, dict(flux=1, Mach=0.1, viscous=0)
+    raise ValueError(name)
+
+
 # ---------------------------------------------------------------- oracle (CPU)
 def _oracle_one(args):
     K, nk = args
@@ -109,8 +140,9 @@ def _oracle_one(args):
 
 
 def oracle_rate(n_elem: int, cores: int):
-    """FP64 CPU oracle, as it stands: n_elem elements of the workload, one per
-    process (spawned), on `cores` host cores.  Returns (elements/s, seconds)."""
+    """FP64 CPU oracle, as it stands: n_elem elements of the inviscid TGV
+    workload, one per process (spawned), on `cores` host cores.  Returns
+    (elements/s, seconds)."""
     import oracle
     oracle.build()
     ctx = mp.get_context("spawn")
@@ -140,7 +172,8 @@ def reference_main(a):
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * tot / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "global_batch": 512, "seq_len": None, "parallelism": "none"},
+        "config": {"workload": WORKLOADS["tgv_inviscid"], "global_batch": 512, "seq_len": None,
+                   "parallelism": "none"},
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -148,27 +181,41 @@ def reference_main(a):
 
 
 # ---------------------------------------------------------------- GPU arm
+def _to_dev(st, dev):
+    import torch
+    q = None if st.q is None else torch.tensor(st.q, device=dev)
+    return torch.tensor(st.v, device=dev), torch.tensor(st.vhat, device=dev), q, torch.tensor(st.vstar, device=dev)
+
+
 def once_main(a):
     """Workload setup, `warmup` condenses and one more, nothing timed: the
     command the ncu summaries under profiles/ are taken with."""
-    import numpy as np
     import torch
-    from paper_2507_22195_gb300 import inputs as I
     from paper_2507_22195_gb300 import mehdg as M
-    mesh = I.periodic_mesh(a.nk, 3, 3)
-    st = I.make_state(mesh, "tgv", 1e-3, 22197, 22198, M0=0.1)
+    mesh, st, kw = workload(a.workload, a.nk, a.block)
     dev = torch.device("cuda:0")
-    v, vh, vs = (torch.tensor(x, device=dev) for x in (st.v, st.vhat, st.vstar))
-    ctx = M.Context(mesh, flux=M.MEHDG_FLUX_KEPES, prec=PREC[a.prec], Mach=0.1)
-    ctx.set_state(v, vh, None, vs)
+    ctx = M.Context(mesh, prec=PREC[a.prec], **kw)
+    ctx.set_state(*_to_dev(st, dev))
     for _ in range(a.warmup + 1):
         ctx.condense()
     torch.cuda.synchronize()
     stat, iters = ctx.status()
-    print(json.dumps({"once": True, "nK": mesh.nK, "prec": a.prec, "status_ok": bool((stat == 0).all()),
-                      "refine_iters": sorted(set(int(x) for x in iters)), "launches": M.mehdg_launch_count()}))
+    print(json.dumps({"once": True, "workload": a.workload, "nK": mesh.nK, "prec": a.prec,
+                      "status_ok": bool((stat == 0).all()), "refine_iters": sorted(set(int(x) for x in iters)),
+                      "launches": M.mehdg_launch_count()}))
     ctx.close()
     return 0
+
+
+def trailing_bytes(ld, nK):
+    """algorithmic bytes of all outer trailing updates of one condensation:
+    C read and written (FP32) and the two operand panels (rest x 256, FP32)"""
+    byt = 0
+    for c0 in range(0, ld, 256):
+        rest = ld - c0 - 256
+        if rest > 0:
+            byt += 8 * rest * rest + 2 * 4 * rest * 256
+    return byt * nK
 
 
 def main():
@@ -178,8 +225,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="bf16x3", choices=list(PREC))
-    ap.add_argument("--nk", type=int, default=8)
-    ap.add_argument("--fp64-sample", type=int, default=2, help="nk of the FP64 comparison mesh (nk^3 elements)")
+    ap.add_argument("--workload", default="tgv_inviscid", choices=list(WORKLOADS))
+    ap.add_argument("--nk", type=int, default=8, help="tgv_inviscid: nk^3 elements")
+    ap.add_argument("--block", type=int, default=4, help="tgv_viscous: block^3 elements of the 16^3 mesh")
+    ap.add_argument("--fp64-sample", type=int, default=8, help="elements of the FP64 comparison (0: skip)")
     ap.add_argument("--cpu-sample", type=int, default=-1, help="elements for the CPU oracle baseline (-1: one per core)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--once", action="store_true", help="one condense after --warmup ones, no timing (for profilers)")
@@ -195,7 +244,7 @@ def main():
 
     # CPU baseline first (spawned pool, before any CUDA call), rank 0 only
     cpu = None
-    if rank == 0 and world == 1 and not a.no_cpu:
+    if rank == 0 and world == 1 and not a.no_cpu and a.workload == "tgv_inviscid":
         cores = min(os.cpu_count() or 1, 16)
         n = cores if a.cpu_sample < 0 else a.cpu_sample
         val, dt = oracle_rate(n, cores)
@@ -215,11 +264,11 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    mesh = I.periodic_mesh(a.nk, 3, 3)
-    st = I.make_state(mesh, "tgv", 1e-3, 22197, 22198, M0=0.1)
-    v, vh, vs = (torch.tensor(x, device=dev) for x in (st.v, st.vhat, st.vstar))
-    ctx = M.Context(mesh, flux=M.MEHDG_FLUX_KEPES, prec=PREC[a.prec], Mach=0.1)
-    ctx.set_state(v, vh, None, vs)
+    mesh, st, kw = workload(a.workload, a.nk, a.block)
+    vis = bool(kw["viscous"])
+    v, vh, q, vs = _to_dev(st, dev)
+    ctx = M.Context(mesh, prec=PREC[a.prec], **kw)
+    ctx.set_state(v, vh, q, vs)
     bh = torch.empty((mesh.n_global_faces, 5, mesh.n2), dtype=torch.float64, device=dev)
 
     def barrier():
@@ -259,14 +308,15 @@ def main():
 
     # end to end through the public API: pinned host inputs -> device,
     # condense, b-hat -> host, every step
-    hv, hvh, hvs = (torch.tensor(x).pin_memory() for x in (st.v, st.vhat, st.vstar))
+    host = [torch.tensor(x).pin_memory() for x in (st.v, st.vhat, st.vstar) + ((st.q,) if vis else ())]
     hb = torch.empty(bh.shape, dtype=torch.float64).pin_memory()
-    v2, vh2, vs2 = torch.empty_like(v), torch.empty_like(vh), torch.empty_like(vs)
-    ctx.set_state(v2, vh2, None, vs2)
+    devb = [torch.empty(h.shape, dtype=torch.float64, device=dev) for h in host]
+    ctx.set_state(devb[0], devb[1], devb[3] if vis else None, devb[2])
     barrier()
     t0 = time.perf_counter()
     for _ in range(a.steps):
-        v2.copy_(hv, non_blocking=True); vh2.copy_(hvh, non_blocking=True); vs2.copy_(hvs, non_blocking=True)
+        for d_, h_ in zip(devb, host):
+            d_.copy_(h_, non_blocking=True)
         ctx.condense(bh)
         hb.copy_(bh, non_blocking=True)
         torch.cuda.current_stream().synchronize()
@@ -276,70 +326,66 @@ def main():
         t = torch.tensor([e2e_s], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    h2d = hv.numel() * 8 + hvh.numel() * 8 + hvs.numel() * 8
+    h2d = sum(h.numel() * 8 for h in host)
     d2h = hb.numel() * 8
-    ctx.set_state(v, vh, None, vs)
+    ctx.set_state(v, vh, q, vs)
 
     # roofline of the dominant kernel: the outer trailing update of the LU
     pk = peaks()
     gem = prof["lu_trailing_update"]
     ld = (5 * mesh.Nn + 255) // 256 * 256
-    # algorithmic bytes of all trailing updates of one step: C read+write (FP32)
-    # and the two operand panels (rest x 256, FP32), per element
-    byt = 0
-    for c0 in range(0, ld, 256):
-        rest = ld - c0 - 256
-        if rest > 0:
-            byt += (8 * rest * rest + 2 * 4 * rest * 256)
-    byt *= mesh.nK * a.steps
+    byt = trailing_bytes(ld, mesh.nK) * a.steps
     if a.prec == "fp64":
         fl = gem["flops"]
-        roof = {"bound": "alu", "achieved": fl / (gem["ms"] / 1e3) / 1e12, "peak": 1.2,
-                "unit": "TFLOP/s", "frac": None, "traffic": None,
-                "note": "FP64 SIMT trailing update; peak = 152 SMs x 64 FP64 FMA/clk x 2 x ~1.9 GHz boost (fallback estimate)"}
-        roof["frac"] = roof["achieved"] / roof["peak"]
+        ach = fl / (gem["ms"] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": 1.25, "unit": "TFLOP/s", "frac": ach / 1.25,
+                "traffic": None, "peak_source": "nominal FP64 rate of GB300 (no measured FP64 peak)",
+                "kernel": "lu_trailing_update (FP64 SIMT, depth 256)", "launches": gem["launches"], "ms": gem["ms"]}
     else:
         ach = byt / (gem["ms"] / 1e3) / 1e9
         hbm = pk.get("hbm_gbs", 6800.0)
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                 "traffic": None, "peak_source": "measured" if "hbm_gbs" in pk else "fallback",
-                "kernel": "lu_trailing_update (depth 256)", "launches": gem["launches"],
+                "kernel": "lu_trailing_update (tcgen05, depth 256)", "launches": gem["launches"],
                 "ms": gem["ms"], "tflops": gem["flops"] / (gem["ms"] / 1e3) / 1e12}
 
-    # FP64 GPU path and error on a small mesh of the same elements
+    # FP64 GPU path and the mixed-vs-FP64 error on the first elements of the same workload
     fp = None
     if a.prec != "fp64" and a.fp64_sample > 0:
-        m2 = I.periodic_mesh(a.fp64_sample, 3, 3)
-        s2 = I.make_state(m2, "tgv", 1e-3, 22197, 22198, M0=0.1)
-        w, wh, ws = (torch.tensor(x, device=dev) for x in (s2.v, s2.vhat, s2.vstar))
+        n_s = min(a.fp64_sample, mesh.nK)
+        m2 = I.sub_mesh(mesh, list(range(n_s)))
+        s2 = I.State(v=st.v[:n_s].copy(), vhat=None, q=None if st.q is None else st.q[:n_s].copy(),
+                     vstar=st.vstar[:n_s].copy())
+        # traces of the sub-mesh: the faces of the first elements, renumbered
+        gid = mesh.face_gid[:n_s]
+        uniq = np.unique(gid)
+        s2.vhat = st.vhat[uniq].copy()
+        w = _to_dev(s2, dev)
         outs = {}
         for pr in ("fp64", a.prec):
-            c2 = M.Context(m2, flux=M.MEHDG_FLUX_KEPES, prec=PREC[pr], Mach=0.1)
-            c2.set_state(w, wh, None, ws)
+            c2 = M.Context(m2, prec=PREC[pr], **kw)
+            c2.set_state(*w)
             b2 = c2.condense()
             barrier()
             t1 = time.perf_counter()
             c2.condense(b2)
             barrier()
-            outs[pr] = (b2.clone(), time.perf_counter() - t1)
+            st2, it2 = c2.status()
+            outs[pr] = (b2.clone(), time.perf_counter() - t1, bool((st2 == 0).all()))
             c2.close()
         err = float(torch.linalg.norm(outs[a.prec][0] - outs["fp64"][0]) / torch.linalg.norm(outs["fp64"][0]))
-        fp = {"value": m2.nK / outs["fp64"][1], "unit": UNIT, "sample": f"{m2.nK} elements ({a.fp64_sample}^3 periodic mesh)",
-              "mixed_same_sample": m2.nK / outs[a.prec][1],
-              "err_bhat_mixed_vs_fp64": err}
+        fp = {"value": n_s / outs["fp64"][1], "unit": UNIT, "sample": f"the first {n_s} elements of the workload",
+              "mixed_same_sample": n_s / outs[a.prec][1], "err_bhat_mixed_vs_fp64": err,
+              "status_ok": outs["fp64"][2] and outs[a.prec][2]}
 
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None,
-            "dtype": {"tf32": "tf32 (f32 accumulate) + f64", "bf16": "bf16 (f32 accumulate) + f64",
-                      "tf32x3": "split tf32 x3 (f32 accumulate) + f64", "bf16x3": "split bf16 x3 (f32 accumulate) + f64",
-                      "fp64": "f64"}[a.prec],
-            "data": "synthetic",
-            "config": {"workload": WORKLOAD, "global_batch": mesh.nK, "seq_len": None,
-                       "parallelism": f"dp{world}" if world > 1 else "none", "nK": mesh.nK, "p": 3, "m": 3,
-                       "N_v": 5 * mesh.Nn, "prec": a.prec,
+            "vs_baseline": None, "dtype": DTYPE[a.prec], "data": "synthetic",
+            "config": {"workload": WORKLOADS[a.workload], "global_batch": mesh.nK, "seq_len": None,
+                       "parallelism": f"dp{world}" if world > 1 else "none", "nK": mesh.nK, "p": mesh.p,
+                       "m": mesh.m, "N_v": 5 * mesh.Nn, "prec": a.prec,
                        "l2": "inputs larger than L2 (dense S^K of all elements: %.1f GB)" % (
                            mesh.nK * ld * ld * (8 if a.prec == "fp64" else 4) / 1e9)},
             "roofline": roof,

@@ -86,6 +86,20 @@ def periodic_mesh(nk: int | tuple, p: int, m: int, lo=0.0, hi=2 * math.pi) -> Me
     return Mesh(p, m, boxes, gid, 3 * nK)
 
 
+def sub_mesh(mesh: Mesh, Ks) -> Mesh:
+    """The elements Ks of a mesh; faces shared inside the subset stay shared,
+    the others become unshared faces (global face ids renumbered)."""
+    Ks = np.asarray(Ks)
+    gid = mesh.face_gid[Ks]
+    uniq, inv = np.unique(gid, return_inverse=True)
+    return Mesh(mesh.p, mesh.m, mesh.boxes[Ks].copy(), inv.reshape(gid.shape).astype(np.int64), len(uniq))
+
+
+def block_elements(nk: int, b: int):
+    """element ids of the b^3 corner block of an nk^3 structured mesh"""
+    return [ix + nk * (iy + nk * iz) for iz in range(b) for iy in range(b) for ix in range(b)]
+
+
 def independent_mesh(nK: int, p: int, m: int, size=1.0, seed=0) -> Mesh:
     """nK macro-elements with unshared faces (each face its own global face)."""
     boxes = np.zeros((nK, 6))
