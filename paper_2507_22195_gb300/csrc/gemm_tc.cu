@@ -246,37 +246,89 @@ __device__ __forceinline__ void op_put(void* out, size_t row_base, int Kp, int k
     }
 }
 
-// A panel: Ap[K][m][seg*Kp + k] = L[r0+m][k0+k] (k < Kd, else 0); 32x32 transposes.
+// eight consecutive K entries of one packed row, as 16-byte stores
 template <bool BF16>
-__global__ void pack_A_kernel(const float* __restrict__ Sall, int64_t ld, int r0, int k0, int M, int Kd, int Kp,
-                              int nseg, void* __restrict__ out) {
-    const int K = blockIdx.z;
-    const float* S = Sall + (size_t)K * ld * ld;
-    __shared__ float t[32][33];
-    const int m0 = blockIdx.x * 32, kk0 = blockIdx.y * 32;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;     // 32 x 8
-    for (int i = ty; i < 32; i += 8) {
-        int k = kk0 + i, m = m0 + tx;
-        t[i][tx] = (k < Kd && m < M) ? S[(size_t)(r0 + m) + (size_t)(k0 + k) * ld] : 0.f;
-    }
-    __syncthreads();
-    for (int i = ty; i < 32; i += 8) {
-        int m = m0 + i, k = kk0 + tx;
-        if (m < M && k < Kp)
-            op_put<BF16, true>(out, ((size_t)K * M + m) * (size_t)(nseg * Kp), Kp, k, nseg, t[tx][i]);
+__device__ __forceinline__ void op_store8(void* out, size_t o, const float (&x)[8]) {
+    if constexpr (BF16) {
+        uint4 u;
+        uint32_t* w = reinterpret_cast<uint32_t*>(&u);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            __nv_bfloat162 h = __floats2bfloat162_rn(x[2 * j], x[2 * j + 1]);
+            w[j] = *reinterpret_cast<uint32_t*>(&h);
+        }
+        *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(out) + o) = u;
+    } else {
+        float4* d = reinterpret_cast<float4*>(reinterpret_cast<float*>(out) + o);
+        d[0] = make_float4(x[0], x[1], x[2], x[3]);
+        d[1] = make_float4(x[4], x[5], x[6], x[7]);
     }
 }
-// B panel: Bp[K][n][seg*Kp + k] = U[k0+k][c0+n] (contiguous in k on both sides)
+// write x[0..8) (K entries k..k+7, k a multiple of 8) into the nseg K-segments of a row
+template <bool BF16, bool IS_A>
+__device__ __forceinline__ void op_put8(void* out, size_t row_base, int Kp, int k, int nseg, const float (&x)[8]) {
+    float hi[8], lo[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) { hi[j] = op_round<BF16>(x[j]); lo[j] = op_round<BF16>(x[j] - hi[j]); }
+    op_store8<BF16>(out, row_base + k, hi);
+    if (nseg == 3) {
+        op_store8<BF16>(out, row_base + Kp + k, IS_A ? hi : lo);
+        op_store8<BF16>(out, row_base + 2 * (size_t)Kp + k, IS_A ? lo : hi);
+    }
+}
+
+// A panel: Ap[K][m][seg*Kp + k] = L[r0+m][k0+k] (k < Kd, else 0).  A 64 (m) x 32 (k)
+// tile is transposed through shared memory; each thread then writes 8
+// consecutive k of one row per segment.  Kp is a multiple of 32.
 template <bool BF16>
-__global__ void pack_B_kernel(const float* __restrict__ Sall, int64_t ld, int k0, int c0, int N, int Kd, int Kp,
-                              int nseg, void* __restrict__ out) {
+__global__ void __launch_bounds__(256)
+pack_A_kernel(const float* __restrict__ Sall, int64_t ld, int r0, int k0, int M, int Kd, int Kp,
+              int nseg, void* __restrict__ out) {
+    const int K = blockIdx.z;
+    const float* S = Sall + (size_t)K * ld * ld;
+    __shared__ float t[32][65];
+    const int m0 = blockIdx.x * 64, kk0 = blockIdx.y * 32;
+    {
+        const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
+        const int m = m0 + tx;
+#pragma unroll
+        for (int i = ty; i < 32; i += 4) {
+            const int k = kk0 + i;
+            t[i][tx] = (k < Kd && m < M) ? S[(size_t)(r0 + m) + (size_t)(k0 + k) * ld] : 0.f;
+        }
+    }
+    __syncthreads();
+    const int ml = threadIdx.x >> 2, kq = (threadIdx.x & 3) * 8;
+    const int m = m0 + ml;
+    if (m >= M) return;
+    float x[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = t[kq + j][ml];
+    op_put8<BF16, true>(out, ((size_t)K * M + m) * (size_t)(nseg * Kp), Kp, kk0 + kq, nseg, x);
+}
+// B panel: Bp[K][n][seg*Kp + k] = U[k0+k][c0+n] (contiguous in k on both sides);
+// one warp per column n, 8 consecutive k per lane.  k0 is a multiple of 4 and
+// ld of 256, so the 16-byte loads are aligned; Kp is a multiple of 8.
+template <bool BF16>
+__global__ void __launch_bounds__(256)
+pack_B_kernel(const float* __restrict__ Sall, int64_t ld, int k0, int c0, int N, int Kd, int Kp,
+              int nseg, void* __restrict__ out) {
     const int K = blockIdx.z;
     const float* S = Sall + (size_t)K * ld * ld;
     const int n = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (n >= N) return;
-    for (int k = threadIdx.x & 31; k < Kp; k += 32) {
-        float x = k < Kd ? S[(size_t)(k0 + k) + (size_t)(c0 + n) * ld] : 0.f;
-        op_put<BF16, false>(out, ((size_t)K * N + n) * (size_t)(nseg * Kp), Kp, k, nseg, x);
+    const float* col = S + (size_t)k0 + (size_t)(c0 + n) * ld;
+    for (int k = (threadIdx.x & 31) * 8; k < Kp; k += 256) {
+        float x[8];
+        if (k + 8 <= Kd) {
+            const float4 a = __ldg(reinterpret_cast<const float4*>(col + k));
+            const float4 b = __ldg(reinterpret_cast<const float4*>(col + k + 4));
+            x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) x[j] = k + j < Kd ? col[k + j] : 0.f;
+        }
+        op_put8<BF16, false>(out, ((size_t)K * N + n) * (size_t)(nseg * Kp), Kp, k, nseg, x);
     }
 }
 
@@ -419,7 +471,7 @@ cudaError_t gemm_tc_update(const LUPlan& P, int r0, int c0, int k0, int M, int N
     void* Bp = w + pan;
     // pack
     {
-        dim3 g((unsigned)((M + 31) / 32), (unsigned)((Kp + 31) / 32), (unsigned)P.nK);
+        dim3 g((unsigned)((M + 63) / 64), (unsigned)(Kp / 32), (unsigned)P.nK);
         if (bf16) pack_A_kernel<true><<<g, 256, 0, st>>>((const float*)P.S, P.ld, r0, k0, M, Kd, Kp, nseg, Ap);
         else pack_A_kernel<false><<<g, 256, 0, st>>>((const float*)P.S, P.ld, r0, k0, M, Kd, Kp, nseg, Ap);
         dim3 gb((unsigned)((N + 7) / 8), 1, (unsigned)P.nK);

@@ -28,10 +28,19 @@ namespace {
 constexpr int LEAF = 32;
 constexpr int PANEL_THREADS = 512;
 
+__device__ __forceinline__ float tabs(float x) { return fabsf(x); }
+__device__ __forceinline__ double tabs(double x) { return fabs(x); }
+
 // ---------------------------------------------------------------- leaf panel
+// One CTA per element; the IB columns of a sub-panel live in shared memory.
+// Row ownership is fixed (row r belongs to thread r mod PANEL_THREADS), so a
+// pivot column costs two barriers: one to publish the per-warp maxima, one
+// after every thread has read the old pivot row and row cc.  The search for
+// the next pivot runs on the values the update has just produced.
 template <class TS, int IB>
 __global__ void __launch_bounds__(PANEL_THREADS)
 panel_kernel(TS* __restrict__ Sall, int64_t ld, int c, int32_t* __restrict__ pivall, int32_t* status) {
+    constexpr int nth = PANEL_THREADS, NW = PANEL_THREADS / 32;
     const int K = blockIdx.x;
     TS* S = Sall + (size_t)K * ld * ld;
     int32_t* piv = pivall + (size_t)K * ld;
@@ -39,103 +48,169 @@ panel_kernel(TS* __restrict__ Sall, int64_t ld, int c, int32_t* __restrict__ piv
     const int R0 = (int)(ld - c);                  // rows of the panel
     TS* X = reinterpret_cast<TS*>(smem_raw);       // [IB][R0] column-major sub-panel
     __shared__ TS Utop[LEAF][IB];
-    __shared__ double red_v[PANEL_THREADS / 32];
-    __shared__ int red_i[PANEL_THREADS / 32];
+    __shared__ TS Lt[LEAF][LEAF + 1];
+    __shared__ TS s_swap[LEAF][2 * IB];
+    __shared__ TS red_v[2][NW];
+    __shared__ int red_i[2][NW];
     __shared__ int s_piv[IB];
-    const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, wid = tid >> 5;
+    __shared__ int s_rows[2 * IB], s_cont[2 * IB], s_nr;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     bool singular = false;
     for (int jb = 0; jb < LEAF; jb += IB) {
         const int R = R0 - jb;                     // rows of this sub-panel, starting at c + jb
         // (a) left-looking update with the earlier sub-panels of this leaf
         if (jb > 0) {
-            // U part: rows c..c+jb-1 of the sub-panel columns, unit-lower forward substitution
-            if (tid < IB) {
-                const int col = c + jb + tid;
-                for (int i = 0; i < jb; ++i) {
-                    TS s = S[(size_t)(c + i) + (size_t)col * ld];
-                    for (int t = 0; t < i; ++t) s -= S[(size_t)(c + i) + (size_t)(c + t) * ld] * Utop[t][tid];
-                    Utop[i][tid] = s;
-                    S[(size_t)(c + i) + (size_t)col * ld] = s;
-                }
-            }
+            // U part: rows c..c+jb-1 of the sub-panel columns, unit-lower forward
+            // substitution with the jb x jb block of L staged in shared memory
+            for (int i = tid; i < jb * jb; i += nth) Lt[i % jb][i / jb] = S[(size_t)(c + i % jb) + (size_t)(c + i / jb) * ld];
+            for (int i = tid; i < jb * IB; i += nth) Utop[i % jb][i / jb] = S[(size_t)(c + i % jb) + (size_t)(c + jb + i / jb) * ld];
             __syncthreads();
-            // L part into shared memory: X[cc][r] = A[c+jb+r][col] - sum_t L[c+jb+r][c+t] U[t][cc]
-            for (int r = tid; r < R; r += nth) {
-                TS acc[IB];
-                for (int cc = 0; cc < IB; ++cc) acc[cc] = S[(size_t)(c + jb + r) + (size_t)(c + jb + cc) * ld];
-                for (int t = 0; t < jb; ++t) {
-                    TS l = S[(size_t)(c + jb + r) + (size_t)(c + t) * ld];
-                    for (int cc = 0; cc < IB; ++cc) acc[cc] -= l * Utop[t][cc];
+            if (tid < IB)
+                for (int i = 1; i < jb; ++i) {
+                    TS s = Utop[i][tid];
+                    for (int t = 0; t < i; ++t) s -= Lt[i][t] * Utop[t][tid];
+                    Utop[i][tid] = s;
                 }
+            __syncthreads();
+            for (int i = tid; i < jb * IB; i += nth) S[(size_t)(c + i % jb) + (size_t)(c + jb + i / jb) * ld] = Utop[i % jb][i / jb];
+            // L part into shared memory: X[cc][r] = A[c+jb+r][col] - sum_t L[c+jb+r][c+t] U[t][cc];
+            // the loads of one row are issued IB at a time
+            for (int r = tid; r < R; r += nth) {
+                const TS* row = S + (size_t)(c + jb + r);
+                TS acc[IB];
+#pragma unroll
+                for (int cc = 0; cc < IB; ++cc) acc[cc] = row[(size_t)(c + jb + cc) * ld];
+                for (int t0 = 0; t0 < jb; t0 += IB) {
+                    TS l[IB];
+#pragma unroll
+                    for (int tt = 0; tt < IB; ++tt) l[tt] = row[(size_t)(c + t0 + tt) * ld];
+#pragma unroll
+                    for (int tt = 0; tt < IB; ++tt)
+#pragma unroll
+                        for (int cc = 0; cc < IB; ++cc) acc[cc] -= l[tt] * Utop[t0 + tt][cc];
+                }
+#pragma unroll
                 for (int cc = 0; cc < IB; ++cc) X[(size_t)cc * R0 + r] = acc[cc];
             }
         } else {
-            for (int r = tid; r < R; r += nth)
-                for (int cc = 0; cc < IB; ++cc) X[(size_t)cc * R0 + r] = S[(size_t)(c + r) + (size_t)(c + cc) * ld];
-        }
-        __syncthreads();
-        // (b) partial pivoting factorisation of the IB columns in shared memory
-        for (int cc = 0; cc < IB; ++cc) {
-            TS* xc = X + (size_t)cc * R0;
-            double best = -1.0; int bi = 0x7fffffff;
-            for (int r = cc + tid; r < R; r += nth) {
-                double a = fabs((double)xc[r]);
-                if (a > best) { best = a; bi = r; }          // increasing r: ties keep the lowest
+            for (int r = tid; r < R; r += nth) {
+                const TS* row = S + (size_t)(c + r);
+                TS v[IB];
+#pragma unroll
+                for (int cc = 0; cc < IB; ++cc) v[cc] = row[(size_t)(c + cc) * ld];
+#pragma unroll
+                for (int cc = 0; cc < IB; ++cc) X[(size_t)cc * R0 + r] = v[cc];
             }
+        }
+        // (b) partial pivoting factorisation of the IB columns in shared memory;
+        // every thread reads and writes only its own rows, except for the two
+        // rows read (by all) between the barriers of a column
+        // (magnitudes compared in the storage precision: the order is that of
+        // their exact FP64 promotions, and it keeps the FP64 pipe free)
+        TS best = (TS)-1; int bi = 0x7fffffff;
+        for (int r = tid; r < R; r += nth) {
+            const TS a = tabs(X[r]);
+            if (a > best) { best = a; bi = r; }          // increasing r: ties keep the lowest
+        }
+        for (int cc = 0; cc < IB; ++cc) {
             for (int o = 16; o > 0; o >>= 1) {
-                double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                TS ob = __shfl_xor_sync(0xffffffffu, best, o);
                 int oi = __shfl_xor_sync(0xffffffffu, bi, o);
                 if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
             }
-            if (lane == 0) { red_v[wid] = best; red_i[wid] = bi; }
+            if (lane == 0) { red_v[cc & 1][wid] = best; red_i[cc & 1][wid] = bi; }
             __syncthreads();
-            if (wid == 0) {
-                best = lane < nth / 32 ? red_v[lane] : -1.0;
-                bi = lane < nth / 32 ? red_i[lane] : 0x7fffffff;
-                for (int o = 16; o > 0; o >>= 1) {
-                    double ob = __shfl_xor_sync(0xffffffffu, best, o);
-                    int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            best = lane < NW ? red_v[cc & 1][lane] : (TS)-1;
+            bi = lane < NW ? red_i[cc & 1][lane] : 0x7fffffff;
+            for (int o = 16; o > 0; o >>= 1) {
+                TS ob = __shfl_xor_sync(0xffffffffu, best, o);
+                int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            // no finite candidate (all zero or NaN): keep the row, report singular
+            if (bi >= R || !(best > (TS)0)) { bi = cc; best = (TS)0; }
+            const int pr = bi;
+            if (best == (TS)0) singular = true;
+            TS prow[IB], crow[IB];
+#pragma unroll
+            for (int q = 0; q < IB; ++q) { prow[q] = X[(size_t)q * R0 + pr]; crow[q] = X[(size_t)q * R0 + cc]; }
+            if (tid == 0) s_piv[cc] = pr;
+            __syncthreads();
+            TS pivv = prow[0];
+#pragma unroll
+            for (int q = 1; q < IB; ++q) if (q == cc) pivv = prow[q];
+            const TS inv = pivv != (TS)0 ? (TS)1 / pivv : (TS)0;
+            best = (TS)-1; bi = 0x7fffffff;
+            for (int r = tid; r < R; r += nth) {
+                if (r < cc) continue;
+                if (r == cc) {                     // row cc takes the pivot row
+                    if (pr != cc) {
+#pragma unroll
+                        for (int q = 0; q < IB; ++q) X[(size_t)q * R0 + r] = prow[q];
+                    }
+                    continue;
                 }
-                // no finite candidate (all zero or NaN): keep the row, report singular
-                if (bi >= R || !(best > 0.0)) { bi = cc; best = 0.0; }
-                if (lane == 0) { s_piv[cc] = bi; red_v[0] = best; }
+                const bool isp = (r == pr);        // row pr takes the old row cc
+                TS v[IB];
+#pragma unroll
+                for (int q = 0; q < IB; ++q) v[q] = (q >= cc) ? (isp ? crow[q] : X[(size_t)q * R0 + r]) : (TS)0;
+                if (isp) {
+#pragma unroll
+                    for (int q = 0; q < IB; ++q) if (q < cc) X[(size_t)q * R0 + r] = crow[q];
+                }
+                TS l = (TS)0;
+#pragma unroll
+                for (int q = 0; q < IB; ++q) if (q == cc) l = v[q] * inv;
+#pragma unroll
+                for (int q = 0; q < IB; ++q) {
+                    if (q == cc) X[(size_t)q * R0 + r] = l;
+                    else if (q > cc) {
+                        const TS nv = v[q] - l * prow[q];
+                        X[(size_t)q * R0 + r] = nv;
+                        if (q == cc + 1) {
+                            const TS a = tabs(nv);
+                            if (a > best) { best = a; bi = r; }
+                        }
+                    }
+                }
             }
-            __syncthreads();
-            const int pr = s_piv[cc];
-            if (red_v[0] == 0.0 || pr >= R) singular = true;
-            // swap rows cc and pr of the sub-panel
-            if (pr != cc && pr < R && tid < IB) {
-                TS t = X[(size_t)tid * R0 + cc];
-                X[(size_t)tid * R0 + cc] = X[(size_t)tid * R0 + pr];
-                X[(size_t)tid * R0 + pr] = t;
-            }
-            __syncthreads();
-            TS pivv = xc[cc];
-            TS inv = pivv != (TS)0 ? (TS)1 / pivv : (TS)0;
-            for (int r = cc + 1 + tid; r < R; r += nth) {
-                TS l = xc[r] * inv;
-                xc[r] = l;
-                for (int c2 = cc + 1; c2 < IB; ++c2) X[(size_t)c2 * R0 + r] -= l * X[(size_t)c2 * R0 + cc];
-            }
-            __syncthreads();
         }
-        // (c) write back, record pivots
-        for (int r = tid; r < R; r += nth)
-            for (int cc = 0; cc < IB; ++cc) S[(size_t)(c + jb + r) + (size_t)(c + jb + cc) * ld] = X[(size_t)cc * R0 + r];
+        // (c) write back the own rows, record pivots
+        for (int r = tid; r < R; r += nth) {
+            TS* row = S + (size_t)(c + jb + r);
+#pragma unroll
+            for (int cc = 0; cc < IB; ++cc) row[(size_t)(c + jb + cc) * ld] = X[(size_t)cc * R0 + r];
+        }
         if (tid < IB) piv[c + jb + tid] = c + jb + s_piv[tid];
-        __syncthreads();
-        // (d) apply the IB swaps to the other columns of the leaf
-        if (tid < LEAF && (tid < jb || tid >= jb + IB)) {
-            const int col = c + tid;
-            for (int cc = 0; cc < IB; ++cc) {
-                int a = c + jb + cc, b = c + jb + s_piv[cc];
-                if (a != b) {
-                    TS t = S[(size_t)a + (size_t)col * ld];
-                    S[(size_t)a + (size_t)col * ld] = S[(size_t)b + (size_t)col * ld];
-                    S[(size_t)b + (size_t)col * ld] = t;
+        // (d) apply the IB swaps to the other columns of the leaf as one net
+        // permutation: slot i (row s_rows[i]) takes the old content of slot s_cont[i]
+        if (tid == 0) {
+            int nr = IB;
+            for (int i = 0; i < IB; ++i) { s_rows[i] = jb + i; s_cont[i] = i; }
+            for (int i = 0; i < IB; ++i) {
+                const int b = jb + s_piv[i];
+                if (b == jb + i) continue;
+                int sb = -1;
+                if (b < jb + IB) sb = b - jb;
+                else {
+                    for (int j = IB; j < nr; ++j) if (s_rows[j] == b) { sb = j; break; }
+                    if (sb < 0) { sb = nr++; s_rows[sb] = b; s_cont[sb] = sb; }
                 }
+                const int t = s_cont[i]; s_cont[i] = s_cont[sb]; s_cont[sb] = t;
             }
+            s_nr = nr;
+        }
+        __syncthreads();
+        const int nr = s_nr;
+        for (int e = tid; e < LEAF * 2 * IB; e += nth) {
+            const int t = e / (2 * IB), i = e % (2 * IB);
+            if (i < nr && (t < jb || t >= jb + IB)) s_swap[t][i] = S[(size_t)(c + s_rows[i]) + (size_t)(c + t) * ld];
+        }
+        __syncthreads();
+        for (int e = tid; e < LEAF * 2 * IB; e += nth) {
+            const int t = e / (2 * IB), i = e % (2 * IB);
+            if (i < nr && (t < jb || t >= jb + IB) && s_cont[i] != i)
+                S[(size_t)(c + s_rows[i]) + (size_t)(c + t) * ld] = s_swap[t][s_cont[i]];
         }
         __syncthreads();
     }

@@ -14,6 +14,7 @@
 // With T = Dual<1> the same code returns R and dR[dv, dvh, dq], the
 // directional derivative used by the refinement residual r - S x, the
 // right-hand side b-hat and the reduced mat-vec (all matrix-free, FP64).
+#include <algorithm>
 #include "physics.cuh"
 #include "kernels.cuh"
 
@@ -145,6 +146,191 @@ residual_volume_kernel(ResidualArgs a) {
     }
 }
 
+// Sum-factorised volume pass (same result as residual_volume_kernel up to
+// rounding order).  Interpolation to the Gauss points and testing against the
+// basis are each three one-dimensional contractions over the tensor indices:
+//   interpolation  nodes (l1,l2,l3) -> (g1,l2,l3) -> (g1,g2,l3) -> (g1,g2,g3)
+//   testing        points (g1,g2,g3) -> (l1,g2,g3) -> (l1,l2,g3) -> (l1,l2,l3)
+// The derivative factors of the weak form ride along as separate partial sums
+// (H after the g1 contraction, J after g2).  Two shared regions alternate:
+//   A: nodal state -> T2 -> H        B: T1 -> point values / integrands -> J
+template <class T, bool VISC>
+__global__ void __launch_bounds__(128)
+residual_volume_sf_kernel(ResidualArgs a, int nA) {
+    const Tab& tb = a.tab;
+    const int K = blockIdx.y, e = blockIdx.x;
+    if (a.skip && a.skip[K]) return;
+    const int p = tb.p, m = tb.m, n = tb.n, ng = tb.ng, Nn = tb.Nn;
+    const int nl = tb.nl, npt = tb.npt, p1 = p + 1;
+    const int e1 = e % m, e2 = (e / m) % m, e3 = e / (m * m);
+    const Phys& ph = a.ph;
+    const bool tt = ph.time_term;
+    const int NIN = 5 + (tt ? 5 : 0) + (VISC ? 15 : 0);     // v, v* (time term), q
+    const int cq = tt ? 10 : 5;
+    constexpr int NHK = VISC ? 7 : 3, NJK = VISC ? 6 : 2;   // partial sums per component k
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* sL = reinterpret_cast<double*>(smem_raw);         // [ng][p1]
+    double* sD = sL + MEHDG_MAXG * (MEHDG_MAXP + 1);          // [ng][p1]
+    double* sW = sD + MEHDG_MAXG * (MEHDG_MAXP + 1);          // [ng]
+    T* RA = reinterpret_cast<T*>(sW + 8);
+    T* RB = RA + nA;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    load_tables(tb, sL, sD, sW);
+    const double* box = a.box + 6 * K;
+    double sc[3], hw[3];
+    for (int d = 0; d < 3; ++d) { double h = (box[3 + d] - box[d]) / m; sc[d] = 2.0 / h; hw[d] = 0.5 * h; }
+    const int64_t oV = (int64_t)K * 5 * Nn, oQ = (int64_t)K * 15 * Nn;
+
+    // nodal state of the micro-element -> A [NIN][nl]
+    for (int i = tid; i < nl; i += nth) {
+        int l1 = i % p1, l2 = (i / p1) % p1, l3 = i / (p1 * p1);
+        int A = (e1 * p + l1) + n * ((e2 * p + l2) + n * (e3 * p + l3));
+        for (int k = 0; k < 5; ++k) {
+            RA[k * nl + i] = load_t<T>(a.v, a.dv, oV + k * Nn + A);
+            if (tt) RA[(5 + k) * nl + i] = load_t<T>(a.vs, nullptr, oV + k * Nn + A);
+        }
+        if (VISC)
+            for (int c = 0; c < 15; ++c) RA[(cq + c) * nl + i] = load_t<T>(a.q, a.dq, oQ + c * Nn + A);
+    }
+    __syncthreads();
+    // interpolation, g1: B[c][g1 + ng (l2 + p1 l3)]
+    {
+        const int s1 = ng * p1 * p1;
+        for (int it = tid; it < NIN * s1; it += nth) {
+            const int c = it / s1, o = it % s1, g1 = o % ng, r = o / ng;
+            const T* src = RA + c * nl + r * p1;
+            T s = cst<T>(0.0);
+            for (int l = 0; l < p1; ++l) s += src[l] * sL[g1 * p1 + l];
+            RB[it] = s;
+        }
+    }
+    __syncthreads();
+    // g2: A[c][g1 + ng (g2 + ng l3)]
+    {
+        const int s1 = ng * p1 * p1, s2 = ng * ng * p1;
+        for (int it = tid; it < NIN * s2; it += nth) {
+            const int c = it / s2, o = it % s2, g1 = o % ng, g2 = (o / ng) % ng, l3 = o / (ng * ng);
+            const T* src = RB + c * s1 + g1 + ng * p1 * l3;
+            T s = cst<T>(0.0);
+            for (int l = 0; l < p1; ++l) s += src[ng * l] * sL[g2 * p1 + l];
+            RA[it] = s;
+        }
+    }
+    __syncthreads();
+    // g3: B[c][x], x = g1 + ng (g2 + ng g3)
+    {
+        const int s2 = ng * ng * p1;
+        for (int it = tid; it < NIN * npt; it += nth) {
+            const int c = it / npt, x = it % npt, g12 = x % (ng * ng), g3 = x / (ng * ng);
+            const T* src = RA + c * s2 + g12;
+            T s = cst<T>(0.0);
+            for (int l = 0; l < p1; ++l) s += src[ng * ng * l] * sL[g3 * p1 + l];
+            RB[it] = s;
+        }
+    }
+    __syncthreads();
+    // point physics, in place in B (each thread touches only its own column x):
+    // rows 0-4 W U, 5-19 W F/G (k*3+j), 20-34 W q (k*3+d), 35-39 W v
+    bool ok = true;
+    for (int x = tid; x < npt; x += nth) {
+        const int g1 = x % ng, g2 = (x / ng) % ng, g3 = x / (ng * ng);
+        T vx[5], vsx[5], qx[15];
+        for (int k = 0; k < 5; ++k) { vx[k] = RB[k * npt + x]; vsx[k] = tt ? RB[(5 + k) * npt + x] : cst<T>(0.0); }
+        if (VISC) for (int c = 0; c < 15; ++c) qx[c] = RB[(cq + c) * npt + x];
+        T U[5], FG[5][3];
+        ok = vol_integrand(ph, vx, vsx, qx, U, FG) && ok;
+        const double W = sW[g1] * hw[0] * sW[g2] * hw[1] * sW[g3] * hw[2];
+        for (int k = 0; k < 5; ++k) {
+            RB[k * npt + x] = U[k] * W;
+            for (int j = 0; j < 3; ++j) RB[(5 + k * 3 + j) * npt + x] = FG[k][j] * W;
+        }
+        if (VISC) {
+            for (int c = 0; c < 15; ++c) RB[(20 + c) * npt + x] = qx[c] * W;
+            for (int k = 0; k < 5; ++k) RB[(35 + k) * npt + x] = vx[k] * W;
+        }
+    }
+    if (!ok && a.status) a.status[K] = MEHDG_ENONPHYS;
+    __syncthreads();
+    // testing, g1: A[k*NHK + j][l1 + p1 (g2 + ng g3)]
+    {
+        const int h1 = p1 * ng * ng;
+        for (int it = tid; it < 5 * h1; it += nth) {
+            const int k = it / h1, o = it % h1, l1 = o % p1, g23 = o / p1;
+            const T* pu = RB + k * npt + g23 * ng;
+            const T* pf = RB + (5 + 3 * k) * npt + g23 * ng;
+            T h[NHK];
+            for (int j = 0; j < NHK; ++j) h[j] = cst<T>(0.0);
+            for (int g = 0; g < ng; ++g) {
+                const double Lg = sL[g * p1 + l1], Dg = sD[g * p1 + l1] * sc[0];
+                h[0] += pu[g] * Lg - pf[g] * Dg;
+                h[1] += pf[npt + g] * Lg;
+                h[2] += pf[2 * npt + g] * Lg;
+                if (VISC) {
+                    const T* pq = RB + (20 + 3 * k) * npt + g23 * ng;
+                    const T pv = RB[(35 + k) * npt + g23 * ng + g];
+                    h[3] += pq[g] * Lg + pv * Dg;
+                    h[4] += pq[npt + g] * Lg;
+                    h[5] += pq[2 * npt + g] * Lg;
+                    h[6] += pv * Lg;
+                }
+            }
+            for (int j = 0; j < NHK; ++j) RA[(k * NHK + j) * h1 + o] = h[j];
+        }
+    }
+    __syncthreads();
+    // g2: B[k*NJK + j][l1 + p1 (l2 + p1 g3)]
+    {
+        const int h1 = p1 * ng * ng, j1 = p1 * p1 * ng;
+        for (int it = tid; it < 5 * j1; it += nth) {
+            const int k = it / j1, o = it % j1, l1 = o % p1, l2 = (o / p1) % p1, g3 = o / (p1 * p1);
+            const T* H = RA + k * NHK * h1 + l1 + p1 * ng * g3;
+            T jv[NJK];
+            for (int j = 0; j < NJK; ++j) jv[j] = cst<T>(0.0);
+            for (int g = 0; g < ng; ++g) {
+                const double Lg = sL[g * p1 + l2], Dg = sD[g * p1 + l2] * sc[1];
+                const int o2 = p1 * g;
+                jv[0] += H[o2] * Lg - H[h1 + o2] * Dg;
+                jv[1] += H[2 * h1 + o2] * Lg;
+                if (VISC) {
+                    jv[2] += H[3 * h1 + o2] * Lg;
+                    jv[3] += H[4 * h1 + o2] * Lg + H[6 * h1 + o2] * Dg;
+                    jv[4] += H[5 * h1 + o2] * Lg;
+                    jv[5] += H[6 * h1 + o2] * Lg;
+                }
+            }
+            for (int j = 0; j < NJK; ++j) RB[(k * NJK + j) * j1 + o] = jv[j];
+        }
+    }
+    __syncthreads();
+    // g3: nodal rows of R_V (and R_Q), added into the element's rows
+    {
+        const int j1 = p1 * p1 * ng;
+        for (int it = tid; it < 5 * nl; it += nth) {
+            const int k = it / nl, i = it % nl, l12 = i % (p1 * p1), l3 = i / (p1 * p1);
+            const int l1 = l12 % p1, l2 = l12 / p1;
+            const T* J = RB + k * NJK * j1 + l12;
+            T rv = cst<T>(0.0), rq0 = cst<T>(0.0), rq1 = cst<T>(0.0), rq2 = cst<T>(0.0);
+            for (int g = 0; g < ng; ++g) {
+                const double Lg = sL[g * p1 + l3], Dg = sD[g * p1 + l3] * sc[2];
+                const int o3 = p1 * p1 * g;
+                rv += J[o3] * Lg - J[j1 + o3] * Dg;
+                if (VISC) {
+                    rq0 += J[2 * j1 + o3] * Lg;
+                    rq1 += J[3 * j1 + o3] * Lg;
+                    rq2 += J[4 * j1 + o3] * Lg + J[5 * j1 + o3] * Dg;
+                }
+            }
+            const int A = (e1 * p + l1) + n * ((e2 * p + l2) + n * (e3 * p + l3));
+            acc_out(a.RV, a.tRV, oV + k * Nn + A, rv);
+            if (VISC) {
+                acc_out(a.RQ, a.tRQ, oQ + (k * 3 + 0) * Nn + A, rq0);
+                acc_out(a.RQ, a.tRQ, oQ + (k * 3 + 1) * Nn + A, rq1);
+                acc_out(a.RQ, a.tRQ, oQ + (k * 3 + 2) * Nn + A, rq2);
+            }
+        }
+    }
+}
+
 template <class T, bool VISC>
 __global__ void __launch_bounds__(128)
 residual_face_kernel(ResidualArgs a) {
@@ -262,6 +448,21 @@ size_t volume_smem_bytes(const Tab& t, bool visc, size_t ts) {
     return head_bytes() + ts * n;
 }
 
+// region sizes (entries) of the sum-factorised volume kernel
+void volume_sf_regions(const Tab& t, bool visc, int& nA, int& nB) {
+    const int p1 = t.p + 1, ng = t.ng;
+    const int nin = 10 + (visc ? 15 : 0);       // v, v* (counted whether or not the time term is on), q
+    const int nout = visc ? 40 : 20, nh = 5 * (visc ? 7 : 3), nj = 5 * (visc ? 6 : 2);
+    nA = std::max(std::max(nin * t.nl, nin * ng * ng * p1), nh * p1 * ng * ng);
+    nB = std::max(std::max(nin * ng * p1 * p1, std::max(nin, nout) * t.npt), nj * p1 * p1 * ng);
+}
+
+size_t volume_sf_smem_bytes(const Tab& t, bool visc, size_t ts) {
+    int nA, nB;
+    volume_sf_regions(t, visc, nA, nB);
+    return head_bytes() + ts * (size_t)(nA + nB);
+}
+
 size_t face_smem_bytes(const Tab& t, bool visc, size_t ts) {
     int fl = (t.p + 1) * (t.p + 1), fpt = t.ng * t.ng;
     size_t n = (size_t)(10 + (visc ? 15 : 0)) * fl + 10 * (size_t)fpt;
@@ -286,11 +487,21 @@ cudaError_t launch_residual(const ResidualArgs& a, int64_t nK, bool visc, bool t
     if ((e = zero(a.RH, a.tRH, 30LL * t.n2, nK, a.skip, st)) != cudaSuccess) return e;
     size_t ts = tangent ? sizeof(Dual<1>) : sizeof(double);
     size_t sv = volume_smem_bytes(t, visc, ts), sf = face_smem_bytes(t, visc, ts);
+    // the sum-factorised volume pass wherever its two regions fit in shared memory
+    int nA, nB;
+    volume_sf_regions(t, visc, nA, nB);
+    const size_t ssf = volume_sf_smem_bytes(t, visc, ts);
+    const bool sf_vol = ssf <= 220 * 1024;
     dim3 gv((unsigned)(t.m * t.m * t.m), (unsigned)nK), gf((unsigned)(6 * t.m * t.m), (unsigned)nK), b(128);
 #define LAUNCH_RES(T, V)                                                                                 \
-    do { cudaFuncSetAttribute(residual_volume_kernel<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sv); \
+    do { if (sf_vol) {                                                                                   \
+             cudaFuncSetAttribute(residual_volume_sf_kernel<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssf); \
+             residual_volume_sf_kernel<T, V><<<gv, b, ssf, st>>>(a, nA);                                  \
+         } else {                                                                                        \
+             cudaFuncSetAttribute(residual_volume_kernel<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sv); \
+             residual_volume_kernel<T, V><<<gv, b, sv, st>>>(a);                                         \
+         }                                                                                               \
          cudaFuncSetAttribute(residual_face_kernel<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf);   \
-         residual_volume_kernel<T, V><<<gv, b, sv, st>>>(a);                                             \
          residual_face_kernel<T, V><<<gf, b, sf, st>>>(a); } while (0)
     if (tangent) { if (visc) LAUNCH_RES(Dual<1>, true); else LAUNCH_RES(Dual<1>, false); }
     else { if (visc) LAUNCH_RES(double, true); else LAUNCH_RES(double, false); }
