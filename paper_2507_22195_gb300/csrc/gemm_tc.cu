@@ -6,20 +6,24 @@
 // 1. pack: L (M x Kd) and U (Kd x N) are copied into K-major operand panels
 //    in the operand type (TF32 rounded to nearest, or BF16), zero-padded in K
 //    to whole 128-byte rows;
-// 2. MMA: one CTA per 128 x BN tile of C (BN = 128, or 32/64 for narrow
-//    updates).  Warp 0 (one lane) streams 128-byte K-chunks of both panels
-//    into a shared-memory ring with TMA (128B swizzle, mbarrier transaction
-//    counts); warp 1 (one lane) issues tcgen05.mma (kind::tf32 or
-//    kind::f16) accumulating in TMEM and releases each ring slot with
-//    tcgen05.commit; warp 2 owns the TMEM allocation;
-// 3. epilogue: the four warps read their 32 TMEM lanes (rows) with
-//    tcgen05.ld.32x32b and subtract from C in place (32 consecutive rows per
-//    warp and column: coalesced 128-byte accesses).
+// 2. MMA: a persistent kernel, one CTA per SM, walks the 128 x BN tiles of C
+//    (BN = 128, or 32/64 for narrow updates) of all elements.  Warp 0 (one
+//    lane) streams 128-byte K-chunks of both panels into a 6-slot
+//    shared-memory ring with TMA (128B swizzle, mbarrier transaction counts);
+//    warp 1 (one lane) issues tcgen05.mma (kind::tf32 or kind::f16) into one
+//    of two TMEM accumulators and releases each ring slot with
+//    tcgen05.commit;
+// 3. epilogue: sixteen warps, four per TMEM lane quarter (32 rows), each on
+//    32 columns: C is read before the accumulator is ready, then C - D is
+//    written in place (32 consecutive rows per warp and column: coalesced
+//    128-byte accesses).  The epilogue of one tile runs while the MMAs of the
+//    next tile fill the other accumulator.
 // Every mbarrier wait is bounded; on timeout the element's status becomes
-// MEHDG_ETIMEOUT, the epilogue is skipped and TMEM is still released.
+// MEHDG_ETIMEOUT, the loops end and TMEM is still released.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <algorithm>
 #include <cstring>
 #include "lu_internal.cuh"
 
@@ -102,36 +106,61 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// STORE = false: C -= A B^T (trailing update); STORE = true: C = A B^T
-// (triangular solve through the inverse of the diagonal block).
+// ---------------------------------------------------------------- streaming kernel
+// Persistent form of the update: one CTA per SM walks the tiles
+// (element-major, then column tiles, then row tiles) with ten warps:
+//   warp 0 (one lane)  TMA: operand chunks into a 6-slot ring;
+//   warp 1 (one lane)  tcgen05.mma into one of two TMEM accumulators (2 x BN
+//                      columns); the whole warp owns the TMEM allocation;
+//   warps 2-17         epilogue: four warps per TMEM lane quarter, each on
+//                      32 of the tile's columns (BN / 32 of them active).  A
+//                      warp fetches its C values for the next tile before it
+//                      waits for that tile's accumulator, so the C reads (32
+//                      per thread in flight) overlap the MMAs, and the stores
+//                      of one tile overlap the MMAs of the next.
+// Every mbarrier wait is bounded; a warp that times out records
+// MEHDG_ETIMEOUT and leaves its loop, the others time out in turn, and TMEM
+// is released after the final barrier.
+constexpr int SSTAGES = 6;
+constexpr int EPI_WARPS = 16;
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_addr(b)) : "memory");
+}
+
+template <int BN>
+constexpr size_t stream_smem_bytes() {
+    return (size_t)SSTAGES * (TM + BN) * CHUNK_BYTES + 1024;
+}
+
 template <int BN, bool BF16, bool STORE>
-__global__ void __launch_bounds__(128)
-tc_update_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+__global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
+tc_stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                  float* __restrict__ Sall, int64_t ld, int r0, int c0, int M, int N, int nchunk, int tiles_m,
-                 int32_t* status) {
+                 int tiles_n, int64_t ntiles, int32_t* status) {
     constexpr int A_BYTES = TM * CHUNK_BYTES;
     constexpr int B_BYTES = BN * CHUNK_BYTES;
     constexpr int CHUNK_K = BF16 ? 64 : 32;
     constexpr uint32_t ID = idesc(TM, BN, BF16 ? 1u : 2u);
+    constexpr int NH = BN / 32;                    // column groups per lane quarter
+    constexpr int W = 32;                          // columns per epilogue warp
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* sA = smem;
-    unsigned char* sB = smem + STAGES * A_BYTES;
-    __shared__ uint64_t full[STAGES], empty[STAGES], done;
+    unsigned char* sB = sA + SSTAGES * A_BYTES;
+    __shared__ uint64_t full[SSTAGES], empty[SSTAGES], acc_full[2], acc_empty[2];
     __shared__ uint32_t tmem_slot;
-    __shared__ int s_fail;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int K = blockIdx.y, tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
+    const int tiles_e = tiles_m * tiles_n;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-        mbar_init(&done, 1);
-        s_fail = 0;
+        for (int s = 0; s < SSTAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], EPI_WARPS); }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 2) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     ::"r"(s_addr(&tmem_slot)), "r"((uint32_t)BN) : "memory");
+                     ::"r"(s_addr(&tmem_slot)), "r"((uint32_t)(2 * BN)) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     tc_fence_before();
@@ -139,77 +168,92 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
 
-    if (warp == 0 && lane == 0) {
-        // producer: TMA ring
-        for (int c = 0; c < nchunk; ++c) {
-            const int s = c % STAGES;
-            if (c >= STAGES && !mbar_wait(&empty[s], ((c / STAGES) - 1) & 1)) { s_fail = 1; break; }
-            mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
-            tma_load_3d(sA + s * A_BYTES, &mapA, &full[s], c * CHUNK_K, tm * TM, K);
-            tma_load_3d(sB + s * B_BYTES, &mapB, &full[s], c * CHUNK_K, tn * BN, K);
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t g = 0;
+            for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+                const int K = (int)(t / tiles_e), rem = (int)(t % tiles_e);
+                const int tm = rem % tiles_m, tn = rem / tiles_m;
+                bool ok = true;
+                for (int c = 0; c < nchunk; ++c, ++g) {
+                    const int s = (int)(g % SSTAGES);
+                    if (g >= SSTAGES && !mbar_wait(&empty[s], ((g / SSTAGES) - 1) & 1)) { ok = false; break; }
+                    mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
+                    tma_load_3d(sA + s * A_BYTES, &mapA, &full[s], c * CHUNK_K, tm * TM, K);
+                    tma_load_3d(sB + s * B_BYTES, &mapB, &full[s], c * CHUNK_K, tn * BN, K);
+                }
+                if (!ok) { if (status) status[K] = MEHDG_ETIMEOUT; break; }
+            }
         }
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer
-        for (int c = 0; c < nchunk; ++c) {
-            const int s = c % STAGES;
-            if (!mbar_wait(&full[s], (c / STAGES) & 1)) { s_fail = 1; break; }
-            tc_fence_after();
-            const uint64_t da = sdesc(s_addr(sA + s * A_BYTES));
-            const uint64_t db = sdesc(s_addr(sB + s * B_BYTES));
+    } else if (warp == 1) {
+        if (lane == 0) {
+            uint32_t g = 0;
+            int i = 0;
+            for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+                const int K = (int)(t / tiles_e), b = i & 1;
+                bool ok = !(i >= 2 && !mbar_wait(&acc_empty[b], ((i >> 1) - 1) & 1));
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(b * BN);
+                for (int c = 0; ok && c < nchunk; ++c, ++g) {
+                    const int s = (int)(g % SSTAGES);
+                    if (!mbar_wait(&full[s], (g / SSTAGES) & 1)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint64_t da = sdesc(s_addr(sA + s * A_BYTES));
+                    const uint64_t db = sdesc(s_addr(sB + s * B_BYTES));
 #pragma unroll
-            for (int j = 0; j < CHUNK_BYTES / 32; ++j)      // 32 bytes of K per instruction
-                umma<BF16>(tmem, da + (uint64_t)(j * 2), db + (uint64_t)(j * 2), ID, (c | j) != 0);
-            umma_commit(&empty[s]);
+                    for (int j = 0; j < CHUNK_BYTES / 32; ++j)
+                        umma<BF16>(d, da + (uint64_t)(j * 2), db + (uint64_t)(j * 2), ID, (c | j) != 0);
+                    umma_commit(&empty[s]);
+                }
+                if (!ok) { if (status) status[K] = MEHDG_ETIMEOUT; break; }
+                umma_commit(&acc_full[b]);
+            }
         }
-        umma_commit(&done);
+    } else {
+        const int ew = warp - 2, q = warp & 3, h = ew >> 2;   // lane quarter q, column group h
+        const bool active = h < NH;
+        float* S0 = Sall;
+        int i = 0;
+        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+            const int K = (int)(t / tiles_e), rem = (int)(t % tiles_e);
+            const int tm = rem % tiles_m, tn = rem / tiles_m, b = i & 1;
+            const int row = tm * TM + 32 * q + lane, col0 = tn * BN + h * W;
+            // columns of this warp's slice inside the update (0 for rows past M)
+            const int nc = (active && row < M) ? min(W, N - col0) : 0;
+            float* Cp = S0 + (size_t)K * ld * ld + (size_t)(r0 + row) + (size_t)(c0 + col0) * ld;
+            float cv[W];
+            if (!STORE) {
+                const float* p = Cp;
+#pragma unroll
+                for (int j = 0; j < W; ++j) { cv[j] = j < nc ? __ldcs(p) : 0.f; p += ld; }
+            }
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[b], (i >> 1) & 1));
+            if (!ok) { if (lane == 0 && status) status[K] = MEHDG_ETIMEOUT; break; }
+            tc_fence_after();
+            if (active) {
+                uint32_t r[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + h * W), r);
+                // a fresh copy of the base pointer, so that the 32 store addresses are
+                // recomputed instead of being kept live from the loads
+                float* p;
+                asm volatile("mov.b64 %0, %1;" : "=l"(p) : "l"(Cp));
+#pragma unroll
+                for (int j = 0; j < W; ++j) {
+                    if (j < nc) __stcs(p, STORE ? __uint_as_float(r[j]) : cv[j] - __uint_as_float(r[j]));
+                    p += ld;
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[b]);
+        }
     }
     __syncwarp();
-    // epilogue: the C values do not depend on the MMA, so the first 32-column
-    // chunk is fetched before waiting for it and each next chunk while the
-    // current one is written (32 independent loads in flight per thread)
-    float* S = Sall + (size_t)K * ld * ld;
-    const int row = tm * TM + warp * 32 + lane;
-    const bool rok = row < M;
-    float* Crow = S + (size_t)(r0 + row) + (size_t)c0 * ld;
-    float cv[32], cn[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) { cv[j] = 0.f; cn[j] = 0.f; }
-    if (!STORE) {
-        const int col0 = tn * BN;
-        if (rok && col0 < N) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) cv[j] = __ldcs(Crow + (size_t)(col0 + j) * ld);
-        }
-    }
-    const bool ok = __all_sync(0xffffffffu, mbar_wait(&done, 0));   // warp-uniform
-    tc_fence_after();
-    if (ok && !s_fail) {
-#pragma unroll 1
-        for (int cc = 0; cc < BN; cc += 32) {
-            const int col0 = tn * BN + cc;
-            const bool has_next = cc + 32 < BN && col0 + 32 < N;
-            if (!STORE && rok && has_next) {
-#pragma unroll
-                for (int j = 0; j < 32; ++j) cn[j] = __ldcs(Crow + (size_t)(col0 + 32 + j) * ld);
-            }
-            uint32_t r[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc, r);
-            if (rok && col0 < N) {
-#pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    __stcs(Crow + (size_t)(col0 + j) * ld, STORE ? __uint_as_float(r[j]) : cv[j] - __uint_as_float(r[j]));
-            }
-#pragma unroll
-            for (int j = 0; j < 32; ++j) cv[j] = cn[j];
-        }
-    } else if (threadIdx.x == 0 && status) {
-        status[K] = MEHDG_ETIMEOUT;
-    }
     tc_fence_before();
     __syncthreads();
-    if (warp == 2) {
+    if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * BN)) : "memory");
     }
 }
 
@@ -358,6 +402,17 @@ bool make_map(CUtensorMap* map, void* base, bool bf16, int Kp, int rows, int64_t
     return r == CUDA_SUCCESS;
 }
 
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
 size_t perm_bytes(int64_t nK) {
     size_t b = (size_t)nK * (1 + 4 * LU_NB) * sizeof(int32_t);
     return (b + 255) & ~(size_t)255;
@@ -369,18 +424,21 @@ size_t panel_bytes(int64_t nK, int64_t ld) {
     return (b + 255) & ~(size_t)255;
 }
 
-template <int BN, bool BF16, bool STORE = false>
-cudaError_t launch_tc(const CUtensorMap& a, const CUtensorMap& b, const LUPlan& P, int r0, int c0, int M, int N,
-                      int nchunk, cudaStream_t st) {
+template <int BN, bool BF16, bool STORE>
+cudaError_t launch_stream(const CUtensorMap& a, const CUtensorMap& b, const LUPlan& P, int r0, int c0, int M, int N,
+                          int nchunk, cudaStream_t st) {
     const int tiles_m = (M + TM - 1) / TM, tiles_n = (N + BN - 1) / BN;
-    const size_t sm = STAGES * (size_t)(TM + BN) * CHUNK_BYTES + 1024;
-    cudaFuncSetAttribute(tc_update_kernel<BN, BF16, STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    dim3 g((unsigned)(tiles_m * tiles_n), (unsigned)P.nK);
-    tc_update_kernel<BN, BF16, STORE><<<g, 128, sm, st>>>(a, b, (float*)P.S, P.ld, r0, c0, M, N, nchunk, tiles_m,
-                                                          P.status);
+    const int64_t ntiles = (int64_t)tiles_m * tiles_n * P.nK;
+    constexpr size_t sm = stream_smem_bytes<BN>();
+    auto kern = tc_stream_kernel<BN, BF16, STORE>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sm_count());
+    kern<<<(unsigned)grid, 64 + 32 * EPI_WARPS, sm, st>>>(a, b, (float*)P.S, P.ld, r0, c0, M, N, nchunk, tiles_m,
+                                                         tiles_n, ntiles, P.status);
     MEHDG_COUNT(1);
     return cudaGetLastError();
 }
+
 
 // Inverse X = L^-1 of the unit-lower 256 x 256 diagonal block L of every
 // element, written as the K-major operand panel Ap[K][m][k] = X[m][k] (TF32
@@ -441,8 +499,8 @@ cudaError_t gemm_tc_trsm256(const LUPlan& P, int c0, int j0, int j1, cudaStream_
     CUtensorMap ma, mb;
     if (!make_map(&ma, Ap, bf16, nseg * Kd, 256, P.nK, TM) || !make_map(&mb, Bp, bf16, nseg * Kd, N, P.nK, BN))
         return cudaErrorInvalidValue;
-#define LS(BNV) (bf16 ? launch_tc<BNV, true, true>(ma, mb, P, c0, j0, 256, N, nchunk, st) \
-                      : launch_tc<BNV, false, true>(ma, mb, P, c0, j0, 256, N, nchunk, st))
+#define LS(BNV) (bf16 ? launch_stream<BNV, true, true>(ma, mb, P, c0, j0, 256, N, nchunk, st) \
+                      : launch_stream<BNV, false, true>(ma, mb, P, c0, j0, 256, N, nchunk, st))
     if (BN == 128) return LS(128);
     if (BN == 64) return LS(64);
     return LS(32);
@@ -483,8 +541,8 @@ cudaError_t gemm_tc_update(const LUPlan& P, int r0, int c0, int k0, int M, int N
     CUtensorMap ma, mb;
     if (!make_map(&ma, Ap, bf16, nseg * Kp, M, P.nK, TM) || !make_map(&mb, Bp, bf16, nseg * Kp, N, P.nK, BN))
         return cudaErrorInvalidValue;
-#define LT(BNV) (bf16 ? launch_tc<BNV, true>(ma, mb, P, r0, c0, M, N, nchunk, st) \
-                      : launch_tc<BNV, false>(ma, mb, P, r0, c0, M, N, nchunk, st))
+#define LT(BNV) (bf16 ? launch_stream<BNV, true, false>(ma, mb, P, r0, c0, M, N, nchunk, st) \
+                      : launch_stream<BNV, false, false>(ma, mb, P, r0, c0, M, N, nchunk, st))
     if (BN == 128) return LT(128);
     if (BN == 64) return LT(64);
     return LT(32);

@@ -33,7 +33,13 @@ def _product(L, U, prec):
                                    (768, 352, 352, 320, 416, 32, 32),
                                    (768, 320, 320, 256, 448, 64, 64),
                                    (1024, 384, 384, 256, 640, 128, 128),
-                                   (640, 128, 384, 96, 512, 256, 32)])
+                                   (640, 128, 384, 96, 512, 256, 32),
+                                   # whole tiles that stop short of the last row (TMA-addressed)
+                                   (768, 256, 256, 0, 384, 256, 256),
+                                   # ragged tiles inside the matrix (per-thread epilogue)
+                                   (768, 260, 256, 0, 300, 200, 64),
+                                   # several tiles per persistent CTA (both C and TMEM buffers reused)
+                                   (2048, 256, 256, 0, 1792, 1792, 256)])
 def test_trailing_update_matches_torch(prec, shape):
     from paper_2507_22195_gb300 import mehdg
     ld, r0, c0, k0, M, N, Kd = shape
