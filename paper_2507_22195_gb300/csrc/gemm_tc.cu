@@ -31,7 +31,6 @@ namespace {
 
 constexpr int TM = 128;           // rows of a C tile (TMEM lanes)
 constexpr int CHUNK_BYTES = 128;  // K bytes per TMA box / swizzle row
-constexpr int STAGES = 2;
 
 __device__ __forceinline__ uint32_t s_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
