@@ -10,7 +10,7 @@
 //                   + sum_faces sum_x w mu_A mu_B dFhat_k/dv_l.
 // Volume contraction by sum factorisation over the three tensor directions
 // (test/trial pair tables per direction; about 2.9M FMA per micro-element at
-// p = 3 instead of 51M pair by pair), per (k,l) block; the pair-by-pair form
+// p = 3 instead of 51M pair by pair), per trial component l; the pair-by-pair form
 // remains for the case whose staging does not fit in shared memory (FP64,
 // p = 4).  Results are added into S with atomics (micro-elements share
 // nodes).  Unknowns are ordered node-major, row (A, k) = 5 A + k, so the
@@ -90,6 +90,12 @@ __device__ __forceinline__ void load_tables(const Tab& tb, double* sL, double* s
 }
 
 // ---------------------------------------------------------------- sum factorised
+// Per trial component l: stage 1 contracts g1 for all five test components k
+// into H1[k][alpha][a1 b1][g2 g3]; then every thread takes items
+// (k, a1, a2, b1, b2), contracts g2 into registers (4 x ng values) and g3 for
+// all (a3, b3), and adds the p1^2 results into S.  Items are ordered k
+// fastest, then a1, so a warp's atomics fall on runs of 5 p1 consecutive rows
+// 5 A + k of one column.
 template <class TS, bool VISC>
 __global__ void __launch_bounds__(256)
 jac_volume_sf_kernel(JacobianArgs a) {
@@ -108,8 +114,7 @@ jac_volume_sf_kernel(JacobianArgs a) {
     double* vl = reinterpret_cast<double*>(uni);            // phase 1: nodal state
     double* vsl = vl + 5 * nl;
     double* ql = vsl + 5 * nl;
-    TS* H1 = reinterpret_cast<TS*>(uni);                     // phase 2: [4][PP][G2]
-    TS* H2 = H1 + 4 * PP * G2;                               // [4][PP][PP][ng]
+    TS* H1 = reinterpret_cast<TS*>(uni);                     // phase 2: [5][4][PP][G2]
     const int tid = threadIdx.x, nth = blockDim.x;
     load_tables(tb, sL, sD, sW);
     double sc[3], hw[3];
@@ -127,40 +132,55 @@ jac_volume_sf_kernel(JacobianArgs a) {
     const TS* M1 = Mt;                       // direction x: tau=0 at [0], tau=1 at [ng*PP]
     const TS* M2 = Mt + 2 * ng * PP;
     const TS* M3 = Mt + 4 * ng * PP;
-    for (int kl = 0; kl < 25; ++kl) {
-        // stage 1: contract g1
-        for (int i = tid; i < 4 * PP * G2; i += nth) {
-            int g23 = i % G2, ab1 = (i / G2) % PP, al = i / (G2 * PP);
+    const int nh1 = 4 * PP * G2;
+    for (int l = 0; l < 5; ++l) {
+        // stage 1: contract g1 (alpha = 1 takes the x derivative of the test function)
+        for (int i = tid; i < 5 * nh1; i += nth) {
+            const int g23 = i % G2, ab1 = (i / G2) % PP, al = (i / (G2 * PP)) & 3, k = i / nh1;
             const TS* Mx = M1 + (al == 1 ? ng * PP : 0);
+            const TS* Pc = P + (size_t)ng * g23 * 100 + 25 * al + 5 * k + l;
             TS s = 0;
-            for (int g1 = 0; g1 < ng; ++g1) s += Mx[g1 * PP + ab1] * P[(size_t)(g1 + ng * g23) * 100 + 25 * al + kl];
+            for (int g1 = 0; g1 < ng; ++g1) s += Mx[g1 * PP + ab1] * Pc[(size_t)g1 * 100];
             H1[i] = s;
         }
         __syncthreads();
-        // stage 2: contract g2
-        for (int i = tid; i < 4 * PP * PP * ng; i += nth) {
-            int g3 = i % ng, ab2 = (i / ng) % PP, ab1 = (i / (ng * PP)) % PP, al = i / (ng * PP * PP);
-            const TS* My = M2 + (al == 2 ? ng * PP : 0);
-            const TS* h = H1 + ((size_t)al * PP + ab1) * G2 + ng * g3;
-            TS s = 0;
-            for (int g2 = 0; g2 < ng; ++g2) s += My[g2 * PP + ab2] * h[g2];
-            H2[i] = s;
-        }
-        __syncthreads();
-        // stage 3: contract g3, sum the four integrand parts, add into S
-        const int k = kl / 5, l = kl % 5;
-        for (int i = tid; i < PP * PP * PP; i += nth) {
-            int ab3 = i % PP, ab2 = (i / PP) % PP, ab1 = i / (PP * PP);
-            TS s = 0;
+        // stages 2 and 3 per item
+        for (int it = tid; it < 5 * PP * PP; it += nth) {
+            int r = it;
+            const int k = r % 5; r /= 5;
+            const int a1 = r % p1; r /= p1;
+            const int a2 = r % p1; r /= p1;
+            const int b1 = r % p1; const int b2 = r / p1;
+            const int ab1 = a1 * p1 + b1, ab2 = a2 * p1 + b2;
+            TS h2[4][MEHDG_MAXG];
+#pragma unroll
             for (int al = 0; al < 4; ++al) {
-                const TS* Mz = M3 + (al == 3 ? ng * PP : 0);
-                const TS* h = H2 + (((size_t)al * PP + ab1) * PP + ab2) * ng;
-                for (int g3 = 0; g3 < ng; ++g3) s += Mz[g3 * PP + ab3] * h[g3];
+                const TS* My = M2 + (al == 2 ? ng * PP : 0) + ab2;
+                const TS* h = H1 + (size_t)k * nh1 + ((size_t)al * PP + ab1) * G2;
+#pragma unroll
+                for (int g3 = 0; g3 < MEHDG_MAXG; ++g3) {
+                    TS s = 0;
+                    if (g3 < ng)
+                        for (int g2 = 0; g2 < ng; ++g2) s += My[g2 * PP] * h[g2 + ng * g3];
+                    h2[al][g3] = s;
+                }
             }
-            int a1 = ab1 / p1, b1 = ab1 % p1, a2 = ab2 / p1, b2 = ab2 % p1, a3 = ab3 / p1, b3 = ab3 % p1;
-            int A = (e1 * p + a1) + n * ((e2 * p + a2) + n * (e3 * p + a3));
-            int B = (e1 * p + b1) + n * ((e2 * p + b2) + n * (e3 * p + b3));
-            atomic_add_t(&S[(size_t)(A * 5 + k) + (size_t)(B * 5 + l) * a.ld], (double)s);
+            const int Arow = (e1 * p + a1) + n * ((e2 * p + a2) + n * (e3 * p));
+            const int Bcol = (e1 * p + b1) + n * ((e2 * p + b2) + n * (e3 * p));
+            for (int a3 = 0; a3 < p1; ++a3)
+                for (int b3 = 0; b3 < p1; ++b3) {
+                    const int ab3 = a3 * p1 + b3;
+                    TS s = 0;
+#pragma unroll
+                    for (int al = 0; al < 4; ++al) {
+                        const TS* Mz = M3 + (al == 3 ? ng * PP : 0) + ab3;
+#pragma unroll
+                        for (int g3 = 0; g3 < MEHDG_MAXG; ++g3)
+                            if (g3 < ng) s += Mz[g3 * PP] * h2[al][g3];
+                    }
+                    const int A = Arow + n * n * a3, B = Bcol + n * n * b3;
+                    atomic_add_t(&S[(size_t)(A * 5 + k) + (size_t)(B * 5 + l) * a.ld], (double)s);
+                }
         }
         __syncthreads();
     }
@@ -521,7 +541,7 @@ size_t sf_smem_bytes(const Tab& t, bool visc, size_t ts) {
     size_t tables = ts * 6 * MEHDG_MAXG * (MEHDG_MAXP + 1) * (MEHDG_MAXP + 1);
     size_t P = ts * 100 * (size_t)t.npt;
     size_t state = sizeof(double) * (size_t)(10 + (visc ? 15 : 0)) * t.nl;
-    size_t hbuf = ts * (4 * PP * G2 + 4 * PP * PP * t.ng);
+    size_t hbuf = ts * 5 * 4 * PP * G2;
     return head + tables + P + (state > hbuf ? state : hbuf) + 16;
 }
 
