@@ -120,33 +120,40 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
 // Every mbarrier wait is bounded; a warp that times out records
 // MEHDG_ETIMEOUT and leaves its loop, the others time out in turn, and TMEM
 // is released after the final barrier.
-constexpr int SSTAGES = 6;
 constexpr int EPI_WARPS = 16;
+constexpr int RING_BYTES = 192 * 1024;   // operand ring budget
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_addr(b)) : "memory");
 }
 
-template <int BN>
-constexpr size_t stream_smem_bytes() {
-    return (size_t)SSTAGES * (TM + BN) * CHUNK_BYTES + 1024;
-}
+// a ring slot holds one K-chunk of A and of B, each as hi (and lo when split)
+template <int BN, bool SPLIT>
+constexpr int stage_bytes() { return (SPLIT ? 2 : 1) * (TM + BN) * CHUNK_BYTES; }
+template <int BN, bool SPLIT>
+constexpr int n_stages() { return RING_BYTES / stage_bytes<BN, SPLIT>() < 6 ? RING_BYTES / stage_bytes<BN, SPLIT>() : 6; }
+template <int BN, bool SPLIT>
+constexpr size_t stream_smem_bytes() { return (size_t)n_stages<BN, SPLIT>() * stage_bytes<BN, SPLIT>() + 1024; }
 
-template <int BN, bool BF16, bool STORE>
+// SPLIT: the panels hold [hi | lo] (segment length kp); each chunk is loaded
+// once per part and takes the three products hi hi, hi lo, lo hi.
+template <int BN, bool BF16, bool STORE, bool SPLIT>
 __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
 tc_stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                 float* __restrict__ Sall, int64_t ld, int r0, int c0, int M, int N, int nchunk, int tiles_m,
-                 int tiles_n, int64_t ntiles, int32_t* status) {
+                 float* __restrict__ Sall, int64_t ld, int r0, int c0, int M, int N, int nchunk, int kp,
+                 int tiles_m, int tiles_n, int64_t ntiles, int32_t* status) {
     constexpr int A_BYTES = TM * CHUNK_BYTES;
     constexpr int B_BYTES = BN * CHUNK_BYTES;
+    constexpr int NP = SPLIT ? 2 : 1;
+    constexpr int STG = stage_bytes<BN, SPLIT>();
+    constexpr int SSTAGES = n_stages<BN, SPLIT>();
     constexpr int CHUNK_K = BF16 ? 64 : 32;
     constexpr uint32_t ID = idesc(TM, BN, BF16 ? 1u : 2u);
     constexpr int NH = BN / 32;                    // column groups per lane quarter
     constexpr int W = 32;                          // columns per epilogue warp
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char* sA = smem;
-    unsigned char* sB = sA + SSTAGES * A_BYTES;
+    // slot s: [A hi | A lo | B hi | B lo] (lo parts only when split)
     __shared__ uint64_t full[SSTAGES], empty[SSTAGES], acc_full[2], acc_empty[2];
     __shared__ uint32_t tmem_slot;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -177,9 +184,14 @@ tc_stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
                 for (int c = 0; c < nchunk; ++c, ++g) {
                     const int s = (int)(g % SSTAGES);
                     if (g >= SSTAGES && !mbar_wait(&empty[s], ((g / SSTAGES) - 1) & 1)) { ok = false; break; }
-                    mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
-                    tma_load_3d(sA + s * A_BYTES, &mapA, &full[s], c * CHUNK_K, tm * TM, K);
-                    tma_load_3d(sB + s * B_BYTES, &mapB, &full[s], c * CHUNK_K, tn * BN, K);
+                    unsigned char* slot = smem + (size_t)s * STG;
+                    mbar_expect_tx(&full[s], STG);
+                    tma_load_3d(slot, &mapA, &full[s], c * CHUNK_K, tm * TM, K);
+                    tma_load_3d(slot + NP * A_BYTES, &mapB, &full[s], c * CHUNK_K, tn * BN, K);
+                    if (SPLIT) {
+                        tma_load_3d(slot + A_BYTES, &mapA, &full[s], kp + c * CHUNK_K, tm * TM, K);
+                        tma_load_3d(slot + NP * A_BYTES + B_BYTES, &mapB, &full[s], kp + c * CHUNK_K, tn * BN, K);
+                    }
                 }
                 if (!ok) { if (status) status[K] = MEHDG_ETIMEOUT; break; }
             }
@@ -197,11 +209,19 @@ tc_stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
                     const int s = (int)(g % SSTAGES);
                     if (!mbar_wait(&full[s], (g / SSTAGES) & 1)) { ok = false; break; }
                     tc_fence_after();
-                    const uint64_t da = sdesc(s_addr(sA + s * A_BYTES));
-                    const uint64_t db = sdesc(s_addr(sB + s * B_BYTES));
+                    unsigned char* slot = smem + (size_t)s * STG;
+                    const uint64_t da = sdesc(s_addr(slot));
+                    const uint64_t db = sdesc(s_addr(slot + NP * A_BYTES));
 #pragma unroll
-                    for (int j = 0; j < CHUNK_BYTES / 32; ++j)
+                    for (int j = 0; j < CHUNK_BYTES / 32; ++j) {
                         umma<BF16>(d, da + (uint64_t)(j * 2), db + (uint64_t)(j * 2), ID, (c | j) != 0);
+                        if (SPLIT) {
+                            const uint64_t dal = sdesc(s_addr(slot + A_BYTES));
+                            const uint64_t dbl = sdesc(s_addr(slot + NP * A_BYTES + B_BYTES));
+                            umma<BF16>(d, da + (uint64_t)(j * 2), dbl + (uint64_t)(j * 2), ID, 1u);
+                            umma<BF16>(d, dal + (uint64_t)(j * 2), db + (uint64_t)(j * 2), ID, 1u);
+                        }
+                    }
                     umma_commit(&empty[s]);
                 }
                 if (!ok) { if (status) status[K] = MEHDG_ETIMEOUT; break; }
@@ -259,9 +279,9 @@ tc_stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
 // ---------------------------------------------------------------- packing
 // Operand rounding: TF32 (round to nearest on 10 mantissa bits, kept in FP32
 // storage) or BF16.  With split precision a product a b is taken as
-// a_hi b_hi + a_hi b_lo + a_lo b_hi (hi = round(x), lo = round(x - hi)): the
-// A panel holds the three K-segments [hi | hi | lo] and the B panel
-// [hi | lo | hi], so one GEMM over the tripled depth gives the sum.
+// a_hi b_hi + a_hi b_lo + a_lo b_hi (hi = round(x), lo = round(x - hi)): both
+// panels hold the two K-segments [hi | lo] and the MMA issuer takes the three
+// products from one ring slot.
 __device__ __forceinline__ float tf32_rn(float x) {
     uint32_t y;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
@@ -277,16 +297,12 @@ __device__ __forceinline__ void op_store(void* out, size_t o, float x) {
     if constexpr (BF16) reinterpret_cast<__nv_bfloat16*>(out)[o] = __float2bfloat16_rn(x);
     else reinterpret_cast<float*>(out)[o] = x;     // already TF32-rounded
 }
-// write x into the nseg K-segments of row `row` (segment pattern sel: A = hi,hi,lo; B = hi,lo,hi)
-template <bool BF16, bool IS_A>
+// write x into the nseg K-segments [hi (| lo)] of a row
+template <bool BF16>
 __device__ __forceinline__ void op_put(void* out, size_t row_base, int Kp, int k, int nseg, float x) {
     const float hi = op_round<BF16>(x);
     op_store<BF16>(out, row_base + k, hi);
-    if (nseg == 3) {
-        const float lo = op_round<BF16>(x - hi);
-        op_store<BF16>(out, row_base + Kp + k, IS_A ? hi : lo);
-        op_store<BF16>(out, row_base + 2 * (size_t)Kp + k, IS_A ? lo : hi);
-    }
+    if (nseg == 2) op_store<BF16>(out, row_base + Kp + k, op_round<BF16>(x - hi));
 }
 
 // eight consecutive K entries of one packed row, as 16-byte stores
@@ -307,17 +323,14 @@ __device__ __forceinline__ void op_store8(void* out, size_t o, const float (&x)[
         d[1] = make_float4(x[4], x[5], x[6], x[7]);
     }
 }
-// write x[0..8) (K entries k..k+7, k a multiple of 8) into the nseg K-segments of a row
-template <bool BF16, bool IS_A>
+// write x[0..8) (K entries k..k+7, k a multiple of 8) into the nseg K-segments [hi (| lo)] of a row
+template <bool BF16>
 __device__ __forceinline__ void op_put8(void* out, size_t row_base, int Kp, int k, int nseg, const float (&x)[8]) {
     float hi[8], lo[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) { hi[j] = op_round<BF16>(x[j]); lo[j] = op_round<BF16>(x[j] - hi[j]); }
     op_store8<BF16>(out, row_base + k, hi);
-    if (nseg == 3) {
-        op_store8<BF16>(out, row_base + Kp + k, IS_A ? hi : lo);
-        op_store8<BF16>(out, row_base + 2 * (size_t)Kp + k, IS_A ? lo : hi);
-    }
+    if (nseg == 2) op_store8<BF16>(out, row_base + Kp + k, lo);
 }
 
 // A panel: Ap[K][m][seg*Kp + k] = L[r0+m][k0+k] (k < Kd, else 0).  A 64 (m) x 32 (k)
@@ -347,7 +360,7 @@ pack_A_kernel(const float* __restrict__ Sall, int64_t ld, int r0, int k0, int M,
     float x[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) x[j] = t[kq + j][ml];
-    op_put8<BF16, true>(out, ((size_t)K * M + m) * (size_t)(nseg * Kp), Kp, kk0 + kq, nseg, x);
+    op_put8<BF16>(out, ((size_t)K * M + m) * (size_t)(nseg * Kp), Kp, kk0 + kq, nseg, x);
 }
 // B panel: Bp[K][n][seg*Kp + k] = U[k0+k][c0+n] (contiguous in k on both sides);
 // one warp per column n, 8 consecutive k per lane.  k0 is a multiple of 4 and
@@ -371,7 +384,7 @@ pack_B_kernel(const float* __restrict__ Sall, int64_t ld, int k0, int c0, int N,
 #pragma unroll
             for (int j = 0; j < 8; ++j) x[j] = k + j < Kd ? col[k + j] : 0.f;
         }
-        op_put8<BF16, false>(out, ((size_t)K * N + n) * (size_t)(nseg * Kp), Kp, k, nseg, x);
+        op_put8<BF16>(out, ((size_t)K * N + n) * (size_t)(nseg * Kp), Kp, k, nseg, x);
     }
 }
 
@@ -417,25 +430,34 @@ size_t perm_bytes(int64_t nK) {
     return (b + 255) & ~(size_t)255;
 }
 
-// one operand panel: ld rows x (3 segments x 256) FP32 per element
+// one operand panel: ld rows x (2 segments x 256) FP32 per element
 size_t panel_bytes(int64_t nK, int64_t ld) {
-    size_t b = (size_t)nK * ld * 3 * LU_NB * 4;
+    size_t b = (size_t)nK * ld * 2 * LU_NB * 4;
     return (b + 255) & ~(size_t)255;
 }
 
-template <int BN, bool BF16, bool STORE>
+template <int BN, bool BF16, bool STORE, bool SPLIT>
 cudaError_t launch_stream(const CUtensorMap& a, const CUtensorMap& b, const LUPlan& P, int r0, int c0, int M, int N,
-                          int nchunk, cudaStream_t st) {
+                          int nchunk, int kp, cudaStream_t st) {
     const int tiles_m = (M + TM - 1) / TM, tiles_n = (N + BN - 1) / BN;
     const int64_t ntiles = (int64_t)tiles_m * tiles_n * P.nK;
-    constexpr size_t sm = stream_smem_bytes<BN>();
-    auto kern = tc_stream_kernel<BN, BF16, STORE>;
+    constexpr size_t sm = stream_smem_bytes<BN, SPLIT>();
+    auto kern = tc_stream_kernel<BN, BF16, STORE, SPLIT>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sm_count());
-    kern<<<(unsigned)grid, 64 + 32 * EPI_WARPS, sm, st>>>(a, b, (float*)P.S, P.ld, r0, c0, M, N, nchunk, tiles_m,
+    kern<<<(unsigned)grid, 64 + 32 * EPI_WARPS, sm, st>>>(a, b, (float*)P.S, P.ld, r0, c0, M, N, nchunk, kp, tiles_m,
                                                          tiles_n, ntiles, P.status);
     MEHDG_COUNT(1);
     return cudaGetLastError();
+}
+
+// one update / solve product with the operand panels already packed
+template <bool BF16, bool STORE, bool SPLIT>
+cudaError_t launch_stream_bn(int BN, const CUtensorMap& a, const CUtensorMap& b, const LUPlan& P, int r0, int c0,
+                             int M, int N, int nchunk, int kp, cudaStream_t st) {
+    if (BN == 128) return launch_stream<128, BF16, STORE, SPLIT>(a, b, P, r0, c0, M, N, nchunk, kp, st);
+    if (BN == 64) return launch_stream<64, BF16, STORE, SPLIT>(a, b, P, r0, c0, M, N, nchunk, kp, st);
+    return launch_stream<32, BF16, STORE, SPLIT>(a, b, P, r0, c0, M, N, nchunk, kp, st);
 }
 
 
@@ -464,7 +486,7 @@ trtri256_kernel(const float* __restrict__ Sall, int64_t ld, int c0, int nseg, vo
         __syncthreads();
     }
     for (int m = tr; m < T; m += 8)
-        op_put<BF16, true>(Ap, ((size_t)K * T + m) * (size_t)(nseg * T), T, 32 * b + tc, nseg, X[m][tc]);
+        op_put<BF16>(Ap, ((size_t)K * T + m) * (size_t)(nseg * T), T, 32 * b + tc, nseg, X[m][tc]);
 }
 
 }  // namespace
@@ -479,10 +501,9 @@ cudaError_t gemm_tc_trsm256(const LUPlan& P, int c0, int j0, int j1, cudaStream_
     // operand rounding, and one-pass TF32 or BF16 here leaves the factors too
     // inexact for the FP64 refinement
     const bool bf16 = false;
-    const int nseg = 3;
-    const int es = bf16 ? 2 : 4;
-    const int chunk_k = CHUNK_BYTES / es;
-    const int nchunk = nseg * Kd / chunk_k;
+    const int nseg = 2;
+    const int chunk_k = CHUNK_BYTES / 4;
+    const int nchunk = Kd / chunk_k;
     unsigned char* w = reinterpret_cast<unsigned char*>(P.work) + perm_bytes(P.nK);
     const size_t pan = panel_bytes(P.nK, P.ld);
     void* Ap = w;
@@ -498,17 +519,12 @@ cudaError_t gemm_tc_trsm256(const LUPlan& P, int c0, int j0, int j1, cudaStream_
     CUtensorMap ma, mb;
     if (!make_map(&ma, Ap, bf16, nseg * Kd, 256, P.nK, TM) || !make_map(&mb, Bp, bf16, nseg * Kd, N, P.nK, BN))
         return cudaErrorInvalidValue;
-#define LS(BNV) (bf16 ? launch_stream<BNV, true, true>(ma, mb, P, c0, j0, 256, N, nchunk, st) \
-                      : launch_stream<BNV, false, true>(ma, mb, P, c0, j0, 256, N, nchunk, st))
-    if (BN == 128) return LS(128);
-    if (BN == 64) return LS(64);
-    return LS(32);
-#undef LS
+    return launch_stream_bn<false, true, true>(BN, ma, mb, P, c0, j0, 256, N, nchunk, Kd, st);
 }
 
 size_t gemm_tc_work_bytes(int64_t nK, int64_t ld, int prec) {
     (void)prec;
-    // two panels of at most ld x (3 x 256) FP32 per element (split precision)
+    // two panels of at most ld x (2 x 256) FP32 per element (split precision)
     return 2 * panel_bytes(nK, ld);
 }
 
@@ -517,11 +533,12 @@ cudaError_t gemm_tc_update(const LUPlan& P, int r0, int c0, int k0, int M, int N
     if (M < TM) return gemm_simt_update_f32(P, r0, c0, k0, M, N, Kd, st);   // a few tiny inner updates
     if (!encoder()) return cudaErrorNotSupported;
     const bool bf16 = P.prec == MEHDG_MIXED_BF16 || P.prec == MEHDG_MIXED_BF16X3;
-    const int nseg = (P.prec == MEHDG_MIXED_TF32X3 || P.prec == MEHDG_MIXED_BF16X3) ? 3 : 1;
+    const bool split = P.prec == MEHDG_MIXED_TF32X3 || P.prec == MEHDG_MIXED_BF16X3;
+    const int nseg = split ? 2 : 1;
     const int es = bf16 ? 2 : 4;
     const int chunk_k = CHUNK_BYTES / es;
     const int Kp = (Kd + chunk_k - 1) / chunk_k * chunk_k;
-    const int nchunk = nseg * Kp / chunk_k;
+    const int nchunk = Kp / chunk_k;
     unsigned char* w = reinterpret_cast<unsigned char*>(P.work) + perm_bytes(P.nK);
     const size_t pan = panel_bytes(P.nK, P.ld);
     void* Ap = w;
@@ -540,12 +557,10 @@ cudaError_t gemm_tc_update(const LUPlan& P, int r0, int c0, int k0, int M, int N
     CUtensorMap ma, mb;
     if (!make_map(&ma, Ap, bf16, nseg * Kp, M, P.nK, TM) || !make_map(&mb, Bp, bf16, nseg * Kp, N, P.nK, BN))
         return cudaErrorInvalidValue;
-#define LT(BNV) (bf16 ? launch_stream<BNV, true, false>(ma, mb, P, r0, c0, M, N, nchunk, st) \
-                      : launch_stream<BNV, false, false>(ma, mb, P, r0, c0, M, N, nchunk, st))
-    if (BN == 128) return LT(128);
-    if (BN == 64) return LT(64);
-    return LT(32);
-#undef LT
+    if (bf16) return split ? launch_stream_bn<true, false, true>(BN, ma, mb, P, r0, c0, M, N, nchunk, Kp, st)
+                           : launch_stream_bn<true, false, false>(BN, ma, mb, P, r0, c0, M, N, nchunk, Kp, st);
+    return split ? launch_stream_bn<false, false, true>(BN, ma, mb, P, r0, c0, M, N, nchunk, Kp, st)
+                 : launch_stream_bn<false, false, false>(BN, ma, mb, P, r0, c0, M, N, nchunk, Kp, st);
 }
 
 // test hook: one trailing update on caller-owned FP32 column-major matrices

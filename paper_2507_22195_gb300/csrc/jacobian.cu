@@ -296,8 +296,10 @@ jac_face_kernel(JacobianArgs a) {
     }
     __syncthreads();
     TS* S = reinterpret_cast<TS*>(a.S) + (size_t)K * a.ld * a.ld;
+    // pairs (ia, ib), ia fastest: a warp's atomics for one (k, l) fall on a few
+    // rows of one or two columns
     for (int r = tid; r < fl * fl; r += nth) {
-        int ia = r / fl, ib = r % fl;
+        int ia = r % fl, ib = r / fl;
         TS acc[25];
         for (int i = 0; i < 25; ++i) acc[i] = 0;
         for (int x = 0; x < fpt; ++x) {

@@ -47,19 +47,23 @@ panel_kernel(TS* __restrict__ Sall, int64_t ld, int c, int32_t* __restrict__ piv
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int R0 = (int)(ld - c);                  // rows of the panel
     TS* X = reinterpret_cast<TS*>(smem_raw);       // [IB][R0] column-major sub-panel
-    __shared__ TS Utop[LEAF][IB];
-    __shared__ TS Lt[LEAF][LEAF + 1];
-    __shared__ TS s_swap[LEAF][2 * IB];
+    constexpr int UT = IB < LEAF ? LEAF : 1;      // left-looking staging, only with several sub-panels
+    __shared__ TS Utop[UT][IB];
+    __shared__ TS Lt[UT][UT + 1];
+    __shared__ TS s_swap[UT][2 * IB];
     __shared__ TS red_v[2][NW];
     __shared__ int red_i[2][NW];
     __shared__ int s_piv[IB];
+    __shared__ TS s_prow[2][IB], s_crow[2][IB];
     __shared__ int s_rows[2 * IB], s_cont[2 * IB], s_nr;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     bool singular = false;
     for (int jb = 0; jb < LEAF; jb += IB) {
         const int R = R0 - jb;                     // rows of this sub-panel, starting at c + jb
         // (a) left-looking update with the earlier sub-panels of this leaf
-        if (jb > 0) {
+        bool staged = false;
+        if constexpr (IB < LEAF) if (jb > 0) {
+            staged = true;
             // U part: rows c..c+jb-1 of the sub-panel columns, unit-lower forward
             // substitution with the jb x jb block of L staged in shared memory
             for (int i = tid; i < jb * jb; i += nth) Lt[i % jb][i / jb] = S[(size_t)(c + i % jb) + (size_t)(c + i / jb) * ld];
@@ -92,7 +96,8 @@ panel_kernel(TS* __restrict__ Sall, int64_t ld, int c, int32_t* __restrict__ piv
 #pragma unroll
                 for (int cc = 0; cc < IB; ++cc) X[(size_t)cc * R0 + r] = acc[cc];
             }
-        } else {
+        }
+        if (!staged) {
             for (int r = tid; r < R; r += nth) {
                 const TS* row = S + (size_t)(c + r);
                 TS v[IB];
@@ -104,7 +109,7 @@ panel_kernel(TS* __restrict__ Sall, int64_t ld, int c, int32_t* __restrict__ piv
         }
         // (b) partial pivoting factorisation of the IB columns in shared memory;
         // every thread reads and writes only its own rows, except for the two
-        // rows read (by all) between the barriers of a column
+        // rows copied to s_prow / s_crow between the barriers of a column.
         // (magnitudes compared in the storage precision: the order is that of
         // their exact FP64 promotions, and it keeps the FP64 pipe free)
         TS best = (TS)-1; int bi = 0x7fffffff;
@@ -112,6 +117,7 @@ panel_kernel(TS* __restrict__ Sall, int64_t ld, int c, int32_t* __restrict__ piv
             const TS a = tabs(X[r]);
             if (a > best) { best = a; bi = r; }          // increasing r: ties keep the lowest
         }
+#pragma unroll
         for (int cc = 0; cc < IB; ++cc) {
             for (int o = 16; o > 0; o >>= 1) {
                 TS ob = __shfl_xor_sync(0xffffffffu, best, o);
@@ -131,46 +137,44 @@ panel_kernel(TS* __restrict__ Sall, int64_t ld, int c, int32_t* __restrict__ piv
             if (bi >= R || !(best > (TS)0)) { bi = cc; best = (TS)0; }
             const int pr = bi;
             if (best == (TS)0) singular = true;
-            TS prow[IB], crow[IB];
-#pragma unroll
-            for (int q = 0; q < IB; ++q) { prow[q] = X[(size_t)q * R0 + pr]; crow[q] = X[(size_t)q * R0 + cc]; }
+            if (tid < IB) { s_prow[cc & 1][tid] = X[(size_t)tid * R0 + pr]; s_crow[cc & 1][tid] = X[(size_t)tid * R0 + cc]; }
             if (tid == 0) s_piv[cc] = pr;
             __syncthreads();
-            TS pivv = prow[0];
-#pragma unroll
-            for (int q = 1; q < IB; ++q) if (q == cc) pivv = prow[q];
+            const TS* prow = s_prow[cc & 1];
+            const TS* crow = s_crow[cc & 1];
+            const TS pivv = prow[cc];
             const TS inv = pivv != (TS)0 ? (TS)1 / pivv : (TS)0;
             best = (TS)-1; bi = 0x7fffffff;
-            for (int r = tid; r < R; r += nth) {
-                if (r < cc) continue;
-                if (r == cc) {                     // row cc takes the pivot row
-                    if (pr != cc) {
+            int r = tid;
+            if (r == cc) {                         // row cc takes the pivot row
+                if (pr != cc) {
 #pragma unroll
-                        for (int q = 0; q < IB; ++q) X[(size_t)q * R0 + r] = prow[q];
-                    }
-                    continue;
+                    for (int q = 0; q < IB; ++q) X[(size_t)q * R0 + r] = prow[q];
                 }
-                const bool isp = (r == pr);        // row pr takes the old row cc
-                TS v[IB];
+                r += nth;
+            } else if (r < cc) {
+                r += nth;
+            }
+            for (; r < R; r += nth) {
+                if (r == pr) {                     // row pr takes the old row cc
 #pragma unroll
-                for (int q = 0; q < IB; ++q) v[q] = (q >= cc) ? (isp ? crow[q] : X[(size_t)q * R0 + r]) : (TS)0;
-                if (isp) {
+                    for (int q = 0; q < cc; ++q) X[(size_t)q * R0 + r] = crow[q];
+                    const TS l = crow[cc] * inv;
+                    X[(size_t)cc * R0 + r] = l;
 #pragma unroll
-                    for (int q = 0; q < IB; ++q) if (q < cc) X[(size_t)q * R0 + r] = crow[q];
-                }
-                TS l = (TS)0;
-#pragma unroll
-                for (int q = 0; q < IB; ++q) if (q == cc) l = v[q] * inv;
-#pragma unroll
-                for (int q = 0; q < IB; ++q) {
-                    if (q == cc) X[(size_t)q * R0 + r] = l;
-                    else if (q > cc) {
-                        const TS nv = v[q] - l * prow[q];
+                    for (int q = cc + 1; q < IB; ++q) {
+                        const TS nv = crow[q] - l * prow[q];
                         X[(size_t)q * R0 + r] = nv;
-                        if (q == cc + 1) {
-                            const TS a = tabs(nv);
-                            if (a > best) { best = a; bi = r; }
-                        }
+                        if (q == cc + 1) { const TS a = tabs(nv); if (a > best) { best = a; bi = r; } }
+                    }
+                } else {
+                    const TS l = X[(size_t)cc * R0 + r] * inv;
+                    X[(size_t)cc * R0 + r] = l;
+#pragma unroll
+                    for (int q = cc + 1; q < IB; ++q) {
+                        const TS nv = X[(size_t)q * R0 + r] - l * prow[q];
+                        X[(size_t)q * R0 + r] = nv;
+                        if (q == cc + 1) { const TS a = tabs(nv); if (a > best) { best = a; bi = r; } }
                     }
                 }
             }
@@ -182,37 +186,39 @@ panel_kernel(TS* __restrict__ Sall, int64_t ld, int c, int32_t* __restrict__ piv
             for (int cc = 0; cc < IB; ++cc) row[(size_t)(c + jb + cc) * ld] = X[(size_t)cc * R0 + r];
         }
         if (tid < IB) piv[c + jb + tid] = c + jb + s_piv[tid];
-        // (d) apply the IB swaps to the other columns of the leaf as one net
-        // permutation: slot i (row s_rows[i]) takes the old content of slot s_cont[i]
-        if (tid == 0) {
-            int nr = IB;
-            for (int i = 0; i < IB; ++i) { s_rows[i] = jb + i; s_cont[i] = i; }
-            for (int i = 0; i < IB; ++i) {
-                const int b = jb + s_piv[i];
-                if (b == jb + i) continue;
-                int sb = -1;
-                if (b < jb + IB) sb = b - jb;
-                else {
-                    for (int j = IB; j < nr; ++j) if (s_rows[j] == b) { sb = j; break; }
-                    if (sb < 0) { sb = nr++; s_rows[sb] = b; s_cont[sb] = sb; }
+        if constexpr (IB < LEAF) {
+            // (d) apply the IB swaps to the other columns of the leaf as one net
+            // permutation: slot i (row s_rows[i]) takes the old content of slot s_cont[i]
+            if (tid == 0) {
+                int nr = IB;
+                for (int i = 0; i < IB; ++i) { s_rows[i] = jb + i; s_cont[i] = i; }
+                for (int i = 0; i < IB; ++i) {
+                    const int b = jb + s_piv[i];
+                    if (b == jb + i) continue;
+                    int sb = -1;
+                    if (b < jb + IB) sb = b - jb;
+                    else {
+                        for (int j = IB; j < nr; ++j) if (s_rows[j] == b) { sb = j; break; }
+                        if (sb < 0) { sb = nr++; s_rows[sb] = b; s_cont[sb] = sb; }
+                    }
+                    const int t = s_cont[i]; s_cont[i] = s_cont[sb]; s_cont[sb] = t;
                 }
-                const int t = s_cont[i]; s_cont[i] = s_cont[sb]; s_cont[sb] = t;
+                s_nr = nr;
             }
-            s_nr = nr;
+            __syncthreads();
+            const int nr = s_nr;
+            for (int e = tid; e < LEAF * 2 * IB; e += nth) {
+                const int t = e / (2 * IB), i = e % (2 * IB);
+                if (i < nr && (t < jb || t >= jb + IB)) s_swap[t][i] = S[(size_t)(c + s_rows[i]) + (size_t)(c + t) * ld];
+            }
+            __syncthreads();
+            for (int e = tid; e < LEAF * 2 * IB; e += nth) {
+                const int t = e / (2 * IB), i = e % (2 * IB);
+                if (i < nr && (t < jb || t >= jb + IB) && s_cont[i] != i)
+                    S[(size_t)(c + s_rows[i]) + (size_t)(c + t) * ld] = s_swap[t][s_cont[i]];
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        const int nr = s_nr;
-        for (int e = tid; e < LEAF * 2 * IB; e += nth) {
-            const int t = e / (2 * IB), i = e % (2 * IB);
-            if (i < nr && (t < jb || t >= jb + IB)) s_swap[t][i] = S[(size_t)(c + s_rows[i]) + (size_t)(c + t) * ld];
-        }
-        __syncthreads();
-        for (int e = tid; e < LEAF * 2 * IB; e += nth) {
-            const int t = e / (2 * IB), i = e % (2 * IB);
-            if (i < nr && (t < jb || t >= jb + IB) && s_cont[i] != i)
-                S[(size_t)(c + s_rows[i]) + (size_t)(c + t) * ld] = s_swap[t][s_cont[i]];
-        }
-        __syncthreads();
     }
     if (singular && tid == 0 && status) status[K] = MEHDG_ESINGULAR;
 }
@@ -446,22 +452,27 @@ solve_kernel(const TS* __restrict__ Sall, int64_t ld, const int32_t* __restrict_
     for (int i = tid; i < ld; i += nth) x[i] = (double)y[i] * mx;
 }
 
+// sub-panel width: the whole leaf when its (ld - c) x 32 block fits in the
+// shared-memory budget, else the widest of 8, 4, 2, 1 that fits (16 would
+// need more registers than the left-looking step can hold)
 template <class TS>
-int pick_ib(int64_t ld) {
-    size_t budget = 200 * 1024;
+int pick_ib(int64_t rows) {
+    const size_t budget = 200 * 1024;
+    if ((size_t)LEAF * rows * sizeof(TS) <= budget) return LEAF;
     int ib = 8;
-    while (ib > 1 && (size_t)ib * ld * sizeof(TS) > budget) ib >>= 1;
+    while (ib > 1 && (size_t)ib * rows * sizeof(TS) > budget) ib >>= 1;
     return ib;
 }
 
 template <class TS>
 cudaError_t launch_panel(TS* S, int64_t ld, int c, int32_t* piv, int32_t* status, int64_t nK, cudaStream_t st) {
-    int ib = pick_ib<TS>(ld);
+    int ib = pick_ib<TS>(ld - c);
     size_t sm = (size_t)ib * (ld - c) * sizeof(TS);
     if (sm < 16) sm = 16;
-#define LP(IB) do { cudaFuncSetAttribute(panel_kernel<TS, IB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(ib * ld * sizeof(TS))); \
+#define LP(IB) do { cudaFuncSetAttribute(panel_kernel<TS, IB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
                     panel_kernel<TS, IB><<<(unsigned)nK, PANEL_THREADS, sm, st>>>(S, ld, c, piv, status); } while (0)
     switch (ib) {
+    case 32: LP(32); break;
     case 8: LP(8); break;
     case 4: LP(4); break;
     case 2: LP(2); break;
