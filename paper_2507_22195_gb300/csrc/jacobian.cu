@@ -318,18 +318,25 @@ jac_face_kernel(JacobianArgs a) {
 // Q-elimination term of S = A_vv - A_vq A_qq^-1 A_qv (eq. R3).  A_qq = I x M
 // with M a tensor product of 1-D mass matrices, so C = A_qq^-1 A_qv acts on
 // the q-component (l, d) along the d-lines only: C = (2/h_d) C1_ref (x) I.
-// Per micro-element and direction d, the block
-//   E[(a,k),(c,l)] = sum_x W d_j phi_a phi_c dG_kj/dq_ld      (= -A_vq, q-direction d)
-// is sum-factorised as for A_vv and then multiplied by C along d:
-//   S[(a,k),(b,l)] += sum_{c_d} E[(a,k),(c_d,b_perp)] (2/h_d) C1_ref[c_d][b_d],
-// b_d running over the whole d-line of the macro-element.
+// Composed with the interpolation of q, the q-trial function of direction d
+// is again a tensor product: the micro-element basis in the two other
+// directions and, along d,
+//   chi_b(x_d) = sum_c phi_c(x_d) (2/h_d) C1_ref[c][b]
+// for every node b of the macro-element's d-line (n of them).  So
+//   S[(a,k),(b,l)] += sum_x W sum_j dG_kj/dq_ld d_j phi_a  psi_{b,d}
+// is sum-factorised like A_vv, with n instead of p+1 trial functions along d:
+// stage 1 contracts g1 into H1[k][j][a1 b1][g2 g3]; items (k, a1, a2, b1, b2)
+// contract g2 into registers and g3 for every (a3, b3).  Items run k fastest,
+// then a1, so a warp's atomics fall on runs of consecutive rows 5 A + k.
+// The five test components k are processed kg at a time (kg = 5 unless the
+// stage-1 buffer would not fit in shared memory).
 template <class TS>
 __global__ void __launch_bounds__(256)
-jac_visc_q_volume_kernel(JacobianArgs a, const double* __restrict__ C1) {
+jac_visc_q_volume_kernel(JacobianArgs a, const double* __restrict__ C1, int kg) {
     const Tab& tb = a.tab;
     const int K = blockIdx.y, e = blockIdx.x;
     const int p = tb.p, m = tb.m, n = tb.n, ng = tb.ng, Nn = tb.Nn, nl = tb.nl, npt = tb.npt, p1 = p + 1;
-    const int PP = p1 * p1, G2 = ng * ng;
+    const int G2 = ng * ng, TW = p1 * n;
     const int eo[3] = {(e % m) * p, ((e / m) % m) * p, (e / (m * m)) * p};
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* sL = reinterpret_cast<double*>(smem_raw);
@@ -338,11 +345,9 @@ jac_visc_q_volume_kernel(JacobianArgs a, const double* __restrict__ C1) {
     double* C1s = sW + 8;                                    // [n][n]
     double* vl = C1s + n * n;                                // [5][nl]
     double* vx = vl + 5 * nl;                                // [npt][5]
-    TS* Mt = reinterpret_cast<TS*>(vx + 5 * npt);            // [3][2][ng][PP]
-    TS* P = Mt + 6 * ng * PP;                                // [npt][100]
-    TS* H1 = P + (size_t)npt * 100;                          // [4][PP][G2]
-    TS* H2 = H1 + 4 * PP * G2;                               // [4][PP][PP][ng]
-    TS* E = H2 + 4 * PP * PP * ng;                           // [PP^3]
+    TS* T = reinterpret_cast<TS*>(vx + 5 * npt);             // [3 dir][2 tau][ng][TW]
+    TS* P = T + 6 * ng * TW;                                 // [npt][3 j][25 kl]
+    TS* H1 = P + (size_t)npt * 75;                           // [kg][3 j][TW][G2]
     const int tid = threadIdx.x, nth = blockDim.x;
     load_tables(tb, sL, sD, sW);
     double sc[3], hw[3];
@@ -354,12 +359,6 @@ jac_visc_q_volume_kernel(JacobianArgs a, const double* __restrict__ C1) {
         for (int k = 0; k < 5; ++k) vl[k * nl + i] = a.v[oV + k * Nn + A];
     }
     __syncthreads();
-    for (int i = tid; i < 6 * ng * PP; i += nth) {
-        int ab = i % PP, g = (i / PP) % ng, dt = i / (PP * ng), d = dt >> 1, tau = dt & 1;
-        int aa = ab / p1, bb = ab % p1;
-        double t = tau ? sD[g * p1 + aa] * sc[d] : sL[g * p1 + aa];
-        Mt[i] = (TS)(t * sL[g * p1 + bb]);
-    }
     for (int x = tid; x < npt; x += nth) {
         int g1 = x % ng, g2 = (x / ng) % ng, g3 = x / (ng * ng);
         double s5[5] = {0, 0, 0, 0, 0};
@@ -371,11 +370,31 @@ jac_visc_q_volume_kernel(JacobianArgs a, const double* __restrict__ C1) {
     }
     __syncthreads();
     TS* S = reinterpret_cast<TS*>(a.S) + (size_t)K * a.ld * a.ld;
-    const TS* M1 = Mt;
-    const TS* M2 = Mt + 2 * ng * PP;
-    const TS* M3 = Mt + 4 * ng * PP;
     for (int d = 0; d < 3; ++d) {
-        // point blocks P[x][1+j][k*5+l] = W dG_kj/dq_ld (G is linear in q)
+        int nb[3];
+        for (int q = 0; q < 3; ++q) nb[q] = q == d ? n : p1;
+        // tables T[dir][tau][g][a * nb + b]: (tau ? dphi_a : phi_a)(g) times phi_b(g),
+        // or chi_b(g) along the line direction d
+        for (int i = tid; i < 6 * ng * TW; i += nth) {
+            const int col = i % TW, g = (i / TW) % ng, dt = i / (TW * ng), dir = dt >> 1, tau = dt & 1;
+            const int w = nb[dir];
+            TS val = 0;
+            if (col < p1 * w) {
+                const int aa = col / w, bb = col % w;
+                const double t = tau ? sD[g * p1 + aa] * sc[dir] : sL[g * p1 + aa];
+                double trial;
+                if (dir == d) {
+                    trial = 0.0;
+                    for (int c = 0; c < p1; ++c) trial += sL[g * p1 + c] * C1s[(eo[d] + c) * n + bb];
+                    trial *= sc[d];
+                } else {
+                    trial = sL[g * p1 + bb];
+                }
+                val = (TS)(t * trial);
+            }
+            T[i] = val;
+        }
+        // point blocks P[x][j][k*5+l] = W dG_kj/dq_ld (G is linear in q)
         for (int x = tid; x < npt; x += nth) {
             int g1 = x % ng, g2 = (x / ng) % ng, g3 = x / (ng * ng);
             Dual<15> v15[5], q15[15], G[5][3];
@@ -383,71 +402,82 @@ jac_visc_q_volume_kernel(JacobianArgs a, const double* __restrict__ C1) {
             for (int c = 0; c < 15; ++c) { q15[c] = mkdual<15>(0.0); q15[c].d[c] = 1.0; }
             visc_flux(v15, q15, a.ph, G);
             double W = sW[g1] * hw[0] * sW[g2] * hw[1] * sW[g3] * hw[2];
-            TS* Px = P + (size_t)x * 100;
-            for (int kl = 0; kl < 25; ++kl) Px[kl] = (TS)0;
+            TS* Px = P + (size_t)x * 75;
             for (int j = 0; j < 3; ++j)
                 for (int k = 0; k < 5; ++k)
-                    for (int l = 0; l < 5; ++l) Px[25 * (1 + j) + k * 5 + l] = (TS)(W * G[k][j].d[l * 3 + d]);
+                    for (int l = 0; l < 5; ++l) Px[25 * j + k * 5 + l] = (TS)(W * G[k][j].d[l * 3 + d]);
         }
         __syncthreads();
-        const double cs = sc[d];        // 2/h_d
-        for (int kl = 0; kl < 25; ++kl) {
-            for (int i = tid; i < 4 * PP * G2; i += nth) {
-                int g23 = i % G2, ab1 = (i / G2) % PP, al = i / (G2 * PP);
-                const TS* Mx = M1 + (al == 1 ? ng * PP : 0);
-                TS s = 0;
-                if (al) for (int g1 = 0; g1 < ng; ++g1) s += Mx[g1 * PP + ab1] * P[(size_t)(g1 + ng * g23) * 100 + 25 * al + kl];
-                H1[i] = s;
-            }
-            __syncthreads();
-            for (int i = tid; i < 4 * PP * PP * ng; i += nth) {
-                int g3 = i % ng, ab2 = (i / ng) % PP, ab1 = (i / (ng * PP)) % PP, al = i / (ng * PP * PP);
-                const TS* My = M2 + (al == 2 ? ng * PP : 0);
-                const TS* h = H1 + ((size_t)al * PP + ab1) * G2 + ng * g3;
-                TS s = 0;
-                if (al) for (int g2 = 0; g2 < ng; ++g2) s += My[g2 * PP + ab2] * h[g2];
-                H2[i] = s;
-            }
-            __syncthreads();
-            for (int i = tid; i < PP * PP * PP; i += nth) {
-                int ab3 = i % PP, ab2 = (i / PP) % PP, ab1 = i / (PP * PP);
-                TS s = 0;
-                for (int al = 1; al < 4; ++al) {
-                    const TS* Mz = M3 + (al == 3 ? ng * PP : 0);
-                    const TS* h = H2 + (((size_t)al * PP + ab1) * PP + ab2) * ng;
-                    for (int g3 = 0; g3 < ng; ++g3) s += Mz[g3 * PP + ab3] * h[g3];
+        const TS* T1 = T + (0 * 2) * ng * TW;         // direction x (tau at + ng * TW)
+        const TS* T2 = T + (1 * 2) * ng * TW;
+        const TS* T3 = T + (2 * 2) * ng * TW;
+        const int nh1 = 3 * TW * G2;
+        for (int l = 0; l < 5; ++l)
+            for (int k0 = 0; k0 < 5; k0 += kg) {
+                const int kn = 5 - k0 < kg ? 5 - k0 : kg;
+                // stage 1: H1[kk][j][a1 * nb0 + b1][g23] = sum_g1 T1_(j==0)[g1][a1 b1] P[x][j][k l]
+                for (int i = tid; i < kn * 3 * p1 * nb[0] * G2; i += nth) {
+                    const int g23 = i % G2, ab1 = (i / G2) % (p1 * nb[0]);
+                    const int j = (i / (G2 * p1 * nb[0])) % 3, kk = i / (G2 * p1 * nb[0] * 3);
+                    const TS* Tx = T1 + (j == 0 ? ng * TW : 0) + ab1;
+                    const TS* Pc = P + (size_t)ng * g23 * 75 + 25 * j + 5 * (k0 + kk) + l;
+                    TS s = 0;
+                    for (int g1 = 0; g1 < ng; ++g1) s += Tx[g1 * TW] * Pc[(size_t)g1 * 75];
+                    H1[(size_t)kk * nh1 + ((size_t)j * TW + ab1) * G2 + g23] = s;
                 }
-                E[i] = s;
-            }
-            __syncthreads();
-            // multiply by C along d and add into S: (a, c_perp, b_d)
-            const int k = kl / 5, l = kl % 5;
-            const int dA = d == 0 ? 1 : 0, dB = d == 2 ? 1 : 2;       // the two other directions
-            for (int i = tid; i < nl * PP * n; i += nth) {
-                int bd = i % n, cp = (i / n) % PP, ia = i / (n * PP);
-                int la[3] = {ia % p1, (ia / p1) % p1, ia / (p1 * p1)};
-                int lc[3];
-                lc[dA] = cp % p1; lc[dB] = cp / p1;
-                double s = 0.0;
-                for (int cd = 0; cd <= p; ++cd) {
-                    lc[d] = cd;
-                    int ab1 = la[0] * p1 + lc[0], ab2 = la[1] * p1 + lc[1], ab3 = la[2] * p1 + lc[2];
-                    s += (double)E[(ab1 * PP + ab2) * PP + ab3] * C1s[(eo[d] + cd) * n + bd];
+                __syncthreads();
+                const int nitem = kn * p1 * p1 * nb[0] * nb[1];
+                for (int it = tid; it < nitem; it += nth) {
+                    int r = it;
+                    const int kk = r % kn; r /= kn;
+                    const int a1 = r % p1; r /= p1;
+                    const int a2 = r % p1; r /= p1;
+                    const int b1 = r % nb[0]; const int b2 = r / nb[0];
+                    const int ab1 = a1 * nb[0] + b1, ab2 = a2 * nb[1] + b2;
+                    TS h2[3][MEHDG_MAXG];
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        const TS* Ty = T2 + (j == 1 ? ng * TW : 0) + ab2;
+                        const TS* h = H1 + (size_t)kk * nh1 + ((size_t)j * TW + ab1) * G2;
+#pragma unroll
+                        for (int g3 = 0; g3 < MEHDG_MAXG; ++g3) {
+                            TS s = 0;
+                            if (g3 < ng)
+                                for (int g2 = 0; g2 < ng; ++g2) s += Ty[g2 * TW] * h[g2 + ng * g3];
+                            h2[j][g3] = s;
+                        }
+                    }
+                    const int k = k0 + kk;
+                    const int A12 = (eo[0] + a1) + n * (eo[1] + a2);
+                    const int B1 = d == 0 ? b1 : eo[0] + b1, B2 = d == 1 ? b2 : eo[1] + b2;
+                    for (int a3 = 0; a3 < p1; ++a3)
+                        for (int b3 = 0; b3 < nb[2]; ++b3) {
+                            const int ab3 = a3 * nb[2] + b3;
+                            TS s = 0;
+#pragma unroll
+                            for (int j = 0; j < 3; ++j) {
+                                const TS* Tz = T3 + (j == 2 ? ng * TW : 0) + ab3;
+#pragma unroll
+                                for (int g3 = 0; g3 < MEHDG_MAXG; ++g3)
+                                    if (g3 < ng) s += Tz[g3 * TW] * h2[j][g3];
+                            }
+                            const int A = A12 + n * n * (eo[2] + a3);
+                            const int B = B1 + n * (B2 + n * (d == 2 ? b3 : eo[2] + b3));
+                            atomic_add_t(&S[(size_t)(A * 5 + k) + (size_t)(B * 5 + l) * a.ld], (double)s);
+                        }
                 }
-                int A = (eo[0] + la[0]) + n * ((eo[1] + la[1]) + n * (eo[2] + la[2]));
-                int bc[3] = {eo[0] + lc[0], eo[1] + lc[1], eo[2] + lc[2]};
-                bc[d] = bd;
-                int B = bc[0] + n * (bc[1] + n * bc[2]);
-                atomic_add_t(&S[(size_t)(A * 5 + k) + (size_t)(B * 5 + l) * a.ld], s * cs);
+                __syncthreads();
             }
-            __syncthreads();
-        }
     }
 }
 
 // face part of -A_vq C: G-hat = G(vhat, q).n depends on the interior q at the
-// face points, A_vq(face) = sum_x w mu_a dGhat_k/dq_ld phi_c (face nodes c),
-// multiplied by C along d (the normal line for d = the face direction).
+// face points, with the same q-trial functions restricted to the face: along
+// the normal direction (d = face direction) chi_b at the face end is the
+// constant (2/h) C1_ref[end][b]; along a tangential direction it is chi_b of
+// that direction.  Per face and q-direction d: stage 1 contracts g1 into
+// H1[k][a1 b1][g2], items (k, a1, a2, b1, b2) contract g2 and add the result
+// (times the normal factor for every b on the normal line when d is normal).
 template <class TS>
 __global__ void __launch_bounds__(256)
 jac_visc_q_face_kernel(JacobianArgs a, const double* __restrict__ C1) {
@@ -459,14 +489,16 @@ jac_visc_q_face_kernel(JacobianArgs a, const double* __restrict__ C1) {
     const int df = f / 2, t1 = df == 0 ? 1 : 0, t2 = df == 2 ? 1 : 2;
     const double sgn = (f & 1) ? 1.0 : -1.0;
     const int iface = (f & 1) ? n - 1 : 0;
-    const int fl = p1 * p1, fpt = ng * ng;
+    const int fl = p1 * p1, fpt = ng * ng, TW = p1 * n;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* sL = reinterpret_cast<double*>(smem_raw);
     double* sW = sL + MEHDG_MAXG * (MEHDG_MAXP + 1);
     double* C1s = sW + 8;             // [n][n]
     double* fh = C1s + n * n;         // [5][fl]
-    TS* PF = reinterpret_cast<TS*>(fh + 5 * fl);   // [fpt][3][25]
-    TS* E = PF + (size_t)fpt * 75;                  // [fl][fl]
+    TS* PF = reinterpret_cast<TS*>(fh + 5 * fl);   // [fpt][3 d][25 kl]
+    TS* T = PF + (size_t)fpt * 75;                  // [2 tangential][ng][TW]
+    TS* H1 = T + 2 * ng * TW;                       // [5][TW][ng]
+    TS* cn = H1 + 5 * TW * ng;                      // [n] normal factors
     const int tid = threadIdx.x, nth = blockDim.x;
     for (int i = tid; i < ng * p1; i += nth) sL[i] = tb.L[i / p1][i % p1];
     if (tid < ng) sW[tid] = tb.w[tid];
@@ -496,34 +528,61 @@ jac_visc_q_face_kernel(JacobianArgs a, const double* __restrict__ C1) {
             for (int k = 0; k < 5; ++k)
                 for (int l = 0; l < 5; ++l) PF[(size_t)x * 75 + d * 25 + k * 5 + l] = (TS)(W * G[k][df].d[l * 3 + d]);
     }
-    __syncthreads();
     TS* S = reinterpret_cast<TS*>(a.S) + (size_t)K * a.ld * a.ld;
+    const int eo1 = e1 * p, eo2 = e2 * p;
     for (int d = 0; d < 3; ++d) {
-        const double cs = 2.0 / h[d];
-        for (int kl = 0; kl < 25; ++kl) {
-            for (int r = tid; r < fl * fl; r += nth) {
-                int ia = r / fl, ic = r % fl;
-                TS s = 0;
-                for (int x = 0; x < fpt; ++x) {
-                    int g1 = x % ng, g2 = x / ng;
-                    s += (TS)(sL[g1 * p1 + ia % p1] * sL[g2 * p1 + ia / p1] * sL[g1 * p1 + ic % p1] *
-                              sL[g2 * p1 + ic / p1]) * PF[(size_t)x * 75 + d * 25 + kl];
+        const int nb1 = d == t1 ? n : p1, nb2 = d == t2 ? n : p1, nn = d == df ? n : 1;
+        __syncthreads();
+        // tables T[u][g][a * nb_u + b] for the tangential directions u = t1, t2
+        for (int i = tid; i < 2 * ng * TW; i += nth) {
+            const int col = i % TW, g = (i / TW) % ng, u = i / (TW * ng);
+            const int dir = u == 0 ? t1 : t2, w = u == 0 ? nb1 : nb2, eo = u == 0 ? eo1 : eo2;
+            TS val = 0;
+            if (col < p1 * w) {
+                const int aa = col / w, bb = col % w;
+                double trial;
+                if (dir == d) {
+                    trial = 0.0;
+                    for (int c = 0; c < p1; ++c) trial += sL[g * p1 + c] * C1s[(eo + c) * n + bb];
+                    trial *= 2.0 / h[d];
+                } else {
+                    trial = sL[g * p1 + bb];
                 }
-                E[r] = s;
+                val = (TS)(sL[g * p1 + aa] * trial);
+            }
+            T[i] = val;
+        }
+        for (int i = tid; i < n; i += nth) cn[i] = d == df ? (TS)(C1s[iface * n + i] * 2.0 / h[d]) : (TS)1;
+        __syncthreads();
+        for (int l = 0; l < 5; ++l) {
+            for (int i = tid; i < 5 * p1 * nb1 * ng; i += nth) {
+                const int g2 = i % ng, ab1 = (i / ng) % (p1 * nb1), k = i / (ng * p1 * nb1);
+                TS s = 0;
+                for (int g1 = 0; g1 < ng; ++g1)
+                    s += T[g1 * TW + ab1] * PF[(size_t)(g1 + ng * g2) * 75 + d * 25 + k * 5 + l];
+                H1[((size_t)k * TW + ab1) * ng + g2] = s;
             }
             __syncthreads();
-            const int k = kl / 5, l = kl % 5;
-            for (int i = tid; i < fl * fl * n; i += nth) {
-                int bd = i % n, ic = (i / n) % fl, ia = i / (n * fl);
-                int ca[3], cc[3];
-                ca[df] = iface; ca[t1] = e1 * p + ia % p1; ca[t2] = e2 * p + ia / p1;
-                cc[df] = iface; cc[t1] = e1 * p + ic % p1; cc[t2] = e2 * p + ic / p1;
-                const int cd = cc[d];
-                cc[d] = bd;
-                int A = ca[0] + n * (ca[1] + n * ca[2]);
-                int B = cc[0] + n * (cc[1] + n * cc[2]);
-                atomic_add_t(&S[(size_t)(A * 5 + k) + (size_t)(B * 5 + l) * a.ld],
-                             -(double)E[ic + fl * ia] * C1s[cd * n + bd] * cs);
+            const int nitem = 5 * p1 * p1 * nb1 * nb2;
+            for (int it = tid; it < nitem; it += nth) {
+                int r = it;
+                const int k = r % 5; r /= 5;
+                const int a1 = r % p1; r /= p1;
+                const int a2 = r % p1; r /= p1;
+                const int b1 = r % nb1; const int b2 = r / nb1;
+                const TS* hk = H1 + ((size_t)k * TW + a1 * nb1 + b1) * ng;
+                const TS* Ty = T + ng * TW + a2 * nb2 + b2;
+                TS s = 0;
+                for (int g2 = 0; g2 < ng; ++g2) s += Ty[g2 * TW] * hk[g2];
+                int ca[3], cb[3];
+                ca[df] = iface; ca[t1] = eo1 + a1; ca[t2] = eo2 + a2;
+                cb[df] = iface; cb[t1] = d == t1 ? b1 : eo1 + b1; cb[t2] = d == t2 ? b2 : eo2 + b2;
+                const int A = ca[0] + n * (ca[1] + n * ca[2]);
+                for (int bd = 0; bd < nn; ++bd) {
+                    if (d == df) cb[df] = bd;
+                    const int B = cb[0] + n * (cb[1] + n * cb[2]);
+                    atomic_add_t(&S[(size_t)(A * 5 + k) + (size_t)(B * 5 + l) * a.ld], -(double)(s * cn[bd]));
+                }
             }
             __syncthreads();
         }
@@ -577,16 +636,19 @@ cudaError_t launch_jacobian(const JacobianArgs& a, int64_t nK, bool fp64, cudaSt
 #undef LJ
     MEHDG_COUNT(2);
     if (visc) {
-        const size_t PP = (size_t)(t.p + 1) * (t.p + 1), G2 = (size_t)t.ng * t.ng;
-        size_t sq = sizeof(double) * (HEAD_DOUBLES + (size_t)t.n * t.n + 5 * (size_t)t.nl + 5 * (size_t)t.npt)
-                  + ts * (6 * (size_t)t.ng * PP + 100 * (size_t)t.npt + 4 * PP * G2 + 4 * PP * PP * t.ng + PP * PP * PP) + 16;
+        const size_t G2 = (size_t)t.ng * t.ng, TW = (size_t)(t.p + 1) * t.n;
+        const size_t base = sizeof(double) * (HEAD_DOUBLES + (size_t)t.n * t.n + 5 * (size_t)t.nl + 5 * (size_t)t.npt)
+                          + ts * (6 * (size_t)t.ng * TW + 75 * (size_t)t.npt) + 16;
+        int kg = 5;
+        while (kg > 1 && base + ts * (size_t)kg * 3 * TW * G2 > 220 * 1024) --kg;
+        const size_t sq = base + ts * (size_t)kg * 3 * TW * G2;
         size_t sqf = sizeof(double) * (MEHDG_MAXG * (MEHDG_MAXP + 1) + 8 + (size_t)t.n * t.n + 5 * (size_t)fl)
-                   + ts * (75 * (size_t)fpt + (size_t)fl * fl) + 16;
+                   + ts * (75 * (size_t)fpt + 2 * (size_t)t.ng * TW + 5 * TW * t.ng + t.n) + 16;
         if (sq > 227 * 1024) return cudaErrorInvalidValue;      // FP64 at p = 4: not supported
 #define LQ(TS)                                                                                          \
         do { cudaFuncSetAttribute(jac_visc_q_volume_kernel<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sq); \
              cudaFuncSetAttribute(jac_visc_q_face_kernel<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sqf); \
-             jac_visc_q_volume_kernel<TS><<<gv, b, sq, st>>>(a, a.C1);                                 \
+             jac_visc_q_volume_kernel<TS><<<gv, b, sq, st>>>(a, a.C1, kg);                             \
              jac_visc_q_face_kernel<TS><<<gf, b, sqf, st>>>(a, a.C1); } while (0)
         if (fp64) LQ(double); else LQ(float);
 #undef LQ
