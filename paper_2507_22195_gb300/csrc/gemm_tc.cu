@@ -425,11 +425,6 @@ int sm_count() {
     return n;
 }
 
-size_t perm_bytes(int64_t nK) {
-    size_t b = (size_t)nK * (1 + 4 * LU_NB) * sizeof(int32_t);
-    return (b + 255) & ~(size_t)255;
-}
-
 // one operand panel: ld rows x (2 segments x 256) FP32 per element
 size_t panel_bytes(int64_t nK, int64_t ld) {
     size_t b = (size_t)nK * ld * 2 * LU_NB * 4;
@@ -504,7 +499,7 @@ cudaError_t gemm_tc_trsm256(const LUPlan& P, int c0, int j0, int j1, cudaStream_
     const int nseg = 2;
     const int chunk_k = CHUNK_BYTES / 4;
     const int nchunk = Kd / chunk_k;
-    unsigned char* w = reinterpret_cast<unsigned char*>(P.work) + perm_bytes(P.nK);
+    unsigned char* w = reinterpret_cast<unsigned char*>(P.work) + lu_perm_bytes(P.nK, P.ld);
     const size_t pan = panel_bytes(P.nK, P.ld);
     void* Ap = w;
     void* Bp = w + pan;
@@ -539,7 +534,7 @@ cudaError_t gemm_tc_update(const LUPlan& P, int r0, int c0, int k0, int M, int N
     const int chunk_k = CHUNK_BYTES / es;
     const int Kp = (Kd + chunk_k - 1) / chunk_k * chunk_k;
     const int nchunk = Kp / chunk_k;
-    unsigned char* w = reinterpret_cast<unsigned char*>(P.work) + perm_bytes(P.nK);
+    unsigned char* w = reinterpret_cast<unsigned char*>(P.work) + lu_perm_bytes(P.nK, P.ld);
     const size_t pan = panel_bytes(P.nK, P.ld);
     void* Ap = w;
     void* Bp = w + pan;
@@ -574,5 +569,5 @@ extern "C" int mehdg_test_trailing_update(int64_t nK, int64_t ld, float* S, int 
 }
 
 extern "C" size_t mehdg_test_trailing_work_bytes(int64_t nK, int64_t ld) {
-    return perm_bytes(nK) + gemm_tc_work_bytes(nK, ld, 1);
+    return lu_perm_bytes(nK, ld) + gemm_tc_work_bytes(nK, ld, 1);
 }

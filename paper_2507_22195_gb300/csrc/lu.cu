@@ -372,84 +372,192 @@ gemm_simt_kernel(TS* __restrict__ Sall, int64_t ld, int r0, int c0, int k0, int 
 }
 
 // ---------------------------------------------------------------- solve
-// One CTA per element: forward substitution with the LINPACK-ordered unit
-// lower factor (outer-panel swaps replayed first), then backward with U.
+// CL CTAs (one thread-block cluster) per element.  The 32-row blocks of the
+// right-hand side are owned cyclically (block b by rank b mod CL, and inside
+// it by warp (b / CL) mod 16); y lives in each CTA's shared memory, and an
+// owned block holds working values while every other block receives the final
+// values its owner broadcasts into the CTA (distributed shared memory).
+// Forward (unit-lower L, LINPACK order): at each outer panel the net
+// permutation kept by the factorisation is applied (gather through
+// distributed shared memory between full cluster barriers); then, block by
+// block, the owning warp of block s+1 first applies block s to its rows,
+// solves its 32 x 32 triangle, broadcasts the result and arrives on the
+// cluster barrier, while the other warps arrive at once and apply block s to
+// their rows.  Backward with U the same way from the last block.  One cluster
+// barrier phase per block; the factors are read once per solve.
 // Arithmetic in the factor precision; r scaled by its max norm.
-template <class TS>
-__global__ void __launch_bounds__(512)
-solve_kernel(const TS* __restrict__ Sall, int64_t ld, const int32_t* __restrict__ pivall,
-             const double* __restrict__ rall, double* __restrict__ xall, const int32_t* skip, int NBo) {
-    const int K = blockIdx.x;
-    if (skip && skip[K]) return;
+__device__ __forceinline__ uint32_t cl_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cl_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cl_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cl_sync() { cl_arrive(); cl_wait(); }
+__device__ __forceinline__ uint32_t cl_map(const void* p, uint32_t rank) {
+    uint32_t a;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+                 : "=r"(a) : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(rank));
+    return a;
+}
+__device__ __forceinline__ void cl_st(uint32_t a, float v) { asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory"); }
+__device__ __forceinline__ void cl_st(uint32_t a, double v) { asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory"); }
+__device__ __forceinline__ float cl_ld(uint32_t a, float) {
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ double cl_ld(uint32_t a, double) {
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a) : "memory");
+    return v;
+}
+
+constexpr int SOLVE_THREADS = 512;
+constexpr int SOLVE_WARPS = SOLVE_THREADS / 32;
+
+template <class TS, int CL>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(SOLVE_THREADS)
+solve_kernel(const TS* __restrict__ Sall, int64_t ld, const int32_t* __restrict__ perms, int64_t nK,
+             const double* __restrict__ rall, double* __restrict__ xall, const int32_t* skip) {
+    constexpr int BPP = LU_NB / 32;                // 32-row blocks per outer panel
+    const int K = blockIdx.x / CL;
+    if (skip && skip[K]) return;                   // the whole cluster leaves together
+    const int rank = CL > 1 ? (int)cl_rank() : 0;
     const TS* S = Sall + (size_t)K * ld * ld;
-    const int32_t* piv = pivall + (size_t)K * ld;
     const double* r = rall + (size_t)K * ld;
     double* x = xall + (size_t)K * ld;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    TS* y = reinterpret_cast<TS*>(smem_raw);
-    __shared__ double red[16];
-    const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, wid = tid >> 5;
+    TS* y = reinterpret_cast<TS*>(smem_raw);        // [ld]
+    TS* tmp = y + ld;                                // [2 NB] permutation gather
+    __shared__ double red[SOLVE_WARPS];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int nb = (int)(ld / 32);
+    auto owner = [](int b) { return b % CL; };
+    auto wslot = [](int b) { return (b / CL) % SOLVE_WARPS; };
+    // the first block this warp owns above (dir > 0) or below (dir < 0) block s
+    auto first_mine = [&](int s, int dir) {
+        // owned blocks of this warp: b = rank + CL (wid + SOLVE_WARPS u)
+        const int step = CL * SOLVE_WARPS, b0 = rank + CL * wid;
+        if (dir > 0) {
+            if (b0 > s) return b0;
+            return b0 + ((s - b0) / step + 1) * step;
+        }
+        if (b0 >= s) return -1;
+        return b0 + ((s - 1 - b0) / step) * step;
+    };
+    auto broadcast = [&](int b, TS v) {
+        for (int rk = 0; rk < CL; ++rk)
+            if (rk != rank) cl_st(cl_map(&y[32 * b + lane], (uint32_t)rk), v);
+    };
+    // row block b -= (L or U)[block b, block s] * y_block(s)
+    auto apply = [&](int b, int s) {
+        const TS* col = S + (size_t)(32 * b + lane) + (size_t)(32 * s) * ld;
+        TS l[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) l[j] = col[(size_t)j * ld];
+        TS acc = y[32 * b + lane];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc -= l[j] * y[32 * s + j];
+        y[32 * b + lane] = acc;
+    };
+    auto tri_lower = [&](int s) {
+        const TS* col = S + (size_t)(32 * s + lane) + (size_t)(32 * s) * ld;
+        TS l[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) l[j] = col[(size_t)j * ld];
+        TS yl = y[32 * s + lane];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            const TS yi = __shfl_sync(0xffffffffu, yl, i);
+            if (lane > i) yl -= l[i] * yi;
+        }
+        y[32 * s + lane] = yl;
+        broadcast(s, yl);
+    };
+    auto tri_upper = [&](int s) {
+        const TS* col = S + (size_t)(32 * s + lane) + (size_t)(32 * s) * ld;
+        TS u[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) u[j] = col[(size_t)j * ld];
+        TS yl = y[32 * s + lane];
+#pragma unroll
+        for (int i = 31; i >= 0; --i) {
+            if (lane == i) yl = yl / u[i];
+            const TS yi = __shfl_sync(0xffffffffu, yl, i);
+            if (lane < i) yl -= u[i] * yi;
+        }
+        y[32 * s + lane] = yl;
+        broadcast(s, yl);
+    };
+
+    // scale by the max norm of r (every CTA of the cluster computes it)
     double mx = 0.0;
-    for (int i = tid; i < ld; i += nth) mx = fmax(mx, fabs(r[i]));
+    for (int i = tid; i < ld; i += SOLVE_THREADS) mx = fmax(mx, fabs(r[i]));
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (lane == 0) red[wid] = mx;
     __syncthreads();
     mx = 0.0;
-    for (int i = 0; i < nth / 32; ++i) mx = fmax(mx, red[i]);
+    for (int i = 0; i < SOLVE_WARPS; ++i) mx = fmax(mx, red[i]);
     const double sc = mx > 0.0 ? 1.0 / mx : 1.0;
-    for (int i = tid; i < ld; i += nth) y[i] = (TS)(r[i] * sc);
-    __syncthreads();
+    for (int i = tid; i < ld; i += SOLVE_THREADS)
+        if (owner(i >> 5) == rank) y[i] = (TS)(r[i] * sc);
+
     // forward
-    for (int c0 = 0; c0 < ld; c0 += NBo) {
-        if (tid == 0)
-            for (int i = c0; i < c0 + NBo; ++i) {
-                int b = piv[i];
-                if (b != i) { TS t = y[i]; y[i] = y[b]; y[b] = t; }
-            }
-        __syncthreads();
-        for (int cb = c0; cb < c0 + NBo; cb += 32) {
-            if (wid == 0) {
-                TS yl = y[cb + lane];
-                for (int i = 0; i < 32; ++i) {
-                    TS yi = __shfl_sync(0xffffffffu, yl, i);
-                    if (lane > i) yl -= S[(size_t)(cb + lane) + (size_t)(cb + i) * ld] * yi;
+    for (int s = 0; s < nb; ++s) {
+        if (s % BPP == 0) {
+            cl_sync();                              // every row below is up to date
+            const int32_t* pl = perms + ((size_t)(s / BPP) * nK + K) * LU_PW;
+            const int nr = pl[0];
+            const int32_t* rows = pl + 1;
+            const int32_t* cont = rows + 2 * LU_NB;
+            for (int i = tid; i < nr; i += SOLVE_THREADS) {
+                const int row = rows[i], ci = cont[i];
+                if (ci != i && owner(row >> 5) == rank) {
+                    const int src = rows[ci], os = owner(src >> 5);
+                    tmp[i] = os == rank ? y[src] : cl_ld(cl_map(&y[src], (uint32_t)os), (TS)0);
                 }
-                y[cb + lane] = yl;
             }
-            __syncthreads();
-            for (int rr = cb + 32 + tid; rr < ld; rr += nth) {
-                TS s = y[rr];
-                const TS* Lr = S + rr + (size_t)cb * ld;
-#pragma unroll 8
-                for (int q = 0; q < 32; ++q) s -= Lr[(size_t)q * ld] * y[cb + q];
-                y[rr] = s;
+            cl_sync();
+            for (int i = tid; i < nr; i += SOLVE_THREADS) {
+                const int row = rows[i];
+                if (cont[i] != i && owner(row >> 5) == rank) y[row] = tmp[i];
             }
-            __syncthreads();
+            cl_sync();
+            if (owner(s) == rank && wid == wslot(s)) tri_lower(s);
+            cl_sync();
+        } else {
+            cl_wait();
         }
+        const bool next_regular = s + 1 < nb && (s + 1) % BPP != 0;
+        const bool crit = next_regular && owner(s + 1) == rank && wid == wslot(s + 1);
+        if (next_regular) {
+            if (crit) { apply(s + 1, s); tri_lower(s + 1); }
+            cl_arrive();
+        }
+        for (int b = first_mine(s, 1); b < nb; b += CL * SOLVE_WARPS)
+            if (!(crit && b == s + 1)) apply(b, s);
     }
     // backward
-    for (int cb = (int)ld - 32; cb >= 0; cb -= 32) {
-        if (wid == 0) {
-            TS yl = y[cb + lane];
-            for (int i = 31; i >= 0; --i) {
-                TS yi = 0;
-                if (lane == i) { yl = yl / S[(size_t)(cb + i) + (size_t)(cb + i) * ld]; }
-                yi = __shfl_sync(0xffffffffu, yl, i);
-                if (lane < i) yl -= S[(size_t)(cb + lane) + (size_t)(cb + i) * ld] * yi;
-            }
-            y[cb + lane] = yl;
+    for (int s = nb - 1; s >= 0; --s) {
+        if (s == nb - 1) {
+            cl_sync();
+            if (owner(s) == rank && wid == wslot(s)) tri_upper(s);
+            cl_sync();
+        } else {
+            cl_wait();
         }
-        __syncthreads();
-        for (int rr = tid; rr < cb; rr += nth) {
-            TS s = y[rr];
-            const TS* Ur = S + rr + (size_t)cb * ld;
-#pragma unroll 8
-            for (int q = 0; q < 32; ++q) s -= Ur[(size_t)q * ld] * y[cb + q];
-            y[rr] = s;
+        const bool crit = s >= 1 && owner(s - 1) == rank && wid == wslot(s - 1);
+        if (s >= 1) {
+            if (crit) { apply(s - 1, s); tri_upper(s - 1); }
+            cl_arrive();
         }
-        __syncthreads();
+        for (int b = first_mine(s, -1); b >= 0; b -= CL * SOLVE_WARPS)
+            if (!(crit && b == s - 1)) apply(b, s);
     }
-    for (int i = tid; i < ld; i += nth) x[i] = (double)y[i] * mx;
+    cl_sync();                                      // no CTA leaves while its y may still be read
+    for (int i = tid; i < ld; i += SOLVE_THREADS)
+        if (owner(i >> 5) == rank) x[i] = (double)y[i] * mx;
 }
 
 // sub-panel width: the whole leaf when its (ld - c) x 32 block fits in the
@@ -483,18 +591,39 @@ cudaError_t launch_panel(TS* S, int64_t ld, int c, int32_t* piv, int32_t* status
     return cudaGetLastError();
 }
 
-template <class TS>
-cudaError_t launch_laswp(const LUPlan& P, int c0, int w, int j0, int j1, cudaStream_t st) {
-    if (j1 <= j0) return cudaSuccess;
-    int32_t* perm = reinterpret_cast<int32_t*>(P.work);
+// net permutation of the swaps piv[c0 .. c0+w) of every element into perm ([nK][LU_PW])
+cudaError_t launch_perm_build(const LUPlan& P, int c0, int w, int32_t* perm, cudaStream_t st) {
     perm_build_kernel<<<(unsigned)((P.nK + 3) / 4), 128, 4 * 4 * w * sizeof(int32_t), st>>>(P.piv, P.ld, c0, w,
                                                                                            perm, (int)P.nK);
+    MEHDG_COUNT(1);
+    return cudaGetLastError();
+}
+
+// outer panel c0's permutation, kept in the workspace for the solves
+int32_t* panel_perm(const LUPlan& P, int c0) {
+    return reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(P.work) + lu_perm_scratch_bytes(P.nK)) +
+           (size_t)(c0 / LU_NB) * P.nK * LU_PW;
+}
+
+// row exchanges of the columns [j0, j1) by a permutation built with width w
+template <class TS>
+cudaError_t launch_laswp_perm(const LUPlan& P, const int32_t* perm, int w, int j0, int j1, cudaStream_t st) {
+    if (j1 <= j0) return cudaSuccess;
     size_t sm = (size_t)8 * 2 * w * sizeof(TS);
     cudaFuncSetAttribute(laswp_kernel<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     dim3 g((unsigned)((j1 - j0 + 7) / 8), (unsigned)P.nK);
     laswp_kernel<TS><<<g, 256, sm, st>>>((TS*)P.S, P.ld, perm, w, j0, j1);
-    MEHDG_COUNT(2);
+    MEHDG_COUNT(1);
     return cudaGetLastError();
+}
+
+template <class TS>
+cudaError_t launch_laswp(const LUPlan& P, int c0, int w, int j0, int j1, cudaStream_t st) {
+    if (j1 <= j0) return cudaSuccess;
+    int32_t* perm = reinterpret_cast<int32_t*>(P.work);
+    cudaError_t e = launch_perm_build(P, c0, w, perm, st);
+    if (e != cudaSuccess) return e;
+    return launch_laswp_perm<TS>(P, perm, w, j0, j1, st);
 }
 
 template <class TS>
@@ -543,8 +672,10 @@ cudaError_t factor_t(const LUPlan& P, cudaStream_t st) {
     for (int c0 = 0; c0 < ld; c0 += LU_NB) {
         int ev = prof_begin(P.prof, PH_LU_PANELS, st);
         if ((e = rec_panel<TS>(P, c0, LU_NB, st)) != cudaSuccess) return e;
+        int32_t* pp = panel_perm(P, c0);
+        if ((e = launch_perm_build(P, c0, LU_NB, pp, st)) != cudaSuccess) return e;
         if (c0 + LU_NB < ld) {
-            if ((e = launch_laswp<TS>(P, c0, LU_NB, c0 + LU_NB, ld, st)) != cudaSuccess) return e;
+            if ((e = launch_laswp_perm<TS>(P, pp, LU_NB, c0 + LU_NB, ld, st)) != cudaSuccess) return e;
             if constexpr (std::is_same<TS, double>::value) e = launch_trsm<TS>(P, c0, LU_NB, c0 + LU_NB, ld, st);
             else e = gemm_tc_trsm256(P, c0, c0 + LU_NB, ld, st);
             if (e != cudaSuccess) return e;
@@ -567,9 +698,7 @@ cudaError_t gemm_simt_update_f32(const LUPlan& P, int r0, int c0, int k0, int M,
 }
 
 size_t lu_work_bytes(int64_t nK, int64_t ld, bool fp64, int prec) {
-    size_t perm = (size_t)nK * (1 + 4 * LU_NB) * sizeof(int32_t);
-    perm = (perm + 255) & ~(size_t)255;
-    return perm + (fp64 ? 0 : gemm_tc_work_bytes(nK, ld, prec));
+    return lu_perm_bytes(nK, ld) + (fp64 ? 0 : gemm_tc_work_bytes(nK, ld, prec));
 }
 
 cudaError_t lu_factor(const LUPlan& P, cudaStream_t st) {
@@ -577,16 +706,37 @@ cudaError_t lu_factor(const LUPlan& P, cudaStream_t st) {
     return factor_t<float>(P, st);
 }
 
-cudaError_t lu_solve(const LUPlan& P, const double* r, double* x, const int32_t* skip, cudaStream_t st) {
-    size_t ts = P.fp64 ? 8 : 4;
-    size_t sm = ts * P.ld;
-    if (P.fp64) {
-        cudaFuncSetAttribute(solve_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        solve_kernel<double><<<(unsigned)P.nK, 512, sm, st>>>((const double*)P.S, P.ld, P.piv, r, x, skip, LU_NB);
-    } else {
-        cudaFuncSetAttribute(solve_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        solve_kernel<float><<<(unsigned)P.nK, 512, sm, st>>>((const float*)P.S, P.ld, P.piv, r, x, skip, LU_NB);
-    }
+namespace {
+template <class TS, int CL>
+cudaError_t launch_solve(const LUPlan& P, const int32_t* perms, const double* r, double* x, const int32_t* skip,
+                         cudaStream_t st) {
+    const size_t sm = sizeof(TS) * ((size_t)P.ld + 2 * LU_NB);
+    cudaFuncSetAttribute(solve_kernel<TS, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    solve_kernel<TS, CL><<<(unsigned)(P.nK * CL), SOLVE_THREADS, sm, st>>>((const TS*)P.S, P.ld, perms, P.nK, r, x,
+                                                                         skip);
     MEHDG_COUNT(1);
     return cudaGetLastError();
+}
+template <class TS>
+cudaError_t solve_t(const LUPlan& P, const int32_t* perms, const double* r, double* x, const int32_t* skip,
+                    cudaStream_t st) {
+    // CTAs per element: enough clusters to give every SM two CTAs, at most 8
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int cl = 1;
+    while (cl < 8 && P.nK * cl < 2 * (int64_t)nsm) cl *= 2;
+    switch (cl) {
+    case 8: return launch_solve<TS, 8>(P, perms, r, x, skip, st);
+    case 4: return launch_solve<TS, 4>(P, perms, r, x, skip, st);
+    case 2: return launch_solve<TS, 2>(P, perms, r, x, skip, st);
+    default: return launch_solve<TS, 1>(P, perms, r, x, skip, st);
+    }
+}
+}  // namespace
+
+cudaError_t lu_solve(const LUPlan& P, const double* r, double* x, const int32_t* skip, cudaStream_t st) {
+    const int32_t* perms = panel_perm(P, 0);
+    if (P.fp64) return solve_t<double>(P, perms, r, x, skip, st);
+    return solve_t<float>(P, perms, r, x, skip, st);
 }

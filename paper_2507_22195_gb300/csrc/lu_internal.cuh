@@ -3,6 +3,15 @@
 #include "kernels.cuh"
 
 constexpr int LU_NB = 256;   // outer panel width (depth of the big trailing update)
+constexpr int LU_PW = 1 + 4 * LU_NB;   // ints of one net permutation: nr, rows[2 NB], cont[2 NB]
+
+// workspace layout: [inner permutation scratch][outer-panel permutations][operand panels]
+// The outer-panel permutations ([ld/NB][nK][LU_PW]) are kept for the solves.
+inline size_t lu_perm_scratch_bytes(int64_t nK) { return ((size_t)nK * LU_PW * 4 + 255) & ~(size_t)255; }
+inline size_t lu_perm_panels_bytes(int64_t nK, int64_t ld) {
+    return ((size_t)(ld / LU_NB) * nK * LU_PW * 4 + 255) & ~(size_t)255;
+}
+inline size_t lu_perm_bytes(int64_t nK, int64_t ld) { return lu_perm_scratch_bytes(nK) + lu_perm_panels_bytes(nK, ld); }
 
 // C[r0.., c0..] -= L[r0.., k0..k0+Kd) * U[k0..k0+Kd, c0..] on the tensor cores
 // (TF32 or BF16 operands, FP32 accumulation), S^K column-major FP32.
