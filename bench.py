@@ -207,6 +207,12 @@ def once_main(a):
     return 0
 
 
+# DRAM bytes per outer-update launch, measured with ncu on the full workload
+# (profiles/tc_stream_outer_tgv512_bf16x3.md); other workloads and precisions
+# were not captured and report null.
+TRAFFIC_PER_LAUNCH = {("tgv_inviscid", 8, "bf16x3"): 37.649e9}
+
+
 def trailing_bytes(ld, nK):
     """algorithmic bytes of all outer trailing updates of one condensation:
     C read and written (FP32) and the two operand panels (rest x 256, FP32)"""
@@ -344,8 +350,11 @@ def main():
     else:
         ach = byt / (gem["ms"] / 1e3) / 1e9
         hbm = pk.get("hbm_gbs", 6800.0)
+        tr = TRAFFIC_PER_LAUNCH.get((a.workload, a.nk, a.prec))
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": None, "peak_source": "measured" if "hbm_gbs" in pk else "fallback",
+                "traffic": tr, "traffic_unit": "bytes per launch" if tr else None,
+                "algorithmic_per_launch": byt / max(gem["launches"], 1),
+                "peak_source": "measured" if "hbm_gbs" in pk else "fallback",
                 "kernel": "lu_trailing_update (tcgen05, depth 256)", "launches": gem["launches"],
                 "ms": gem["ms"], "tflops": gem["flops"] / (gem["ms"] / 1e3) / 1e12}
 

@@ -26,6 +26,7 @@
 #include <algorithm>
 #include <cstring>
 #include "lu_internal.cuh"
+#include "prof.cuh"
 
 namespace {
 
@@ -523,7 +524,8 @@ size_t gemm_tc_work_bytes(int64_t nK, int64_t ld, int prec) {
     return 2 * panel_bytes(nK, ld);
 }
 
-cudaError_t gemm_tc_update(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st) {
+cudaError_t gemm_tc_update(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st,
+                           int ph_pack, int ph_gemm, double flops) {
     if (M <= 0 || N <= 0) return cudaSuccess;
     if (M < TM) return gemm_simt_update_f32(P, r0, c0, k0, M, N, Kd, st);   // a few tiny inner updates
     if (!encoder()) return cudaErrorNotSupported;
@@ -540,6 +542,7 @@ cudaError_t gemm_tc_update(const LUPlan& P, int r0, int c0, int k0, int M, int N
     void* Bp = w + pan;
     // pack
     {
+        const int ev = ph_pack >= 0 ? prof_begin(P.prof, ph_pack, st) : -1;
         dim3 g((unsigned)((M + 63) / 64), (unsigned)(Kp / 32), (unsigned)P.nK);
         if (bf16) pack_A_kernel<true><<<g, 256, 0, st>>>((const float*)P.S, P.ld, r0, k0, M, Kd, Kp, nseg, Ap);
         else pack_A_kernel<false><<<g, 256, 0, st>>>((const float*)P.S, P.ld, r0, k0, M, Kd, Kp, nseg, Ap);
@@ -547,15 +550,20 @@ cudaError_t gemm_tc_update(const LUPlan& P, int r0, int c0, int k0, int M, int N
         if (bf16) pack_B_kernel<true><<<gb, 256, 0, st>>>((const float*)P.S, P.ld, k0, c0, N, Kd, Kp, nseg, Bp);
         else pack_B_kernel<false><<<gb, 256, 0, st>>>((const float*)P.S, P.ld, k0, c0, N, Kd, Kp, nseg, Bp);
         MEHDG_COUNT(2);
+        if (ev >= 0) prof_end(P.prof, ev, st, 0.0);
     }
     const int BN = N >= 128 ? 128 : (N >= 64 ? 64 : 32);
     CUtensorMap ma, mb;
     if (!make_map(&ma, Ap, bf16, nseg * Kp, M, P.nK, TM) || !make_map(&mb, Bp, bf16, nseg * Kp, N, P.nK, BN))
         return cudaErrorInvalidValue;
-    if (bf16) return split ? launch_stream_bn<true, false, true>(BN, ma, mb, P, r0, c0, M, N, nchunk, Kp, st)
-                           : launch_stream_bn<true, false, false>(BN, ma, mb, P, r0, c0, M, N, nchunk, Kp, st);
-    return split ? launch_stream_bn<false, false, true>(BN, ma, mb, P, r0, c0, M, N, nchunk, Kp, st)
-                 : launch_stream_bn<false, false, false>(BN, ma, mb, P, r0, c0, M, N, nchunk, Kp, st);
+    const int ev = ph_gemm >= 0 ? prof_begin(P.prof, ph_gemm, st) : -1;
+    cudaError_t e;
+    if (bf16) e = split ? launch_stream_bn<true, false, true>(BN, ma, mb, P, r0, c0, M, N, nchunk, Kp, st)
+                        : launch_stream_bn<true, false, false>(BN, ma, mb, P, r0, c0, M, N, nchunk, Kp, st);
+    else e = split ? launch_stream_bn<false, false, true>(BN, ma, mb, P, r0, c0, M, N, nchunk, Kp, st)
+                   : launch_stream_bn<false, false, false>(BN, ma, mb, P, r0, c0, M, N, nchunk, Kp, st);
+    if (ev >= 0) prof_end(P.prof, ev, st, flops);
+    return e;
 }
 
 // test hook: one trailing update on caller-owned FP32 column-major matrices

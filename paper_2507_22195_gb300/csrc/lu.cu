@@ -647,9 +647,16 @@ cudaError_t launch_gemm_simt(const LUPlan& P, int r0, int c0, int k0, int M, int
 }
 
 template <class TS>
-cudaError_t trailing_update(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st) {
-    if constexpr (std::is_same<TS, double>::value) return launch_gemm_simt<double>(P, r0, c0, k0, M, N, Kd, st);
-    else return gemm_tc_update(P, r0, c0, k0, M, N, Kd, st);
+cudaError_t trailing_update(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st,
+                            int ph_pack = -1, int ph_gemm = -1, double flops = 0.0) {
+    if constexpr (std::is_same<TS, double>::value) {
+        const int ev = ph_gemm >= 0 ? prof_begin(P.prof, ph_gemm, st) : -1;
+        cudaError_t e = launch_gemm_simt<double>(P, r0, c0, k0, M, N, Kd, st);
+        if (ev >= 0) prof_end(P.prof, ev, st, flops);
+        return e;
+    } else {
+        return gemm_tc_update(P, r0, c0, k0, M, N, Kd, st, ph_pack, ph_gemm, flops);
+    }
 }
 
 template <class TS>
@@ -683,9 +690,9 @@ cudaError_t factor_t(const LUPlan& P, cudaStream_t st) {
         prof_end(P.prof, ev, st, 0.0);
         if (c0 + LU_NB < ld) {
             int rest = ld - (c0 + LU_NB);
-            ev = prof_begin(P.prof, PH_GEMM_OUTER, st);
-            if ((e = trailing_update<TS>(P, c0 + LU_NB, c0 + LU_NB, c0, rest, rest, LU_NB, st)) != cudaSuccess) return e;
-            prof_end(P.prof, ev, st, 2.0 * rest * (double)rest * LU_NB * (double)P.nK);
+            if ((e = trailing_update<TS>(P, c0 + LU_NB, c0 + LU_NB, c0, rest, rest, LU_NB, st, PH_PACK_OUTER,
+                                         PH_GEMM_OUTER, 2.0 * rest * (double)rest * LU_NB * (double)P.nK)) != cudaSuccess)
+                return e;
         }
     }
     return cudaSuccess;

@@ -15,7 +15,10 @@ inline size_t lu_perm_bytes(int64_t nK, int64_t ld) { return lu_perm_scratch_byt
 
 // C[r0.., c0..] -= L[r0.., k0..k0+Kd) * U[k0..k0+Kd, c0..] on the tensor cores
 // (TF32 or BF16 operands, FP32 accumulation), S^K column-major FP32.
-cudaError_t gemm_tc_update(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st);
+// With ph_gemm >= 0 the update kernel alone is timed under that phase (flops
+// recorded with it) and the operand packing under ph_pack.
+cudaError_t gemm_tc_update(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st,
+                           int ph_pack = -1, int ph_gemm = -1, double flops = 0.0);
 size_t gemm_tc_work_bytes(int64_t nK, int64_t ld, int prec);
 // rows [c0, c0+256) of the columns [j0, j1) := L11^-1 (same rows), on the
 // tensor cores through the explicit inverse of the unit-lower block L11

@@ -4,7 +4,7 @@
 #include <vector>
 #include <cuda_runtime.h>
 
-enum { PH_RESIDUAL = 0, PH_JACOBIAN, PH_LU_PANELS, PH_GEMM_OUTER, PH_SOLVE, PH_TANGENT, PH_N };
+enum { PH_RESIDUAL = 0, PH_JACOBIAN, PH_LU_PANELS, PH_GEMM_OUTER, PH_SOLVE, PH_TANGENT, PH_PACK_OUTER, PH_N };
 
 struct Prof {
     bool on = false;

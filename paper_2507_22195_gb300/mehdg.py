@@ -20,7 +20,7 @@ MEHDG_FP64, MEHDG_MIXED_TF32, MEHDG_MIXED_BF16, MEHDG_MIXED_TF32X3, MEHDG_MIXED_
 ERRORS = {0: "MEHDG_OK", -1: "MEHDG_EINVAL", -2: "MEHDG_ENONPHYS", -3: "MEHDG_ESINGULAR",
           -4: "MEHDG_ENOCONV", -5: "MEHDG_ECUDA", -6: "MEHDG_ENOMEM", -7: "MEHDG_ESTATE",
           -8: "MEHDG_ETIMEOUT"}
-PHASES = ["residual", "jacobian", "lu_panels", "lu_trailing_update", "solve", "tangent"]
+PHASES = ["residual", "jacobian", "lu_panels", "lu_trailing_update", "solve", "tangent", "lu_pack_outer"]
 
 EXPORTED = ["mehdg_default_params", "mehdg_create", "mehdg_set_mesh", "mehdg_set_state",
             "mehdg_residual", "mehdg_condense", "mehdg_apply_condensed", "mehdg_recover",
