@@ -469,16 +469,22 @@ trtri256_kernel(const float* __restrict__ Sall, int64_t ld, int c0, int nseg, vo
     const int K = blockIdx.y, b = blockIdx.x;
     const float* S = Sall + (size_t)K * ld * ld;
     __shared__ float X[T][33];
-    __shared__ float Lc[T];
+    __shared__ float Lc[2][T];
     const int tc = threadIdx.x & 31, tr = threadIdx.x >> 5;
     const int col = 32 * b + tc;
     for (int i = tr; i < T; i += 8) X[i][tc] = (i == col) ? 1.f : 0.f;
-    __syncthreads();
-    for (int t = 32 * b; t < T - 1; ++t) {
-        for (int i = t + 1 + threadIdx.x; i < T; i += 256) Lc[i] = S[(size_t)(c0 + i) + (size_t)(c0 + t) * ld];
+    // column t of L is loaded one step ahead (thread i holds row i), so the
+    // global latency overlaps the previous step's update
+    const int i_own = threadIdx.x;                  // T == blockDim.x
+    const int t0 = 32 * b;
+    float ln = (t0 < T - 1 && i_own > t0) ? S[(size_t)(c0 + i_own) + (size_t)(c0 + t0) * ld] : 0.f;
+    for (int t = t0; t < T - 1; ++t) {
+        Lc[t & 1][i_own] = ln;
         __syncthreads();
+        if (t + 1 < T - 1) ln = i_own > t + 1 ? S[(size_t)(c0 + i_own) + (size_t)(c0 + t + 1) * ld] : 0.f;
         const float xt = X[t][tc];
-        for (int i = t + 1 + tr; i < T; i += 8) X[i][tc] -= Lc[i] * xt;
+        const float* lc = Lc[t & 1];
+        for (int i = t + 1 + tr; i < T; i += 8) X[i][tc] -= lc[i] * xt;
         __syncthreads();
     }
     for (int m = tr; m < T; m += 8)

@@ -4,13 +4,13 @@
 // an identity block, so pivots never leave the true rows).  The factorisation
 // is right-looking over outer panels of NB = 256 columns; each outer panel is
 // factored recursively (halves, down to 32-column leaves):
-//   leaf   : one CTA per element factors the (ld-c) x 32 panel, 8 (or fewer)
-//            columns at a time in shared memory with partial pivoting
-//            (largest |a|, ties to the lowest row), left-looking between the
-//            sub-panels;
-//   inner  : row swaps, TRSM with the unit-lower triangle, trailing update
-//            of the right half (narrow GEMM), recursion on the right half,
-//            row swaps of the left half;
+//   leaf   : one CTA per element factors the (ld-c) x 32 panel, the whole
+//            leaf or 8 (or fewer) columns at a time in shared memory with
+//            partial pivoting (largest |a|, ties to the lowest row),
+//            left-looking between the sub-panels, and applies its row
+//            exchanges to the other 224 columns of the outer panel;
+//   inner  : TRSM with the unit-lower triangle, trailing update of the right
+//            half (narrow GEMM), recursion on the right half;
 //   outer  : row swaps and TRSM of the rows right of the panel, then the
 //            trailing update C -= L21 U12 with depth 256.
 // Rows left of an outer panel are not swapped again (LINPACK order); the
@@ -56,6 +56,8 @@ panel_kernel(TS* __restrict__ Sall, int64_t ld, int c, int32_t* __restrict__ piv
     __shared__ int s_piv[IB];
     __shared__ TS s_prow[2][IB], s_crow[2][IB];
     __shared__ int s_rows[2 * IB], s_cont[2 * IB], s_nr;
+    __shared__ int s_pall[LEAF];                   // the leaf's pivots, relative to c
+    __shared__ int s_lrows[2 * LEAF], s_lcont[2 * LEAF], s_lnr;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     bool singular = false;
     for (int jb = 0; jb < LEAF; jb += IB) {
@@ -78,33 +80,63 @@ panel_kernel(TS* __restrict__ Sall, int64_t ld, int c, int32_t* __restrict__ piv
             __syncthreads();
             for (int i = tid; i < jb * IB; i += nth) S[(size_t)(c + i % jb) + (size_t)(c + jb + i / jb) * ld] = Utop[i % jb][i / jb];
             // L part into shared memory: X[cc][r] = A[c+jb+r][col] - sum_t L[c+jb+r][c+t] U[t][cc];
-            // the loads of one row are issued IB at a time
-            for (int r = tid; r < R; r += nth) {
-                const TS* row = S + (size_t)(c + jb + r);
-                TS acc[IB];
+            // two rows per thread and iteration, IB loads of each row at a time
+            constexpr int RB = 2;
+            for (int rb = tid; rb < R; rb += nth * RB) {
+                TS acc[RB][IB];
 #pragma unroll
-                for (int cc = 0; cc < IB; ++cc) acc[cc] = row[(size_t)(c + jb + cc) * ld];
+                for (int u = 0; u < RB; ++u) {
+                    const int r = rb + u * nth;
+                    const TS* row = S + (size_t)(c + jb + (r < R ? r : 0));
+#pragma unroll
+                    for (int cc = 0; cc < IB; ++cc) acc[u][cc] = r < R ? row[(size_t)(c + jb + cc) * ld] : (TS)0;
+                }
                 for (int t0 = 0; t0 < jb; t0 += IB) {
-                    TS l[IB];
+                    TS l[RB][IB];
 #pragma unroll
-                    for (int tt = 0; tt < IB; ++tt) l[tt] = row[(size_t)(c + t0 + tt) * ld];
+                    for (int u = 0; u < RB; ++u) {
+                        const int r = rb + u * nth;
+                        const TS* row = S + (size_t)(c + jb + (r < R ? r : 0));
 #pragma unroll
-                    for (int tt = 0; tt < IB; ++tt)
+                        for (int tt = 0; tt < IB; ++tt) l[u][tt] = r < R ? row[(size_t)(c + t0 + tt) * ld] : (TS)0;
+                    }
 #pragma unroll
-                        for (int cc = 0; cc < IB; ++cc) acc[cc] -= l[tt] * Utop[t0 + tt][cc];
+                    for (int u = 0; u < RB; ++u)
+#pragma unroll
+                        for (int tt = 0; tt < IB; ++tt)
+#pragma unroll
+                            for (int cc = 0; cc < IB; ++cc) acc[u][cc] -= l[u][tt] * Utop[t0 + tt][cc];
                 }
 #pragma unroll
-                for (int cc = 0; cc < IB; ++cc) X[(size_t)cc * R0 + r] = acc[cc];
+                for (int u = 0; u < RB; ++u) {
+                    const int r = rb + u * nth;
+                    if (r < R) {
+#pragma unroll
+                        for (int cc = 0; cc < IB; ++cc) X[(size_t)cc * R0 + r] = acc[u][cc];
+                    }
+                }
             }
         }
         if (!staged) {
-            for (int r = tid; r < R; r += nth) {
-                const TS* row = S + (size_t)(c + r);
-                TS v[IB];
+            // several rows per thread and iteration, so 32 loads are in flight
+            constexpr int RB = IB >= 32 ? 1 : 32 / IB;
+            for (int rb = tid; rb < R; rb += nth * RB) {
+                TS v[RB][IB];
 #pragma unroll
-                for (int cc = 0; cc < IB; ++cc) v[cc] = row[(size_t)(c + cc) * ld];
+                for (int u = 0; u < RB; ++u) {
+                    const int r = rb + u * nth;
+                    const TS* row = S + (size_t)(c + (r < R ? r : 0));
 #pragma unroll
-                for (int cc = 0; cc < IB; ++cc) X[(size_t)cc * R0 + r] = v[cc];
+                    for (int cc = 0; cc < IB; ++cc) v[u][cc] = r < R ? row[(size_t)(c + cc) * ld] : (TS)0;
+                }
+#pragma unroll
+                for (int u = 0; u < RB; ++u) {
+                    const int r = rb + u * nth;
+                    if (r < R) {
+#pragma unroll
+                        for (int cc = 0; cc < IB; ++cc) X[(size_t)cc * R0 + r] = v[u][cc];
+                    }
+                }
             }
         }
         // (b) partial pivoting factorisation of the IB columns in shared memory;
@@ -185,7 +217,7 @@ panel_kernel(TS* __restrict__ Sall, int64_t ld, int c, int32_t* __restrict__ piv
 #pragma unroll
             for (int cc = 0; cc < IB; ++cc) row[(size_t)(c + jb + cc) * ld] = X[(size_t)cc * R0 + r];
         }
-        if (tid < IB) piv[c + jb + tid] = c + jb + s_piv[tid];
+        if (tid < IB) { piv[c + jb + tid] = c + jb + s_piv[tid]; s_pall[jb + tid] = jb + s_piv[tid]; }
         if constexpr (IB < LEAF) {
             // (d) apply the IB swaps to the other columns of the leaf as one net
             // permutation: slot i (row s_rows[i]) takes the old content of slot s_cont[i]
@@ -218,6 +250,52 @@ panel_kernel(TS* __restrict__ Sall, int64_t ld, int c, int32_t* __restrict__ piv
                     S[(size_t)(c + s_rows[i]) + (size_t)(c + t) * ld] = s_swap[t][s_cont[i]];
             }
             __syncthreads();
+        }
+    }
+    // (e) the leaf's row exchanges on the other columns of its outer panel, as
+    // one net permutation of at most 64 rows (slot i, row c + s_lrows[i], takes
+    // the old content of slot s_lcont[i]); one warp per column, the values in
+    // registers and exchanged by shuffles
+    __syncthreads();
+    if (wid == 0) {
+        for (int i = lane; i < 2 * LEAF; i += 32) { s_lrows[i] = i; s_lcont[i] = i; }
+        __syncwarp();
+        int nr = LEAF;
+        for (int i = 0; i < LEAF; ++i) {
+            const int b = s_pall[i];
+            if (b == i) continue;
+            int sb;
+            if (b < LEAF) sb = b;
+            else {
+                const unsigned hit = __ballot_sync(0xffffffffu, LEAF + lane < nr && s_lrows[LEAF + lane] == b);
+                if (hit) sb = LEAF + __ffs(hit) - 1;
+                else {
+                    sb = nr++;
+                    if (lane == 0) s_lrows[sb] = b;
+                }
+            }
+            __syncwarp();
+            if (lane == 0) { const int t = s_lcont[i]; s_lcont[i] = s_lcont[sb]; s_lcont[sb] = t; }
+            __syncwarp();
+        }
+        if (lane == 0) s_lnr = nr;
+    }
+    __syncthreads();
+    {
+        const int nr = s_lnr;
+        const int c0 = (c / LU_NB) * LU_NB, nleft = c - c0;
+        const int r0 = s_lrows[lane], r1 = s_lrows[lane + 32];
+        const int q0 = s_lcont[lane], q1 = s_lcont[lane + 32];
+        const bool w0 = lane < nr && q0 != lane, w1 = lane + 32 < nr && q1 != lane + 32;
+        for (int j = wid; j < LU_NB - LEAF; j += nth / 32) {
+            const int col = j < nleft ? c0 + j : c + j - nleft + LEAF;
+            TS* Sc = S + (size_t)col * ld + c;
+            const TS v0 = lane < nr ? Sc[r0] : (TS)0;
+            const TS v1 = lane + 32 < nr ? Sc[r1] : (TS)0;
+            const TS a0 = __shfl_sync(0xffffffffu, v0, q0 & 31), b0 = __shfl_sync(0xffffffffu, v1, q0 & 31);
+            const TS a1 = __shfl_sync(0xffffffffu, v0, q1 & 31), b1 = __shfl_sync(0xffffffffu, v1, q1 & 31);
+            if (w0) Sc[r0] = q0 < 32 ? a0 : b0;
+            if (w1) Sc[r1] = q1 < 32 ? a1 : b1;
         }
     }
     if (singular && tid == 0 && status) status[K] = MEHDG_ESINGULAR;
@@ -617,14 +695,6 @@ cudaError_t launch_laswp_perm(const LUPlan& P, const int32_t* perm, int w, int j
     return cudaGetLastError();
 }
 
-template <class TS>
-cudaError_t launch_laswp(const LUPlan& P, int c0, int w, int j0, int j1, cudaStream_t st) {
-    if (j1 <= j0) return cudaSuccess;
-    int32_t* perm = reinterpret_cast<int32_t*>(P.work);
-    cudaError_t e = launch_perm_build(P, c0, w, perm, st);
-    if (e != cudaSuccess) return e;
-    return launch_laswp_perm<TS>(P, perm, w, j0, j1, st);
-}
 
 template <class TS>
 cudaError_t launch_trsm(const LUPlan& P, int c0, int t, int j0, int j1, cudaStream_t st) {
@@ -663,13 +733,13 @@ template <class TS>
 cudaError_t rec_panel(const LUPlan& P, int c, int w, cudaStream_t st) {
     cudaError_t e;
     if (w == LEAF) return launch_panel<TS>((TS*)P.S, P.ld, c, P.piv, P.status, P.nK, st);
+    // (every leaf applies its row exchanges to all columns of the outer panel,
+    // so the halves need no separate exchange passes)
     int h = w / 2;
     if ((e = rec_panel<TS>(P, c, h, st)) != cudaSuccess) return e;
-    if ((e = launch_laswp<TS>(P, c, h, c + h, c + w, st)) != cudaSuccess) return e;
     if ((e = launch_trsm<TS>(P, c, h, c + h, c + w, st)) != cudaSuccess) return e;
     if ((e = trailing_update<TS>(P, c + h, c + h, c, (int)P.ld - (c + h), h, h, st)) != cudaSuccess) return e;
-    if ((e = rec_panel<TS>(P, c + h, h, st)) != cudaSuccess) return e;
-    return launch_laswp<TS>(P, c + h, h, c, c + h, st);
+    return rec_panel<TS>(P, c + h, h, st);
 }
 
 template <class TS>
