@@ -491,37 +491,81 @@ trtri256_kernel(const float* __restrict__ Sall, int64_t ld, int c0, int nseg, vo
         op_put<BF16>(Ap, ((size_t)K * T + m) * (size_t)(nseg * T), T, 32 * b + tc, nseg, X[m][tc]);
 }
 
+// Row exchanges of the outer panel c0 on the trailing columns, fused with the
+// packing of the TRSM's B operand: one warp per column gathers the rows of
+// the net permutation (the 256 block rows and the rows below that take
+// part), writes the rows below that change, and writes the new block rows
+// as the split-TF32 panel Bp[K][n][hi 256 | lo 256].  The block rows of S are
+// not written back: the TRSM product overwrites them.
+__global__ void __launch_bounds__(256)
+laswp_pack_kernel(float* __restrict__ Sall, int64_t ld, const int32_t* __restrict__ perm, int j0, int N,
+                  float* __restrict__ Bp) {
+    const int K = blockIdx.y;
+    float* S = Sall + (size_t)K * ld * ld;
+    const int32_t* pl = perm + (size_t)K * LU_PW;
+    const int nr = pl[0];
+    const int32_t* rows = pl + 1;
+    const int32_t* cont = rows + 2 * LU_NB;
+    __shared__ float buf[8][2 * LU_NB];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n = blockIdx.x * 8 + warp;
+    if (n >= N) return;
+    float* Sc = S + (size_t)(j0 + n) * ld;
+    float* b = buf[warp];
+    for (int i = lane; i < nr; i += 32) b[i] = Sc[rows[i]];
+    __syncwarp();
+    float* out = Bp + ((size_t)K * N + n) * (size_t)(2 * LU_NB);
+    for (int i = lane; i < nr; i += 32) {
+        const int ci = cont[i];
+        const float v = b[ci];
+        if (i < LU_NB) {
+            const float hi = tf32_rn(v);
+            out[i] = hi;
+            out[LU_NB + i] = tf32_rn(v - hi);
+        } else if (ci != i) {
+            Sc[rows[i]] = v;
+        }
+    }
+}
+
 }  // namespace
 
 // Rows [c0, c0+256) of the columns [j0, j1): U12 = L11^-1 A12 on the tensor
 // cores, through the explicit inverse of the unit-lower block L11.
-cudaError_t gemm_tc_trsm256(const LUPlan& P, int c0, int j0, int j1, cudaStream_t st) {
-    const int N = j1 - j0, Kd = LU_NB;
-    if (N <= 0) return cudaSuccess;
-    if (!encoder()) return cudaErrorNotSupported;
-    // split TF32 in every mixed mode: the explicit inverse of L11 amplifies
-    // operand rounding, and one-pass TF32 or BF16 here leaves the factors too
-    // inexact for the FP64 refinement
-    const bool bf16 = false;
-    const int nseg = 2;
-    const int chunk_k = CHUNK_BYTES / 4;
-    const int nchunk = Kd / chunk_k;
-    unsigned char* w = reinterpret_cast<unsigned char*>(P.work) + lu_perm_bytes(P.nK, P.ld);
-    const size_t pan = panel_bytes(P.nK, P.ld);
-    void* Ap = w;
-    void* Bp = w + pan;
+namespace {
+// the TRSM product with B = rows [c0, c0+256) of the columns [j0, j0+N), packed in Bp
+cudaError_t trsm256_product(const LUPlan& P, int c0, int j0, int N, void* Ap, void* Bp, cudaStream_t st) {
+    const int Kd = LU_NB, nseg = 2, nchunk = Kd / (CHUNK_BYTES / 4);
     {
         dim3 gt(LU_NB / 32, (unsigned)P.nK);
         trtri256_kernel<false><<<gt, 256, 0, st>>>((const float*)P.S, P.ld, c0, nseg, Ap);
+        MEHDG_COUNT(1);
     }
-    dim3 gb((unsigned)((N + 7) / 8), 1, (unsigned)P.nK);
-    pack_B_kernel<false><<<gb, 256, 0, st>>>((const float*)P.S, P.ld, c0, j0, N, Kd, Kd, nseg, Bp);
-    MEHDG_COUNT(2);
     const int BN = N >= 128 ? 128 : (N >= 64 ? 64 : 32);
     CUtensorMap ma, mb;
-    if (!make_map(&ma, Ap, bf16, nseg * Kd, 256, P.nK, TM) || !make_map(&mb, Bp, bf16, nseg * Kd, N, P.nK, BN))
+    if (!make_map(&ma, Ap, false, nseg * Kd, 256, P.nK, TM) || !make_map(&mb, Bp, false, nseg * Kd, N, P.nK, BN))
         return cudaErrorInvalidValue;
     return launch_stream_bn<false, true, true>(BN, ma, mb, P, c0, j0, 256, N, nchunk, Kd, st);
+}
+}  // namespace
+
+// The outer step right of panel c0: row exchanges of the columns [c0+256, ld)
+// by the panel's net permutation, fused with the packing of B, then the TRSM
+// U12 = L11^-1 A12 of their rows [c0, c0+256) on the tensor cores in split
+// TF32 (every mixed mode: the explicit inverse of L11 amplifies operand
+// rounding, and one-pass TF32 or BF16 here leaves the factors too inexact for
+// the FP64 refinement).
+cudaError_t gemm_tc_swap_trsm256(const LUPlan& P, const int32_t* perm, int c0, cudaStream_t st) {
+    const int j0 = c0 + LU_NB, N = (int)P.ld - j0;
+    if (N <= 0) return cudaSuccess;
+    if (!encoder()) return cudaErrorNotSupported;
+    unsigned char* w = reinterpret_cast<unsigned char*>(P.work) + lu_perm_bytes(P.nK, P.ld);
+    void* Ap = w;
+    float* Bp = reinterpret_cast<float*>(w + panel_bytes(P.nK, P.ld));
+    dim3 gb((unsigned)((N + 7) / 8), (unsigned)P.nK);
+    laswp_pack_kernel<<<gb, 256, 0, st>>>((float*)P.S, P.ld, perm, j0, N, Bp);
+    MEHDG_COUNT(1);
+    return trsm256_product(P, c0, j0, N, Ap, Bp, st);
 }
 
 size_t gemm_tc_work_bytes(int64_t nK, int64_t ld, int prec) {

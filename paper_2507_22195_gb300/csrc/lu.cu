@@ -18,6 +18,7 @@
 // The trailing updates run on the tensor cores for the mixed precisions
 // (gemm_tc.cu) and on the FP64 pipe for MEHDG_FP64.
 #include <cstdio>
+#include <cstdlib>
 #include <type_traits>
 #include "common.cuh"
 #include "kernels.cuh"
@@ -752,9 +753,12 @@ cudaError_t factor_t(const LUPlan& P, cudaStream_t st) {
         int32_t* pp = panel_perm(P, c0);
         if ((e = launch_perm_build(P, c0, LU_NB, pp, st)) != cudaSuccess) return e;
         if (c0 + LU_NB < ld) {
-            if ((e = launch_laswp_perm<TS>(P, pp, LU_NB, c0 + LU_NB, ld, st)) != cudaSuccess) return e;
-            if constexpr (std::is_same<TS, double>::value) e = launch_trsm<TS>(P, c0, LU_NB, c0 + LU_NB, ld, st);
-            else e = gemm_tc_trsm256(P, c0, c0 + LU_NB, ld, st);
+            if constexpr (std::is_same<TS, double>::value) {
+                if ((e = launch_laswp_perm<TS>(P, pp, LU_NB, c0 + LU_NB, ld, st)) != cudaSuccess) return e;
+                e = launch_trsm<TS>(P, c0, LU_NB, c0 + LU_NB, ld, st);
+            } else {
+                e = gemm_tc_swap_trsm256(P, pp, c0, st);
+            }
             if (e != cudaSuccess) return e;
         }
         prof_end(P.prof, ev, st, 0.0);
@@ -803,6 +807,11 @@ cudaError_t solve_t(const LUPlan& P, const int32_t* perms, const double* r, doub
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     int cl = 1;
     while (cl < 8 && P.nK * cl < 2 * (int64_t)nsm) cl *= 2;
+    // MEHDG_SOLVE_CTAS (1, 2, 4 or 8) overrides the choice, e.g. to test every variant
+    if (const char* f = std::getenv("MEHDG_SOLVE_CTAS")) {
+        const int v = std::atoi(f);
+        if (v == 1 || v == 2 || v == 4 || v == 8) cl = v;
+    }
     switch (cl) {
     case 8: return launch_solve<TS, 8>(P, perms, r, x, skip, st);
     case 4: return launch_solve<TS, 4>(P, perms, r, x, skip, st);

@@ -20,7 +20,7 @@ inline size_t lu_perm_bytes(int64_t nK, int64_t ld) { return lu_perm_scratch_byt
 cudaError_t gemm_tc_update(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st,
                            int ph_pack = -1, int ph_gemm = -1, double flops = 0.0);
 size_t gemm_tc_work_bytes(int64_t nK, int64_t ld, int prec);
-// rows [c0, c0+256) of the columns [j0, j1) := L11^-1 (same rows), on the
-// tensor cores through the explicit inverse of the unit-lower block L11
-cudaError_t gemm_tc_trsm256(const LUPlan& P, int c0, int j0, int j1, cudaStream_t st);
+// row exchanges of the columns right of outer panel c0 by its net permutation
+// (perm: [nK][LU_PW]) and the TRSM of their rows [c0, c0+256), fused
+cudaError_t gemm_tc_swap_trsm256(const LUPlan& P, const int32_t* perm, int c0, cudaStream_t st);
 cudaError_t gemm_simt_update_f32(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st);

@@ -114,6 +114,29 @@ def test_condense_apply_recover_match_oracle(name, prec):
     ctx.close()
 
 
+@pytest.mark.parametrize("ctas", [1, 2, 4, 8])
+def test_solve_cluster_sizes_match_oracle(ctas, monkeypatch):
+    """the solve with 1, 2, 4 and 8 CTAs per element (normally chosen from the
+    element count) on a mesh with three outer panels per element"""
+    monkeypatch.setenv("MEHDG_SOLVE_CTAS", str(ctas))
+    mesh, st, kw = case("vortex_p2m2")
+    ctx = M().Context(mesh, flux=2, prec=M().MEHDG_MIXED_BF16X3, **kw)
+    v, vh, q, vs = to_dev(st)
+    ctx.set_state(v, vh, q, vs)
+    bh = ctx.condense()
+    dvh_np = I.random_direction(st.vhat.shape, 77, 1e-3)
+    dV = ctx.recover(torch.tensor(dvh_np, device="cuda:0"))
+    torch.cuda.synchronize()
+    stat, iters = ctx.status()
+    assert (stat == 0).all(), (stat, iters)
+    prm = oracle.params(flux=2, **kw)
+    bh_o, _ = oracle.condense_mesh(prm, mesh, st)
+    dV_o, _ = oracle.recover_mesh(prm, mesh, st, dvh_np)
+    e = (rel(bh, bh_o), rel(dV, dV_o))
+    assert max(e) < 1e-8, (e, iters)
+    ctx.close()
+
+
 def test_newton_step_matches_brute_force():
     """condense -> dense global solve of sum A-hat (built column by column with
     apply_condensed) -> recover equals the oracle's monolithic solve"""
