@@ -459,36 +459,79 @@ cudaError_t launch_stream_bn(int BN, const CUtensorMap& a, const CUtensorMap& b,
 
 // Inverse X = L^-1 of the unit-lower 256 x 256 diagonal block L of every
 // element, written as the K-major operand panel Ap[K][m][k] = X[m][k] (TF32
-// rounded or BF16).  One CTA per (32-column block of X, element): the block
-// column of L X = I is solved by column-oriented forward substitution, 32
-// columns x 8 row groups, with the columns of L staged in shared memory.
+// rounded, split into [hi | lo] when nseg = 2).  One CTA per (32-column block
+// jb of X, element), by block forward substitution over the 32-row blocks ib:
+//   X[ib] = L[ib][ib]^-1 (E[ib] - sum_{jb <= kb < ib} L[ib][kb] X[kb]),
+// E the identity's block.  The 32 x 32 products run from shared memory (each
+// thread 4 outputs), the next block of L is fetched into registers while the
+// current one is used, and the unit-lower diagonal solves are done by the
+// warps, 4 columns each, with shuffles.
 template <bool BF16>
 __global__ void __launch_bounds__(256)
 trtri256_kernel(const float* __restrict__ Sall, int64_t ld, int c0, int nseg, void* __restrict__ Ap) {
-    constexpr int T = 256;
-    const int K = blockIdx.y, b = blockIdx.x;
-    const float* S = Sall + (size_t)K * ld * ld;
-    __shared__ float X[T][33];
-    __shared__ float Lc[2][T];
-    const int tc = threadIdx.x & 31, tr = threadIdx.x >> 5;
-    const int col = 32 * b + tc;
-    for (int i = tr; i < T; i += 8) X[i][tc] = (i == col) ? 1.f : 0.f;
-    // column t of L is loaded one step ahead (thread i holds row i), so the
-    // global latency overlaps the previous step's update
-    const int i_own = threadIdx.x;                  // T == blockDim.x
-    const int t0 = 32 * b;
-    float ln = (t0 < T - 1 && i_own > t0) ? S[(size_t)(c0 + i_own) + (size_t)(c0 + t0) * ld] : 0.f;
-    for (int t = t0; t < T - 1; ++t) {
-        Lc[t & 1][i_own] = ln;
+    constexpr int T = 256, NB = T / 32;
+    const int K = blockIdx.y, jb = blockIdx.x;
+    const float* L = Sall + (size_t)K * ld * ld + (size_t)c0 + (size_t)c0 * ld;   // L[i][k] = L[i + k ld]
+    __shared__ float Xs[NB][32][33];
+    __shared__ float Lb[2][32][33];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int r = tid >> 3, c4 = (tid & 7) * 4;       // product layout: row r, columns c4..c4+3
+    // block sequence: for ib = jb..7: (ib, jb), (ib, jb+1), ..., (ib, ib)
+    int total = 0;
+    for (int ib = jb; ib < NB; ++ib) total += ib - jb + 1;
+    auto fetch = [&](int ib, int kb, float (&v)[4]) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = tid + 256 * u, i = e & 31, k = e >> 5;
+            v[u] = L[(size_t)(32 * ib + i) + (size_t)(32 * kb + k) * ld];
+        }
+    };
+    float acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = (r == c4 + q) ? 1.f : 0.f;   // E block of ib = jb
+    float nxt[4];
+    fetch(jb, jb, nxt);
+    int ib = jb, kb = jb;
+    for (int n = 0; n < total; ++n) {
+        float (*lb)[33] = Lb[n & 1];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) { const int e = tid + 256 * u; lb[e & 31][e >> 5] = nxt[u]; }
         __syncthreads();
-        if (t + 1 < T - 1) ln = i_own > t + 1 ? S[(size_t)(c0 + i_own) + (size_t)(c0 + t + 1) * ld] : 0.f;
-        const float xt = X[t][tc];
-        const float* lc = Lc[t & 1];
-        for (int i = t + 1 + tr; i < T; i += 8) X[i][tc] -= lc[i] * xt;
-        __syncthreads();
+        const int ib2 = kb < ib ? ib : ib + 1, kb2 = kb < ib ? kb + 1 : jb;
+        if (n + 1 < total) fetch(ib2, kb2, nxt);
+        if (kb < ib) {
+#pragma unroll 8
+            for (int k = 0; k < 32; ++k) {
+                const float l = lb[r][k];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[q] -= l * Xs[kb][k][c4 + q];
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) Xs[ib][r][c4 + q] = acc[q];
+            __syncthreads();
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) {
+                const int col = 4 * warp + cc;
+                float x = Xs[ib][lane][col];
+#pragma unroll
+                for (int k = 0; k < 32; ++k) {
+                    const float xk = __shfl_sync(0xffffffffu, x, k);
+                    if (lane > k) x -= lb[lane][k] * xk;
+                }
+                Xs[ib][lane][col] = x;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] = 0.f;
+        }
+        ib = ib2; kb = kb2;
     }
-    for (int m = tr; m < T; m += 8)
-        op_put<BF16>(Ap, ((size_t)K * T + m) * (size_t)(nseg * T), T, 32 * b + tc, nseg, X[m][tc]);
+    __syncthreads();
+    for (int m = warp; m < T; m += 8) {
+        const int mb = m >> 5;
+        const float x = mb < jb ? 0.f : Xs[mb][m & 31][lane];
+        op_put<BF16>(Ap, ((size_t)K * T + m) * (size_t)(nseg * T), T, 32 * jb + lane, nseg, x);
+    }
 }
 
 // Row exchanges of the outer panel c0 on the trailing columns, fused with the
