@@ -42,6 +42,7 @@ void free_mesh(mehdg_ctx* c) {
     dfree(c->d_res); dfree(c->d_dx); dfree(c->d_nrm); dfree(c->d_status); dfree(c->d_iters); dfree(c->d_conv);
     dfree(c->d_cnt); dfree(c->d_S); dfree(c->d_piv); dfree(c->d_work);
     dfree(c->d_RQ); dfree(c->d_z); dfree(c->d_dq); dfree(c->d_qt1); dfree(c->d_qt2); dfree(c->d_Minv); dfree(c->d_C1);
+    dfree(c->d_pj); c->pj_ready = false;
     if (c->h_cnt) { cudaFreeHost(c->h_cnt); c->h_cnt = nullptr; }
     c->nK = 0; c->condensed = false;
 }
@@ -88,6 +89,7 @@ int tangent(mehdg_ctx* c, const double* dv, const double* dvh, const double* dq,
             const int32_t* skip, cudaStream_t st) {
     ResidualArgs a = base_args(c);
     a.dv = dv; a.dvh = dvh; a.dq = viscous(c) ? dq : nullptr; a.tRV = tRV; a.tRH = tRH; a.skip = skip;
+    a.pj = c->pj_ready ? c->d_pj : nullptr;      // linear volume pass from the stored point Jacobians
     int ev = prof_begin(&c->prof, PH_TANGENT, st);
     TRY(launch_residual(a, c->nK, viscous(c), true, st));
     prof_end(&c->prof, ev, st, 0.0);
@@ -231,6 +233,7 @@ int mehdg_set_mesh(mehdg_ctx* c, int64_t nK, const int32_t* p, const int32_t* m,
         DALLOC(c->d_Minv, sizeof(double) * t.n * t.n);
         DALLOC(c->d_C1, sizeof(double) * t.n * t.n);
     }
+    if (!vis) DALLOC(c->d_pj, sizeof(double) * 100 * (size_t)nK * t.m * t.m * t.m * t.npt);
     DALLOC(c->d_S, Sbytes);
     DALLOC(c->d_piv, sizeof(int32_t) * nK * c->Npad);
     c->work_bytes = lu_work_bytes(nK, c->Npad, fp64, c->prm.prec);
@@ -264,6 +267,7 @@ int mehdg_set_state(mehdg_ctx* c, const double* v, const double* vhat, const dou
     }
     c->v = v; c->vh = vhat; c->q = q; c->vs = vstar;
     c->condensed = false;
+    c->pj_ready = false;
     return MEHDG_OK;
 }
 
@@ -309,7 +313,9 @@ int mehdg_condense(mehdg_ctx* c, double* bhat, double* Ahat_local, void* stream)
     JacobianArgs ja;
     ja.tab = c->tab; ja.ph = c->ph; ja.box = c->d_box; ja.v = c->v; ja.vs = c->vs; ja.vh = c->vh; ja.q = c->q;
     ja.gid = c->d_gid; ja.S = c->d_S; ja.ld = ld; ja.status = c->d_status; ja.C1 = c->d_C1;
+    ja.pj = c->d_pj;
     TRY(launch_jacobian(ja, nK, fp64, st));
+    c->pj_ready = c->d_pj != nullptr;
     prof_end(&c->prof, ev, st, 0.0);
     // LU
     LUPlan P = plan(c);

@@ -166,6 +166,8 @@ struct mehdg_ctx {
     double* d_dq = nullptr;             // q-direction of a tangent
     double *d_qt1 = nullptr, *d_qt2 = nullptr;   // line-operator scratch
     double *d_Minv = nullptr, *d_C1 = nullptr;   // [n][n] 1-D tables
+    double* d_pj = nullptr;             // [nK][m^3][npt][100] weighted FP64 point Jacobians (inviscid)
+    bool pj_ready = false;              // d_pj holds the Jacobians at the current state
     double* d_r = nullptr;              // [nK][Npad] FP64 right-hand side
     double* d_x = nullptr;              // [nK][Npad] FP64 solution
     double* d_res = nullptr;            // [nK][Npad] FP64 refinement residual

@@ -68,10 +68,18 @@ __device__ void volume_point_jacobians(const JacobianArgs& a, int K, int e1, int
         ok = vol_integrand(a.ph, dv, dvs, dq, U, FG) && ok;
         double W = sW[g1] * hw[0] * sW[g2] * hw[1] * sW[g3] * hw[2];
         TS* Px = P + (size_t)x * 100;
+        double* Gx = a.pj ? a.pj + (((size_t)K * tb.m * tb.m * tb.m + e1 + tb.m * (e2 + tb.m * e3)) * npt + x) * 100
+                          : nullptr;
         for (int k = 0; k < 5; ++k)
             for (int l = 0; l < 5; ++l) {
-                Px[k * 5 + l] = (TS)(W * U[k].d[l]);
-                for (int j = 0; j < 3; ++j) Px[25 * (1 + j) + k * 5 + l] = (TS)(-W * FG[k][j].d[l]);
+                const double u = W * U[k].d[l];
+                Px[k * 5 + l] = (TS)u;
+                if (Gx) Gx[k * 5 + l] = u;
+                for (int j = 0; j < 3; ++j) {
+                    const double f = -W * FG[k][j].d[l];
+                    Px[25 * (1 + j) + k * 5 + l] = (TS)f;
+                    if (Gx) Gx[25 * (1 + j) + k * 5 + l] = f;
+                }
             }
     }
     if (!ok && a.status) a.status[K] = MEHDG_ENONPHYS;

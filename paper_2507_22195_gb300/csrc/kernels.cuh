@@ -13,6 +13,7 @@ struct ResidualArgs {
     double *tRV, *tRQ, *tRH;              // tangents (tangent launches only)
     int32_t* status;
     const int32_t* skip;                  // [nK] nonzero = skip element (may be null)
+    const double* pj;                     // stored point Jacobians: tangent volume pass is linear (may be null)
 };
 
 cudaError_t launch_residual(const ResidualArgs& a, int64_t nK, bool visc, bool tangent, cudaStream_t st);
@@ -44,6 +45,7 @@ struct JacobianArgs {
     int64_t ld;
     int32_t* status;
     const double* C1;         // [n][n] M1_ref^-1 G1_ref (viscous only)
+    double* pj;               // if set: the weighted FP64 point Jacobians [nK][m^3][npt][100] (inviscid)
 };
 cudaError_t launch_jacobian(const JacobianArgs& a, int64_t nK, bool fp64, cudaStream_t st);
 cudaError_t launch_pad_identity(void* S, int64_t nK, int64_t ld, int Nv, bool fp64, cudaStream_t st);

@@ -15,6 +15,7 @@
 // directional derivative used by the refinement residual r - S x, the
 // right-hand side b-hat and the reduced mat-vec (all matrix-free, FP64).
 #include <algorithm>
+#include <type_traits>
 #include "physics.cuh"
 #include "kernels.cuh"
 
@@ -154,9 +155,15 @@ residual_volume_kernel(ResidualArgs a) {
 // The derivative factors of the weak form ride along as separate partial sums
 // (H after the g1 contraction, J after g2).  Two shared regions alternate:
 //   A: nodal state -> T2 -> H        B: T1 -> point values / integrands -> J
-template <class T, bool VISC>
+//
+// LIN = true: the tangent dR_V[dv] of the inviscid volume pass from the stored
+// weighted point Jacobians a.pj (written by the Jacobian kernel at the same
+// state): only dv is interpolated, the point step is a 20 x 5 product per
+// Gauss point instead of the dual-number physics, and the result goes to tRV.
+template <class T, bool VISC, bool LIN>
 __global__ void __launch_bounds__(128)
 residual_volume_sf_kernel(ResidualArgs a, int nA) {
+    static_assert(!LIN || (!VISC && std::is_same<T, double>::value), "linear pass: inviscid FP64 only");
     const Tab& tb = a.tab;
     const int K = blockIdx.y, e = blockIdx.x;
     if (a.skip && a.skip[K]) return;
@@ -164,7 +171,7 @@ residual_volume_sf_kernel(ResidualArgs a, int nA) {
     const int nl = tb.nl, npt = tb.npt, p1 = p + 1;
     const int e1 = e % m, e2 = (e / m) % m, e3 = e / (m * m);
     const Phys& ph = a.ph;
-    const bool tt = ph.time_term;
+    const bool tt = !LIN && ph.time_term;
     const int NIN = 5 + (tt ? 5 : 0) + (VISC ? 15 : 0);     // v, v* (time term), q
     const int cq = tt ? 10 : 5;
     constexpr int NHK = VISC ? 7 : 3, NJK = VISC ? 6 : 2;   // partial sums per component k
@@ -186,7 +193,8 @@ residual_volume_sf_kernel(ResidualArgs a, int nA) {
         int l1 = i % p1, l2 = (i / p1) % p1, l3 = i / (p1 * p1);
         int A = (e1 * p + l1) + n * ((e2 * p + l2) + n * (e3 * p + l3));
         for (int k = 0; k < 5; ++k) {
-            RA[k * nl + i] = load_t<T>(a.v, a.dv, oV + k * Nn + A);
+            if constexpr (LIN) RA[k * nl + i] = a.dv[oV + k * Nn + A];
+            else RA[k * nl + i] = load_t<T>(a.v, a.dv, oV + k * Nn + A);
             if (tt) RA[(5 + k) * nl + i] = load_t<T>(a.vs, nullptr, oV + k * Nn + A);
         }
         if (VISC)
@@ -232,6 +240,28 @@ residual_volume_sf_kernel(ResidualArgs a, int nA) {
     // point physics, in place in B (each thread touches only its own column x):
     // rows 0-4 W U, 5-19 W F/G (k*3+j), 20-34 W q (k*3+d), 35-39 W v
     bool ok = true;
+    if constexpr (LIN) {
+        // rows 0-4: W dU/dv dv; rows 5-19: W dFG/dv dv (the stored blocks carry -W)
+        const double* Gb = a.pj + ((size_t)K * m * m * m + e) * npt * 100;
+        for (int x = tid; x < npt; x += nth) {
+            double dvx[5];
+            for (int l = 0; l < 5; ++l) dvx[l] = RB[l * npt + x];
+            const double* Gx = Gb + (size_t)x * 100;
+            for (int k = 0; k < 5; ++k) {
+                double u = 0.0, f0 = 0.0, f1 = 0.0, f2 = 0.0;
+                for (int l = 0; l < 5; ++l) {
+                    u += Gx[k * 5 + l] * dvx[l];
+                    f0 += Gx[25 + k * 5 + l] * dvx[l];
+                    f1 += Gx[50 + k * 5 + l] * dvx[l];
+                    f2 += Gx[75 + k * 5 + l] * dvx[l];
+                }
+                RB[k * npt + x] = u;
+                RB[(5 + k * 3 + 0) * npt + x] = -f0;
+                RB[(5 + k * 3 + 1) * npt + x] = -f1;
+                RB[(5 + k * 3 + 2) * npt + x] = -f2;
+            }
+        }
+    } else
     for (int x = tid; x < npt; x += nth) {
         const int g1 = x % ng, g2 = (x / ng) % ng, g3 = x / (ng * ng);
         T vx[5], vsx[5], qx[15];
@@ -321,7 +351,8 @@ residual_volume_sf_kernel(ResidualArgs a, int nA) {
                 }
             }
             const int A = (e1 * p + l1) + n * ((e2 * p + l2) + n * (e3 * p + l3));
-            acc_out(a.RV, a.tRV, oV + k * Nn + A, rv);
+            if constexpr (LIN) { if (a.tRV) atomicAdd(a.tRV + oV + k * Nn + A, (double)rv); }
+            else acc_out(a.RV, a.tRV, oV + k * Nn + A, rv);
             if (VISC) {
                 acc_out(a.RQ, a.tRQ, oQ + (k * 3 + 0) * Nn + A, rq0);
                 acc_out(a.RQ, a.tRQ, oQ + (k * 3 + 1) * Nn + A, rq1);
@@ -495,15 +526,25 @@ cudaError_t launch_residual(const ResidualArgs& a, int64_t nK, bool visc, bool t
     dim3 gv((unsigned)(t.m * t.m * t.m), (unsigned)nK), gf((unsigned)(6 * t.m * t.m), (unsigned)nK), b(128);
 #define LAUNCH_RES(T, V)                                                                                 \
     do { if (sf_vol) {                                                                                   \
-             cudaFuncSetAttribute(residual_volume_sf_kernel<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssf); \
-             residual_volume_sf_kernel<T, V><<<gv, b, ssf, st>>>(a, nA);                                  \
+             cudaFuncSetAttribute(residual_volume_sf_kernel<T, V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssf); \
+             residual_volume_sf_kernel<T, V, false><<<gv, b, ssf, st>>>(a, nA);                                  \
          } else {                                                                                        \
              cudaFuncSetAttribute(residual_volume_kernel<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sv); \
              residual_volume_kernel<T, V><<<gv, b, sv, st>>>(a);                                         \
          }                                                                                               \
          cudaFuncSetAttribute(residual_face_kernel<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf);   \
          residual_face_kernel<T, V><<<gf, b, sf, st>>>(a); } while (0)
-    if (tangent) { if (visc) LAUNCH_RES(Dual<1>, true); else LAUNCH_RES(Dual<1>, false); }
+    if (tangent && !visc && a.pj && sf_vol) {
+        // linear volume pass from the stored point Jacobians (none when dv = 0:
+        // the volume integrand does not depend on the traces), then the dual face pass
+        if (a.dv) {
+            const size_t sl = volume_sf_smem_bytes(t, false, sizeof(double));
+            cudaFuncSetAttribute(residual_volume_sf_kernel<double, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl);
+            residual_volume_sf_kernel<double, false, true><<<gv, b, sl, st>>>(a, nA);
+        }
+        cudaFuncSetAttribute(residual_face_kernel<Dual<1>, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf);
+        residual_face_kernel<Dual<1>, false><<<gf, b, sf, st>>>(a);
+    } else if (tangent) { if (visc) LAUNCH_RES(Dual<1>, true); else LAUNCH_RES(Dual<1>, false); }
     else { if (visc) LAUNCH_RES(double, true); else LAUNCH_RES(double, false); }
 #undef LAUNCH_RES
     MEHDG_COUNT(2);
