@@ -142,6 +142,22 @@ int mehdg_apply_condensed(mehdg_ctx* ctx, const double* x, double* y, void* stre
  * or ignored for Euler) from dVhat [G][5][n^2].  Needs a prior condense. */
 int mehdg_recover(mehdg_ctx* ctx, const double* dVhat, double* dV, double* dQ, void* stream);
 
+/* Global trace solve of Algorithm 1: dVhat with sum_K A-hat^K dVhat = bhat
+ * (eq. R5 summed over the elements), by restarted GMRES(restart) without a
+ * preconditioner, matrix-free through mehdg_apply_condensed (needs a prior
+ * condense).  bhat and dVhat are device arrays [G][5][n^2]; dVhat holds the
+ * initial guess on entry (zeros are fine) and the iterate on return.  Stops
+ * when ||bhat - A dVhat||_2 <= rtol ||bhat||_2 (checked on the true residual
+ * at every restart) or after max_iter products with A.  iters and relres
+ * (HOST, may be NULL) receive the products used and the final relative
+ * residual.  Returns MEHDG_ENOCONV (with the iterate in dVhat) when the
+ * tolerance was not met, MEHDG_EINVAL for bad arguments, MEHDG_ESTATE
+ * before condense, MEHDG_ENOMEM if the (restart + 2) trace vectors of its
+ * workspace cannot be allocated (kept in the context for later calls).
+ * Synchronises the stream at every Arnoldi step. */
+int mehdg_solve_condensed(mehdg_ctx* ctx, const double* bhat, double* dVhat, double rtol, int restart,
+                          int max_iter, int* iters, double* relres, void* stream);
+
 /* Copy the per-element status words (0 or a negative code above) of the
  * last call into the HOST array per_K_status [nK]; synchronises the device.
  * Also copies, if iters != NULL, the refinement sweeps used per element. */
@@ -157,8 +173,9 @@ int mehdg_profile_enable(mehdg_ctx* ctx, int enable);
 /* Per-phase sums since profile_enable (synchronises the device): event-timed
  * milliseconds, launches timed and algorithmic flops (host arrays of length
  * nphase).  Phases: 0 residual, 1 Jacobian assembly, 2 LU panels (leaf
- * panels, swaps, TRSM, inner updates), 3 LU outer trailing update (depth
- * 256), 4 triangular solves, 5 matrix-free tangent residuals. */
+ * panels, swaps, TRSM, inner updates), 3 LU outer trailing update kernel
+ * (depth 256), 4 triangular solves, 5 matrix-free tangent residuals,
+ * 6 operand packing of the outer trailing updates. */
 int mehdg_profile_read(mehdg_ctx* ctx, double* ms, int64_t* launches, double* flops, int nphase);
 
 /* Number of kernels this library has launched since it was loaded. */

@@ -43,6 +43,7 @@ void free_mesh(mehdg_ctx* c) {
     dfree(c->d_cnt); dfree(c->d_S); dfree(c->d_piv); dfree(c->d_work);
     dfree(c->d_RQ); dfree(c->d_z); dfree(c->d_dq); dfree(c->d_qt1); dfree(c->d_qt2); dfree(c->d_Minv); dfree(c->d_C1);
     dfree(c->d_pj); c->pj_ready = false;
+    if (c->d_krylov) { cudaFree(c->d_krylov); c->d_krylov = nullptr; c->krylov_bytes = 0; }
     if (c->h_cnt) { cudaFreeHost(c->h_cnt); c->h_cnt = nullptr; }
     c->nK = 0; c->condensed = false;
 }

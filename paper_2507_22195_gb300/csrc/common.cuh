@@ -184,6 +184,8 @@ struct mehdg_ctx {
     size_t work_bytes = 0;
     float* d_rf = nullptr;              // [nK][Npad] FP32 solve vector
     bool condensed = false;
+    void* d_krylov = nullptr;           // GMRES basis and scratch of the trace solve (first use)
+    size_t krylov_bytes = 0;
     Prof prof;
 };
 

@@ -26,7 +26,7 @@ EXPORTED = ["mehdg_default_params", "mehdg_create", "mehdg_set_mesh", "mehdg_set
             "mehdg_residual", "mehdg_condense", "mehdg_apply_condensed", "mehdg_recover",
             "mehdg_status", "mehdg_last_error", "mehdg_destroy", "mehdg_profile_enable",
             "mehdg_profile_read", "mehdg_launch_count", "mehdg_test_trailing_update",
-            "mehdg_test_trailing_work_bytes", "mehdg_residual_static"]
+            "mehdg_test_trailing_work_bytes", "mehdg_residual_static", "mehdg_solve_condensed"]
 
 
 class mehdg_params(C.Structure):
@@ -62,6 +62,7 @@ def load(path: str | None = None):
     L.mehdg_apply_condensed.argtypes = [_vp, _vp, _vp, _vp]
     L.mehdg_recover.argtypes = [_vp, _vp, _vp, _vp, _vp]
     L.mehdg_status.argtypes = [_vp, _vp, _vp]
+    L.mehdg_solve_condensed.argtypes = [_vp, _vp, _vp, C.c_double, C.c_int, C.c_int, _vp, _vp, _vp]
     L.mehdg_last_error.argtypes = [_vp]
     L.mehdg_last_error.restype = C.c_char_p
     L.mehdg_destroy.argtypes = [_vp]
@@ -134,6 +135,18 @@ def mehdg_set_state(ctx, v, vhat, q, vstar, stream=None):
 def mehdg_residual(ctx, R_V, R_Q, R_Vhat, stream=None):
     _check(ctx, load().mehdg_residual(ctx, _ptr(R_V), _ptr(R_Q), _ptr(R_Vhat), _stream(stream)),
            "mehdg_residual")
+
+
+def mehdg_solve_condensed(ctx, bhat, dVhat, rtol=1e-10, restart=30, max_iter=500, stream=None, check=True):
+    """GMRES on sum A-hat dVhat = bhat; dVhat (device) holds the initial guess
+    and receives the iterate.  Returns (products used, relative residual)."""
+    it = C.c_int(0)
+    res = C.c_double(0.0)
+    rc = load().mehdg_solve_condensed(ctx, _ptr(bhat), _ptr(dVhat), float(rtol), int(restart), int(max_iter),
+                                      C.byref(it), C.byref(res), _stream(stream))
+    if check:
+        _check(ctx, rc, "mehdg_solve_condensed")
+    return it.value, res.value
 
 
 def mehdg_condense(ctx, bhat, Ahat_local=None, stream=None):
@@ -256,6 +269,13 @@ class Context:
         y = torch.empty_like(x)
         mehdg_apply_condensed(self.ctx, x, y)
         return y
+
+    def solve_condensed(self, bhat, x0=None, rtol=1e-10, restart=30, max_iter=500):
+        """global trace solve (GMRES); returns (dVhat, products, relative residual)"""
+        import torch
+        x = torch.zeros_like(bhat) if x0 is None else x0.clone()
+        it, res = mehdg_solve_condensed(self.ctx, bhat, x, rtol, restart, max_iter)
+        return x, it, res
 
     def recover(self, dvh, with_dQ=False):
         import torch

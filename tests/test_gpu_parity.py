@@ -159,6 +159,46 @@ def test_newton_step_matches_brute_force():
     ctx.close()
 
 
+@pytest.mark.parametrize("prec", [0, 4])
+def test_newton_step_with_gmres_trace_solve_matches_brute_force(prec):
+    """condense -> GMRES on sum A-hat (matrix-free) -> recover equals the
+    oracle's monolithic solve of the whole (V, V-hat) Newton system.  The
+    restart length covers the whole trace system of this mesh, so GMRES is
+    exact in exact arithmetic (without a preconditioner restarted GMRES
+    stagnates on these systems: condition numbers ~1e5, spectrum spread over
+    the left half-plane)."""
+    mesh = I.periodic_mesh(2, 1, 1)
+    st = I.make_state(mesh, "tgv", 1e-2, 5, 6, M0=0.3)
+    ctx = M().Context(mesh, flux=2, prec=prec, Mach=0.3)
+    ctx.set_state(*to_dev(st))
+    bh = ctx.condense()
+    x, it, res = ctx.solve_condensed(bh, rtol=1e-13, restart=bh.numel(), max_iter=2 * bh.numel())
+    dV = ctx.recover(x)
+    torch.cuda.synchronize()
+    stat, _ = ctx.status()
+    assert (stat == 0).all()
+    assert res <= 1e-13 and 0 < it <= bh.numel()
+    prm = oracle.params(flux=2, Mach=0.3)
+    _, dV_o, dH_o = oracle.brute_force(prm, mesh, st)
+    tol = 1e-9 if prec == 0 else 1e-8
+    assert rel(x, dH_o) < tol and rel(dV, dV_o) < tol, (rel(x, dH_o), rel(dV, dV_o), it)
+    ctx.close()
+
+
+def test_gmres_reports_no_convergence():
+    mesh = I.periodic_mesh(2, 1, 1)
+    st = I.make_state(mesh, "tgv", 1e-2, 5, 6, M0=0.3)
+    ctx = M().Context(mesh, flux=2, prec=M().MEHDG_FP64, Mach=0.3)
+    ctx.set_state(*to_dev(st))
+    bh = ctx.condense()
+    x = torch.zeros_like(bh)
+    it, res = M().mehdg_solve_condensed(ctx.ctx, bh, x, rtol=1e-14, restart=2, max_iter=3, check=False)
+    assert it == 3 and res > 1e-14
+    with pytest.raises(M().MehdgError):
+        M().mehdg_solve_condensed(ctx.ctx, bh, torch.zeros_like(bh), rtol=1e-14, restart=2, max_iter=3)
+    ctx.close()
+
+
 def test_nonphysical_state_reports_status():
     mesh, st, kw = case("vortex_p2m1")
     st.v[3, 4, :] = 0.5           # beta = -v5 < 0 in element 3
