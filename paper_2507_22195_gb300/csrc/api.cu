@@ -44,6 +44,10 @@ void free_mesh(mehdg_ctx* c) {
     dfree(c->d_RQ); dfree(c->d_z); dfree(c->d_dq); dfree(c->d_qt1); dfree(c->d_qt2); dfree(c->d_Minv); dfree(c->d_C1);
     dfree(c->d_pj); c->pj_ready = false;
     if (c->d_krylov) { cudaFree(c->d_krylov); c->d_krylov = nullptr; c->krylov_bytes = 0; }
+    if (c->lu_graph) { cudaGraphExecDestroy(c->lu_graph); c->lu_graph = nullptr; }
+    if (c->lu_ev_in) { cudaEventDestroy(c->lu_ev_in); c->lu_ev_in = nullptr; }
+    if (c->lu_ev_out) { cudaEventDestroy(c->lu_ev_out); c->lu_ev_out = nullptr; }
+    if (c->lu_stream) { cudaStreamDestroy(c->lu_stream); c->lu_stream = nullptr; }
     if (c->h_cnt) { cudaFreeHost(c->h_cnt); c->h_cnt = nullptr; }
     c->nK = 0; c->condensed = false;
 }
@@ -62,6 +66,40 @@ QProjArgs qargs(mehdg_ctx* c) {
     q.tab = c->tab; q.box = c->d_box; q.gid = c->d_gid; q.Minv = c->d_Minv; q.C1 = c->d_C1;
     q.tmp1 = c->d_qt1; q.tmp2 = c->d_qt2;
     return q;
+}
+
+// LU of every S^K.  The sequence of launches depends only on the mesh and
+// the precision, so it is captured into a CUDA graph on the first call and
+// replayed afterwards (on the context's own stream, ordered after and before
+// the caller's stream by events); with phase profiling on, the launches are
+// issued directly so that the phase events sit between them.
+cudaError_t factor_all(mehdg_ctx* c, const LUPlan& P, cudaStream_t st) {
+    if (c->prof.on) return lu_factor(P, st);
+    cudaError_t e;
+    if (!c->lu_graph) {
+        if (!c->lu_stream && (e = cudaStreamCreateWithFlags(&c->lu_stream, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        if (!c->lu_ev_in && (e = cudaEventCreateWithFlags(&c->lu_ev_in, cudaEventDisableTiming)) != cudaSuccess) return e;
+        if (!c->lu_ev_out && (e = cudaEventCreateWithFlags(&c->lu_ev_out, cudaEventDisableTiming)) != cudaSuccess) return e;
+        const long long before = g_mehdg_launches.load();
+        if ((e = cudaStreamBeginCapture(c->lu_stream, cudaStreamCaptureModeRelaxed)) != cudaSuccess) return e;
+        const cudaError_t ef = lu_factor(P, c->lu_stream);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(c->lu_stream, &g);
+        if (ef != cudaSuccess || e != cudaSuccess) { if (g) cudaGraphDestroy(g); return ef != cudaSuccess ? ef : e; }
+        e = cudaGraphInstantiate(&c->lu_graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { c->lu_graph = nullptr; return e; }
+        c->lu_graph_launches = g_mehdg_launches.load() - before;
+        g_mehdg_launches -= c->lu_graph_launches;      // counted when they run
+    }
+    if ((e = cudaEventRecord(c->lu_ev_in, st)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(c->lu_stream, c->lu_ev_in, 0)) != cudaSuccess ||
+        (e = cudaGraphLaunch(c->lu_graph, c->lu_stream)) != cudaSuccess ||
+        (e = cudaEventRecord(c->lu_ev_out, c->lu_stream)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(st, c->lu_ev_out, 0)) != cudaSuccess)
+        return e;
+    g_mehdg_launches += c->lu_graph_launches;
+    return cudaSuccess;
 }
 
 LUPlan plan(mehdg_ctx* c) {
@@ -320,7 +358,7 @@ int mehdg_condense(mehdg_ctx* c, double* bhat, double* Ahat_local, void* stream)
     prof_end(&c->prof, ev, st, 0.0);
     // LU
     LUPlan P = plan(c);
-    TRY(lu_factor(P, st));
+    TRY(factor_all(c, P, st));
     // y = S^-1 (-R_V + A_vq z)
     if (vis) {
         if ((rc = tangent(c, nullptr, nullptr, c->d_z, c->d_tRV, nullptr, nullptr, st))) return rc;

@@ -184,6 +184,10 @@ struct mehdg_ctx {
     size_t work_bytes = 0;
     float* d_rf = nullptr;              // [nK][Npad] FP32 solve vector
     bool condensed = false;
+    cudaGraphExec_t lu_graph = nullptr; // the factorisation's launches, captured on first use
+    cudaStream_t lu_stream = nullptr;   // stream the graph is replayed on
+    cudaEvent_t lu_ev_in = nullptr, lu_ev_out = nullptr;
+    long long lu_graph_launches = 0;    // kernels in the graph
     void* d_krylov = nullptr;           // GMRES basis and scratch of the trace solve (first use)
     size_t krylov_bytes = 0;
     Prof prof;
