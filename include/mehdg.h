@@ -142,6 +142,18 @@ int mehdg_apply_condensed(mehdg_ctx* ctx, const double* x, double* y, void* stre
  * or ignored for Euler) from dVhat [G][5][n^2].  Needs a prior condense. */
 int mehdg_recover(mehdg_ctx* ctx, const double* dVhat, double* dV, double* dQ, void* stream);
 
+/* Vector-Jacobian product of the residual of eq. s32 at the state (Euler
+ * only): g_v = (dR_V/dv)^T lam_V + (dR_Vhat/dv)^T lam_Vhat and g_vhat =
+ * (dR_V/dvhat)^T lam_V + (dR_Vhat/dvhat)^T lam_Vhat, for cotangents lam_V
+ * [nK][5][Nn] and lam_Vhat [G][5][n^2] (of the trace residual summed over
+ * both sides; may be NULL = 0).  Device arrays; g_v [nK][5][Nn] and g_vhat
+ * [G][5][n^2] are overwritten.  Point states and point Jacobians are
+ * recomputed from the nodal state (nothing is kept from the forward
+ * residual).  MEHDG_EINVAL for a viscous context, MEHDG_ESTATE before
+ * set_state; a non-physical point sets the element's status. */
+int mehdg_residual_vjp(mehdg_ctx* ctx, const double* lam_V, const double* lam_Vhat, double* g_v,
+                       double* g_vhat, void* stream);
+
 /* Global trace solve of Algorithm 1: dVhat with sum_K A-hat^K dVhat = bhat
  * (eq. R5 summed over the elements), by restarted GMRES(restart) without a
  * preconditioner, matrix-free through mehdg_apply_condensed (needs a prior

@@ -277,6 +277,25 @@ def residual_mesh(prm, mesh, st, Ks=None):
     return RV, RQ, RH
 
 
+def residual_vjp_mesh(prm, mesh, st, lam_V, lam_H):
+    """VJP of the residual of eq. s32 (Euler), by definition: the transposed
+    complex-step Jacobian blocks of every element applied to the cotangents,
+    g_v[K] = Avv^T lam_V[K] + Ahv^T lam_H(K), g_vhat = sum_K scatter(Avh^T
+    lam_V[K] + Ahh^T lam_H(K)), with lam_H(K) the element's six faces of the
+    global cotangent lam_H [G,5,n2]."""
+    p, m, Nn, n2 = mesh.p, mesh.m, mesh.Nn, mesh.n2
+    gv = np.zeros((mesh.nK, 5, Nn))
+    gh = np.zeros((mesh.n_global_faces, 5, n2))
+    for K in range(mesh.nK):
+        vh = gather_trace(mesh, st.vhat, K)
+        B = jacobian_K(prm, p, m, mesh.boxes[K], st.v[K], st.vstar[K], vh, None)
+        lv = lam_V[K].ravel()
+        lh = gather_trace(mesh, lam_H, K).ravel()
+        gv[K] = (B["Avv"].T @ lv + B["Ahv"].T @ lh).reshape(5, Nn)
+        scatter_trace(mesh, (B["Avh"].T @ lv + B["Ahh"].T @ lh).reshape(6, 5, n2), K, gh)
+    return gv, gh
+
+
 def element_system(prm, mesh, st, K):
     p, m = mesh.p, mesh.m
     vh = gather_trace(mesh, st.vhat, K)

@@ -135,6 +135,7 @@ template <> __device__ __forceinline__ double cst<double>(double x) { return x; 
 template <> __device__ __forceinline__ Dual<1> cst<Dual<1>>(double x) { return mkdual<1>(x); }
 template <> __device__ __forceinline__ Dual<5> cst<Dual<5>>(double x) { return mkdual<5>(x); }
 template <> __device__ __forceinline__ Dual<15> cst<Dual<15>>(double x) { return mkdual<15>(x); }
+template <> __device__ __forceinline__ Dual<10> cst<Dual<10>>(double x) { return mkdual<10>(x); }
 
 // ------------------------------------------------------------------ context
 struct DeviceLU;   // defined in lu.cuh

@@ -113,7 +113,7 @@ panel_kernel(TS* __restrict__ Sall, int64_t ld, int c, int32_t* __restrict__ piv
                     const int r = rb + u * nth;
                     if (r < R) {
 #pragma unroll
-                        for (int cc = 0; cc < IB; ++cc) X[(size_t)cc * R0 + r] = acc[u][cc];
+                        for (int cc = 0; cc < IB; ++cc) X[cc * R0 + r] = acc[u][cc];
                     }
                 }
             }
@@ -135,7 +135,7 @@ panel_kernel(TS* __restrict__ Sall, int64_t ld, int c, int32_t* __restrict__ piv
                     const int r = rb + u * nth;
                     if (r < R) {
 #pragma unroll
-                        for (int cc = 0; cc < IB; ++cc) X[(size_t)cc * R0 + r] = v[u][cc];
+                        for (int cc = 0; cc < IB; ++cc) X[cc * R0 + r] = v[u][cc];
                     }
                 }
             }
@@ -170,7 +170,7 @@ panel_kernel(TS* __restrict__ Sall, int64_t ld, int c, int32_t* __restrict__ piv
             if (bi >= R || !(best > (TS)0)) { bi = cc; best = (TS)0; }
             const int pr = bi;
             if (best == (TS)0) singular = true;
-            if (tid < IB) { s_prow[cc & 1][tid] = X[(size_t)tid * R0 + pr]; s_crow[cc & 1][tid] = X[(size_t)tid * R0 + cc]; }
+            if (tid < IB) { s_prow[cc & 1][tid] = X[tid * R0 + pr]; s_crow[cc & 1][tid] = X[tid * R0 + cc]; }
             if (tid == 0) s_piv[cc] = pr;
             __syncthreads();
             const TS* prow = s_prow[cc & 1];
@@ -182,7 +182,7 @@ panel_kernel(TS* __restrict__ Sall, int64_t ld, int c, int32_t* __restrict__ piv
             if (r == cc) {                         // row cc takes the pivot row
                 if (pr != cc) {
 #pragma unroll
-                    for (int q = 0; q < IB; ++q) X[(size_t)q * R0 + r] = prow[q];
+                    for (int q = 0; q < IB; ++q) X[q * R0 + r] = prow[q];
                 }
                 r += nth;
             } else if (r < cc) {
@@ -191,22 +191,22 @@ panel_kernel(TS* __restrict__ Sall, int64_t ld, int c, int32_t* __restrict__ piv
             for (; r < R; r += nth) {
                 if (r == pr) {                     // row pr takes the old row cc
 #pragma unroll
-                    for (int q = 0; q < cc; ++q) X[(size_t)q * R0 + r] = crow[q];
+                    for (int q = 0; q < cc; ++q) X[q * R0 + r] = crow[q];
                     const TS l = crow[cc] * inv;
-                    X[(size_t)cc * R0 + r] = l;
+                    X[cc * R0 + r] = l;
 #pragma unroll
                     for (int q = cc + 1; q < IB; ++q) {
                         const TS nv = crow[q] - l * prow[q];
-                        X[(size_t)q * R0 + r] = nv;
+                        X[q * R0 + r] = nv;
                         if (q == cc + 1) { const TS a = tabs(nv); if (a > best) { best = a; bi = r; } }
                     }
                 } else {
-                    const TS l = X[(size_t)cc * R0 + r] * inv;
-                    X[(size_t)cc * R0 + r] = l;
+                    const TS l = X[cc * R0 + r] * inv;
+                    X[cc * R0 + r] = l;
 #pragma unroll
                     for (int q = cc + 1; q < IB; ++q) {
-                        const TS nv = X[(size_t)q * R0 + r] - l * prow[q];
-                        X[(size_t)q * R0 + r] = nv;
+                        const TS nv = X[q * R0 + r] - l * prow[q];
+                        X[q * R0 + r] = nv;
                         if (q == cc + 1) { const TS a = tabs(nv); if (a > best) { best = a; bi = r; } }
                     }
                 }
@@ -216,7 +216,7 @@ panel_kernel(TS* __restrict__ Sall, int64_t ld, int c, int32_t* __restrict__ piv
         for (int r = tid; r < R; r += nth) {
             TS* row = S + (size_t)(c + jb + r);
 #pragma unroll
-            for (int cc = 0; cc < IB; ++cc) row[(size_t)(c + jb + cc) * ld] = X[(size_t)cc * R0 + r];
+            for (int cc = 0; cc < IB; ++cc) row[(size_t)(c + jb + cc) * ld] = X[cc * R0 + r];
         }
         if (tid < IB) { piv[c + jb + tid] = c + jb + s_piv[tid]; s_pall[jb + tid] = jb + s_piv[tid]; }
         if constexpr (IB < LEAF) {

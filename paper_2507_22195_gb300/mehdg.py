@@ -26,7 +26,8 @@ EXPORTED = ["mehdg_default_params", "mehdg_create", "mehdg_set_mesh", "mehdg_set
             "mehdg_residual", "mehdg_condense", "mehdg_apply_condensed", "mehdg_recover",
             "mehdg_status", "mehdg_last_error", "mehdg_destroy", "mehdg_profile_enable",
             "mehdg_profile_read", "mehdg_launch_count", "mehdg_test_trailing_update",
-            "mehdg_test_trailing_work_bytes", "mehdg_residual_static", "mehdg_solve_condensed"]
+            "mehdg_test_trailing_work_bytes", "mehdg_residual_static", "mehdg_solve_condensed",
+            "mehdg_residual_vjp"]
 
 
 class mehdg_params(C.Structure):
@@ -63,6 +64,7 @@ def load(path: str | None = None):
     L.mehdg_recover.argtypes = [_vp, _vp, _vp, _vp, _vp]
     L.mehdg_status.argtypes = [_vp, _vp, _vp]
     L.mehdg_solve_condensed.argtypes = [_vp, _vp, _vp, C.c_double, C.c_int, C.c_int, _vp, _vp, _vp]
+    L.mehdg_residual_vjp.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
     L.mehdg_last_error.argtypes = [_vp]
     L.mehdg_last_error.restype = C.c_char_p
     L.mehdg_destroy.argtypes = [_vp]
@@ -147,6 +149,11 @@ def mehdg_solve_condensed(ctx, bhat, dVhat, rtol=1e-10, restart=30, max_iter=500
     if check:
         _check(ctx, rc, "mehdg_solve_condensed")
     return it.value, res.value
+
+
+def mehdg_residual_vjp(ctx, lam_V, lam_Vhat, g_v, g_vhat, stream=None):
+    _check(ctx, load().mehdg_residual_vjp(ctx, _ptr(lam_V), _ptr(lam_Vhat), _ptr(g_v), _ptr(g_vhat),
+                                          _stream(stream)), "mehdg_residual_vjp")
 
 
 def mehdg_condense(ctx, bhat, Ahat_local=None, stream=None):
@@ -277,6 +284,15 @@ class Context:
         it, res = mehdg_solve_condensed(self.ctx, bhat, x, rtol, restart, max_iter)
         return x, it, res
 
+    def residual_vjp(self, lam_V, lam_Vhat=None):
+        """(g_v, g_vhat): the residual's VJP at the current state (Euler)"""
+        import torch
+        m = self.mesh
+        gv = torch.empty((m.nK, 5, m.Nn), dtype=torch.float64, device=lam_V.device)
+        gh = torch.empty((m.n_global_faces, 5, m.n2), dtype=torch.float64, device=lam_V.device)
+        mehdg_residual_vjp(self.ctx, lam_V, lam_Vhat, gv, gh)
+        return gv, gh
+
     def recover(self, dvh, with_dQ=False):
         import torch
         m = self.mesh
@@ -287,3 +303,28 @@ class Context:
 
     def status(self):
         return mehdg_status(self.ctx, self.mesh.nK)
+
+
+def residual_function():
+    """torch.autograd.Function: (R_V, R_Vhat) = residual(v, vhat) of an Euler
+    Context at a fixed v*, with the backward pass through mehdg_residual_vjp."""
+    import torch
+
+    class Residual(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, v, vhat, context, vstar):
+            context.set_state(v.detach().contiguous(), vhat.detach().contiguous(), None, vstar)
+            RV, _, RH = context.residual()
+            fctx.context = context
+            fctx.save_for_backward(v, vhat, vstar)
+            return RV, RH
+
+        @staticmethod
+        def backward(fctx, gRV, gRH):
+            v, vhat, vstar = fctx.saved_tensors
+            context = fctx.context
+            context.set_state(v.detach().contiguous(), vhat.detach().contiguous(), None, vstar)
+            gv, gh = context.residual_vjp(gRV.contiguous(), None if gRH is None else gRH.contiguous())
+            return gv, gh, None, None
+
+    return Residual

@@ -426,3 +426,31 @@ def test_dof_tables():
         for m in (1, 2):
             loc, glo = oracle.dof_counts_tet(r["p"], m, r["N_ele"])
             assert loc == r[f"m{m}_local"] and glo == r[f"m{m}_global"], (r, m, loc, glo)
+
+
+def test_oracle_residual_vjp_against_central_differences():
+    """the oracle's VJP (transposed complex-step blocks, assembled over the
+    mesh) against central differences of the oracle residual.  ES flux: the
+    KEPES flux's theta = sqrt(|(P - Phat)/(P + Phat)|) has an unbounded
+    derivative as P -> Phat, so central differences of it converge only as
+    the step goes to zero."""
+    import numpy as np
+    from paper_2507_22195_gb300 import inputs as I
+    mesh = I.periodic_mesh((2, 1, 1), 1, 1)
+    st = I.make_state(mesh, "tgv", 1e-2, 5, 6, M0=0.3)
+    prm = oracle.params(flux=1, Mach=0.3)
+    g = np.random.default_rng(3)
+    lv = g.standard_normal((mesh.nK, 5, mesh.Nn))
+    lh = g.standard_normal((mesh.n_global_faces, 5, mesh.n2))
+    gv, gh = oracle.residual_vjp_mesh(prm, mesh, st, lv, lh)
+    dv = g.standard_normal(st.v.shape)
+    dh = g.standard_normal(st.vhat.shape)
+    eps = 1e-6
+    vals = []
+    for sgn in (1.0, -1.0):
+        s2 = I.State(v=st.v + sgn * eps * dv, vhat=st.vhat + sgn * eps * dh, q=None, vstar=st.vstar)
+        rv, _, rh = oracle.residual_mesh(prm, mesh, s2)
+        vals.append((rv * lv).sum() + (rh * lh).sum())
+    fd = (vals[0] - vals[1]) / (2 * eps)
+    ad = (gv * dv).sum() + (gh * dh).sum()
+    assert abs(fd - ad) < 1e-7 * abs(ad), (fd, ad)
