@@ -38,8 +38,8 @@ __device__ __forceinline__ double tabs(double x) { return fabs(x); }
 // pivot column costs two barriers: one to publish the per-warp maxima, one
 // after every thread has read the old pivot row and row cc.  The search for
 // the next pivot runs on the values the update has just produced.
-template <class TS, int IB>
-__global__ void __launch_bounds__(PANEL_THREADS)
+template <class TS, int IB, int MINB>
+__global__ void __launch_bounds__(PANEL_THREADS, MINB)
 panel_kernel(TS* __restrict__ Sall, int64_t ld, int c, int32_t* __restrict__ pivall, int32_t* status) {
     constexpr int nth = PANEL_THREADS, NW = PANEL_THREADS / 32;
     const int K = blockIdx.x;
@@ -643,21 +643,31 @@ solve_kernel(const TS* __restrict__ Sall, int64_t ld, const int32_t* __restrict_
 // shared-memory budget, else the widest of 8, 4, 2, 1 that fits (16 would
 // need more registers than the left-looking step can hold)
 template <class TS>
-int pick_ib(int64_t rows) {
-    const size_t budget = 200 * 1024;
+int pick_ib(int64_t rows, bool two_per_sm) {
+    // with more elements than SMs, two CTAs per SM (the leaf is latency-bound:
+    // a second element's leaf hides the barriers of the first) as long as the
+    // sub-panel stays >= 4 wide; otherwise the widest sub-panel that fits
+    const size_t budget1 = 200 * 1024, budget = two_per_sm ? 100 * 1024 : budget1;
     if ((size_t)LEAF * rows * sizeof(TS) <= budget) return LEAF;
     int ib = 8;
-    while (ib > 1 && (size_t)ib * rows * sizeof(TS) > budget) ib >>= 1;
+    while (ib > 4 && (size_t)ib * rows * sizeof(TS) > budget) ib >>= 1;
+    while (ib > 1 && (size_t)ib * rows * sizeof(TS) > budget1) ib >>= 1;
     return ib;
 }
 
 template <class TS>
 cudaError_t launch_panel(TS* S, int64_t ld, int c, int32_t* piv, int32_t* status, int64_t nK, cudaStream_t st) {
-    int ib = pick_ib<TS>(ld - c);
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const bool two = nK > nsm;
+    int ib = pick_ib<TS>(ld - c, two);
     size_t sm = (size_t)ib * (ld - c) * sizeof(TS);
     if (sm < 16) sm = 16;
-#define LP(IB) do { cudaFuncSetAttribute(panel_kernel<TS, IB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
-                    panel_kernel<TS, IB><<<(unsigned)nK, PANEL_THREADS, sm, st>>>(S, ld, c, piv, status); } while (0)
+    // two CTAs per SM: registers capped at 64 per thread; one: up to 128
+#define LP2(IB, MB) do { cudaFuncSetAttribute(panel_kernel<TS, IB, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+                         panel_kernel<TS, IB, MB><<<(unsigned)nK, PANEL_THREADS, sm, st>>>(S, ld, c, piv, status); } while (0)
+#define LP(IB) do { if (two) LP2(IB, 2); else LP2(IB, 1); } while (0)
     switch (ib) {
     case 32: LP(32); break;
     case 8: LP(8); break;
@@ -666,6 +676,7 @@ cudaError_t launch_panel(TS* S, int64_t ld, int c, int32_t* piv, int32_t* status
     default: LP(1); break;
     }
 #undef LP
+#undef LP2
     MEHDG_COUNT(1);
     return cudaGetLastError();
 }
