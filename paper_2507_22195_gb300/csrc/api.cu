@@ -42,11 +42,13 @@ void free_mesh(mehdg_ctx* c) {
     dfree(c->d_res); dfree(c->d_dx); dfree(c->d_nrm); dfree(c->d_status); dfree(c->d_iters); dfree(c->d_conv);
     dfree(c->d_cnt); dfree(c->d_S); dfree(c->d_piv); dfree(c->d_work);
     dfree(c->d_RQ); dfree(c->d_z); dfree(c->d_dq); dfree(c->d_qt1); dfree(c->d_qt2); dfree(c->d_Minv); dfree(c->d_C1);
-    dfree(c->d_pj); c->pj_ready = false;
+    dfree(c->d_pj); dfree(c->d_pjf); c->pj_ready = false;
     if (c->d_krylov) { cudaFree(c->d_krylov); c->d_krylov = nullptr; c->krylov_bytes = 0; }
     if (c->lu_graph) { cudaGraphExecDestroy(c->lu_graph); c->lu_graph = nullptr; }
     if (c->lu_ev_in) { cudaEventDestroy(c->lu_ev_in); c->lu_ev_in = nullptr; }
     if (c->lu_ev_out) { cudaEventDestroy(c->lu_ev_out); c->lu_ev_out = nullptr; }
+    if (c->zs_ev_in) { cudaEventDestroy(c->zs_ev_in); c->zs_ev_in = nullptr; }
+    if (c->zs_ev_out) { cudaEventDestroy(c->zs_ev_out); c->zs_ev_out = nullptr; }
     if (c->lu_stream) { cudaStreamDestroy(c->lu_stream); c->lu_stream = nullptr; }
     if (c->h_cnt) { cudaFreeHost(c->h_cnt); c->h_cnt = nullptr; }
     c->nK = 0; c->condensed = false;
@@ -129,6 +131,7 @@ int tangent(mehdg_ctx* c, const double* dv, const double* dvh, const double* dq,
     ResidualArgs a = base_args(c);
     a.dv = dv; a.dvh = dvh; a.dq = viscous(c) ? dq : nullptr; a.tRV = tRV; a.tRH = tRH; a.skip = skip;
     a.pj = c->pj_ready ? c->d_pj : nullptr;      // linear volume pass from the stored point Jacobians
+    a.pjf = c->pj_ready ? c->d_pjf : nullptr;    // linear face pass when the trace direction is 0
     int ev = prof_begin(&c->prof, PH_TANGENT, st);
     TRY(launch_residual(a, c->nK, viscous(c), true, st));
     prof_end(&c->prof, ev, st, 0.0);
@@ -273,6 +276,7 @@ int mehdg_set_mesh(mehdg_ctx* c, int64_t nK, const int32_t* p, const int32_t* m,
         DALLOC(c->d_C1, sizeof(double) * t.n * t.n);
     }
     if (!vis) DALLOC(c->d_pj, sizeof(double) * 100 * (size_t)nK * t.m * t.m * t.m * t.npt);
+    if (!vis) DALLOC(c->d_pjf, sizeof(double) * 25 * (size_t)nK * 6 * t.m * t.m * t.ng * t.ng);
     DALLOC(c->d_S, Sbytes);
     DALLOC(c->d_piv, sizeof(int32_t) * nK * c->Npad);
     c->work_bytes = lu_work_bytes(nK, c->Npad, fp64, c->prm.prec);
@@ -336,6 +340,16 @@ int mehdg_condense(mehdg_ctx* c, double* bhat, double* Ahat_local, void* stream)
     const int64_t nK = c->nK, ld = c->Npad;
     TRY(cudaMemsetAsync(c->d_status, 0, sizeof(int32_t) * nK, st));
     TRY(cudaMemsetAsync(c->d_iters, 0, sizeof(int32_t) * nK, st));
+    // S^K := 0 on the context's side stream while the (FP64-bound) residual
+    // runs; the Jacobian waits for it
+    const size_t sbytes = (size_t)nK * ld * ld * (fp64 ? 8 : 4);
+    if (!c->lu_stream) TRY(cudaStreamCreateWithFlags(&c->lu_stream, cudaStreamNonBlocking));
+    if (!c->zs_ev_in) TRY(cudaEventCreateWithFlags(&c->zs_ev_in, cudaEventDisableTiming));
+    if (!c->zs_ev_out) TRY(cudaEventCreateWithFlags(&c->zs_ev_out, cudaEventDisableTiming));
+    TRY(cudaEventRecord(c->zs_ev_in, st));
+    TRY(cudaStreamWaitEvent(c->lu_stream, c->zs_ev_in, 0));
+    TRY(cudaMemsetAsync(c->d_S, 0, sbytes, c->lu_stream));
+    TRY(cudaEventRecord(c->zs_ev_out, c->lu_stream));
     // residual at the state
     ResidualArgs a = base_args(c);
     a.RV = c->d_RV; a.RH = c->d_RHloc; a.RQ = vis ? c->d_RQ : nullptr;
@@ -346,13 +360,13 @@ int mehdg_condense(mehdg_ctx* c, double* bhat, double* Ahat_local, void* stream)
     int rc;
     if (vis && (rc = qproj(c, 1.0, nullptr, 0.0, nullptr, 0.0, c->d_z, nullptr, st))) return rc;
     // S^K = A_vv - A_vq C (dense), padded identity
+    TRY(cudaStreamWaitEvent(st, c->zs_ev_out, 0));
     ev = prof_begin(&c->prof, PH_JACOBIAN, st);
-    TRY(cudaMemsetAsync(c->d_S, 0, (size_t)nK * ld * ld * (fp64 ? 8 : 4), st));
     TRY(launch_pad_identity(c->d_S, nK, ld, c->Nv, fp64, st));
     JacobianArgs ja;
     ja.tab = c->tab; ja.ph = c->ph; ja.box = c->d_box; ja.v = c->v; ja.vs = c->vs; ja.vh = c->vh; ja.q = c->q;
     ja.gid = c->d_gid; ja.S = c->d_S; ja.ld = ld; ja.status = c->d_status; ja.C1 = c->d_C1;
-    ja.pj = c->d_pj;
+    ja.pj = c->d_pj; ja.pjf = c->d_pjf;
     TRY(launch_jacobian(ja, nK, fp64, st));
     c->pj_ready = c->d_pj != nullptr;
     prof_end(&c->prof, ev, st, 0.0);

@@ -168,6 +168,7 @@ struct mehdg_ctx {
     double *d_qt1 = nullptr, *d_qt2 = nullptr;   // line-operator scratch
     double *d_Minv = nullptr, *d_C1 = nullptr;   // [n][n] 1-D tables
     double* d_pj = nullptr;             // [nK][m^3][npt][100] weighted FP64 point Jacobians (inviscid)
+    double* d_pjf = nullptr;            // [nK][6 m^2][fpt][25] weighted FP64 face blocks dFhat/dv (inviscid)
     bool pj_ready = false;              // d_pj holds the Jacobians at the current state
     double* d_r = nullptr;              // [nK][Npad] FP64 right-hand side
     double* d_x = nullptr;              // [nK][Npad] FP64 solution
@@ -188,6 +189,7 @@ struct mehdg_ctx {
     cudaGraphExec_t lu_graph = nullptr; // the factorisation's launches, captured on first use
     cudaStream_t lu_stream = nullptr;   // stream the graph is replayed on
     cudaEvent_t lu_ev_in = nullptr, lu_ev_out = nullptr;
+    cudaEvent_t zs_ev_in = nullptr, zs_ev_out = nullptr;   // zeroing of S beside the residual
     long long lu_graph_launches = 0;    // kernels in the graph
     void* d_krylov = nullptr;           // GMRES basis and scratch of the trace solve (first use)
     size_t krylov_bytes = 0;

@@ -300,7 +300,10 @@ jac_face_kernel(JacobianArgs a) {
         face_integrand(a.ph, dv, dh, dq, d, sgn, Fh);
         double W = sW[g1] * hw1 * sW[g2] * hw2;
         for (int k = 0; k < 5; ++k)
-            for (int l = 0; l < 5; ++l) P[x * 25 + k * 5 + l] = (TS)(W * Fh[k].d[l]);
+            for (int l = 0; l < 5; ++l) {
+                P[x * 25 + k * 5 + l] = (TS)(W * Fh[k].d[l]);
+                if (a.pjf) a.pjf[(((size_t)K * 6 * m * m + blockIdx.x) * fpt + x) * 25 + k * 5 + l] = W * Fh[k].d[l];
+            }
     }
     __syncthreads();
     TS* S = reinterpret_cast<TS*>(a.S) + (size_t)K * a.ld * a.ld;

@@ -14,6 +14,7 @@ struct ResidualArgs {
     int32_t* status;
     const int32_t* skip;                  // [nK] nonzero = skip element (may be null)
     const double* pj;                     // stored point Jacobians: tangent volume pass is linear (may be null)
+    const double* pjf;                    // stored face point Jacobians dFhat/dv: face pass linear when dvh = 0
 };
 
 cudaError_t launch_residual(const ResidualArgs& a, int64_t nK, bool visc, bool tangent, cudaStream_t st);
@@ -46,6 +47,7 @@ struct JacobianArgs {
     int32_t* status;
     const double* C1;         // [n][n] M1_ref^-1 G1_ref (viscous only)
     double* pj;               // if set: the weighted FP64 point Jacobians [nK][m^3][npt][100] (inviscid)
+    double* pjf;              // if set: the weighted FP64 face blocks dFhat/dv [nK][6 m^2][fpt][25] (inviscid)
 };
 cudaError_t launch_jacobian(const JacobianArgs& a, int64_t nK, bool fp64, cudaStream_t st);
 cudaError_t launch_pad_identity(void* S, int64_t nK, int64_t ld, int Nv, bool fp64, cudaStream_t st);

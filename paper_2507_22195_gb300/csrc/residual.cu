@@ -442,6 +442,62 @@ residual_face_kernel(ResidualArgs a) {
     }
 }
 
+// Linear face pass of the tangent along dv alone (dvhat = 0, Euler): the
+// stored weighted face blocks W dFhat/dv of the Jacobian kernel, applied to dv
+// interpolated to the face points and tested against the face nodes; adds
+// into tRV and into the element's side of the trace tangent tRH.
+__global__ void __launch_bounds__(128)
+residual_face_lin_kernel(ResidualArgs a) {
+    const Tab& tb = a.tab;
+    const int K = blockIdx.y;
+    if (a.skip && a.skip[K]) return;
+    const int p = tb.p, m = tb.m, n = tb.n, ng = tb.ng, Nn = tb.Nn, n2 = tb.n2, p1 = p + 1;
+    const int f = blockIdx.x / (m * m), e = blockIdx.x % (m * m);
+    const int e1 = e % m, e2 = e / m;
+    const int d = f / 2, t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+    const int fl = p1 * p1, fpt = ng * ng;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* sL = reinterpret_cast<double*>(smem_raw);          // [ng][p1]
+    double* fd = sL + MEHDG_MAXG * (MEHDG_MAXP + 1);           // [5][fl] dv on the face nodes
+    double* pF = fd + 5 * fl;                                  // [5][fpt]
+    int* nodeA = reinterpret_cast<int*>(pF + 5 * fpt);         // [fl]
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (int i = tid; i < ng * p1; i += nth) sL[i] = tb.L[i / p1][i % p1];
+    const int64_t oV = (int64_t)K * 5 * Nn, oH = (int64_t)K * 30 * n2;
+    for (int i = tid; i < fl; i += nth) {
+        const int c1 = e1 * p + i % p1, c2 = e2 * p + i / p1;
+        int idx[3]; idx[d] = (f & 1) ? n - 1 : 0; idx[t1] = c1; idx[t2] = c2;
+        const int A = idx[0] + n * (idx[1] + n * idx[2]);
+        nodeA[i] = A;
+        for (int k = 0; k < 5; ++k) fd[k * fl + i] = a.dv[oV + k * Nn + A];
+    }
+    __syncthreads();
+    const double* Gb = a.pjf + ((size_t)K * 6 * m * m + blockIdx.x) * fpt * 25;
+    for (int x = tid; x < fpt; x += nth) {
+        const int g1 = x % ng, g2 = x / ng;
+        double dvx[5] = {0, 0, 0, 0, 0};
+        for (int i = 0; i < fl; ++i) {
+            const double mu = sL[g1 * p1 + i % p1] * sL[g2 * p1 + i / p1];
+            for (int k = 0; k < 5; ++k) dvx[k] += fd[k * fl + i] * mu;
+        }
+        const double* Gx = Gb + (size_t)x * 25;
+        for (int k = 0; k < 5; ++k) {
+            double s = 0.0;
+            for (int l = 0; l < 5; ++l) s += Gx[k * 5 + l] * dvx[l];
+            pF[k * fpt + x] = s;
+        }
+    }
+    __syncthreads();
+    for (int r = tid; r < fl * 5; r += nth) {
+        const int i = r % fl, k = r / fl;
+        const int l1 = i % p1, l2 = i / p1;
+        double s = 0.0;
+        for (int x = 0; x < fpt; ++x) s += pF[k * fpt + x] * sL[(x % ng) * p1 + l1] * sL[(x / ng) * p1 + l2];
+        if (a.tRV) atomicAdd(a.tRV + oV + k * Nn + nodeA[i], s);
+        if (a.tRH) atomicAdd(a.tRH + oH + (f * 5 + k) * n2 + (e1 * p + l1) + n * (e2 * p + l2), s);
+    }
+}
+
 // sum the (one or two) element sides of every global face
 __global__ void trace_gather_kernel(const double* __restrict__ loc, const int64_t* __restrict__ g2l,
                                     int64_t G, int n2, double* __restrict__ out, double alpha,
@@ -542,8 +598,17 @@ cudaError_t launch_residual(const ResidualArgs& a, int64_t nK, bool visc, bool t
             cudaFuncSetAttribute(residual_volume_sf_kernel<double, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl);
             residual_volume_sf_kernel<double, false, true><<<gv, b, sl, st>>>(a, nA);
         }
-        cudaFuncSetAttribute(residual_face_kernel<Dual<1>, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf);
-        residual_face_kernel<Dual<1>, false><<<gf, b, sf, st>>>(a);
+        if (a.pjf && !a.dvh) {
+            if (a.dv) {
+                const int fl = (t.p + 1) * (t.p + 1), fpt = t.ng * t.ng;
+                const size_t sfl = sizeof(double) * (MEHDG_MAXG * (MEHDG_MAXP + 1) + 5 * (size_t)fl + 5 * (size_t)fpt)
+                                 + sizeof(int) * fl + 16;
+                residual_face_lin_kernel<<<gf, b, sfl, st>>>(a);
+            }
+        } else {
+            cudaFuncSetAttribute(residual_face_kernel<Dual<1>, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf);
+            residual_face_kernel<Dual<1>, false><<<gf, b, sf, st>>>(a);
+        }
     } else if (tangent) { if (visc) LAUNCH_RES(Dual<1>, true); else LAUNCH_RES(Dual<1>, false); }
     else { if (visc) LAUNCH_RES(double, true); else LAUNCH_RES(double, false); }
 #undef LAUNCH_RES
