@@ -38,10 +38,16 @@ __device__ __forceinline__ double tabs(double x) { return fabs(x); }
 // pivot column costs two barriers: one to publish the per-warp maxima, one
 // after every thread has read the old pivot row and row cc.  The search for
 // the next pivot runs on the values the update has just produced.
+// one FP32 CTA per SM (fewer elements than SMs): 1024 threads; otherwise 512
+// (FP64 keeps 512 so that its registers do not spill)
+template <class TS, int MINB> constexpr int panel_threads() {
+    return (MINB == 1 && sizeof(TS) == 4) ? 2 * PANEL_THREADS : PANEL_THREADS;
+}
+
 template <class TS, int IB, int MINB>
-__global__ void __launch_bounds__(PANEL_THREADS, MINB)
+__global__ void __launch_bounds__(panel_threads<TS, MINB>(), MINB)
 panel_kernel(TS* __restrict__ Sall, int64_t ld, int c, int32_t* __restrict__ pivall, int32_t* status) {
-    constexpr int nth = PANEL_THREADS, NW = PANEL_THREADS / 32;
+    constexpr int nth = panel_threads<TS, MINB>(), NW = nth / 32;
     const int K = blockIdx.x;
     TS* S = Sall + (size_t)K * ld * ld;
     int32_t* piv = pivall + (size_t)K * ld;
@@ -666,7 +672,7 @@ cudaError_t launch_panel(TS* S, int64_t ld, int c, int32_t* piv, int32_t* status
     if (sm < 16) sm = 16;
     // two CTAs per SM: registers capped at 64 per thread; one: up to 128
 #define LP2(IB, MB) do { cudaFuncSetAttribute(panel_kernel<TS, IB, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
-                         panel_kernel<TS, IB, MB><<<(unsigned)nK, PANEL_THREADS, sm, st>>>(S, ld, c, piv, status); } while (0)
+                         panel_kernel<TS, IB, MB><<<(unsigned)nK, panel_threads<TS, MB>(), sm, st>>>(S, ld, c, piv, status); } while (0)
 #define LP(IB) do { if (two) LP2(IB, 2); else LP2(IB, 1); } while (0)
     switch (ib) {
     case 32: LP(32); break;
