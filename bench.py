@@ -334,6 +334,21 @@ def main():
         e2e_s = float(t.item())
     h2d = sum(h.numel() * 8 for h in host)
     d2h = hb.numel() * 8
+    # recovery (eq. R2, R6) timed on its own, after the condensation above, for a
+    # seeded trace increment
+    dvh = torch.tensor(I.random_direction(st.vhat.shape, 77, 1e-3), device=dev)
+    ctx.recover(dvh)
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    r0.record(stream)
+    for _ in range(a.steps):
+        ctx.recover(dvh)
+    r1.record(stream)
+    barrier()
+    rec = {"value": world * mesh.nK * a.steps / (r0.elapsed_time(r1) / 1e3), "unit": "macro-elements/s",
+           "ms_per_step": r0.elapsed_time(r1) / a.steps,
+           "what": "recover: dV = S^-1(-R_V - A_v,vhat dVhat) with FP64 refinement (and dQ when viscous), "
+                   "seeded dVhat"}
     ctx.set_state(v, vh, q, vs)
 
     # roofline of the dominant kernel: the outer trailing update of the LU
@@ -407,6 +422,7 @@ def main():
             "status_ok": bool((stat == 0).all()),
             "phases_ms_per_step": {k: round(vv["ms"] / a.steps, 3) for k, vv in prof.items()},
             "fp64_gpu": fp,
+            "recover": rec,
         }
         print(json.dumps(out))
     ctx.close()

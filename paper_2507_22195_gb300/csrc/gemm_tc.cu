@@ -142,7 +142,7 @@ template <int BN, bool BF16, bool STORE, bool SPLIT>
 __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
 tc_stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                  float* __restrict__ Sall, int64_t ld, int r0, int c0, int M, int N, int nchunk, int kp,
-                 int tiles_m, int tiles_n, int64_t ntiles, int32_t* status) {
+                 int tiles_m, int tiles_n, int64_t ntiles, int32_t* status, __nv_bfloat16* bq, int bq_kp) {
     constexpr int A_BYTES = TM * CHUNK_BYTES;
     constexpr int B_BYTES = BN * CHUNK_BYTES;
     constexpr int NP = SPLIT ? 2 : 1;
@@ -261,6 +261,21 @@ tc_stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
                 for (int j = 0; j < W; ++j) {
                     if (j < nc) __stcs(p, STORE ? __uint_as_float(r[j]) : cv[j] - __uint_as_float(r[j]));
                     p += ld;
+                }
+                if (STORE && bq) {
+                    // the same product as the next update's split-BF16 B operand
+                    // (row = its K index, column = its N index): [hi | lo] rows
+                    __nv_bfloat16* qb = bq + ((size_t)K * N + col0) * (size_t)(2 * bq_kp) + row;
+#pragma unroll
+                    for (int j = 0; j < W; ++j) {
+                        if (j < nc) {
+                            const float v = __uint_as_float(r[j]);
+                            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+                            qb[0] = hi;
+                            qb[bq_kp] = __float2bfloat16_rn(v - __bfloat162float(hi));
+                        }
+                        qb += 2 * bq_kp;
+                    }
                 }
             }
             tc_fence_before();
@@ -434,7 +449,7 @@ size_t panel_bytes(int64_t nK, int64_t ld) {
 
 template <int BN, bool BF16, bool STORE, bool SPLIT>
 cudaError_t launch_stream(const CUtensorMap& a, const CUtensorMap& b, const LUPlan& P, int r0, int c0, int M, int N,
-                          int nchunk, int kp, cudaStream_t st) {
+                          int nchunk, int kp, cudaStream_t st, void* bq = nullptr, int bq_kp = 0) {
     const int tiles_m = (M + TM - 1) / TM, tiles_n = (N + BN - 1) / BN;
     const int64_t ntiles = (int64_t)tiles_m * tiles_n * P.nK;
     constexpr size_t sm = stream_smem_bytes<BN, SPLIT>();
@@ -442,7 +457,8 @@ cudaError_t launch_stream(const CUtensorMap& a, const CUtensorMap& b, const LUPl
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sm_count());
     kern<<<(unsigned)grid, 64 + 32 * EPI_WARPS, sm, st>>>(a, b, (float*)P.S, P.ld, r0, c0, M, N, nchunk, kp, tiles_m,
-                                                         tiles_n, ntiles, P.status);
+                                                         tiles_n, ntiles, P.status,
+                                                         reinterpret_cast<__nv_bfloat16*>(bq), bq_kp);
     MEHDG_COUNT(1);
     return cudaGetLastError();
 }
@@ -450,10 +466,10 @@ cudaError_t launch_stream(const CUtensorMap& a, const CUtensorMap& b, const LUPl
 // one update / solve product with the operand panels already packed
 template <bool BF16, bool STORE, bool SPLIT>
 cudaError_t launch_stream_bn(int BN, const CUtensorMap& a, const CUtensorMap& b, const LUPlan& P, int r0, int c0,
-                             int M, int N, int nchunk, int kp, cudaStream_t st) {
-    if (BN == 128) return launch_stream<128, BF16, STORE, SPLIT>(a, b, P, r0, c0, M, N, nchunk, kp, st);
-    if (BN == 64) return launch_stream<64, BF16, STORE, SPLIT>(a, b, P, r0, c0, M, N, nchunk, kp, st);
-    return launch_stream<32, BF16, STORE, SPLIT>(a, b, P, r0, c0, M, N, nchunk, kp, st);
+                             int M, int N, int nchunk, int kp, cudaStream_t st, void* bq = nullptr, int bq_kp = 0) {
+    if (BN == 128) return launch_stream<128, BF16, STORE, SPLIT>(a, b, P, r0, c0, M, N, nchunk, kp, st, bq, bq_kp);
+    if (BN == 64) return launch_stream<64, BF16, STORE, SPLIT>(a, b, P, r0, c0, M, N, nchunk, kp, st, bq, bq_kp);
+    return launch_stream<32, BF16, STORE, SPLIT>(a, b, P, r0, c0, M, N, nchunk, kp, st, bq, bq_kp);
 }
 
 
@@ -577,7 +593,7 @@ laswp_pack_kernel(float* __restrict__ Sall, int64_t ld, const int32_t* __restric
 // cores, through the explicit inverse of the unit-lower block L11.
 namespace {
 // the TRSM product with B = rows [c0, c0+256) of the columns [j0, j0+N), packed in Bp
-cudaError_t trsm256_product(const LUPlan& P, int c0, int j0, int N, void* Ap, void* Bp, cudaStream_t st) {
+cudaError_t trsm256_product(const LUPlan& P, int c0, int j0, int N, void* Ap, void* Bp, void* bq, cudaStream_t st) {
     const int Kd = LU_NB, nseg = 2, nchunk = Kd / (CHUNK_BYTES / 4);
     {
         dim3 gt(LU_NB / 32, (unsigned)P.nK);
@@ -588,7 +604,7 @@ cudaError_t trsm256_product(const LUPlan& P, int c0, int j0, int N, void* Ap, vo
     CUtensorMap ma, mb;
     if (!make_map(&ma, Ap, false, nseg * Kd, 256, P.nK, TM) || !make_map(&mb, Bp, false, nseg * Kd, N, P.nK, BN))
         return cudaErrorInvalidValue;
-    return launch_stream_bn<false, true, true>(BN, ma, mb, P, c0, j0, 256, N, nchunk, Kd, st);
+    return launch_stream_bn<false, true, true>(BN, ma, mb, P, c0, j0, 256, N, nchunk, Kd, st, bq, LU_NB);
 }
 }  // namespace
 
@@ -598,27 +614,35 @@ cudaError_t trsm256_product(const LUPlan& P, int c0, int j0, int N, void* Ap, vo
 // TF32 (every mixed mode: the explicit inverse of L11 amplifies operand
 // rounding, and one-pass TF32 or BF16 here leaves the factors too inexact for
 // the FP64 refinement).
-cudaError_t gemm_tc_swap_trsm256(const LUPlan& P, const int32_t* perm, int c0, cudaStream_t st) {
+cudaError_t gemm_tc_swap_trsm256(const LUPlan& P, const int32_t* perm, int c0, cudaStream_t st,
+                                 const void** update_b) {
+    if (update_b) *update_b = nullptr;
     const int j0 = c0 + LU_NB, N = (int)P.ld - j0;
     if (N <= 0) return cudaSuccess;
     if (!encoder()) return cudaErrorNotSupported;
     unsigned char* w = reinterpret_cast<unsigned char*>(P.work) + lu_perm_bytes(P.nK, P.ld);
+    const size_t pan = panel_bytes(P.nK, P.ld);
     void* Ap = w;
-    float* Bp = reinterpret_cast<float*>(w + panel_bytes(P.nK, P.ld));
+    float* Bp = reinterpret_cast<float*>(w + pan);
+    // split BF16: the product also writes the next update's B panel (third panel)
+    void* bq = P.prec == MEHDG_MIXED_BF16X3 ? (void*)(w + 2 * pan) : nullptr;
     dim3 gb((unsigned)((N + 7) / 8), (unsigned)P.nK);
     laswp_pack_kernel<<<gb, 256, 0, st>>>((float*)P.S, P.ld, perm, j0, N, Bp);
     MEHDG_COUNT(1);
-    return trsm256_product(P, c0, j0, N, Ap, Bp, st);
+    cudaError_t e = trsm256_product(P, c0, j0, N, Ap, Bp, bq, st);
+    if (e == cudaSuccess && update_b) *update_b = bq;
+    return e;
 }
 
 size_t gemm_tc_work_bytes(int64_t nK, int64_t ld, int prec) {
     (void)prec;
-    // two panels of at most ld x (2 x 256) FP32 per element (split precision)
-    return 2 * panel_bytes(nK, ld);
+    // three panels of at most ld x (2 x 256) FP32 per element (split precision):
+    // A, B, and the next update's B written by the TRSM product
+    return 3 * panel_bytes(nK, ld);
 }
 
 cudaError_t gemm_tc_update(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st,
-                           int ph_pack, int ph_gemm, double flops) {
+                           int ph_pack, int ph_gemm, double flops, const void* b_packed) {
     if (M <= 0 || N <= 0) return cudaSuccess;
     if (M < TM) return gemm_simt_update_f32(P, r0, c0, k0, M, N, Kd, st);   // a few tiny inner updates
     if (!encoder()) return cudaErrorNotSupported;
@@ -632,17 +656,20 @@ cudaError_t gemm_tc_update(const LUPlan& P, int r0, int c0, int k0, int M, int N
     unsigned char* w = reinterpret_cast<unsigned char*>(P.work) + lu_perm_bytes(P.nK, P.ld);
     const size_t pan = panel_bytes(P.nK, P.ld);
     void* Ap = w;
-    void* Bp = w + pan;
+    void* Bp = b_packed ? const_cast<void*>(b_packed) : (void*)(w + pan);
     // pack
     {
         const int ev = ph_pack >= 0 ? prof_begin(P.prof, ph_pack, st) : -1;
         dim3 g((unsigned)((M + 63) / 64), (unsigned)(Kp / 32), (unsigned)P.nK);
         if (bf16) pack_A_kernel<true><<<g, 256, 0, st>>>((const float*)P.S, P.ld, r0, k0, M, Kd, Kp, nseg, Ap);
         else pack_A_kernel<false><<<g, 256, 0, st>>>((const float*)P.S, P.ld, r0, k0, M, Kd, Kp, nseg, Ap);
-        dim3 gb((unsigned)((N + 7) / 8), 1, (unsigned)P.nK);
-        if (bf16) pack_B_kernel<true><<<gb, 256, 0, st>>>((const float*)P.S, P.ld, k0, c0, N, Kd, Kp, nseg, Bp);
-        else pack_B_kernel<false><<<gb, 256, 0, st>>>((const float*)P.S, P.ld, k0, c0, N, Kd, Kp, nseg, Bp);
-        MEHDG_COUNT(2);
+        MEHDG_COUNT(1);
+        if (!b_packed) {
+            dim3 gb((unsigned)((N + 7) / 8), 1, (unsigned)P.nK);
+            if (bf16) pack_B_kernel<true><<<gb, 256, 0, st>>>((const float*)P.S, P.ld, k0, c0, N, Kd, Kp, nseg, Bp);
+            else pack_B_kernel<false><<<gb, 256, 0, st>>>((const float*)P.S, P.ld, k0, c0, N, Kd, Kp, nseg, Bp);
+            MEHDG_COUNT(1);
+        }
         if (ev >= 0) prof_end(P.prof, ev, st, 0.0);
     }
     const int BN = N >= 128 ? 128 : (N >= 64 ? 64 : 32);

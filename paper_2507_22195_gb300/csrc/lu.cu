@@ -736,14 +736,14 @@ cudaError_t launch_gemm_simt(const LUPlan& P, int r0, int c0, int k0, int M, int
 
 template <class TS>
 cudaError_t trailing_update(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st,
-                            int ph_pack = -1, int ph_gemm = -1, double flops = 0.0) {
+                            int ph_pack = -1, int ph_gemm = -1, double flops = 0.0, const void* b_packed = nullptr) {
     if constexpr (std::is_same<TS, double>::value) {
         const int ev = ph_gemm >= 0 ? prof_begin(P.prof, ph_gemm, st) : -1;
         cudaError_t e = launch_gemm_simt<double>(P, r0, c0, k0, M, N, Kd, st);
         if (ev >= 0) prof_end(P.prof, ev, st, flops);
         return e;
     } else {
-        return gemm_tc_update(P, r0, c0, k0, M, N, Kd, st, ph_pack, ph_gemm, flops);
+        return gemm_tc_update(P, r0, c0, k0, M, N, Kd, st, ph_pack, ph_gemm, flops, b_packed);
     }
 }
 
@@ -768,13 +768,14 @@ cudaError_t factor_t(const LUPlan& P, cudaStream_t st) {
         int ev = prof_begin(P.prof, PH_LU_PANELS, st);
         if ((e = rec_panel<TS>(P, c0, LU_NB, st)) != cudaSuccess) return e;
         int32_t* pp = panel_perm(P, c0);
+        const void* upd_b = nullptr;
         if ((e = launch_perm_build(P, c0, LU_NB, pp, st)) != cudaSuccess) return e;
         if (c0 + LU_NB < ld) {
             if constexpr (std::is_same<TS, double>::value) {
                 if ((e = launch_laswp_perm<TS>(P, pp, LU_NB, c0 + LU_NB, ld, st)) != cudaSuccess) return e;
                 e = launch_trsm<TS>(P, c0, LU_NB, c0 + LU_NB, ld, st);
             } else {
-                e = gemm_tc_swap_trsm256(P, pp, c0, st);
+                e = gemm_tc_swap_trsm256(P, pp, c0, st, &upd_b);
             }
             if (e != cudaSuccess) return e;
         }
@@ -782,7 +783,8 @@ cudaError_t factor_t(const LUPlan& P, cudaStream_t st) {
         if (c0 + LU_NB < ld) {
             int rest = ld - (c0 + LU_NB);
             if ((e = trailing_update<TS>(P, c0 + LU_NB, c0 + LU_NB, c0, rest, rest, LU_NB, st, PH_PACK_OUTER,
-                                         PH_GEMM_OUTER, 2.0 * rest * (double)rest * LU_NB * (double)P.nK)) != cudaSuccess)
+                                         PH_GEMM_OUTER, 2.0 * rest * (double)rest * LU_NB * (double)P.nK,
+                                         upd_b)) != cudaSuccess)
                 return e;
         }
     }

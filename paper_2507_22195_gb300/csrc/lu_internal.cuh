@@ -17,10 +17,14 @@ inline size_t lu_perm_bytes(int64_t nK, int64_t ld) { return lu_perm_scratch_byt
 // (TF32 or BF16 operands, FP32 accumulation), S^K column-major FP32.
 // With ph_gemm >= 0 the update kernel alone is timed under that phase (flops
 // recorded with it) and the operand packing under ph_pack.
+// b_packed: the B panel already packed (split BF16) by the TRSM product, or null
 cudaError_t gemm_tc_update(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st,
-                           int ph_pack = -1, int ph_gemm = -1, double flops = 0.0);
+                           int ph_pack = -1, int ph_gemm = -1, double flops = 0.0, const void* b_packed = nullptr);
 size_t gemm_tc_work_bytes(int64_t nK, int64_t ld, int prec);
 // row exchanges of the columns right of outer panel c0 by its net permutation
 // (perm: [nK][LU_PW]) and the TRSM of their rows [c0, c0+256), fused
-cudaError_t gemm_tc_swap_trsm256(const LUPlan& P, const int32_t* perm, int c0, cudaStream_t st);
+// (update_b, if not null, receives the next update's packed B panel, or null
+// when the precision mode does not fuse it)
+cudaError_t gemm_tc_swap_trsm256(const LUPlan& P, const int32_t* perm, int c0, cudaStream_t st,
+                                 const void** update_b);
 cudaError_t gemm_simt_update_f32(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st);
