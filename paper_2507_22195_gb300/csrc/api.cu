@@ -14,6 +14,7 @@
 // the q-direction built by the line operators of qproj.cu.
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 #include "common.cuh"
@@ -76,7 +77,10 @@ QProjArgs qargs(mehdg_ctx* c) {
 // the caller's stream by events); with phase profiling on, the launches are
 // issued directly so that the phase events sit between them.
 cudaError_t factor_all(mehdg_ctx* c, const LUPlan& P, cudaStream_t st) {
-    if (c->prof.on) return lu_factor(P, st);
+    // MEHDG_NO_GRAPH=1: direct launches (e.g. under a kernel profiler that
+    // replays launches one by one)
+    static const bool no_graph = [] { const char* e = std::getenv("MEHDG_NO_GRAPH"); return e && e[0] == '1'; }();
+    if (c->prof.on || no_graph) return lu_factor(P, st);
     cudaError_t e;
     if (!c->lu_graph) {
         if (!c->lu_stream && (e = cudaStreamCreateWithFlags(&c->lu_stream, cudaStreamNonBlocking)) != cudaSuccess) return e;

@@ -167,8 +167,8 @@ struct mehdg_ctx {
     double* d_dq = nullptr;             // q-direction of a tangent
     double *d_qt1 = nullptr, *d_qt2 = nullptr;   // line-operator scratch
     double *d_Minv = nullptr, *d_C1 = nullptr;   // [n][n] 1-D tables
-    double* d_pj = nullptr;             // [nK][m^3][npt][100] weighted FP64 point Jacobians (inviscid)
-    double* d_pjf = nullptr;            // [nK][6 m^2][fpt][25] weighted FP64 face blocks dFhat/dv (inviscid)
+    double* d_pj = nullptr;             // [nK][m^3][100][npt] weighted FP64 point Jacobians (inviscid)
+    double* d_pjf = nullptr;            // [nK][6 m^2][25][fpt] weighted FP64 face blocks dFhat/dv (inviscid)
     bool pj_ready = false;              // d_pj holds the Jacobians at the current state
     double* d_r = nullptr;              // [nK][Npad] FP64 right-hand side
     double* d_x = nullptr;              // [nK][Npad] FP64 solution

@@ -68,17 +68,18 @@ __device__ void volume_point_jacobians(const JacobianArgs& a, int K, int e1, int
         ok = vol_integrand(a.ph, dv, dvs, dq, U, FG) && ok;
         double W = sW[g1] * hw[0] * sW[g2] * hw[1] * sW[g3] * hw[2];
         TS* Px = P + (size_t)x * 100;
-        double* Gx = a.pj ? a.pj + (((size_t)K * tb.m * tb.m * tb.m + e1 + tb.m * (e2 + tb.m * e3)) * npt + x) * 100
+        // stored point-fastest, [K][micro-element][100][npt]: coalesced over the points
+        double* Gx = a.pj ? a.pj + ((size_t)K * tb.m * tb.m * tb.m + e1 + tb.m * (e2 + tb.m * e3)) * 100 * npt + x
                           : nullptr;
         for (int k = 0; k < 5; ++k)
             for (int l = 0; l < 5; ++l) {
                 const double u = W * U[k].d[l];
                 Px[k * 5 + l] = (TS)u;
-                if (Gx) Gx[k * 5 + l] = u;
+                if (Gx) Gx[(size_t)(k * 5 + l) * npt] = u;
                 for (int j = 0; j < 3; ++j) {
                     const double f = -W * FG[k][j].d[l];
                     Px[25 * (1 + j) + k * 5 + l] = (TS)f;
-                    if (Gx) Gx[25 * (1 + j) + k * 5 + l] = f;
+                    if (Gx) Gx[(size_t)(25 * (1 + j) + k * 5 + l) * npt] = f;
                 }
             }
     }
@@ -302,7 +303,7 @@ jac_face_kernel(JacobianArgs a) {
         for (int k = 0; k < 5; ++k)
             for (int l = 0; l < 5; ++l) {
                 P[x * 25 + k * 5 + l] = (TS)(W * Fh[k].d[l]);
-                if (a.pjf) a.pjf[(((size_t)K * 6 * m * m + blockIdx.x) * fpt + x) * 25 + k * 5 + l] = W * Fh[k].d[l];
+                if (a.pjf) a.pjf[(((size_t)K * 6 * m * m + blockIdx.x) * 25 + k * 5 + l) * fpt + x] = W * Fh[k].d[l];
             }
     }
     __syncthreads();

@@ -242,18 +242,18 @@ residual_volume_sf_kernel(ResidualArgs a, int nA) {
     bool ok = true;
     if constexpr (LIN) {
         // rows 0-4: W dU/dv dv; rows 5-19: W dFG/dv dv (the stored blocks carry -W)
-        const double* Gb = a.pj + ((size_t)K * m * m * m + e) * npt * 100;
+        const double* Gb = a.pj + ((size_t)K * m * m * m + e) * 100 * npt;   // [100][npt]
         for (int x = tid; x < npt; x += nth) {
             double dvx[5];
             for (int l = 0; l < 5; ++l) dvx[l] = RB[l * npt + x];
-            const double* Gx = Gb + (size_t)x * 100;
+            const double* Gx = Gb + x;
             for (int k = 0; k < 5; ++k) {
                 double u = 0.0, f0 = 0.0, f1 = 0.0, f2 = 0.0;
                 for (int l = 0; l < 5; ++l) {
-                    u += Gx[k * 5 + l] * dvx[l];
-                    f0 += Gx[25 + k * 5 + l] * dvx[l];
-                    f1 += Gx[50 + k * 5 + l] * dvx[l];
-                    f2 += Gx[75 + k * 5 + l] * dvx[l];
+                    u += Gx[(size_t)(k * 5 + l) * npt] * dvx[l];
+                    f0 += Gx[(size_t)(25 + k * 5 + l) * npt] * dvx[l];
+                    f1 += Gx[(size_t)(50 + k * 5 + l) * npt] * dvx[l];
+                    f2 += Gx[(size_t)(75 + k * 5 + l) * npt] * dvx[l];
                 }
                 RB[k * npt + x] = u;
                 RB[(5 + k * 3 + 0) * npt + x] = -f0;
@@ -472,7 +472,7 @@ residual_face_lin_kernel(ResidualArgs a) {
         for (int k = 0; k < 5; ++k) fd[k * fl + i] = a.dv[oV + k * Nn + A];
     }
     __syncthreads();
-    const double* Gb = a.pjf + ((size_t)K * 6 * m * m + blockIdx.x) * fpt * 25;
+    const double* Gb = a.pjf + ((size_t)K * 6 * m * m + blockIdx.x) * 25 * fpt;   // [25][fpt]
     for (int x = tid; x < fpt; x += nth) {
         const int g1 = x % ng, g2 = x / ng;
         double dvx[5] = {0, 0, 0, 0, 0};
@@ -480,10 +480,10 @@ residual_face_lin_kernel(ResidualArgs a) {
             const double mu = sL[g1 * p1 + i % p1] * sL[g2 * p1 + i / p1];
             for (int k = 0; k < 5; ++k) dvx[k] += fd[k * fl + i] * mu;
         }
-        const double* Gx = Gb + (size_t)x * 25;
+        const double* Gx = Gb + x;
         for (int k = 0; k < 5; ++k) {
             double s = 0.0;
-            for (int l = 0; l < 5; ++l) s += Gx[k * 5 + l] * dvx[l];
+            for (int l = 0; l < 5; ++l) s += Gx[(size_t)(k * 5 + l) * fpt] * dvx[l];
             pF[k * fpt + x] = s;
         }
     }
