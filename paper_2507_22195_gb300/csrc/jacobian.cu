@@ -67,18 +67,18 @@ __device__ void volume_point_jacobians(const JacobianArgs& a, int K, int e1, int
         Dual<5> U[5], FG[5][3];
         ok = vol_integrand(a.ph, dv, dvs, dq, U, FG) && ok;
         double W = sW[g1] * hw[0] * sW[g2] * hw[1] * sW[g3] * hw[2];
-        TS* Px = P + (size_t)x * 100;
+        TS* Px = P ? P + (size_t)x * 100 : nullptr;
         // stored point-fastest, [K][micro-element][100][npt]: coalesced over the points
         double* Gx = a.pj ? a.pj + ((size_t)K * tb.m * tb.m * tb.m + e1 + tb.m * (e2 + tb.m * e3)) * 100 * npt + x
                           : nullptr;
         for (int k = 0; k < 5; ++k)
             for (int l = 0; l < 5; ++l) {
                 const double u = W * U[k].d[l];
-                Px[k * 5 + l] = (TS)u;
+                if (Px) Px[k * 5 + l] = (TS)u;
                 if (Gx) Gx[(size_t)(k * 5 + l) * npt] = u;
                 for (int j = 0; j < 3; ++j) {
                     const double f = -W * FG[k][j].d[l];
-                    Px[25 * (1 + j) + k * 5 + l] = (TS)f;
+                    if (Px) Px[25 * (1 + j) + k * 5 + l] = (TS)f;
                     if (Gx) Gx[(size_t)(25 * (1 + j) + k * 5 + l) * npt] = f;
                 }
             }
@@ -105,8 +105,33 @@ __device__ __forceinline__ void load_tables(const Tab& tb, double* sL, double* s
 // all (a3, b3), and adds the p1^2 results into S.  Items are ordered k
 // fastest, then a1, so a warp's atomics fall on runs of 5 p1 consecutive rows
 // 5 A + k of one column.
-template <class TS, bool VISC>
-__global__ void __launch_bounds__(256)
+// Point pass alone (inviscid, with a.pj): the dual-number physics at the
+// Gauss points of one micro-element, written to a.pj.  Its 255 registers no
+// longer hold the contraction below to one CTA per SM.
+__global__ void __launch_bounds__(128)
+jac_points_kernel(JacobianArgs a) {
+    const Tab& tb = a.tab;
+    const int K = blockIdx.y, e = blockIdx.x;
+    const int m = tb.m, nl = tb.nl;
+    const int e1 = e % m, e2 = (e / m) % m, e3 = e / (m * m);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* sL = reinterpret_cast<double*>(smem_raw);
+    double* sD = sL + MEHDG_MAXG * (MEHDG_MAXP + 1);
+    double* sW = sD + MEHDG_MAXG * (MEHDG_MAXP + 1);
+    double* vl = sW + 8;
+    double* vsl = vl + 5 * nl;
+    double* ql = vsl + 5 * nl;
+    load_tables(tb, sL, sD, sW);
+    double sc[3], hw[3];
+    geometry(a, K, sc, hw);
+    __syncthreads();
+    volume_point_jacobians<float, false>(a, K, e1, e2, e3, sL, sW, hw, vl, vsl, ql, (float*)nullptr);
+}
+
+// PRE: the point blocks come from a.pj (written by jac_points_kernel) instead
+// of being computed here.
+template <class TS, bool VISC, bool PRE = false>
+__global__ void __launch_bounds__(256, PRE ? 2 : 1)
 jac_volume_sf_kernel(JacobianArgs a) {
     const Tab& tb = a.tab;
     const int K = blockIdx.y, e = blockIdx.x;
@@ -136,7 +161,16 @@ jac_volume_sf_kernel(JacobianArgs a) {
         double t = tau ? sD[g * p1 + aa] * sc[d] : sL[g * p1 + aa];
         Mt[i] = (TS)(t * sL[g * p1 + bb]);
     }
-    volume_point_jacobians<TS, VISC>(a, K, e1, e2, e3, sL, sW, hw, vl, vsl, ql, P);
+    if constexpr (PRE) {
+        const double* Gb = a.pj + ((size_t)K * m * m * m + e) * 100 * npt;    // [100][npt]
+        for (int i = tid; i < 100 * npt; i += nth) {
+            const int idx = i / npt, x = i % npt;
+            P[(size_t)x * 100 + idx] = (TS)Gb[i];
+        }
+        __syncthreads();
+    } else {
+        volume_point_jacobians<TS, VISC>(a, K, e1, e2, e3, sL, sW, hw, vl, vsl, ql, P);
+    }
     TS* S = reinterpret_cast<TS*>(a.S) + (size_t)K * a.ld * a.ld;
     const TS* M1 = Mt;                       // direction x: tau=0 at [0], tau=1 at [ng*PP]
     const TS* M2 = Mt + 2 * ng * PP;
@@ -634,7 +668,14 @@ cudaError_t launch_jacobian(const JacobianArgs& a, int64_t nK, bool fp64, cudaSt
               + ts * 25 * (size_t)fpt + 64;
     dim3 gv(t.m * t.m * t.m, (unsigned)nK), gf(6 * t.m * t.m, (unsigned)nK), b(256);
 #define LJ(TS, V)                                                                                        \
-    do { if (use_sf) {                                                                                   \
+    do { if (use_sf && !V && a.pj) {                                                                     \
+             const size_t sp = sizeof(double) * (HEAD_DOUBLES + 10 * (size_t)t.nl) + 16;                 \
+             cudaFuncSetAttribute(jac_points_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp); \
+             jac_points_kernel<<<gv, 128, sp, st>>>(a);                                                  \
+             cudaFuncSetAttribute(jac_volume_sf_kernel<TS, V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sv); \
+             jac_volume_sf_kernel<TS, V, true><<<gv, b, sv, st>>>(a);                                    \
+             MEHDG_COUNT(1);                                                                             \
+         } else if (use_sf) {                                                                            \
              cudaFuncSetAttribute(jac_volume_sf_kernel<TS, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sv); \
              jac_volume_sf_kernel<TS, V><<<gv, b, sv, st>>>(a);                                          \
          } else {                                                                                        \
