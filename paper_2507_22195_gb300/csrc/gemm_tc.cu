@@ -571,7 +571,14 @@ laswp_pack_kernel(float* __restrict__ Sall, int64_t ld, const int32_t* __restric
     if (n >= N) return;
     float* Sc = S + (size_t)(j0 + n) * ld;
     float* b = buf[warp];
-    for (int i = lane; i < nr; i += 32) b[i] = Sc[rows[i]];
+    // gather, four rows per lane and iteration so that their loads overlap
+    for (int i0 = lane; i0 < nr; i0 += 128) {
+        float v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) { const int i = i0 + 32 * u; v[u] = i < nr ? Sc[rows[i]] : 0.f; }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) { const int i = i0 + 32 * u; if (i < nr) b[i] = v[u]; }
+    }
     __syncwarp();
     float* out = Bp + ((size_t)K * N + n) * (size_t)(2 * LU_NB);
     for (int i = lane; i < nr; i += 32) {

@@ -294,15 +294,30 @@ panel_kernel(TS* __restrict__ Sall, int64_t ld, int c, int32_t* __restrict__ piv
         const int r0 = s_lrows[lane], r1 = s_lrows[lane + 32];
         const int q0 = s_lcont[lane], q1 = s_lcont[lane + 32];
         const bool w0 = lane < nr && q0 != lane, w1 = lane + 32 < nr && q1 != lane + 32;
-        for (int j = wid; j < LU_NB - LEAF; j += nth / 32) {
-            const int col = j < nleft ? c0 + j : c + j - nleft + LEAF;
-            TS* Sc = S + (size_t)col * ld + c;
-            const TS v0 = lane < nr ? Sc[r0] : (TS)0;
-            const TS v1 = lane + 32 < nr ? Sc[r1] : (TS)0;
-            const TS a0 = __shfl_sync(0xffffffffu, v0, q0 & 31), b0 = __shfl_sync(0xffffffffu, v1, q0 & 31);
-            const TS a1 = __shfl_sync(0xffffffffu, v0, q1 & 31), b1 = __shfl_sync(0xffffffffu, v1, q1 & 31);
-            if (w0) Sc[r0] = q0 < 32 ? a0 : b0;
-            if (w1) Sc[r1] = q1 < 32 ? a1 : b1;
+        // four columns per warp and iteration: their loads are in flight together
+        constexpr int CU = 4;
+        const int nw = nth / 32;
+        for (int j0 = wid * CU; j0 < LU_NB - LEAF; j0 += nw * CU) {
+            TS v0[CU], v1[CU];
+            TS* Sc[CU];
+#pragma unroll
+            for (int u = 0; u < CU; ++u) {
+                const int j = j0 + u;
+                const int col = j < nleft ? c0 + j : c + j - nleft + LEAF;
+                Sc[u] = S + (size_t)col * ld + c;
+                const bool in = j < LU_NB - LEAF;
+                v0[u] = in && lane < nr ? Sc[u][r0] : (TS)0;
+                v1[u] = in && lane + 32 < nr ? Sc[u][r1] : (TS)0;
+            }
+#pragma unroll
+            for (int u = 0; u < CU; ++u) {
+                const TS a0 = __shfl_sync(0xffffffffu, v0[u], q0 & 31), b0 = __shfl_sync(0xffffffffu, v1[u], q0 & 31);
+                const TS a1 = __shfl_sync(0xffffffffu, v0[u], q1 & 31), b1 = __shfl_sync(0xffffffffu, v1[u], q1 & 31);
+                if (j0 + u < LU_NB - LEAF) {
+                    if (w0) Sc[u][r0] = q0 < 32 ? a0 : b0;
+                    if (w1) Sc[u][r1] = q1 < 32 ? a1 : b1;
+                }
+            }
         }
     }
     if (singular && tid == 0 && status) status[K] = MEHDG_ESINGULAR;
