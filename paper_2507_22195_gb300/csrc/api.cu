@@ -43,7 +43,7 @@ void free_mesh(mehdg_ctx* c) {
     dfree(c->d_res); dfree(c->d_dx); dfree(c->d_nrm); dfree(c->d_status); dfree(c->d_iters); dfree(c->d_conv);
     dfree(c->d_cnt); dfree(c->d_S); dfree(c->d_piv); dfree(c->d_work);
     dfree(c->d_RQ); dfree(c->d_z); dfree(c->d_dq); dfree(c->d_qt1); dfree(c->d_qt2); dfree(c->d_Minv); dfree(c->d_C1);
-    dfree(c->d_pj); dfree(c->d_pjf); c->pj_ready = false;
+    dfree(c->d_pj); dfree(c->d_pjf); dfree(c->d_pq); c->pj_ready = false;
     if (c->d_krylov) { cudaFree(c->d_krylov); c->d_krylov = nullptr; c->krylov_bytes = 0; }
     if (c->lu_graph) { cudaGraphExecDestroy(c->lu_graph); c->lu_graph = nullptr; }
     if (c->lu_ev_in) { cudaEventDestroy(c->lu_ev_in); c->lu_ev_in = nullptr; }
@@ -281,6 +281,7 @@ int mehdg_set_mesh(mehdg_ctx* c, int64_t nK, const int32_t* p, const int32_t* m,
     }
     if (!vis) DALLOC(c->d_pj, sizeof(double) * 100 * (size_t)nK * t.m * t.m * t.m * t.npt);
     if (!vis) DALLOC(c->d_pjf, sizeof(double) * 25 * (size_t)nK * 6 * t.m * t.m * t.ng * t.ng);
+    if (vis) DALLOC(c->d_pq, sizeof(double) * 225 * (size_t)nK * t.m * t.m * t.m * t.npt);
     DALLOC(c->d_S, Sbytes);
     DALLOC(c->d_piv, sizeof(int32_t) * nK * c->Npad);
     c->work_bytes = lu_work_bytes(nK, c->Npad, fp64, c->prm.prec);
@@ -370,7 +371,7 @@ int mehdg_condense(mehdg_ctx* c, double* bhat, double* Ahat_local, void* stream)
     JacobianArgs ja;
     ja.tab = c->tab; ja.ph = c->ph; ja.box = c->d_box; ja.v = c->v; ja.vs = c->vs; ja.vh = c->vh; ja.q = c->q;
     ja.gid = c->d_gid; ja.S = c->d_S; ja.ld = ld; ja.status = c->d_status; ja.C1 = c->d_C1;
-    ja.pj = c->d_pj; ja.pjf = c->d_pjf;
+    ja.pj = c->d_pj; ja.pjf = c->d_pjf; ja.pq = c->d_pq;
     TRY(launch_jacobian(ja, nK, fp64, st));
     c->pj_ready = c->d_pj != nullptr;
     prof_end(&c->prof, ev, st, 0.0);

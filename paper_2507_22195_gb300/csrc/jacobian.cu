@@ -376,8 +376,56 @@ jac_face_kernel(JacobianArgs a) {
 // then a1, so a warp's atomics fall on runs of consecutive rows 5 A + k.
 // The five test components k are processed kg at a time (kg = 5 unless the
 // stage-1 buffer would not fit in shared memory).
-template <class TS>
-__global__ void __launch_bounds__(256)
+// Point pass of the Q-elimination term: dG/dq at every Gauss point of one
+// micro-element from one 15-direction dual evaluation (G is linear in q),
+// stored weighted and point-fastest: a.pq[K][e][d*75 + j*25 + k*5 + l][npt] =
+// W dG_kj/dq_ld.
+__global__ void __launch_bounds__(128)
+jac_visc_q_points_kernel(JacobianArgs a) {
+    const Tab& tb = a.tab;
+    const int K = blockIdx.y, e = blockIdx.x;
+    const int p = tb.p, m = tb.m, n = tb.n, ng = tb.ng, Nn = tb.Nn, nl = tb.nl, npt = tb.npt, p1 = p + 1;
+    const int eo[3] = {(e % m) * p, ((e / m) % m) * p, (e / (m * m)) * p};
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* sL = reinterpret_cast<double*>(smem_raw);
+    double* sD = sL + MEHDG_MAXG * (MEHDG_MAXP + 1);
+    double* sW = sD + MEHDG_MAXG * (MEHDG_MAXP + 1);
+    double* vl = sW + 8;                                     // [5][nl]
+    const int tid = threadIdx.x, nth = blockDim.x;
+    load_tables(tb, sL, sD, sW);
+    double sc[3], hw[3];
+    geometry(a, K, sc, hw);
+    const int64_t oV = (int64_t)K * 5 * Nn;
+    for (int i = tid; i < nl; i += nth) {
+        int A = (eo[0] + i % p1) + n * ((eo[1] + (i / p1) % p1) + n * (eo[2] + i / (p1 * p1)));
+        for (int k = 0; k < 5; ++k) vl[k * nl + i] = a.v[oV + k * Nn + A];
+    }
+    __syncthreads();
+    double* Gb = a.pq + ((size_t)K * m * m * m + e) * 225 * npt;
+    for (int x = tid; x < npt; x += nth) {
+        const int g1 = x % ng, g2 = (x / ng) % ng, g3 = x / (ng * ng);
+        Dual<15> v15[5], q15[15], G[5][3];
+        for (int k = 0; k < 5; ++k) {
+            double s5 = 0.0;
+            for (int i = 0; i < nl; ++i)
+                s5 += sL[g1 * p1 + i % p1] * sL[g2 * p1 + (i / p1) % p1] * sL[g3 * p1 + i / (p1 * p1)] * vl[k * nl + i];
+            v15[k] = mkdual<15>(s5);
+        }
+        for (int c = 0; c < 15; ++c) { q15[c] = mkdual<15>(0.0); q15[c].d[c] = 1.0; }
+        visc_flux(v15, q15, a.ph, G);
+        const double W = sW[g1] * hw[0] * sW[g2] * hw[1] * sW[g3] * hw[2];
+        for (int d = 0; d < 3; ++d)
+            for (int j = 0; j < 3; ++j)
+                for (int k = 0; k < 5; ++k)
+                    for (int l = 0; l < 5; ++l)
+                        Gb[(size_t)(d * 75 + j * 25 + k * 5 + l) * npt + x] = W * G[k][j].d[l * 3 + d];
+    }
+}
+
+// PRE: the point blocks come from a.pq (jac_visc_q_points_kernel) instead of
+// three dual evaluations per point here
+template <class TS, bool PRE = false>
+__global__ void __launch_bounds__(256, PRE ? 2 : 1)
 jac_visc_q_volume_kernel(JacobianArgs a, const double* __restrict__ C1, int kg) {
     const Tab& tb = a.tab;
     const int K = blockIdx.y, e = blockIdx.x;
@@ -400,19 +448,21 @@ jac_visc_q_volume_kernel(JacobianArgs a, const double* __restrict__ C1, int kg) 
     geometry(a, K, sc, hw);
     for (int i = tid; i < n * n; i += nth) C1s[i] = C1[i];
     const int64_t oV = (int64_t)K * 5 * Nn;
-    for (int i = tid; i < nl; i += nth) {
-        int A = (eo[0] + i % p1) + n * ((eo[1] + (i / p1) % p1) + n * (eo[2] + i / (p1 * p1)));
-        for (int k = 0; k < 5; ++k) vl[k * nl + i] = a.v[oV + k * Nn + A];
-    }
-    __syncthreads();
-    for (int x = tid; x < npt; x += nth) {
-        int g1 = x % ng, g2 = (x / ng) % ng, g3 = x / (ng * ng);
-        double s5[5] = {0, 0, 0, 0, 0};
-        for (int i = 0; i < nl; ++i) {
-            double f = sL[g1 * p1 + i % p1] * sL[g2 * p1 + (i / p1) % p1] * sL[g3 * p1 + i / (p1 * p1)];
-            for (int k = 0; k < 5; ++k) s5[k] += f * vl[k * nl + i];
+    if constexpr (!PRE) {
+        for (int i = tid; i < nl; i += nth) {
+            int A = (eo[0] + i % p1) + n * ((eo[1] + (i / p1) % p1) + n * (eo[2] + i / (p1 * p1)));
+            for (int k = 0; k < 5; ++k) vl[k * nl + i] = a.v[oV + k * Nn + A];
         }
-        for (int k = 0; k < 5; ++k) vx[x * 5 + k] = s5[k];
+        __syncthreads();
+        for (int x = tid; x < npt; x += nth) {
+            int g1 = x % ng, g2 = (x / ng) % ng, g3 = x / (ng * ng);
+            double s5[5] = {0, 0, 0, 0, 0};
+            for (int i = 0; i < nl; ++i) {
+                double f = sL[g1 * p1 + i % p1] * sL[g2 * p1 + (i / p1) % p1] * sL[g3 * p1 + i / (p1 * p1)];
+                for (int k = 0; k < 5; ++k) s5[k] += f * vl[k * nl + i];
+            }
+            for (int k = 0; k < 5; ++k) vx[x * 5 + k] = s5[k];
+        }
     }
     __syncthreads();
     TS* S = reinterpret_cast<TS*>(a.S) + (size_t)K * a.ld * a.ld;
@@ -441,6 +491,10 @@ jac_visc_q_volume_kernel(JacobianArgs a, const double* __restrict__ C1, int kg) 
             T[i] = val;
         }
         // point blocks P[x][j][k*5+l] = W dG_kj/dq_ld (G is linear in q)
+        if constexpr (PRE) {
+            const double* Gb = a.pq + ((size_t)K * m * m * m + e) * 225 * npt + (size_t)d * 75 * npt;
+            for (int i = tid; i < 75 * npt; i += nth) P[(size_t)(i % npt) * 75 + i / npt] = (TS)Gb[i];
+        } else
         for (int x = tid; x < npt; x += nth) {
             int g1 = x % ng, g2 = (x / ng) % ng, g3 = x / (ng * ng);
             Dual<15> v15[5], q15[15], G[5][3];
@@ -692,16 +746,30 @@ cudaError_t launch_jacobian(const JacobianArgs& a, int64_t nK, bool fp64, cudaSt
         const size_t G2 = (size_t)t.ng * t.ng, TW = (size_t)(t.p + 1) * t.n;
         const size_t base = sizeof(double) * (HEAD_DOUBLES + (size_t)t.n * t.n + 5 * (size_t)t.nl + 5 * (size_t)t.npt)
                           + ts * (6 * (size_t)t.ng * TW + 75 * (size_t)t.npt) + 16;
+        // with the point pass separate (a.pq) the contraction runs two CTAs per SM
+        // if its shared memory fits in half an SM's; otherwise one, with the
+        // largest k group that fits
+        const size_t per_k = ts * 3 * TW * G2;
+        const bool pre = a.pq && base + per_k <= 110 * 1024;
+        const size_t limit = pre ? 110 * 1024 : 220 * 1024;
         int kg = 5;
-        while (kg > 1 && base + ts * (size_t)kg * 3 * TW * G2 > 220 * 1024) --kg;
-        const size_t sq = base + ts * (size_t)kg * 3 * TW * G2;
+        while (kg > 1 && base + (size_t)kg * per_k > limit) --kg;
+        const size_t sq = base + (size_t)kg * per_k;
         size_t sqf = sizeof(double) * (MEHDG_MAXG * (MEHDG_MAXP + 1) + 8 + (size_t)t.n * t.n + 5 * (size_t)fl)
                    + ts * (75 * (size_t)fpt + 2 * (size_t)t.ng * TW + 5 * TW * t.ng + t.n) + 16;
         if (sq > 227 * 1024) return cudaErrorInvalidValue;      // FP64 at p = 4: not supported
 #define LQ(TS)                                                                                          \
-        do { cudaFuncSetAttribute(jac_visc_q_volume_kernel<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sq); \
+        do { if (pre) {                                                                                 \
+                 const size_t sp = sizeof(double) * (HEAD_DOUBLES + 5 * (size_t)t.nl) + 16;             \
+                 jac_visc_q_points_kernel<<<gv, 128, sp, st>>>(a);                                      \
+                 cudaFuncSetAttribute(jac_visc_q_volume_kernel<TS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sq); \
+                 jac_visc_q_volume_kernel<TS, true><<<gv, b, sq, st>>>(a, a.C1, kg);                    \
+                 MEHDG_COUNT(1);                                                                        \
+             } else {                                                                                   \
+                 cudaFuncSetAttribute(jac_visc_q_volume_kernel<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sq); \
+                 jac_visc_q_volume_kernel<TS><<<gv, b, sq, st>>>(a, a.C1, kg);                          \
+             }                                                                                          \
              cudaFuncSetAttribute(jac_visc_q_face_kernel<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sqf); \
-             jac_visc_q_volume_kernel<TS><<<gv, b, sq, st>>>(a, a.C1, kg);                             \
              jac_visc_q_face_kernel<TS><<<gf, b, sqf, st>>>(a, a.C1); } while (0)
         if (fp64) LQ(double); else LQ(float);
 #undef LQ

@@ -48,6 +48,7 @@ struct JacobianArgs {
     const double* C1;         // [n][n] M1_ref^-1 G1_ref (viscous only)
     double* pj;               // if set: the weighted FP64 point Jacobians [nK][m^3][100][npt] (inviscid)
     double* pjf;              // if set: the weighted FP64 face blocks dFhat/dv [nK][6 m^2][25][fpt] (inviscid)
+    double* pq;               // if set: scratch for the viscous point blocks dG/dq [nK][m^3][225][npt]
 };
 cudaError_t launch_jacobian(const JacobianArgs& a, int64_t nK, bool fp64, cudaStream_t st);
 cudaError_t launch_pad_identity(void* S, int64_t nK, int64_t ld, int Nv, bool fp64, cudaStream_t st);
