@@ -179,8 +179,16 @@ panel_kernel(TS* __restrict__ Sall, int64_t ld, int c, int32_t* __restrict__ piv
             if (tid < IB) { s_prow[cc & 1][tid] = X[tid * R0 + pr]; s_crow[cc & 1][tid] = X[tid * R0 + cc]; }
             if (tid == 0) s_piv[cc] = pr;
             __syncthreads();
-            const TS* prow = s_prow[cc & 1];
-            const TS* crow = s_crow[cc & 1];
+            // narrow sub-panels: the pivot row and the old row cc in registers (the
+            // row loop stores to X, which the compiler cannot tell apart from s_prow)
+            constexpr int HR = IB <= 8 ? IB : 1;
+            TS prow_r[HR], crow_r[HR];
+            if constexpr (IB <= 8) {
+#pragma unroll
+                for (int q = 0; q < IB; ++q) { prow_r[q] = s_prow[cc & 1][q]; crow_r[q] = s_crow[cc & 1][q]; }
+            }
+            const TS* prow = IB <= 8 ? prow_r : s_prow[cc & 1];
+            const TS* crow = IB <= 8 ? crow_r : s_crow[cc & 1];
             const TS pivv = prow[cc];
             const TS inv = pivv != (TS)0 ? (TS)1 / pivv : (TS)0;
             best = (TS)-1; bi = 0x7fffffff;

@@ -114,6 +114,31 @@ def test_condense_apply_recover_match_oracle(name, prec):
     ctx.close()
 
 
+@pytest.mark.parametrize("viscous", [False, True])
+@pytest.mark.parametrize("prec", [0, 4])
+def test_condense_64_elements_matches_oracle(viscous, prec):
+    """a 4^3 mesh: every kernel's grid spans 64 elements (more CTAs than the
+    small parity cases, grid rows past the first wave of SMs)"""
+    mesh = I.periodic_mesh(4, 2, 1)
+    st = I.make_state(mesh, "tgv", 1e-2, 5, 6, viscous=viscous, M0=0.3)
+    kw = dict(Mach=0.3, Re=100.0, viscous=1) if viscous else dict(Mach=0.3)
+    ctx = M().Context(mesh, flux=1, prec=prec, **kw)
+    ctx.set_state(*to_dev(st))
+    bh = ctx.condense()
+    dvh_np = I.random_direction(st.vhat.shape, 79, 1e-3)
+    dV = ctx.recover(torch.tensor(dvh_np, device="cuda:0"))
+    torch.cuda.synchronize()
+    stat, iters = ctx.status()
+    assert (stat == 0).all(), (stat, iters)
+    prm = oracle.params(flux=1, **kw)
+    bh_o, _ = oracle.condense_mesh(prm, mesh, st)
+    dV_o, _ = oracle.recover_mesh(prm, mesh, st, dvh_np)
+    tol = 1e-10 if prec == 0 else 1e-8
+    e = (rel(bh, bh_o), rel(dV, dV_o))
+    assert max(e) < tol, (e, iters)
+    ctx.close()
+
+
 @pytest.mark.parametrize("ctas", [1, 2, 4, 8])
 def test_solve_cluster_sizes_match_oracle(ctas, monkeypatch):
     """the solve with 1, 2, 4 and 8 CTAs per element (normally chosen from the
