@@ -757,6 +757,55 @@ cudaError_t launch_gemm_simt(const LUPlan& P, int r0, int c0, int k0, int M, int
     return cudaGetLastError();
 }
 
+// The 32-wide inner update of the mixed-precision LU in exact FP32 on the
+// SIMT pipe: C[r0+i, c0+j] -= sum_k L[r0+i, k0+k] U[k0+k, c0+j], j, k < 32.
+// One thread per row, its 32 L and 32 C values loaded together (64 loads in
+// flight), U staged in shared memory and read as broadcast float4; 32
+// independent accumulators.  (The tensor-core path would pack both operands
+// for a K = 32 product first.)
+__global__ void __launch_bounds__(128)
+update32_kernel(float* __restrict__ Sall, int64_t ld, int r0, int c0, int k0, int M) {
+    const int K = blockIdx.y;
+    float* S = Sall + (size_t)K * ld * ld;
+    __shared__ __align__(16) float U[32][32];
+    for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) {
+        const int k = i & 31, j = i >> 5;
+        U[k][j] = S[(size_t)(k0 + k) + (size_t)(c0 + j) * ld];
+    }
+    __syncthreads();
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= M) return;
+    const float* pl = S + (size_t)(r0 + r) + (size_t)k0 * ld;
+    const float* pc = S + (size_t)(r0 + r) + (size_t)c0 * ld;
+    float l[32], acc[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) { l[k] = pl[0]; pl += ld; }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) { acc[j] = pc[0]; pc += ld; }
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+#pragma unroll
+        for (int j = 0; j < 32; j += 4) {
+            const float4 u = *reinterpret_cast<const float4*>(&U[k][j]);
+            acc[j] = fmaf(-l[k], u.x, acc[j]);
+            acc[j + 1] = fmaf(-l[k], u.y, acc[j + 1]);
+            acc[j + 2] = fmaf(-l[k], u.z, acc[j + 2]);
+            acc[j + 3] = fmaf(-l[k], u.w, acc[j + 3]);
+        }
+    }
+    float* q = S + (size_t)(r0 + r) + (size_t)c0 * ld;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) { q[0] = acc[j]; q += ld; }
+}
+
+cudaError_t launch_update32(const LUPlan& P, int r0, int c0, int k0, int M, cudaStream_t st) {
+    if (M <= 0) return cudaSuccess;
+    dim3 g((unsigned)((M + 127) / 128), (unsigned)P.nK);
+    update32_kernel<<<g, 128, 0, st>>>((float*)P.S, P.ld, r0, c0, k0, M);
+    MEHDG_COUNT(1);
+    return cudaGetLastError();
+}
+
 template <class TS>
 cudaError_t trailing_update(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st,
                             int ph_pack = -1, int ph_gemm = -1, double flops = 0.0, const void* b_packed = nullptr) {
@@ -766,6 +815,7 @@ cudaError_t trailing_update(const LUPlan& P, int r0, int c0, int k0, int M, int 
         if (ev >= 0) prof_end(P.prof, ev, st, flops);
         return e;
     } else {
+        if (N == 32 && Kd == 32 && !b_packed) return launch_update32(P, r0, c0, k0, M, st);
         return gemm_tc_update(P, r0, c0, k0, M, N, Kd, st, ph_pack, ph_gemm, flops, b_packed);
     }
 }
