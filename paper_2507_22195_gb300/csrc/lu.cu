@@ -411,6 +411,7 @@ trsm_kernel(TS* __restrict__ Sall, int64_t ld, int c0, int t, int j0, int j1) {
     TS* S = Sall + (size_t)K * ld * ld;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TS* X = reinterpret_cast<TS*>(smem_raw);        // [t][32]
+    TS* Lo = X + (size_t)t * 32;                     // [t - 32][33]: L below the diagonal block
     __shared__ TS Lb[32][33];
     const int tc = threadIdx.x & 31, tr = threadIdx.x >> 5;
     const int col = j0 + blockIdx.x * 32 + tc;
@@ -419,19 +420,32 @@ trsm_kernel(TS* __restrict__ Sall, int64_t ld, int c0, int t, int j0, int j1) {
     __syncthreads();
     for (int rb = 0; rb < t; rb += 32) {
         for (int i = tr; i < 32; i += 8) Lb[i][tc] = S[(size_t)(c0 + rb + i) + (size_t)(c0 + rb + tc) * ld];
+        // the L rows below the block, staged with coalesced loads (lane = row)
+        for (int i0 = rb + 32; i0 < t; i0 += 32)
+            for (int q = tr; q < 32; q += 8)
+                if (i0 + tc < t) Lo[(i0 + tc - 32) * 33 + q] = S[(size_t)(c0 + i0 + tc) + (size_t)(c0 + rb + q) * ld];
         __syncthreads();
         if (tr == 0) {
-            for (int i = 1; i < 32; ++i) {
-                TS s = X[(rb + i) * 32 + tc];
-                for (int q = 0; q < i; ++q) s -= Lb[i][q] * X[(rb + q) * 32 + tc];
-                X[(rb + i) * 32 + tc] = s;
-            }
+            // the 32 x 32 unit-lower block, one column per lane, in registers:
+            // once x[q] is final every later row takes its term (the same
+            // subtraction order per entry as the row-by-row form, but 31 - q
+            // independent updates per step instead of one dependent chain)
+            TS x[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) x[i] = X[(rb + i) * 32 + tc];
+#pragma unroll
+            for (int q = 0; q < 31; ++q)
+#pragma unroll
+                for (int i = q + 1; i < 32; ++i) x[i] -= Lb[i][q] * x[q];
+#pragma unroll
+            for (int i = 1; i < 32; ++i) X[(rb + i) * 32 + tc] = x[i];
         }
         __syncthreads();
         for (int i = rb + 32 + tr; i < t; i += 8) {
             TS s = X[i * 32 + tc];
-            const TS* Lr = S + (size_t)(c0 + i) + (size_t)(c0 + rb) * ld;
-            for (int q = 0; q < 32; ++q) s -= Lr[(size_t)q * ld] * X[(rb + q) * 32 + tc];
+            const TS* Lr = Lo + (i - 32) * 33;
+#pragma unroll 8
+            for (int q = 0; q < 32; ++q) s -= Lr[q] * X[(rb + q) * 32 + tc];
             X[i * 32 + tc] = s;
         }
         __syncthreads();
@@ -740,7 +754,7 @@ cudaError_t launch_laswp_perm(const LUPlan& P, const int32_t* perm, int w, int j
 template <class TS>
 cudaError_t launch_trsm(const LUPlan& P, int c0, int t, int j0, int j1, cudaStream_t st) {
     if (j1 <= j0) return cudaSuccess;
-    size_t sm = (size_t)t * 32 * sizeof(TS);
+    size_t sm = ((size_t)t * 32 + (size_t)(t > 32 ? t - 32 : 0) * 33) * sizeof(TS);
     cudaFuncSetAttribute(trsm_kernel<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     dim3 g((unsigned)((j1 - j0 + 31) / 32), (unsigned)P.nK);
     trsm_kernel<TS><<<g, 256, sm, st>>>((TS*)P.S, P.ld, c0, t, j0, j1);
