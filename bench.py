@@ -180,6 +180,24 @@ def reference_main(a):
     return 0
 
 
+# ---------------------------------------------------------------- ranks
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """The largest x over all ranks (x itself without a process group): each
+    rank times its own replica, and the job's time is the slowest rank's."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, n_elem: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput: every rank condenses its own n_elem elements per
+    step (weak scaling), in `seconds` of the slowest rank."""
+    return world * n_elem * steps / seconds
+
+
 # ---------------------------------------------------------------- GPU arm
 def _to_dev(st, dev):
     import torch
@@ -309,11 +327,8 @@ def main():
     M.mehdg_profile_enable(ctx.ctx, False)
     clocks = clk.stop()
     stat, iters = ctx.status()
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * mesh.nK * a.steps / (ms / 1e3)
+    ms = max_over_ranks(ms, dist, dev)
+    value = job_rate(world, mesh.nK, a.steps, ms / 1e3)
 
     # end to end through the public API: pinned host inputs -> device,
     # condense, b-hat -> host, every step
@@ -331,10 +346,7 @@ def main():
         torch.cuda.current_stream().synchronize()
     barrier()
     e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dist, dev)
     h2d = sum(h.numel() * 8 for h in host)
     d2h = hb.numel() * 8
     # recovery (eq. R2, R6) timed on its own, after the condensation above, for a
@@ -348,8 +360,9 @@ def main():
         ctx.recover(dvh)
     r1.record(stream)
     barrier()
-    rec = {"value": world * mesh.nK * a.steps / (r0.elapsed_time(r1) / 1e3), "unit": "macro-elements/s",
-           "ms_per_step": r0.elapsed_time(r1) / a.steps,
+    rec_ms = max_over_ranks(r0.elapsed_time(r1), dist, dev)
+    rec = {"value": job_rate(world, mesh.nK, a.steps, rec_ms / 1e3), "unit": "macro-elements/s",
+           "ms_per_step": rec_ms / a.steps,
            "what": "recover: dV = S^-1(-R_V - A_v,vhat dVhat) with FP64 refinement (and dQ when viscous), "
                    "seeded dVhat"}
     ctx.set_state(v, vh, q, vs)
@@ -417,7 +430,7 @@ def main():
                            mesh.nK * ld * ld * (8 if a.prec == "fp64" else 4) / 1e9)},
             "roofline": roof,
             "cpu_baseline": cpu,
-            "e2e": {"value": world * mesh.nK * a.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": {"value": job_rate(world, mesh.nK, a.steps, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "clocks": clocks,
