@@ -136,6 +136,7 @@ int tangent(mehdg_ctx* c, const double* dv, const double* dvh, const double* dq,
     a.dv = dv; a.dvh = dvh; a.dq = viscous(c) ? dq : nullptr; a.tRV = tRV; a.tRH = tRH; a.skip = skip;
     a.pj = c->pj_ready ? c->d_pj : nullptr;      // linear volume pass from the stored point Jacobians
     a.pjf = c->pj_ready ? c->d_pjf : nullptr;    // linear face pass when the trace direction is 0
+    a.pq = c->pj_ready ? c->d_pq : nullptr;      // viscous: dG/dq blocks for the linear volume pass
     int ev = prof_begin(&c->prof, PH_TANGENT, st);
     TRY(launch_residual(a, c->nK, viscous(c), true, st));
     prof_end(&c->prof, ev, st, 0.0);
@@ -279,7 +280,7 @@ int mehdg_set_mesh(mehdg_ctx* c, int64_t nK, const int32_t* p, const int32_t* m,
         DALLOC(c->d_Minv, sizeof(double) * t.n * t.n);
         DALLOC(c->d_C1, sizeof(double) * t.n * t.n);
     }
-    if (!vis) DALLOC(c->d_pj, sizeof(double) * 100 * (size_t)nK * t.m * t.m * t.m * t.npt);
+    DALLOC(c->d_pj, sizeof(double) * 100 * (size_t)nK * t.m * t.m * t.m * t.npt);
     if (!vis) DALLOC(c->d_pjf, sizeof(double) * 25 * (size_t)nK * 6 * t.m * t.m * t.ng * t.ng);
     if (vis) DALLOC(c->d_pq, sizeof(double) * 225 * (size_t)nK * t.m * t.m * t.m * t.npt);
     DALLOC(c->d_S, Sbytes);

@@ -503,9 +503,14 @@ jac_visc_q_volume_kernel(JacobianArgs a, const double* __restrict__ C1, int kg) 
             visc_flux(v15, q15, a.ph, G);
             double W = sW[g1] * hw[0] * sW[g2] * hw[1] * sW[g3] * hw[2];
             TS* Px = P + (size_t)x * 75;
+            double* Gq = a.pq ? a.pq + ((size_t)K * m * m * m + e) * 225 * npt + (size_t)d * 75 * npt + x : nullptr;
             for (int j = 0; j < 3; ++j)
                 for (int k = 0; k < 5; ++k)
-                    for (int l = 0; l < 5; ++l) Px[25 * j + k * 5 + l] = (TS)(W * G[k][j].d[l * 3 + d]);
+                    for (int l = 0; l < 5; ++l) {
+                        const double gv = W * G[k][j].d[l * 3 + d];
+                        Px[25 * j + k * 5 + l] = (TS)gv;
+                        if (Gq) Gq[(size_t)(25 * j + k * 5 + l) * npt] = gv;   // also kept for the tangents
+                    }
         }
         __syncthreads();
         const TS* T1 = T + (0 * 2) * ng * TW;         // direction x (tau at + ng * TW)

@@ -15,6 +15,8 @@ struct ResidualArgs {
     const int32_t* skip;                  // [nK] nonzero = skip element (may be null)
     const double* pj;                     // stored point Jacobians: tangent volume pass is linear (may be null)
     const double* pjf;                    // stored face point Jacobians dFhat/dv: face pass linear when dvh = 0
+    const double* pq;                     // stored viscous blocks W dG/dq [nK][m^3][225][npt] (with pj: the
+                                          // viscous volume tangent is linear in dv and dq)
 };
 
 cudaError_t launch_residual(const ResidualArgs& a, int64_t nK, bool visc, bool tangent, cudaStream_t st);

@@ -156,10 +156,13 @@ residual_volume_kernel(ResidualArgs a) {
 // (H after the g1 contraction, J after g2).  Two shared regions alternate:
 //   A: nodal state -> T2 -> H        B: T1 -> point values / integrands -> J
 //
-// LIN = true: the tangent dR_V[dv] of the inviscid volume pass from the stored
-// weighted point Jacobians a.pj (written by the Jacobian kernel at the same
-// state): only dv is interpolated, the point step is a 20 x 5 product per
-// Gauss point instead of the dual-number physics, and the result goes to tRV.
+// LIN = true: the tangent dR_V[dv] of the volume pass from the stored weighted
+// point Jacobians a.pj (written by the Jacobian kernels at the same state):
+// only dv is interpolated, the point step is a 20 x 5 product per Gauss point
+// instead of the dual-number physics, and the result goes to tRV.  On the
+// viscous path (a.pq and a.dq set) dq is interpolated as well and the stored
+// W dG/dq blocks add their 15 x 15 product per point: G is linear in q and its
+// v-derivative at fixed q is part of the stored flux blocks.
 template <class T, bool VISC, bool LIN>
 __global__ void __launch_bounds__(128)
 residual_volume_sf_kernel(ResidualArgs a, int nA) {
@@ -172,7 +175,8 @@ residual_volume_sf_kernel(ResidualArgs a, int nA) {
     const int e1 = e % m, e2 = (e / m) % m, e3 = e / (m * m);
     const Phys& ph = a.ph;
     const bool tt = !LIN && ph.time_term;
-    const int NIN = 5 + (tt ? 5 : 0) + (VISC ? 15 : 0);     // v, v* (time term), q
+    const bool lq = LIN && a.pq && a.dq;                     // linear pass with the q-direction
+    const int NIN = 5 + (tt ? 5 : 0) + (VISC || lq ? 15 : 0);     // v, v* (time term), q
     const int cq = tt ? 10 : 5;
     constexpr int NHK = VISC ? 7 : 3, NJK = VISC ? 6 : 2;   // partial sums per component k
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -193,12 +197,14 @@ residual_volume_sf_kernel(ResidualArgs a, int nA) {
         int l1 = i % p1, l2 = (i / p1) % p1, l3 = i / (p1 * p1);
         int A = (e1 * p + l1) + n * ((e2 * p + l2) + n * (e3 * p + l3));
         for (int k = 0; k < 5; ++k) {
-            if constexpr (LIN) RA[k * nl + i] = a.dv[oV + k * Nn + A];
+            if constexpr (LIN) RA[k * nl + i] = a.dv ? a.dv[oV + k * Nn + A] : 0.0;
             else RA[k * nl + i] = load_t<T>(a.v, a.dv, oV + k * Nn + A);
             if (tt) RA[(5 + k) * nl + i] = load_t<T>(a.vs, nullptr, oV + k * Nn + A);
         }
         if (VISC)
             for (int c = 0; c < 15; ++c) RA[(cq + c) * nl + i] = load_t<T>(a.q, a.dq, oQ + c * Nn + A);
+        if constexpr (LIN)
+            if (lq) for (int c = 0; c < 15; ++c) RA[(cq + c) * nl + i] = a.dq[oQ + c * Nn + A];
     }
     __syncthreads();
     // interpolation, g1: B[c][g1 + ng (l2 + p1 l3)]
@@ -243,22 +249,31 @@ residual_volume_sf_kernel(ResidualArgs a, int nA) {
     if constexpr (LIN) {
         // rows 0-4: W dU/dv dv; rows 5-19: W dFG/dv dv (the stored blocks carry -W)
         const double* Gb = a.pj + ((size_t)K * m * m * m + e) * 100 * npt;   // [100][npt]
+        // viscous: W dG_kj/dq_(l,d) at [d*75 + j*25 + k*5 + l][npt], q component l*3 + d
+        const double* Qb = lq ? a.pq + ((size_t)K * m * m * m + e) * 225 * npt : nullptr;
         for (int x = tid; x < npt; x += nth) {
-            double dvx[5];
+            double dvx[5], dqx[15];
             for (int l = 0; l < 5; ++l) dvx[l] = RB[l * npt + x];
+            if (lq) for (int c = 0; c < 15; ++c) dqx[c] = RB[(cq + c) * npt + x];
             const double* Gx = Gb + x;
             for (int k = 0; k < 5; ++k) {
-                double u = 0.0, f0 = 0.0, f1 = 0.0, f2 = 0.0;
+                double u = 0.0, f[3] = {0.0, 0.0, 0.0};
                 for (int l = 0; l < 5; ++l) {
                     u += Gx[(size_t)(k * 5 + l) * npt] * dvx[l];
-                    f0 += Gx[(size_t)(25 + k * 5 + l) * npt] * dvx[l];
-                    f1 += Gx[(size_t)(50 + k * 5 + l) * npt] * dvx[l];
-                    f2 += Gx[(size_t)(75 + k * 5 + l) * npt] * dvx[l];
+                    f[0] += Gx[(size_t)(25 + k * 5 + l) * npt] * dvx[l];
+                    f[1] += Gx[(size_t)(50 + k * 5 + l) * npt] * dvx[l];
+                    f[2] += Gx[(size_t)(75 + k * 5 + l) * npt] * dvx[l];
                 }
                 RB[k * npt + x] = u;
-                RB[(5 + k * 3 + 0) * npt + x] = -f0;
-                RB[(5 + k * 3 + 1) * npt + x] = -f1;
-                RB[(5 + k * 3 + 2) * npt + x] = -f2;
+                for (int j = 0; j < 3; ++j) {
+                    double g = 0.0;
+                    if (lq) {
+                        const double* Qx = Qb + (size_t)(j * 25 + k * 5) * npt + x;
+                        for (int d = 0; d < 3; ++d)
+                            for (int l = 0; l < 5; ++l) g += Qx[(size_t)(d * 75 + l) * npt] * dqx[l * 3 + d];
+                    }
+                    RB[(5 + k * 3 + j) * npt + x] = g - f[j];
+                }
             }
         }
     } else
@@ -590,15 +605,19 @@ cudaError_t launch_residual(const ResidualArgs& a, int64_t nK, bool visc, bool t
          }                                                                                               \
          cudaFuncSetAttribute(residual_face_kernel<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf);   \
          residual_face_kernel<T, V><<<gf, b, sf, st>>>(a); } while (0)
-    if (tangent && !visc && a.pj && sf_vol) {
-        // linear volume pass from the stored point Jacobians (none when dv = 0:
-        // the volume integrand does not depend on the traces), then the dual face pass
-        if (a.dv) {
-            const size_t sl = volume_sf_smem_bytes(t, false, sizeof(double));
+    if (tangent && a.pj && sf_vol && (!visc || (a.pq && !a.RQ && !a.tRQ))) {
+        // linear volume pass from the stored point Jacobians (none when dv = 0
+        // and dq = 0: the volume integrand does not depend on the traces), then
+        // the dual face pass (viscous: always; its R_Q rows are not asked for)
+        if (a.dv || (visc && a.dq)) {
+            const size_t sl = volume_sf_smem_bytes(t, visc, sizeof(double));
             cudaFuncSetAttribute(residual_volume_sf_kernel<double, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl);
             residual_volume_sf_kernel<double, false, true><<<gv, b, sl, st>>>(a, nA);
         }
-        if (a.pjf && !a.dvh) {
+        if (visc) {
+            cudaFuncSetAttribute(residual_face_kernel<Dual<1>, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf);
+            residual_face_kernel<Dual<1>, true><<<gf, b, sf, st>>>(a);
+        } else if (a.pjf && !a.dvh) {
             if (a.dv) {
                 const int fl = (t.p + 1) * (t.p + 1), fpt = t.ng * t.ng;
                 const size_t sfl = sizeof(double) * (MEHDG_MAXG * (MEHDG_MAXP + 1) + 5 * (size_t)fl + 5 * (size_t)fpt)
