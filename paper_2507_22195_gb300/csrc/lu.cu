@@ -10,7 +10,8 @@
 //            left-looking between the sub-panels, and applies its row
 //            exchanges to the other 224 columns of the outer panel;
 //   inner  : TRSM with the unit-lower triangle, trailing update of the right
-//            half (narrow GEMM), recursion on the right half;
+//            half (width 32 in FP32 on the SIMT pipe, 64 and 128 on the tensor
+//            cores), recursion on the right half;
 //   outer  : row swaps and TRSM of the rows right of the panel, then the
 //            trailing update C -= L21 U12 with depth 256.
 // Rows left of an outer panel are not swapped again (LINPACK order); the
