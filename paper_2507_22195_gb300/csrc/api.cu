@@ -43,7 +43,7 @@ void free_mesh(mehdg_ctx* c) {
     dfree(c->d_res); dfree(c->d_dx); dfree(c->d_nrm); dfree(c->d_status); dfree(c->d_iters); dfree(c->d_conv);
     dfree(c->d_cnt); dfree(c->d_S); dfree(c->d_piv); dfree(c->d_work);
     dfree(c->d_RQ); dfree(c->d_z); dfree(c->d_dq); dfree(c->d_qt1); dfree(c->d_qt2); dfree(c->d_Minv); dfree(c->d_C1);
-    dfree(c->d_pj); dfree(c->d_pjf); dfree(c->d_pq); c->pj_ready = false;
+    dfree(c->d_pj); dfree(c->d_pjf); dfree(c->d_pq); dfree(c->d_pqf); c->pj_ready = false;
     if (c->d_krylov) { cudaFree(c->d_krylov); c->d_krylov = nullptr; c->krylov_bytes = 0; }
     if (c->lu_graph) { cudaGraphExecDestroy(c->lu_graph); c->lu_graph = nullptr; }
     if (c->lu_ev_in) { cudaEventDestroy(c->lu_ev_in); c->lu_ev_in = nullptr; }
@@ -137,6 +137,7 @@ int tangent(mehdg_ctx* c, const double* dv, const double* dvh, const double* dq,
     a.pj = c->pj_ready ? c->d_pj : nullptr;      // linear volume pass from the stored point Jacobians
     a.pjf = c->pj_ready ? c->d_pjf : nullptr;    // linear face pass when the trace direction is 0
     a.pq = c->pj_ready ? c->d_pq : nullptr;      // viscous: dG/dq blocks for the linear volume pass
+    a.pqf = c->pj_ready ? c->d_pqf : nullptr;    // viscous: dGhat/dq blocks for the linear face pass
     int ev = prof_begin(&c->prof, PH_TANGENT, st);
     TRY(launch_residual(a, c->nK, viscous(c), true, st));
     prof_end(&c->prof, ev, st, 0.0);
@@ -281,7 +282,8 @@ int mehdg_set_mesh(mehdg_ctx* c, int64_t nK, const int32_t* p, const int32_t* m,
         DALLOC(c->d_C1, sizeof(double) * t.n * t.n);
     }
     DALLOC(c->d_pj, sizeof(double) * 100 * (size_t)nK * t.m * t.m * t.m * t.npt);
-    if (!vis) DALLOC(c->d_pjf, sizeof(double) * 25 * (size_t)nK * 6 * t.m * t.m * t.ng * t.ng);
+    DALLOC(c->d_pjf, sizeof(double) * 25 * (size_t)nK * 6 * t.m * t.m * t.ng * t.ng);
+    if (vis) DALLOC(c->d_pqf, sizeof(double) * 75 * (size_t)nK * 6 * t.m * t.m * t.ng * t.ng);
     if (vis) DALLOC(c->d_pq, sizeof(double) * 225 * (size_t)nK * t.m * t.m * t.m * t.npt);
     DALLOC(c->d_S, Sbytes);
     DALLOC(c->d_piv, sizeof(int32_t) * nK * c->Npad);
@@ -372,7 +374,7 @@ int mehdg_condense(mehdg_ctx* c, double* bhat, double* Ahat_local, void* stream)
     JacobianArgs ja;
     ja.tab = c->tab; ja.ph = c->ph; ja.box = c->d_box; ja.v = c->v; ja.vs = c->vs; ja.vh = c->vh; ja.q = c->q;
     ja.gid = c->d_gid; ja.S = c->d_S; ja.ld = ld; ja.status = c->d_status; ja.C1 = c->d_C1;
-    ja.pj = c->d_pj; ja.pjf = c->d_pjf; ja.pq = c->d_pq;
+    ja.pj = c->d_pj; ja.pjf = c->d_pjf; ja.pq = c->d_pq; ja.pqf = c->d_pqf;
     TRY(launch_jacobian(ja, nK, fp64, st));
     c->pj_ready = c->d_pj != nullptr;
     prof_end(&c->prof, ev, st, 0.0);

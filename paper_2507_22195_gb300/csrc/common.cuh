@@ -169,7 +169,8 @@ struct mehdg_ctx {
     double *d_Minv = nullptr, *d_C1 = nullptr;   // [n][n] 1-D tables
     double* d_pj = nullptr;             // [nK][m^3][100][npt] weighted FP64 point Jacobians (inviscid)
     double* d_pjf = nullptr;            // [nK][6 m^2][25][fpt] weighted FP64 face blocks dFhat/dv (inviscid)
-    double* d_pq = nullptr;             // [nK][m^3][225][npt] viscous point blocks dG/dq (Jacobian scratch)
+    double* d_pq = nullptr;             // [nK][m^3][225][npt] viscous point blocks W dG/dq
+    double* d_pqf = nullptr;            // [nK][6 m^2][75][fpt] viscous face blocks W dGhat/dq
     bool pj_ready = false;              // d_pj holds the Jacobians at the current state
     double* d_r = nullptr;              // [nK][Npad] FP64 right-hand side
     double* d_x = nullptr;              // [nK][Npad] FP64 solution

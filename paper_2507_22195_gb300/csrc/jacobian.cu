@@ -629,9 +629,14 @@ jac_visc_q_face_kernel(JacobianArgs a, const double* __restrict__ C1) {
         for (int c = 0; c < 15; ++c) { q15[c] = mkdual<15>(0.0); q15[c].d[c] = 1.0; }
         visc_flux(v15, q15, a.ph, G);
         const double W = sW[g1] * hw1 * sW[g2] * hw2 * sgn;
+        double* Gq = a.pqf ? a.pqf + ((size_t)K * 6 * m * m + blockIdx.x) * 75 * fpt + x : nullptr;
         for (int d = 0; d < 3; ++d)
             for (int k = 0; k < 5; ++k)
-                for (int l = 0; l < 5; ++l) PF[(size_t)x * 75 + d * 25 + k * 5 + l] = (TS)(W * G[k][df].d[l * 3 + d]);
+                for (int l = 0; l < 5; ++l) {
+                    const double gv = W * G[k][df].d[l * 3 + d];
+                    PF[(size_t)x * 75 + d * 25 + k * 5 + l] = (TS)gv;
+                    if (Gq) Gq[(size_t)(d * 25 + k * 5 + l) * fpt] = gv;   // also kept for the tangents
+                }
     }
     TS* S = reinterpret_cast<TS*>(a.S) + (size_t)K * a.ld * a.ld;
     const int eo1 = e1 * p, eo2 = e2 * p;

@@ -17,6 +17,8 @@ struct ResidualArgs {
     const double* pjf;                    // stored face point Jacobians dFhat/dv: face pass linear when dvh = 0
     const double* pq;                     // stored viscous blocks W dG/dq [nK][m^3][225][npt] (with pj: the
                                           // viscous volume tangent is linear in dv and dq)
+    const double* pqf;                    // stored viscous face blocks W dGhat/dq [nK][6 m^2][75][fpt] (with
+                                          // pjf: the viscous face tangent is linear when dvh = 0)
 };
 
 cudaError_t launch_residual(const ResidualArgs& a, int64_t nK, bool visc, bool tangent, cudaStream_t st);
@@ -51,6 +53,7 @@ struct JacobianArgs {
     double* pj;               // if set: the weighted FP64 point Jacobians [nK][m^3][100][npt] (inviscid)
     double* pjf;              // if set: the weighted FP64 face blocks dFhat/dv [nK][6 m^2][25][fpt] (inviscid)
     double* pq;               // if set: scratch for the viscous point blocks dG/dq [nK][m^3][225][npt]
+    double* pqf;              // if set: the weighted FP64 viscous face blocks dGhat/dq [nK][6 m^2][75][fpt]
 };
 cudaError_t launch_jacobian(const JacobianArgs& a, int64_t nK, bool fp64, cudaStream_t st);
 cudaError_t launch_pad_identity(void* S, int64_t nK, int64_t ld, int Nv, bool fp64, cudaStream_t st);

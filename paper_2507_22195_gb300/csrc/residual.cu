@@ -457,9 +457,10 @@ residual_face_kernel(ResidualArgs a) {
     }
 }
 
-// Linear face pass of the tangent along dv alone (dvhat = 0, Euler): the
-// stored weighted face blocks W dFhat/dv of the Jacobian kernel, applied to dv
-// interpolated to the face points and tested against the face nodes; adds
+// Linear face pass of the tangent with dvhat = 0: the stored weighted face
+// blocks W d(Fhat + Ghat)/dv of the Jacobian kernel, applied to dv
+// interpolated to the face points, plus on the viscous path the blocks
+// W dGhat/dq applied to the interior dq; tested against the face nodes, added
 // into tRV and into the element's side of the trace tangent tRH.
 __global__ void __launch_bounds__(128)
 residual_face_lin_kernel(ResidualArgs a) {
@@ -473,8 +474,10 @@ residual_face_lin_kernel(ResidualArgs a) {
     const int fl = p1 * p1, fpt = ng * ng;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* sL = reinterpret_cast<double*>(smem_raw);          // [ng][p1]
+    const bool lq = a.pqf && a.dq;
     double* fd = sL + MEHDG_MAXG * (MEHDG_MAXP + 1);           // [5][fl] dv on the face nodes
-    double* pF = fd + 5 * fl;                                  // [5][fpt]
+    double* fdq = fd + 5 * fl;                                 // [15][fl] dq on the face nodes (viscous)
+    double* pF = fdq + (lq ? 15 * fl : 0);                     // [5][fpt]
     int* nodeA = reinterpret_cast<int*>(pF + 5 * fpt);         // [fl]
     const int tid = threadIdx.x, nth = blockDim.x;
     for (int i = tid; i < ng * p1; i += nth) sL[i] = tb.L[i / p1][i % p1];
@@ -484,21 +487,29 @@ residual_face_lin_kernel(ResidualArgs a) {
         int idx[3]; idx[d] = (f & 1) ? n - 1 : 0; idx[t1] = c1; idx[t2] = c2;
         const int A = idx[0] + n * (idx[1] + n * idx[2]);
         nodeA[i] = A;
-        for (int k = 0; k < 5; ++k) fd[k * fl + i] = a.dv[oV + k * Nn + A];
+        for (int k = 0; k < 5; ++k) fd[k * fl + i] = a.dv ? a.dv[oV + k * Nn + A] : 0.0;
+        if (lq) for (int c = 0; c < 15; ++c) fdq[c * fl + i] = a.dq[(int64_t)K * 15 * Nn + c * Nn + A];
     }
     __syncthreads();
     const double* Gb = a.pjf + ((size_t)K * 6 * m * m + blockIdx.x) * 25 * fpt;   // [25][fpt]
+    // viscous: W dGhat_k/dq_(l,d) at [d*25 + k*5 + l][fpt], q component l*3 + d
+    const double* Qb = lq ? a.pqf + ((size_t)K * 6 * m * m + blockIdx.x) * 75 * fpt : nullptr;
     for (int x = tid; x < fpt; x += nth) {
         const int g1 = x % ng, g2 = x / ng;
-        double dvx[5] = {0, 0, 0, 0, 0};
+        double dvx[5] = {0, 0, 0, 0, 0}, dqx[15];
+        for (int c = 0; c < 15; ++c) dqx[c] = 0.0;
         for (int i = 0; i < fl; ++i) {
             const double mu = sL[g1 * p1 + i % p1] * sL[g2 * p1 + i / p1];
             for (int k = 0; k < 5; ++k) dvx[k] += fd[k * fl + i] * mu;
+            if (lq) for (int c = 0; c < 15; ++c) dqx[c] += fdq[c * fl + i] * mu;
         }
         const double* Gx = Gb + x;
         for (int k = 0; k < 5; ++k) {
             double s = 0.0;
             for (int l = 0; l < 5; ++l) s += Gx[(size_t)(k * 5 + l) * fpt] * dvx[l];
+            if (lq)
+                for (int d = 0; d < 3; ++d)
+                    for (int l = 0; l < 5; ++l) s += Qb[(size_t)(d * 25 + k * 5 + l) * fpt + x] * dqx[l * 3 + d];
             pF[k * fpt + x] = s;
         }
     }
@@ -607,23 +618,27 @@ cudaError_t launch_residual(const ResidualArgs& a, int64_t nK, bool visc, bool t
          residual_face_kernel<T, V><<<gf, b, sf, st>>>(a); } while (0)
     if (tangent && a.pj && sf_vol && (!visc || (a.pq && !a.RQ && !a.tRQ))) {
         // linear volume pass from the stored point Jacobians (none when dv = 0
-        // and dq = 0: the volume integrand does not depend on the traces), then
-        // the dual face pass (viscous: always; its R_Q rows are not asked for)
+        // and dq = 0: the volume integrand does not depend on the traces; on the
+        // viscous path only when the R_Q rows are not asked for), then the face
+        // pass: linear when the trace direction is 0, else dual numbers
         if (a.dv || (visc && a.dq)) {
             const size_t sl = volume_sf_smem_bytes(t, visc, sizeof(double));
             cudaFuncSetAttribute(residual_volume_sf_kernel<double, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl);
             residual_volume_sf_kernel<double, false, true><<<gv, b, sl, st>>>(a, nA);
         }
-        if (visc) {
-            cudaFuncSetAttribute(residual_face_kernel<Dual<1>, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf);
-            residual_face_kernel<Dual<1>, true><<<gf, b, sf, st>>>(a);
-        } else if (a.pjf && !a.dvh) {
-            if (a.dv) {
+        if (a.pjf && !a.dvh && (!visc || a.pqf)) {
+            // linear face pass (viscous: with the dGhat/dq blocks); nothing to add
+            // when neither dv nor dq is set
+            if (a.dv || (visc && a.dq)) {
                 const int fl = (t.p + 1) * (t.p + 1), fpt = t.ng * t.ng;
-                const size_t sfl = sizeof(double) * (MEHDG_MAXG * (MEHDG_MAXP + 1) + 5 * (size_t)fl + 5 * (size_t)fpt)
+                const size_t sfl = sizeof(double) * (MEHDG_MAXG * (MEHDG_MAXP + 1) + (visc ? 20 : 5) * (size_t)fl +
+                                                     5 * (size_t)fpt)
                                  + sizeof(int) * fl + 16;
                 residual_face_lin_kernel<<<gf, b, sfl, st>>>(a);
             }
+        } else if (visc) {
+            cudaFuncSetAttribute(residual_face_kernel<Dual<1>, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf);
+            residual_face_kernel<Dual<1>, true><<<gf, b, sf, st>>>(a);
         } else {
             cudaFuncSetAttribute(residual_face_kernel<Dual<1>, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf);
             residual_face_kernel<Dual<1>, false><<<gf, b, sf, st>>>(a);
