@@ -113,7 +113,12 @@ int mehdg_create(mehdg_ctx** out, const mehdg_params* prm);
  * face_gid: host [nK][6], global face of each local face, in
  * [0, n_global_faces); a global face used by two elements couples them
  * (interior face), one used once is an unshared face.  Allocates the device
- * workspaces (one dense S^K per element in the precision of prm->prec). */
+ * workspaces: one dense S^K per element in the precision of prm->prec (ld^2
+ * values, ld = N_v rounded up to 256), three LU operand panels of 2 KB per
+ * row of S^K (mixed precisions), and the FP64 point and
+ * face Jacobians that make the tangents linear (100 doubles per volume Gauss
+ * point and 25 per face point; viscous 225 and 75 more).  Returns
+ * MEHDG_ENOMEM when they do not fit. */
 int mehdg_set_mesh(mehdg_ctx* ctx, int64_t nK, const int32_t* p, const int32_t* m,
                    const double* box, const int64_t* face_gid, int64_t n_global_faces);
 
