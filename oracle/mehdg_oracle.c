@@ -1070,7 +1070,7 @@ void orc_dof_counts_tet(int p, int m, long n_tet, long *dof_local, long *dof_glo
     *dof_global = n_macro * 4 / 2 * nodes_face * 5;
 }
 
-/* hexahedral analogue used by this build (faces not shared within K) */
+/* hexahedral analogue: hex micro-elements, the six faces of K independent */
 void orc_dof_counts_hex(int p, int m, long n_macro, int viscous, long *dof_local, long *dof_global)
 {
     long n = (long)m * p + 1;
