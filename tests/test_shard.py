@@ -58,7 +58,7 @@ def _run(world, viscous):
         return dict(out)
 
 
-@pytest.mark.parametrize("world,viscous", [(2, False), (3, False), (2, True)])
+@pytest.mark.parametrize("world,viscous", [(2, False), (3, False), (4, False), (2, True)])
 def test_sharded_condensation_matches_whole_mesh(world, viscous):
     mesh, st, prm = _case(viscous)
     bh_all, Ahats = oracle.condense_mesh(prm, mesh, st, want_Ahat=True)
