@@ -126,45 +126,43 @@ def workload(name, nk=8, block=4):
 
 
 # ---------------------------------------------------------------- oracle (CPU)
-def _oracle_one(args):
-    K, nk = args
-    import oracle
-    from paper_2507_22195_gb300 import inputs as I
-    mesh = I.periodic_mesh(nk, 3, 3)
-    st = I.make_state(mesh, "tgv", 1e-3, 22197, 22198, M0=0.1)
-    prm = oracle.params(flux=oracle.KEPES, Mach=0.1)
-    t = time.time()
-    R, B = oracle.element_system(prm, mesh, st, K)
-    oracle.condense_K(0, R, B, False)
-    return time.time() - t
-
-
-def oracle_rate(n_elem: int, cores: int):
-    """FP64 CPU oracle, as it stands: n_elem elements of the inviscid TGV
-    workload, one per process (spawned), on `cores` host cores.  Returns
-    (elements/s, seconds)."""
+def oracle_sample(mesh, st, prm_kw, Ks, dvh, procs):
+    """The FP64 CPU oracle, as it stands, on the elements Ks of a workload
+    (residual, complex-step Jacobian, dense GEPP, b-hat and dV for the trace
+    increment dvh), one element per spawned process on `procs` host cores.
+    Returns (elements/s over the wall time, [seconds per element],
+    {K: dV^K})."""
     import oracle
     oracle.build()
-    ctx = mp.get_context("spawn")
+    prm = oracle.params(**prm_kw)
     t = time.time()
-    with ctx.Pool(cores) as pool:
-        pool.map(_oracle_one, [(K * 37 % 512, 8) for K in range(n_elem)])
+    res = oracle.condense_elements(prm, mesh, st, Ks, dvh, procs=procs)
     dt = time.time() - t
-    return n_elem / dt, dt
+    return len(Ks) / dt, [r[3] for r in res], {K: r[1] for K, r in zip(Ks, res)}
+
+
+def _oracle_prm(kw):
+    return dict(flux=kw["flux"], Mach=kw["Mach"], Re=kw.get("Re", 1600.0), Pr=kw.get("Pr", 0.71),
+                viscous=kw["viscous"])
 
 
 def reference_main(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    from paper_2507_22195_gb300 import inputs as I
     cores = min(os.cpu_count() or 1, 16)
     per_step = cores                     # one element per core per step
+    mesh, st, kw = workload("tgv_inviscid")
+    dvh = I.random_direction(st.vhat.shape, 77, 1e-3)
+    Ks = [K * 37 % mesh.nK for K in range(per_step)]
     for _ in range(a.warmup):
-        oracle_rate(per_step, cores)
+        oracle_sample(mesh, st, _oracle_prm(kw), Ks, dvh, cores)
     times = []
     for _ in range(a.steps):
-        _, dt = oracle_rate(per_step, cores)
-        times.append(dt)
+        t = time.time()
+        oracle_sample(mesh, st, _oracle_prm(kw), Ks, dvh, cores)
+        times.append(time.time() - t)
     tot = sum(times)
     val = per_step * a.steps / tot
     sample = f"{per_step} of the 512 elements per step (element ids 37k mod 512), one per process"
@@ -228,10 +226,12 @@ def once_main(a):
     return 0
 
 
-# DRAM bytes per outer-update launch, measured with ncu on the full workload
-# (profiles/tc_stream_outer_tgv512_bf16x3.md); other workloads and precisions
+# DRAM bytes / algorithmic bytes of the outer trailing update (split BF16),
+# measured with ncu on one launch of a 27-element case of the same kernel
+# (3^3 elements of the p = 3, m = 3 TGV, 2.8 GB of S): C is streamed once per
+# launch, so the ratio carries over to the full workload.  Other precisions
 # were not captured and report null.
-TRAFFIC_PER_LAUNCH = {("tgv_inviscid", 8, "bf16x3"): 37.633e9}
+TRAFFIC_RATIO = {"bf16x3": 0.987}
 
 
 def trailing_bytes(ld, nK):
@@ -245,6 +245,99 @@ def trailing_bytes(ld, nK):
     return byt * nK
 
 
+def rel_per_element(a, b):
+    """max over the leading index of ||a_i - b_i|| / ||b_i|| (numpy arrays)"""
+    import numpy as np
+    a2, b2 = a.reshape(a.shape[0], -1), b.reshape(b.shape[0], -1)
+    return float((np.linalg.norm(a2 - b2, axis=1) / np.linalg.norm(b2, axis=1)).max())
+
+
+def timed_condense(ctx, bh, steps, barrier):
+    """device time of `steps` condensations (CUDA events on the current stream)"""
+    import torch
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.condense(bh)
+    e1.record(stream)
+    barrier()
+    return e0.elapsed_time(e1)
+
+
+def fp64_full(mesh, st, kw, dev, bh_mixed, dV_mixed, dvh, barrier, M):
+    """The FP64 GPU path on the whole workload: one timed condensation (its
+    kernels were loaded by the subset comparison before), b-hat and the
+    recovered dV against the mixed path's"""
+    import torch
+    ld = (5 * mesh.Nn + 255) // 256 * 256
+    c = M.Context(mesh, prec=PREC["fp64"], **kw)
+    c.set_state(*_to_dev(st, dev))
+    bh = torch.empty_like(bh_mixed)
+    ms = timed_condense(c, bh, 1, barrier)
+    st64, it64 = c.status()
+    dV = c.recover(dvh)
+    torch.cuda.synchronize()
+    out = {"value": mesh.nK / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": 1,
+           "sample": f"all {mesh.nK} elements (FP64 S: {mesh.nK * 8 * ld * ld / 1e9:.1f} GB)",
+           "err_bhat_mixed_vs_fp64": rel_per_element(bh_mixed.cpu().numpy(), bh.cpu().numpy()),
+           "err_dV_mixed_vs_fp64": rel_per_element(dV_mixed, dV.cpu().numpy()),
+           "refine_iters": sorted(set(int(x) for x in it64)), "status_ok": bool((st64 == 0).all())}
+    c.close()
+    return out
+
+
+def subset_compare(mesh, st, kw, dev, n_s, prec, barrier, M):
+    """FP64 and mixed GPU paths on the first n_s elements of a workload: rates
+    (one untimed and one timed condensation each) and the b-hat error"""
+    import numpy as np
+    import torch
+    from paper_2507_22195_gb300 import inputs as I
+    m2 = I.sub_mesh(mesh, list(range(n_s)))
+    s2 = I.State(v=st.v[:n_s].copy(), vhat=st.vhat[np.unique(mesh.face_gid[:n_s])].copy(),
+                 q=None if st.q is None else st.q[:n_s].copy(), vstar=st.vstar[:n_s].copy())
+    w = _to_dev(s2, dev)
+    outs = {}
+    for pr in ("fp64", prec):
+        c2 = M.Context(m2, prec=PREC[pr], **kw)
+        c2.set_state(*w)
+        b2 = c2.condense()
+        ms = timed_condense(c2, b2, 1, barrier)
+        st2, _ = c2.status()
+        outs[pr] = (b2.cpu().numpy(), ms, bool((st2 == 0).all()))
+        c2.close()
+    return {"value": n_s / (outs["fp64"][1] / 1e3), "unit": UNIT, "sample": f"the first {n_s} elements",
+            "mixed_same_sample": n_s / (outs[prec][1] / 1e3),
+            "err_bhat_mixed_vs_fp64": rel_per_element(outs[prec][0], outs["fp64"][0]),
+            "status_ok": outs["fp64"][2] and outs[prec][2]}
+
+
+def viscous_wave(block, dev, barrier, M, steps=2):
+    """configs[2]: one wave of the viscous TGV (a block^3 block of the 16^3 x
+    4^3 mesh, p = 3; block 7 holds 166 GB of FP32 S, under 60 % of HBM) in
+    split BF16 and split TF32, and the FP64 GPU path on its first 8 elements"""
+    mesh, st, kw = workload("tgv_viscous", block=block)
+    out = {"workload": f"viscous TGV Re=1600, {block}^3 block of the 16^3 x 4^3 mesh, p=3, ES",
+           "nK": mesh.nK, "N_v": 5 * mesh.Nn, "steps": steps, "warmup": 1}
+    w = _to_dev(st, dev)
+    import torch
+    for pr in ("bf16x3", "tf32x3"):
+        c = M.Context(mesh, prec=PREC[pr], **kw)
+        c.set_state(*w)
+        bh = c.condense()
+        ms = timed_condense(c, bh, steps, barrier)
+        stt, it = c.status()
+        out[pr] = {"value": mesh.nK * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+                   "refine_iters": sorted(set(int(x) for x in it)), "status_ok": bool((stt == 0).all())}
+        c.close()
+        del bh
+    del w
+    torch.cuda.empty_cache()
+    out["fp64_gpu"] = subset_compare(mesh, st, kw, dev, 8, "bf16x3", barrier, M)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -255,7 +348,10 @@ def main():
     ap.add_argument("--workload", default="tgv_inviscid", choices=list(WORKLOADS))
     ap.add_argument("--nk", type=int, default=8, help="tgv_inviscid: nk^3 elements")
     ap.add_argument("--block", type=int, default=4, help="tgv_viscous: block^3 elements of the 16^3 mesh")
-    ap.add_argument("--fp64-sample", type=int, default=8, help="elements of the FP64 comparison (0: skip)")
+    ap.add_argument("--fp64-sample", type=int, default=8, help="elements of the FP64 subset comparison (0: skip)")
+    ap.add_argument("--no-fp64-full", action="store_true", help="skip the FP64 GPU path on the whole workload")
+    ap.add_argument("--viscous-block", type=int, default=7,
+                    help="block^3 elements of the viscous TGV timed beside the headline (0: skip)")
     ap.add_argument("--cpu-sample", type=int, default=-1, help="elements for the CPU oracle baseline (-1: one per core)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--once", action="store_true", help="one condense after --warmup ones, no timing (for profilers)")
@@ -268,20 +364,37 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2507_22195_gb300 import inputs as I
+    mesh, st, kw = workload(a.workload, a.nk, a.block)
+    vis = bool(kw["viscous"])
+    dvh_np = I.random_direction(st.vhat.shape, 77, 1e-3)
 
-    # CPU baseline first (spawned pool, before any CUDA call), rank 0 only
-    cpu = None
+    # CPU baseline and oracle reference values first (spawned pool, before any
+    # CUDA call), rank 0 only: the oracle condenses a sample of the same
+    # elements and recovers dV for the same seeded trace increment
+    cpu, ref_dV = None, {}
     if rank == 0 and world == 1 and not a.no_cpu and a.workload == "tgv_inviscid":
         cores = min(os.cpu_count() or 1, 16)
         n = cores if a.cpu_sample < 0 else a.cpu_sample
-        val, dt = oracle_rate(n, cores)
+        Ks = [K * 37 % mesh.nK for K in range(n)]
+        t0 = time.time()
+        val, per, ref_dV = oracle_sample(mesh, st, _oracle_prm(kw), Ks, dvh_np, cores)
+        dt = time.time() - t0
+        vmesh, vst, vkw = workload("vortex")
+        vval, vper, _ = oracle_sample(vmesh, vst, _oracle_prm(vkw), list(range(vmesh.nK)), None,
+                                      min(cores, vmesh.nK))
         cpu = {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{n} of the 512 elements (residual, complex-step Jacobian, dense GEPP, b-hat), "
-                         f"one per process, {dt:.1f} s wall"}
+               "sample": f"{n} of the 512 elements (ids 37k mod 512: residual, complex-step Jacobian, dense GEPP, "
+                         f"b-hat, dV), one per spawned process, {dt:.1f} s wall",
+               "single_core": {"value": 1.0 / statistics.mean(per), "unit": UNIT,
+                               "what": "1 / mean seconds per element of one process while all cores are busy"},
+               "configs0_vortex": {"value": vval, "single_core": 1.0 / statistics.mean(vper), "unit": UNIT,
+                                   "sample": f"all {vmesh.nK} elements of the 2^3 x 2^3, p = 2 vortex (ES)"},
+               "configs2_viscous": "not timed: the oracle's dense A_qq of a p = 3, m = 4 element is 8.7 GB and "
+                                   "its GEPP alone is 2.4e13 flop (hours on one core)"}
 
     import numpy as np
     import torch
-    from paper_2507_22195_gb300 import inputs as I
     from paper_2507_22195_gb300 import mehdg as M
 
     torch.cuda.set_device(local)
@@ -291,8 +404,6 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    mesh, st, kw = workload(a.workload, a.nk, a.block)
-    vis = bool(kw["viscous"])
     v, vh, q, vs = _to_dev(st, dev)
     ctx = M.Context(mesh, prec=PREC[a.prec], **kw)
     ctx.set_state(v, vh, q, vs)
@@ -313,15 +424,7 @@ def main():
     time.sleep(0.3)
     M.mehdg_profile_enable(ctx.ctx, True)
     n0 = M.mehdg_launch_count()
-    stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    e0.record(stream)
-    for _ in range(a.steps):
-        ctx.condense(bh)
-    e1.record(stream)
-    barrier()
-    ms = e0.elapsed_time(e1)
+    ms = timed_condense(ctx, bh, a.steps, barrier)
     launches = M.mehdg_launch_count() - n0
     prof = M.mehdg_profile_read(ctx.ctx)
     M.mehdg_profile_enable(ctx.ctx, False)
@@ -351,13 +454,17 @@ def main():
     d2h = hb.numel() * 8
     # recovery (eq. R2, R6) timed on its own, after the condensation above, for a
     # seeded trace increment
-    dvh = torch.tensor(I.random_direction(st.vhat.shape, 77, 1e-3), device=dev)
-    ctx.recover(dvh)
+    ctx.set_state(v, vh, q, vs)
+    del devb
+    ctx.condense(bh)
+    dvh = torch.tensor(dvh_np, device=dev)
+    dV = ctx.recover(dvh)
+    stream = torch.cuda.current_stream()
     r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     r0.record(stream)
     for _ in range(a.steps):
-        ctx.recover(dvh)
+        ctx.recover(dvh, out=dV)
     r1.record(stream)
     barrier()
     rec_ms = max_over_ranks(r0.elapsed_time(r1), dist, dev)
@@ -365,13 +472,21 @@ def main():
            "ms_per_step": rec_ms / a.steps,
            "what": "recover: dV = S^-1(-R_V - A_v,vhat dVhat) with FP64 refinement (and dQ when viscous), "
                    "seeded dVhat"}
-    ctx.set_state(v, vh, q, vs)
+    dV_np = dV.cpu().numpy()
+    bh_mixed = bh.clone()
+    err_or = None
+    if ref_dV:
+        e = [float(np.linalg.norm(dV_np[K] - d) / np.linalg.norm(d)) for K, d in ref_dV.items()]
+        err_or = {"value": max(e), "what": "max over the oracle's sample elements of ||dV^K_gpu - dV^K_oracle|| / "
+                                           "||dV^K_oracle||, dV recovered for the seeded dVhat after this "
+                                           "condensation", "elements": sorted(ref_dV)}
 
     # roofline of the dominant kernel: the outer trailing update of the LU
     pk = peaks()
     gem = prof["lu_trailing_update"]
     ld = (5 * mesh.Nn + 255) // 256 * 256
     byt = trailing_bytes(ld, mesh.nK) * a.steps
+    roof_t = None
     if a.prec == "fp64":
         fl = gem["flops"]
         ach = fl / (gem["ms"] / 1e3) / 1e12
@@ -381,42 +496,41 @@ def main():
     else:
         ach = byt / (gem["ms"] / 1e3) / 1e9
         hbm = pk.get("hbm_gbs", 6800.0)
-        tr = TRAFFIC_PER_LAUNCH.get((a.workload, a.nk, a.prec))
+        ratio = TRAFFIC_RATIO.get(a.prec) if a.workload == "tgv_inviscid" else None
+        tr = ratio * byt / max(gem["launches"], 1) if ratio else None
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": tr, "traffic_unit": "bytes per launch" if tr else None,
+                "traffic": tr, "traffic_unit": "bytes per launch (27-element ncu capture, scaled)" if tr else None,
                 "algorithmic_per_launch": byt / max(gem["launches"], 1),
                 "peak_source": "measured" if "hbm_gbs" in pk else "fallback",
                 "kernel": "lu_trailing_update (tcgen05, depth 256)", "launches": gem["launches"],
-                "ms": gem["ms"], "tflops": gem["flops"] / (gem["ms"] / 1e3) / 1e12}
-
-    # FP64 GPU path and the mixed-vs-FP64 error on the first elements of the same workload
+                "ms": gem["ms"]}
+        # the same kernel on the method's work: 2 rest^2 256 flop per outer
+        # update (the LU's 2/3 N^3 less the panels), against the sustained
+        # BF16 rate; the split modes issue three products per flop counted here
+        sus = pk.get("bf16_tflops_sustained", 1700.0)
+        tfl = gem["flops"] / (gem["ms"] / 1e3) / 1e12
+        roof_t = {"bound": "tensor", "achieved": tfl, "peak": sus, "unit": "TFLOP/s", "frac": tfl / sus,
+                  "peak_source": "measured sustained bf16" if "bf16_tflops_sustained" in pk else "fallback",
+                  "flops_per_step": gem["flops"] / a.steps,
+                  "lu_method_flops_per_step": 2.0 / 3.0 * (5 * mesh.Nn) ** 3 * mesh.nK,
+                  "tensor_products_per_flop": 3 if a.prec.endswith("x3") else 1,
+                  "traffic_vs_compulsory": byt / a.steps / (2 * 4 * ld * ld * mesh.nK)}
     fp = None
     if a.prec != "fp64" and a.fp64_sample > 0:
-        n_s = min(a.fp64_sample, mesh.nK)
-        m2 = I.sub_mesh(mesh, list(range(n_s)))
-        s2 = I.State(v=st.v[:n_s].copy(), vhat=None, q=None if st.q is None else st.q[:n_s].copy(),
-                     vstar=st.vstar[:n_s].copy())
-        # traces of the sub-mesh: the faces of the first elements, renumbered
-        gid = mesh.face_gid[:n_s]
-        uniq = np.unique(gid)
-        s2.vhat = st.vhat[uniq].copy()
-        w = _to_dev(s2, dev)
-        outs = {}
-        for pr in ("fp64", a.prec):
-            c2 = M.Context(m2, prec=PREC[pr], **kw)
-            c2.set_state(*w)
-            b2 = c2.condense()
-            barrier()
-            t1 = time.perf_counter()
-            c2.condense(b2)
-            barrier()
-            st2, it2 = c2.status()
-            outs[pr] = (b2.clone(), time.perf_counter() - t1, bool((st2 == 0).all()))
-            c2.close()
-        err = float(torch.linalg.norm(outs[a.prec][0] - outs["fp64"][0]) / torch.linalg.norm(outs["fp64"][0]))
-        fp = {"value": n_s / outs["fp64"][1], "unit": UNIT, "sample": f"the first {n_s} elements of the workload",
-              "mixed_same_sample": n_s / outs[a.prec][1], "err_bhat_mixed_vs_fp64": err,
-              "status_ok": outs["fp64"][2] and outs[a.prec][2]}
+        ctx.close()
+        del bh
+        torch.cuda.empty_cache()
+        fp = {"subset": subset_compare(mesh, st, kw, dev, min(a.fp64_sample, mesh.nK), a.prec, barrier, M)}
+        if not a.no_fp64_full:
+            fp["full"] = fp64_full(mesh, st, kw, dev, bh_mixed, dV_np, dvh, barrier, M)
+            fp.update(value=fp["full"]["value"], unit=UNIT)
+    else:
+        ctx.close()
+    del v, vh, q, vs
+    torch.cuda.empty_cache()
+    visc = None
+    if a.workload == "tgv_inviscid" and a.viscous_block > 0 and world == 1:
+        visc = viscous_wave(a.viscous_block, dev, barrier, M)
 
     if rank == 0:
         out = {
@@ -429,7 +543,9 @@ def main():
                        "l2": "inputs larger than L2 (dense S^K of all elements: %.1f GB)" % (
                            mesh.nK * ld * ld * (8 if a.prec == "fp64" else 4) / 1e9)},
             "roofline": roof,
+            "roofline_tensor": roof_t,
             "cpu_baseline": cpu,
+            "err_vs_oracle": err_or,
             "e2e": {"value": job_rate(world, mesh.nK, a.steps, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
@@ -438,10 +554,10 @@ def main():
             "status_ok": bool((stat == 0).all()),
             "phases_ms_per_step": {k: round(vv["ms"] / a.steps, 3) for k, vv in prof.items()},
             "fp64_gpu": fp,
+            "viscous_tgv": visc,
             "recover": rec,
         }
         print(json.dumps(out))
-    ctx.close()
     if dist:
         dist.destroy_process_group()
     return 0

@@ -207,12 +207,15 @@ int64_t mehdg_launch_count(void);
  * v, vhat, q (NULL for Euler), vstar, R_V, R_Q (NULL for Euler), R_Vhat in
  * the layouts above.  Its scratch is one static device array of 24 MiB per
  * GPU, held until the process exits; the call needs
- * nK * 30 n^2 doubles + 2 n_global_faces int64 (+ alignment) of it and
- * returns MEHDG_EINVAL (message on stderr) when that does not fit.  The
- * first call made on a device looks up the array's device address (once per
- * device).  Calls share the array: calls that overlap on the GPU race.  The
- * call synchronises `stream` once, after checking the face ids on the device
- * and before the residual kernels read with them. */
+ * nK * 30 n^2 doubles + 2 n_global_faces int64 + nK int32 (+ alignment) of
+ * it and returns MEHDG_EINVAL (message on stderr) when that does not fit.
+ * The first call made on a device looks up the array's device address (once
+ * per device).  Calls share the array: calls that overlap on the GPU race.
+ * The call synchronises `stream` twice: after checking the face ids on the
+ * device (before the residual kernels read with them), and at the end to
+ * read the elements' status words; a non-physical state at any point
+ * returns MEHDG_ENONPHYS (count and first element on stderr), with the
+ * outputs written but not meaningful for those elements. */
 int mehdg_residual_static(const mehdg_params* prm, int64_t nK, int p, int m, const double* box,
                           const int64_t* face_gid, int64_t n_global_faces, const double* v,
                           const double* vhat, const double* q, const double* vstar, double* R_V,

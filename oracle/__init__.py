@@ -377,3 +377,45 @@ def brute_force(prm, mesh, st):
     dV = d[nq_tot:offH].reshape(nK, 5, Nn)
     dH = d[offH:].reshape(mesh.n_global_faces, 5, n2)
     return dQ, dV, dH
+
+
+# ---------------------------------------------------------------- element samples in parallel
+def _condense_one(args):
+    """worker: b-hat^K and, for a trace increment, dV^K (eq. R2) and dQ^K
+    (eq. R6) of one element, from its own data only; also the seconds taken"""
+    import time
+    fields, p, m, box, v, vs, vh_loc, q, dvh_loc = args
+    prm = Params(*fields)
+    t = time.time()
+    R = residual_K(prm, p, m, box, v, vs, vh_loc, q)
+    B = jacobian_K(prm, p, m, box, v, vs, vh_loc, q)
+    bh, _, dV, dQ = condense_K(prm.viscous, R, B, False, dvh_loc)
+    return bh, dV, dQ, time.time() - t
+
+
+def condense_elements(prm, mesh, st, Ks, dvh_global=None, procs=1):
+    """For each element K in Ks: (b-hat^K [6,5,n2], dV^K [5,Nn] or None,
+    dQ^K or None, seconds).  Elements are independent (Algorithm 1, local
+    parts), so a sample of a large mesh is condensed without the others;
+    procs > 1 runs them in a spawned process pool."""
+    fields = tuple(getattr(prm, f) for f, _ in Params._fields_)
+    jobs = []
+    for K in Ks:
+        vh = gather_trace(mesh, st.vhat, K)
+        dvh = None if dvh_global is None else gather_trace(mesh, dvh_global, K).ravel()
+        q = None if st.q is None else np.ascontiguousarray(st.q[K])
+        jobs.append((fields, mesh.p, mesh.m, mesh.boxes[K].copy(), np.ascontiguousarray(st.v[K]),
+                     np.ascontiguousarray(st.vstar[K]), vh, q, dvh))
+    if procs <= 1:
+        out = [_condense_one(j) for j in jobs]
+    else:
+        import multiprocessing as mp
+        build()
+        with mp.get_context("spawn").Pool(procs) as pool:
+            out = pool.map(_condense_one, jobs)
+    Nn, n2 = mesh.Nn, mesh.n2
+    res = []
+    for bh, dV, dQ, t in out:
+        res.append((bh.reshape(6, 5, n2), None if dV is None else dV.reshape(5, Nn),
+                    None if dQ is None else dQ.reshape(5, 3, Nn), t))
+    return res

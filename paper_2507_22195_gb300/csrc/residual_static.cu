@@ -32,11 +32,24 @@ constexpr int kMaxDevices = 64;
 std::mutex g_addr_mu;
 unsigned char* g_addr[kMaxDevices] = {};
 
-// face map: slot 0 = smallest element side (K*6+f) on the face, slot 1 = the other one
+// face map: slot 0 = smallest element side (K*6+f) on the face, slot 1 = the other one.
+// err[0]: face-id check; err[1], err[2]: number and first index of the
+// elements whose status word is set (filled by status_summary_kernel)
 __global__ void g2l_init_kernel(int64_t* g2l, int64_t G, int32_t* err) {
     int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (g == 0) *err = 0;
+    if (g == 0) { err[0] = 0; err[1] = 0; err[2] = INT_MAX; }
     if (g < G) { g2l[2 * g] = LLONG_MAX; g2l[2 * g + 1] = -1; }
+}
+__global__ void status_zero_kernel(int32_t* status, int64_t nK) {
+    int64_t K = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (K < nK) status[K] = 0;
+}
+__global__ void status_summary_kernel(const int32_t* status, int64_t nK, int32_t* err) {
+    int64_t K = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (K < nK && status[K] != 0) {
+        atomicAdd(&err[1], 1);
+        atomicMin(&err[2], (int)K);
+    }
 }
 __global__ void g2l_min_kernel(const int64_t* gid, int64_t nK, int64_t G, int64_t* g2l, int32_t* err) {
     int64_t kf = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -104,10 +117,11 @@ extern "C" int mehdg_residual_static(const mehdg_params* prm, int64_t nK, int p,
     const size_t side_bytes = (size_t)nK * 30 * tab.n2 * sizeof(double);
     const size_t map_off = (side_bytes + 255) & ~(size_t)255;
     const size_t map_bytes = (size_t)G * 2 * sizeof(int64_t);
-    const size_t err_off = (map_off + map_bytes + 255) & ~(size_t)255;
+    const size_t stat_off = (map_off + map_bytes + 255) & ~(size_t)255;
+    const size_t err_off = (stat_off + (size_t)nK * sizeof(int32_t) + 255) & ~(size_t)255;
     if (err_off + 256 > kStaticScratchBytes) {
         snprintf(t_err, sizeof(t_err),
-                 "needs %zu bytes of scratch, the static array holds %zu (nK x 30 n^2 doubles + 2 G int64)",
+                 "needs %zu bytes of scratch, the static array holds %zu (nK x 30 n^2 doubles + 2 G int64 + nK int32)",
                  err_off + 256, kStaticScratchBytes);
         report(t_err);
         return MEHDG_EINVAL;
@@ -116,6 +130,7 @@ extern "C" int mehdg_residual_static(const mehdg_params* prm, int64_t nK, int p,
     if (!base) { report(t_err); return MEHDG_ECUDA; }
     double* RHloc = reinterpret_cast<double*>(base);
     int64_t* g2l = reinterpret_cast<int64_t*>(base + map_off);
+    int32_t* dstat = reinterpret_cast<int32_t*>(base + stat_off);
     int32_t* derr = reinterpret_cast<int32_t*>(base + err_off);
     cudaStream_t st = (cudaStream_t)stream;
 
@@ -134,7 +149,8 @@ extern "C" int mehdg_residual_static(const mehdg_params* prm, int64_t nK, int p,
     g2l_min_kernel<<<(unsigned)((6 * nK + bs - 1) / bs), bs, 0, st>>>(face_gid, nK, G, g2l, derr);
     g2l_other_kernel<<<(unsigned)((6 * nK + bs - 1) / bs), bs, 0, st>>>(face_gid, nK, G, g2l, derr);
     g2l_finish_kernel<<<(unsigned)((G + bs - 1) / bs), bs, 0, st>>>(g2l, G);
-    MEHDG_COUNT(4);
+    status_zero_kernel<<<(unsigned)((nK + bs - 1) / bs), bs, 0, st>>>(dstat, nK);
+    MEHDG_COUNT(5);
     // the face ids index the trace arrays: check them before any kernel reads with them
     int32_t herr = 0;
     cudaError_t e = cudaMemcpyAsync(&herr, derr, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
@@ -153,12 +169,28 @@ extern "C" int mehdg_residual_static(const mehdg_params* prm, int64_t nK, int p,
     a.tab = tab; a.ph = ph; a.box = box; a.gid = face_gid;
     a.v = v; a.vs = vstar; a.vh = vhat; a.q = q;
     a.RV = R_V; a.RQ = prm->viscous ? R_Q : nullptr; a.RH = RHloc;
+    a.status = dstat;
     e = launch_residual(a, nK, prm->viscous != 0, false, st);
     if (e == cudaSuccess) e = launch_trace_gather(RHloc, g2l, G, tab.n2, R_Vhat, 1.0, nullptr, 0.0, st);
+    if (e == cudaSuccess) {
+        status_summary_kernel<<<(unsigned)((nK + bs - 1) / bs), bs, 0, st>>>(dstat, nK, derr);
+        MEHDG_COUNT(1);
+        e = cudaGetLastError();
+    }
+    // second synchronisation: the elements' status words (a non-physical
+    // state at a point: beta <= 0, rho <= 0 or a non-finite value)
+    int32_t hsum[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hsum, derr + 1, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         snprintf(t_err, sizeof(t_err), "launch failed: %s", cudaGetErrorString(e));
         report(t_err);
         return MEHDG_ECUDA;
+    }
+    if (hsum[0] > 0) {
+        snprintf(t_err, sizeof(t_err), "non-physical state in %d element(s), first element %d", hsum[0], hsum[1]);
+        report(t_err);
+        return MEHDG_ENONPHYS;
     }
     return MEHDG_OK;
 }

@@ -109,6 +109,17 @@ def independent_mesh(nK: int, p: int, m: int, size=1.0, seed=0) -> Mesh:
     return Mesh(p, m, boxes, gid, 6 * nK)
 
 
+def unshared(mesh: Mesh, Ks=None) -> Mesh:
+    """The elements Ks of a mesh (default: all) with every face unshared:
+    element K's local face f becomes global face 6 K' + f (K' = position in
+    Ks).  The elements keep their boxes, so the input fields vary from
+    element to element."""
+    Ks = np.arange(mesh.nK) if Ks is None else np.asarray(Ks)
+    nK = len(Ks)
+    gid = np.arange(6 * nK, dtype=np.int64).reshape(nK, 6)
+    return Mesh(mesh.p, mesh.m, mesh.boxes[Ks].copy(), gid, 6 * nK)
+
+
 def node_coords_1d(lo: float, hi: float, p: int, m: int) -> np.ndarray:
     xi = np.array(_GLL[p])
     h = (hi - lo) / m
@@ -251,27 +262,3 @@ def make_state(mesh: Mesh, kind: str, amp: float, seed_v: int, seed_vh: int,
 def random_direction(shape, seed: int, amp: float = 1.0) -> np.ndarray:
     r = np.random.Generator(np.random.PCG64(seed))
     return r.uniform(-amp, amp, size=shape)
-
-
-# ---------------------------------------------------------------- workloads
-def workload(name: str, nK_override: int | None = None):
-    """Named workloads: returns (mesh, state, params dict)."""
-    if name == "vortex":      # 2^3 macro-elements x 2^3 micro, p=2, [0,10]^3
-        mesh = periodic_mesh(2, 2, 2, 0.0, 10.0)
-        st = make_state(mesh, "vortex", 1e-3, 22195, 22196, period=10.0)
-        prm = dict(gamma=GAMMA, Re=1.0, Pr=0.71, Mach=1.0 / math.sqrt(GAMMA), dt=1.0,
-                   viscous=0, flux=1)
-        return mesh, st, prm
-    if name == "tgv_inviscid":   # 8^3 x 3^3, p=3
-        nk = 8 if nK_override is None else nK_override
-        mesh = periodic_mesh(nk, 3, 3)
-        st = make_state(mesh, "tgv", 1e-3, 22197, 22198, M0=0.1)
-        prm = dict(gamma=GAMMA, Re=1600.0, Pr=0.71, Mach=0.1, dt=1.0, viscous=0, flux=2)
-        return mesh, st, prm
-    if name == "tgv_viscous":    # 16^3 x 4^3, p=3
-        nk = 16 if nK_override is None else nK_override
-        mesh = periodic_mesh(nk, 3, 4)
-        st = make_state(mesh, "tgv", 1e-3, 22201, 22202, viscous=True, M0=0.1)
-        prm = dict(gamma=GAMMA, Re=1600.0, Pr=0.71, Mach=0.1, dt=1.0, viscous=1, flux=1)
-        return mesh, st, prm
-    raise ValueError(name)

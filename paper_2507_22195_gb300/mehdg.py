@@ -293,10 +293,10 @@ class Context:
         mehdg_residual_vjp(self.ctx, lam_V, lam_Vhat, gv, gh)
         return gv, gh
 
-    def recover(self, dvh, with_dQ=False):
+    def recover(self, dvh, with_dQ=False, out=None):
         import torch
         m = self.mesh
-        dV = torch.empty((m.nK, 5, m.Nn), dtype=torch.float64, device=dvh.device)
+        dV = torch.empty((m.nK, 5, m.Nn), dtype=torch.float64, device=dvh.device) if out is None else out
         dQ = torch.empty((m.nK, 5, 3, m.Nn), dtype=torch.float64, device=dvh.device) if self.params.viscous else None
         mehdg_recover(self.ctx, dvh, dV, dQ)
         return (dV, dQ) if with_dQ else dV

@@ -60,3 +60,30 @@ def test_static_residual_rejects_oversized_problems():
     prm = M.mehdg_default_params()
     with pytest.raises(M.MehdgError, match="EINVAL"):
         M.mehdg_residual_static(prm, p, m, box, gid, 6 * nK, x, x, None, x, x, None, x)
+
+
+def test_static_residual_reports_nonphysical_state():
+    """beta = -v5 < 0 in one element: MEHDG_ENONPHYS, and the next call on a
+    physical state (the status words in the shared array start from zero
+    again) returns OK with the context residual's values"""
+    from paper_2507_22195_gb300 import mehdg as M
+    mesh = I.periodic_mesh(2, 2, 1, 0.0, 10.0)
+    st = I.make_state(mesh, "vortex", 1e-3, 22195, 22196, period=10.0)
+    dev = torch.device("cuda:0")
+    v, vh, vs = (torch.tensor(a, device=dev) for a in (st.v, st.vhat, st.vstar))
+    bad = v.clone()
+    bad[3, 4, :] = 0.5
+    prm = M.mehdg_default_params(flux=M.MEHDG_FLUX_ES, Mach=0.1)
+    box = torch.tensor(mesh.boxes, device=dev)
+    gid = torch.tensor(mesh.face_gid, device=dev)
+    RV = torch.empty((mesh.nK, 5, mesh.Nn), dtype=torch.float64, device=dev)
+    RH = torch.empty((mesh.n_global_faces, 5, mesh.n2), dtype=torch.float64, device=dev)
+    with pytest.raises(M.MehdgError, match="ENONPHYS"):
+        M.mehdg_residual_static(prm, mesh.p, mesh.m, box, gid, mesh.n_global_faces, bad, vh, None, vs, RV, None, RH)
+    M.mehdg_residual_static(prm, mesh.p, mesh.m, box, gid, mesh.n_global_faces, v, vh, None, vs, RV, None, RH)
+    ctx = M.Context(mesh, flux=M.MEHDG_FLUX_ES, prec=M.MEHDG_FP64, Mach=0.1)
+    ctx.set_state(v, vh, None, vs)
+    RV_ref, _, RH_ref = ctx.residual()
+    torch.cuda.synchronize()
+    assert rel(RV, RV_ref) < 1e-11 and rel(RH, RH_ref) < 1e-11
+    ctx.close()
