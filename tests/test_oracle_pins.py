@@ -198,6 +198,127 @@ def test_barth_scaling_at_equal_states():
             assert np.allclose(R @ np.diag(T) @ R.T, oracle.A0(v), rtol=1e-12, atol=1e-13)
 
 
+def _Fn_of_u(u, n, g=G):
+    """normal inviscid flux (eq. C5) written in conservative variables"""
+    rho, m, E = u[0], u[1:4], u[4]
+    V = m / rho
+    P = (g - 1.0) * (E - 0.5 * rho * V @ V)
+    vn = V @ n
+    return np.concatenate([[rho * vn], rho * V * vn + P * n, [(E + P) * vn]])
+
+
+def _jac_fd(f, x, h=1e-6):
+    """central-difference Jacobian, columns d f / d x_j"""
+    cols = []
+    for j in range(len(x)):
+        e = np.zeros(len(x)); e[j] = h * max(1.0, abs(x[j]))
+        cols.append((f(x + e) - f(x - e)) / (2 * e[j]))
+    return np.stack(cols, axis=1)
+
+
+def _An_eig(v, n):
+    """A_n = d(F.n)/du at the state v, from the conservative-variable flux
+    above, and its eigenvalues/eigenvectors sorted by eigenvalue (numpy)"""
+    u = oracle.u_of_v(v)
+    An = _jac_fd(lambda uu: _Fn_of_u(uu, n), u, 1e-7)
+    w, X = np.linalg.eig(An)
+    o = np.argsort(w.real)
+    return An, w.real[o], X.real[:, o]
+
+
+def _general_normals():
+    rng = np.random.default_rng(21)
+    out = normals()
+    for _ in range(3):
+        n = rng.normal(size=3); out.append(n / np.linalg.norm(n))
+    return out
+
+
+def test_kepes_eigenvectors_order_and_equal_state_dissipation():
+    """KEPES at equal states (eqs. KEPES3-KEPES5): the columns of R-bar are
+    right eigenvectors of the normal flux Jacobian A_n = d(F.n)/du with the
+    eigenvalues v_n - c, v_n, v_n, v_n, v_n + c in that order (A_n from the
+    conservative flux, its eigenvalues from a numerical eigendecomposition),
+    and |Lambda-bar| (theta = 0) holds the reading's |v_n| + c, |v_n|, |v_n|,
+    |v_n|, |v_n| + c, with c the spectral gap of A_n; the flux's dissipation
+    F_KEPES - F_EC at a small pressure-preserving jump equals
+    -1/2 R |Lambda| T R^T [[v]] with these parts."""
+    rng = np.random.default_rng(22)
+    for _ in range(8):
+        v = rand_state(rng)
+        rho, V, P = oracle.prim_of_v(v)
+        for n in _general_normals():
+            An, w, X = _An_eig(v, n)
+            vn = V @ n
+            c = 0.5 * (w[4] - w[0])                 # spectral gap of A_n
+            assert np.allclose(w, [vn - c, vn, vn, vn, vn + c], atol=1e-8)
+            assert abs(c - math.sqrt(G * P / rho)) < 1e-8
+            R, L, T = oracle.kepes_parts(v, v, n)
+            lam = np.array([vn - c, vn, vn, vn, vn + c])
+            assert np.allclose(An @ R, R @ np.diag(lam), atol=1e-7 * np.abs(R).max())
+            assert np.allclose(L, [abs(vn) + c, abs(vn), abs(vn), abs(vn), abs(vn) + c], rtol=1e-12)
+            # a jump of density and velocity at equal pressure: theta = 0
+            rho2, V2 = rho * (1 + 1e-3), V + 1e-3 * rng.uniform(-1, 1, 3)
+            vh = I.entropy_vars(np.array(rho2), [np.array(x) for x in V2], np.array(P)).astype(float)
+            R2, L2, T2 = oracle.kepes_parts(vh, v, n)
+            diss = oracle.flux_num(oracle.KEPES, vh, v, n) - oracle.flux_num(oracle.EC, vh, v, n)
+            dv = vh - v
+            assert np.allclose(diss, -0.5 * R2 @ np.diag(L2 * T2) @ R2.T @ dv, rtol=1e-9,
+                               atol=1e-12 * np.abs(diss).max())
+
+
+def test_kepes_hybrid_theta_from_pressure_ratio():
+    """|Lambda-bar| = (1 - theta)|lambda| + theta lambda_max with theta =
+    sqrt(|(P - P-hat)/(P + P-hat)|): under the reading |lambda_1| = |lambda_5|
+    = lambda_max = |v_n-bar| + c-bar, entries 1 and 5 stay lambda_max and the
+    middle ones equal |v_n-bar| + theta c-bar, so theta is recovered from the
+    parts and compared with the pressures; c-bar = sqrt(gamma P-bar / rho^ln)
+    with P-bar = rho-bar / beta-bar (eq. EC); a large pressure ratio drives
+    theta towards 1 (LF dissipation everywhere)."""
+    rng = np.random.default_rng(23)
+    for ratio in (1.0 + 1e-6, 1.3, 4.0, 1e4):
+        for _ in range(4):
+            rho, P = rng.uniform(0.5, 2.0), rng.uniform(0.4, 2.0)
+            V, Vh = rng.uniform(-0.3, 0.3, 3), rng.uniform(-0.3, 0.3, 3)
+            rhoh, Ph = rho * rng.uniform(0.8, 1.2), P * ratio
+            v = I.entropy_vars(np.array(rho), [np.array(x) for x in V], np.array(P)).astype(float)
+            vh = I.entropy_vars(np.array(rhoh), [np.array(x) for x in Vh], np.array(Ph)).astype(float)
+            for n in _general_normals():
+                R, L, T = oracle.kepes_parts(vh, v, n)
+                vnb = abs(0.5 * (V + Vh) @ n)
+                Pb = 0.5 * (rho + rhoh) / (0.5 * (rho / P + rhoh / Ph))
+                cb = math.sqrt(G * Pb / oracle.logmean(rho, rhoh))
+                theta = math.sqrt(abs((P - Ph) / (P + Ph)))
+                assert abs(L[0] - (vnb + cb)) < 1e-12 and abs(L[4] - (vnb + cb)) < 1e-12
+                assert np.allclose(L[1:4], vnb + theta * cb, rtol=1e-12)
+                if ratio > 1e3:
+                    assert np.all(L[1:4] > 0.97 * L[0])
+
+
+def test_es_sigma_is_the_spectral_radius_at_vhat():
+    """ES flux (eq. Flux_En_Inv): at equal states d F/dv - d F/dv-hat =
+    sigma A0 (the averages of F cancel), and at any pair of states
+    F - 1/2 (F(v-hat) + F(v)).n = -1/2 sigma(v-hat) A0(v-hat) [[v]], where
+    sigma(v-hat) = lambda_max = the spectral radius of A_n(v-hat) from a
+    numerical eigendecomposition (not a formula for the wave speed)."""
+    rng = np.random.default_rng(24)
+    for _ in range(6):
+        v = rand_state(rng)
+        vh = v + rng.uniform(-2e-2, 2e-2, 5)
+        for n in _general_normals():
+            _, w, _ = _An_eig(v, n)
+            sig = np.abs(w).max()
+            Jv = _jac_fd(lambda x: oracle.flux_num(oracle.ES, v, x, n), v, 1e-6)
+            Jh = _jac_fd(lambda x: oracle.flux_num(oracle.ES, x, v, n), v, 1e-6)
+            A0 = oracle.A0(v)
+            assert np.allclose(Jv - Jh, sig * A0, rtol=1e-6, atol=1e-7 * np.abs(A0).max())
+            _, wh, _ = _An_eig(vh, n)
+            sigh = np.abs(wh).max()
+            diss = oracle.flux_num(oracle.ES, vh, v, n) - 0.5 * (oracle.flux_phys(vh, n) + oracle.flux_phys(v, n))
+            assert np.allclose(diss, -0.5 * sigh * oracle.A0(vh) @ (vh - v), rtol=1e-7,
+                               atol=1e-9 * np.abs(diss).max())
+
+
 # ---------------------------------------------------------------- viscous
 def test_viscous_flux_dissipates_entropy_and_is_linear_in_q():
     """sum_j q_j . G_j = -q^T K q <= 0 (eq. entropy evolution diffuse) and
@@ -227,6 +348,93 @@ def test_viscous_flux_vanishes_for_rigid_rotation():
     q[0] = -beta * V @ gradV
     q[1:4] = beta * gradV
     assert np.abs(oracle.visc_flux(prm, v, q.ravel())).max() < 1e-15
+
+
+VPRM = dict(viscous=1, Re=1600.0, Mach=0.1, Pr=0.71)
+
+
+def _q_const_rho_P(V, gradV, rho, P):
+    """grad v at constant rho and P (eq. s222): dv1 = -beta V.grad V,
+    dv_{2..4} = beta grad V, dv5 = 0, as [5][3] with q[k][d] = dv_k/dx_d"""
+    beta = rho / P
+    q = np.zeros((5, 3))
+    q[0] = -beta * V @ gradV
+    q[1:4] = beta * gradV
+    return q
+
+
+def test_viscous_shear_stress_couette():
+    """Couette shear V = (a y, 0, 0) at uniform rho, P: tau_xy = tau_yx =
+    (Mach/Re) a (eq. C6 with mu/Re_c = Mach/Re), every other stress 0, no
+    heat flux; G = -[0, tau, tau V - phi] (eq. C5), so G_{x,y} = G_{y,x} =
+    -(Mach/Re) a and the energy row -(tau V)_y = -(Mach/Re) a^2 y"""
+    prm = oracle.params(**VPRM)
+    mu = VPRM["Mach"] / VPRM["Re"]
+    rho, P, a, y = 1.1, 0.8, 0.37, 0.6
+    V = np.array([a * y, 0.0, 0.0])
+    gradV = np.zeros((3, 3)); gradV[0, 1] = a
+    v = I.entropy_vars(np.array(rho), [np.array(c) for c in V], np.array(P)).astype(float)
+    Gv = oracle.visc_flux(prm, v, _q_const_rho_P(V, gradV, rho, P).ravel())
+    exp = np.zeros((5, 3))
+    exp[1, 1] = -mu * a          # momentum x, flux in y
+    exp[2, 0] = -mu * a          # momentum y, flux in x
+    exp[4, 1] = -mu * a * a * y  # energy, flux in y
+    assert np.allclose(Gv, exp, rtol=1e-12, atol=1e-18)
+
+
+def test_viscous_bulk_coefficient_uniaxial_stretch():
+    """V = (b x, 0, 0): div V = b, so tau_xx = mu (2 + lambda) b and
+    tau_yy = tau_zz = mu lambda b; lambda = -2/3 (Stokes) gives 4/3 mu b and
+    -2/3 mu b (any other bulk coefficient fails)"""
+    prm = oracle.params(**VPRM)
+    mu = VPRM["Mach"] / VPRM["Re"]
+    rho, P, b, x = 0.9, 1.3, 0.21, -0.4
+    V = np.array([b * x, 0.0, 0.0])
+    gradV = np.zeros((3, 3)); gradV[0, 0] = b
+    v = I.entropy_vars(np.array(rho), [np.array(c) for c in V], np.array(P)).astype(float)
+    Gv = oracle.visc_flux(prm, v, _q_const_rho_P(V, gradV, rho, P).ravel())
+    tau = np.diag([4.0 / 3.0 * mu * b, -2.0 / 3.0 * mu * b, -2.0 / 3.0 * mu * b])
+    exp = np.zeros((5, 3))
+    exp[1:4] = -tau
+    exp[4] = -(tau @ V)
+    assert np.allclose(Gv, exp, rtol=1e-12, atol=1e-18)
+
+
+def test_viscous_heat_flux_linear_temperature():
+    """At rest with uniform P and T = T0 + c x (gamma P = rho T): tau = 0 and
+    G_energy = phi = -kappa dT/dx e_x with kappa = (Mach/Re) / ((gamma-1) Pr)
+    (the reading of eq. C6: mu c_p / Pr, c_p = 1/(gamma-1)); grad v by
+    fourth-order differences of eq. s222 along x"""
+    prm = oracle.params(**VPRM)
+    kap = VPRM["Mach"] / VPRM["Re"] / ((G - 1.0) * VPRM["Pr"])
+    P, T0, c, x0 = 0.75, 1.05, 0.3, 0.2
+
+    def vx(x):
+        T = T0 + c * x
+        rho = G * P / T
+        return I.entropy_vars(np.array(rho), [np.array(0.0)] * 3, np.array(P)).astype(float)
+
+    h = 1e-3
+    dvdx = (8 * (vx(x0 + h) - vx(x0 - h)) - (vx(x0 + 2 * h) - vx(x0 - 2 * h))) / (12 * h)
+    q = np.zeros((5, 3)); q[:, 0] = dvdx
+    Gv = oracle.visc_flux(prm, vx(x0), q.ravel())
+    exp = np.zeros((5, 3)); exp[4, 0] = -kap * c
+    assert np.allclose(Gv, exp, rtol=1e-9, atol=1e-15)
+
+
+def test_viscous_face_penalty_sigma_vis():
+    """eq. Flux_En_Vis: with q = 0 the viscous face flux adds exactly
+    -1/2 sigma^vis [[v]], sigma^vis = (1/Re) diag(0, 1, 1, 1,
+    1/((gamma-1) M^2 Pr)), component by component, to the inviscid flux"""
+    rng = np.random.default_rng(25)
+    pv, pi = oracle.params(flux=oracle.ES, **VPRM), oracle.params(flux=oracle.ES, Mach=VPRM["Mach"])
+    Re, M, Pr = VPRM["Re"], VPRM["Mach"], VPRM["Pr"]
+    sv = np.array([0.0, 1.0, 1.0, 1.0, 1.0 / ((G - 1.0) * M * M * Pr)]) / Re
+    for _ in range(10):
+        v, vh = rand_state(rng), rand_state(rng)
+        for n in normals():
+            d = oracle.face_flux(pv, vh, v, np.zeros(15), n) - oracle.face_flux(pi, vh, v, None, n)
+            assert np.allclose(d, -0.5 * sv * (vh - v), rtol=1e-10, atol=1e-16)
 
 
 # ---------------------------------------------------------------- residual
