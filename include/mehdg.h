@@ -180,6 +180,14 @@ int mehdg_solve_condensed(mehdg_ctx* ctx, const double* bhat, double* dVhat, dou
  * Also copies, if iters != NULL, the refinement sweeps used per element. */
 int mehdg_status(mehdg_ctx* ctx, int32_t* per_K_status, int32_t* iters);
 
+/* The per-element status words (and, if iters != NULL, the refinement
+ * sweeps) of the last call, copied on `stream` into the DEVICE arrays
+ * per_K_status [nK] and iters [nK]: asynchronous, valid after a
+ * synchronisation of that stream (the form Algorithm 1's local steps need
+ * when the status stays on the GPU).  The work of the last call must have
+ * been enqueued on the same stream or be ordered before it. */
+int mehdg_status_device(mehdg_ctx* ctx, int32_t* per_K_status, int32_t* iters, void* stream);
+
 /* Message of the last error of this context (static storage of ctx). */
 const char* mehdg_last_error(const mehdg_ctx* ctx);
 

@@ -52,7 +52,7 @@ void free_mesh(mehdg_ctx* c) {
     if (c->zs_ev_out) { cudaEventDestroy(c->zs_ev_out); c->zs_ev_out = nullptr; }
     if (c->lu_stream) { cudaStreamDestroy(c->lu_stream); c->lu_stream = nullptr; }
     if (c->h_cnt) { cudaFreeHost(c->h_cnt); c->h_cnt = nullptr; }
-    c->nK = 0; c->condensed = false;
+    c->nK = 0; c->condensed = false; c->lu_graph_failed = false;
 }
 
 ResidualArgs base_args(mehdg_ctx* c) {
@@ -80,21 +80,43 @@ cudaError_t factor_all(mehdg_ctx* c, const LUPlan& P, cudaStream_t st) {
     // MEHDG_NO_GRAPH=1: direct launches (e.g. under a kernel profiler that
     // replays launches one by one)
     static const bool no_graph = [] { const char* e = std::getenv("MEHDG_NO_GRAPH"); return e && e[0] == '1'; }();
-    if (c->prof.on || no_graph) return lu_factor(P, st);
+    if (c->prof.on || no_graph || c->lu_graph_failed) return lu_factor(P, st);
     cudaError_t e;
     if (!c->lu_graph) {
         if (!c->lu_stream && (e = cudaStreamCreateWithFlags(&c->lu_stream, cudaStreamNonBlocking)) != cudaSuccess) return e;
         if (!c->lu_ev_in && (e = cudaEventCreateWithFlags(&c->lu_ev_in, cudaEventDisableTiming)) != cudaSuccess) return e;
         if (!c->lu_ev_out && (e = cudaEventCreateWithFlags(&c->lu_ev_out, cudaEventDisableTiming)) != cudaSuccess) return e;
         const long long before = g_mehdg_launches.load();
-        if ((e = cudaStreamBeginCapture(c->lu_stream, cudaStreamCaptureModeRelaxed)) != cudaSuccess) return e;
-        const cudaError_t ef = lu_factor(P, c->lu_stream);
+        // A capture can fail or be invalidated from outside (a tool that
+        // serialises launches, another thread's illegal call during the
+        // capture).  Then the context stops capturing and launches the same
+        // kernels directly, now and on later calls (lu_graph_failed).
         cudaGraph_t g = nullptr;
-        e = cudaStreamEndCapture(c->lu_stream, &g);
-        if (ef != cudaSuccess || e != cudaSuccess) { if (g) cudaGraphDestroy(g); return ef != cudaSuccess ? ef : e; }
-        e = cudaGraphInstantiate(&c->lu_graph, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) { c->lu_graph = nullptr; return e; }
+        cudaError_t ef = cudaStreamBeginCapture(c->lu_stream, cudaStreamCaptureModeRelaxed);
+        if (ef == cudaSuccess) {
+            ef = lu_factor(P, c->lu_stream);
+            e = cudaStreamEndCapture(c->lu_stream, &g);
+            if (ef == cudaSuccess) ef = e;
+        }
+        if (ef == cudaSuccess) {
+            ef = cudaGraphInstantiate(&c->lu_graph, g, 0);
+            if (ef != cudaSuccess) c->lu_graph = nullptr;
+        }
+        if (g) cudaGraphDestroy(g);
+        if (ef != cudaSuccess) {
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(c->lu_stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+                cudaGraph_t g2 = nullptr;
+                cudaStreamEndCapture(c->lu_stream, &g2);
+                if (g2) cudaGraphDestroy(g2);
+            }
+            (void)cudaGetLastError();                   // capture errors are not sticky: clear the record
+            g_mehdg_launches = before;                  // nothing of the failed capture ran
+            c->lu_graph_failed = true;
+            fprintf(stderr, "mehdg: LU graph capture failed (%s); launching its kernels directly\n",
+                    cudaGetErrorString(ef));
+            return lu_factor(P, st);
+        }
         c->lu_graph_launches = g_mehdg_launches.load() - before;
         g_mehdg_launches -= c->lu_graph_launches;      // counted when they run
     }
@@ -446,6 +468,17 @@ int mehdg_status(mehdg_ctx* c, int32_t* per_K_status, int32_t* iters) {
     TRY(cudaDeviceSynchronize());
     if (per_K_status) TRY(cudaMemcpy(per_K_status, c->d_status, sizeof(int32_t) * c->nK, cudaMemcpyDeviceToHost));
     if (iters) TRY(cudaMemcpy(iters, c->d_iters, sizeof(int32_t) * c->nK, cudaMemcpyDeviceToHost));
+    return MEHDG_OK;
+}
+
+int mehdg_status_device(mehdg_ctx* c, int32_t* per_K_status, int32_t* iters, void* stream) {
+    if (!c) return MEHDG_EINVAL;
+    if (c->nK == 0) return MEHDG_ESTATE;
+    if (!per_K_status && !iters) return MEHDG_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (per_K_status)
+        TRY(cudaMemcpyAsync(per_K_status, c->d_status, sizeof(int32_t) * c->nK, cudaMemcpyDeviceToDevice, st));
+    if (iters) TRY(cudaMemcpyAsync(iters, c->d_iters, sizeof(int32_t) * c->nK, cudaMemcpyDeviceToDevice, st));
     return MEHDG_OK;
 }
 

@@ -193,6 +193,7 @@ struct mehdg_ctx {
     cudaEvent_t lu_ev_in = nullptr, lu_ev_out = nullptr;
     cudaEvent_t zs_ev_in = nullptr, zs_ev_out = nullptr;   // zeroing of S beside the residual
     long long lu_graph_launches = 0;    // kernels in the graph
+    bool lu_graph_failed = false;       // capture failed once: the LU is launched directly
     void* d_krylov = nullptr;           // GMRES basis and scratch of the trace solve (first use)
     size_t krylov_bytes = 0;
     Prof prof;

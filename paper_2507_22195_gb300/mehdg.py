@@ -27,7 +27,7 @@ EXPORTED = ["mehdg_default_params", "mehdg_create", "mehdg_set_mesh", "mehdg_set
             "mehdg_status", "mehdg_last_error", "mehdg_destroy", "mehdg_profile_enable",
             "mehdg_profile_read", "mehdg_launch_count", "mehdg_test_trailing_update",
             "mehdg_test_trailing_work_bytes", "mehdg_residual_static", "mehdg_solve_condensed",
-            "mehdg_residual_vjp"]
+            "mehdg_residual_vjp", "mehdg_status_device"]
 
 
 class mehdg_params(C.Structure):
@@ -63,6 +63,7 @@ def load(path: str | None = None):
     L.mehdg_apply_condensed.argtypes = [_vp, _vp, _vp, _vp]
     L.mehdg_recover.argtypes = [_vp, _vp, _vp, _vp, _vp]
     L.mehdg_status.argtypes = [_vp, _vp, _vp]
+    L.mehdg_status_device.argtypes = [_vp, _vp, _vp, _vp]
     L.mehdg_solve_condensed.argtypes = [_vp, _vp, _vp, C.c_double, C.c_int, C.c_int, _vp, _vp, _vp]
     L.mehdg_residual_vjp.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
     L.mehdg_last_error.argtypes = [_vp]
@@ -173,6 +174,15 @@ def mehdg_status(ctx, nK):
     it = np.zeros(nK, dtype=np.int32)
     _check(ctx, load().mehdg_status(ctx, st.ctypes.data, it.ctypes.data), "mehdg_status")
     return st, it
+
+
+def mehdg_status_device(ctx, status, iters=None, stream=None):
+    """status, iters: int32 CUDA tensors [nK], filled asynchronously on the stream"""
+    import torch
+    for t in (status, iters):
+        assert t is None or (t.is_cuda and t.dtype == torch.int32 and t.is_contiguous())
+    _check(ctx, load().mehdg_status_device(ctx, status.data_ptr(), None if iters is None else iters.data_ptr(),
+                                           _stream(stream)), "mehdg_status_device")
 
 
 def mehdg_last_error(ctx) -> str:

@@ -13,8 +13,11 @@ counting every face once.
 
 Trace vectors are torch tensors [faces][5][n^2] in the rank's local face
 numbering (that of `inputs.sub_mesh`), on any device. The exchange uses
-torch.distributed: gloo on the host, NCCL between GPUs. It moves 5 n^2
-values per shared face and does no arithmetic of the method beyond the sums.
+torch.distributed point-to-point operations posted together as one batch
+(batch_isend_irecv), so that no rank's send waits behind its own receive;
+it moves 5 n^2 values per shared face and does no arithmetic of the method
+beyond the sums.  It is tested with gloo ranks on the host; the NCCL path
+between GPUs has not been run (every run available here has one GPU).
 """
 from __future__ import annotations
 
@@ -85,16 +88,16 @@ class Shard:
         if dist is None or not self.peers:
             return t
         import torch
-        sends, recvs, reqs = [], [], []
+        sends, recvs, ops = [], [], []
         for r, idx in self.peers.items():
             ii = torch.as_tensor(idx, device=t.device)
             buf = t.index_select(0, ii).contiguous()
             got = torch.empty_like(buf)
             sends.append(buf)
             recvs.append((ii, got))
-            reqs.append(dist.isend(buf, dst=r))
-            reqs.append(dist.irecv(got, src=r))
-        for q in reqs:
+            ops.append(dist.P2POp(dist.isend, buf, r))
+            ops.append(dist.P2POp(dist.irecv, got, r))
+        for q in dist.batch_isend_irecv(ops):
             q.wait()
         for ii, got in recvs:
             t.index_add_(0, ii, got)
@@ -105,7 +108,7 @@ class Shard:
         (by the lowest rank that touches it)."""
         import torch
         own = torch.as_tensor(self.owned, device=a.device)
-        s = (a[own] * b[own]).sum().reshape(1).to(torch.float64)
+        s = (a[own].to(torch.float64) * b[own].to(torch.float64)).sum().reshape(1)
         if dist is not None and self.world > 1:
             dist.all_reduce(s, op=dist.ReduceOp.SUM)
         return float(s.item())

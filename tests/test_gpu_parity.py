@@ -303,6 +303,11 @@ def test_nonphysical_state_reports_status():
     ctx.residual()
     stat, _ = ctx.status()
     assert stat[3] == -2 and (np.delete(stat, 3) == 0).all()
+    # the same words through the device form, on the current stream
+    d = torch.full((mesh.nK,), 7, dtype=torch.int32, device="cuda:0")
+    M().mehdg_status_device(ctx.ctx, d)
+    torch.cuda.current_stream().synchronize()
+    assert (d.cpu().numpy() == stat).all()
     ctx.close()
 
 

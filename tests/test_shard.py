@@ -1,7 +1,7 @@
-"""The sharded trace system on the host: two (and three) gloo ranks, each
-condensing its own slab of a periodic mesh with the oracle; after the
-shared-face exchange every rank's b-hat and A-hat x equal the whole mesh's on
-its faces, and the distributed dot product equals the global one (eq. s32c,
+"""The sharded trace system on the host: two, three and four gloo ranks,
+each condensing its own slab of a periodic mesh with the oracle; after the
+shared-face exchange every rank's R_V-hat, b-hat and A-hat x equal the whole
+mesh's on its faces, and the distributed dot product equals the global one (eq. s32c,
 Algorithm 1: sums over the elements on both sides of every face)."""
 import os
 import socket
@@ -46,7 +46,9 @@ def _rank(rank, world, port, viscous, out):
         y = oracle.assemble_Ahat(sh.mesh, Ahats) @ x.ravel()
         y = sh.sum_shared(torch.tensor(y.reshape(x.shape)), dist)
         d = sh.dot(torch.tensor(x), y, dist)
-        out[rank] = (sh.gfaces, bh.numpy(), y.numpy(), d, {r: len(v) for r, v in sh.peers.items()})
+        _, _, rh = oracle.residual_mesh(prm, sh.mesh, ls)
+        rh = sh.sum_shared(torch.tensor(rh), dist)
+        out[rank] = (sh.gfaces, bh.numpy(), y.numpy(), d, {r: len(v) for r, v in sh.peers.items()}, rh.numpy())
     finally:
         dist.destroy_process_group()
 
@@ -64,13 +66,15 @@ def test_sharded_condensation_matches_whole_mesh(world, viscous):
     bh_all, Ahats = oracle.condense_mesh(prm, mesh, st, want_Ahat=True)
     x = I.random_direction(st.vhat.shape, 91, 1.0)
     y_all = (oracle.assemble_Ahat(mesh, Ahats) @ x.ravel()).reshape(x.shape)
+    _, _, rh_all = oracle.residual_mesh(prm, mesh, st)
     res = _run(world, viscous)
     assert sorted(res) == list(range(world))
     seen = np.zeros(mesh.n_global_faces, dtype=int)
-    for rank, (gf, bh, y, d, peers) in res.items():
-        scale_b, scale_y = np.abs(bh_all).max(), np.abs(y_all).max()
+    for rank, (gf, bh, y, d, peers, rh) in res.items():
+        scale_b, scale_y, scale_r = np.abs(bh_all).max(), np.abs(y_all).max(), np.abs(rh_all).max()
         assert np.abs(bh - bh_all[gf]).max() <= 1e-12 * scale_b, rank
         assert np.abs(y - y_all[gf]).max() <= 1e-12 * scale_y, rank
+        assert np.abs(rh - rh_all[gf]).max() <= 1e-12 * scale_r, rank
         assert d == pytest.approx(float(np.sum(x * y_all)), rel=1e-12)
         assert peers, "every slab of a periodic mesh borders another rank"
         seen[gf] += 1
