@@ -338,6 +338,80 @@ def viscous_wave(block, dev, barrier, M, steps=2):
     return out
 
 
+def uneven_batch(nK, dev, barrier, M, sample_per_group=2):
+    """configs[4]: nK macro-elements with p in {1..4} and m in {2, 3, 4}
+    drawn with seed 22199, each a TGV-like field with its own Mach number
+    M0 ~ U(0.1, 0.3) plus U(-1e-2, 1e-2), viscous (Re 1600, Pr 0.71), ES flux,
+    split BF16 with FP64 refinement: autotuned, then one timed condensation of
+    the whole batch (groups streamed in waves when they exceed the memory
+    budget); beside it the FP64 GPU path and the same mixed path on a seeded
+    sample of every group the FP64 viscous Jacobian supports (p <= 3)"""
+    import numpy as np
+    import torch
+    from paper_2507_22195_gb300 import inputs as I
+    mesh = I.uneven_batch(nK, 22199)
+    st = I.make_uneven_state(mesh, 1e-2, 22200, 22201, 22202, M0_range=(0.1, 0.3), viscous=True)
+    kw = dict(flux=1, Mach=0.1, Re=1600.0, Pr=0.71, viscous=1)
+    d = torch.device(dev)
+    w = [torch.tensor(x, device=d) for x in (st.v, st.vhat, st.q, st.vstar)]
+    ctx = M.BatchContext(mesh, prec=PREC["bf16x3"], **kw)
+    ctx.set_state(*w)
+    t0 = time.perf_counter()
+    ctx.autotune(trial_max=16)
+    torch.cuda.synchronize()
+    tune_s = time.perf_counter() - t0
+    bh = torch.empty(int(mesh.toff[-1]), dtype=torch.float64, device=d)
+    ms = timed_condense(ctx, bh, 1, barrier)
+    stat, it = ctx.status()
+    rep = ctx.report()
+    ctx.close()
+    del w
+    torch.cuda.empty_cache()
+    # FP64 and mixed on a seeded sample of each group with p <= 3
+    r = np.random.Generator(np.random.PCG64(22203))
+    Ks = []
+    for key in sorted(set(zip(mesh.p.tolist(), mesh.m.tolist()))):
+        if key[0] > 3:
+            continue
+        ids = np.flatnonzero((mesh.p == key[0]) & (mesh.m == key[1]))
+        Ks += sorted(r.choice(ids, size=min(sample_per_group, len(ids)), replace=False).tolist())
+    sub = I.UnevenMesh(mesh.p[Ks], mesh.m[Ks], mesh.boxes[Ks], np.arange(6 * len(Ks), dtype=np.int64).reshape(-1, 6),
+                       6 * len(Ks))
+    voff, toff = mesh.voff, mesh.toff
+    pick = lambda a, off, sc: np.concatenate([a[sc * off[K]:sc * off[K + 1]] for K in Ks])
+    pickt = lambda a: np.concatenate([a[toff[g]:toff[g + 1]] for K in Ks for g in mesh.face_gid[K]])
+    ss = I.State(v=pick(st.v, voff, 1), vhat=pickt(st.vhat), q=pick(st.q, voff, 3), vstar=pick(st.vstar, voff, 1))
+    ws = [torch.tensor(x, device=d) for x in (ss.v, ss.vhat, ss.q, ss.vstar)]
+    outs = {}
+    for pr in ("fp64", "bf16x3"):
+        c = M.BatchContext(sub, prec=PREC[pr], **kw)
+        c.set_state(*ws)
+        b = c.condense()
+        msp = timed_condense(c, b, 1, barrier)
+        s2, _ = c.status()
+        outs[pr] = (b.cpu().numpy(), msp, bool((s2 == 0).all()))
+        c.close()
+    tf = sub.toff
+    errs = [np.linalg.norm(outs["bf16x3"][0][tf[6 * i]:tf[6 * i + 6]] - outs["fp64"][0][tf[6 * i]:tf[6 * i + 6]]) /
+            np.linalg.norm(outs["fp64"][0][tf[6 * i]:tf[6 * i + 6]]) for i in range(len(Ks))]
+    groups = {f"p{g['p']}m{g['m']}": {"elements": g["elements"], "wave": g["wave"], "leaf_ctas": g["leaf_ctas"],
+                                      "solve_ctas": g["solve_ctas"],
+                                      "trials_ms": [round(t["ms"], 3) for t in g.get("trials", [])]}
+              for g in rep["groups"]}
+    return {"workload": f"{nK} independent macro-elements, p in {{1..4}} x m in {{2,3,4}} (seed 22199), TGV-like "
+                        f"fields M0 ~ U(0.1,0.3) + U(-1e-2,1e-2), viscous Re=1600 Pr=0.71, ES, split bf16 x3 + f64 "
+                        f"refinement, autotuned",
+            "value": nK / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": 1,
+            "status_ok": bool((stat == 0).all()), "refine_iters": sorted(set(int(x) for x in it)),
+            "resident": rep["resident"], "budget_gb": rep["budget_bytes"] / 1e9, "autotune_s": tune_s,
+            "groups": groups,
+            "fp64_gpu": {"value": len(Ks) / (outs["fp64"][1] / 1e3), "unit": UNIT,
+                         "mixed_same_sample": len(Ks) / (outs["bf16x3"][1] / 1e3),
+                         "sample": f"{len(Ks)} elements: {sample_per_group} per (p, m) group with p <= 3 (seed 22203)",
+                         "err_bhat_mixed_vs_fp64_max_per_element": float(max(errs)),
+                         "status_ok": outs["fp64"][2] and outs["bf16x3"][2]}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -352,6 +426,8 @@ def main():
     ap.add_argument("--no-fp64-full", action="store_true", help="skip the FP64 GPU path on the whole workload")
     ap.add_argument("--viscous-block", type=int, default=7,
                     help="block^3 elements of the viscous TGV timed beside the headline (0: skip)")
+    ap.add_argument("--uneven", type=int, default=4096,
+                    help="elements of the uneven (p, m) batch timed beside the headline (0: skip)")
     ap.add_argument("--cpu-sample", type=int, default=-1, help="elements for the CPU oracle baseline (-1: one per core)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--once", action="store_true", help="one condense after --warmup ones, no timing (for profilers)")
@@ -531,6 +607,10 @@ def main():
     visc = None
     if a.workload == "tgv_inviscid" and a.viscous_block > 0 and world == 1:
         visc = viscous_wave(a.viscous_block, dev, barrier, M)
+    torch.cuda.empty_cache()
+    unev = None
+    if a.workload == "tgv_inviscid" and a.uneven > 0 and world == 1:
+        unev = uneven_batch(a.uneven, dev, barrier, M)
 
     if rank == 0:
         out = {
@@ -555,6 +635,7 @@ def main():
             "phases_ms_per_step": {k: round(vv["ms"] / a.steps, 3) for k, vv in prof.items()},
             "fp64_gpu": fp,
             "viscous_tgv": visc,
+            "uneven_batch": unev,
             "recover": rec,
         }
         print(json.dumps(out))

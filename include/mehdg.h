@@ -107,9 +107,21 @@ void mehdg_default_params(mehdg_params* prm);
 /* Create a context.  prm: host pointer, copied.  *out receives the handle. */
 int mehdg_create(mehdg_ctx** out, const mehdg_params* prm);
 
-/* Mesh (Sec. 3.1): nK macro-elements, all with the same degree p (1..4) and
- * micro-element count m per direction (p[], m[]: host arrays of length nK;
- * mixed values return MEHDG_EINVAL).  box: host [nK][6] = x0 y0 z0 x1 y1 z1.
+/* Mesh (Sec. 3.1): nK macro-elements of degree p[K] (1..4) and micro-element
+ * count m[K] per direction (p[], m[]: host arrays of length nK).  When they
+ * differ between elements the context becomes a BATCH context: elements are
+ * grouped by (p, m) and each group runs through its own uniform workspaces
+ * (groups in order of decreasing cost per element, 2/3 N_v^3 dominating);
+ * state and trace arrays are then flattened (element K's [5][Nn(K)] block at
+ * voff[K], face g's [5][n_g^2] block at toff[g]; see mehdg_batch_layout), a
+ * face shared by two elements must join equal n = m p + 1, and the
+ * workspaces of all groups must fit 60 % of the free device memory for the
+ * factors to be kept (otherwise condense streams each group in balanced
+ * waves of elements that fit, keeps no factors, and apply/recover/solve
+ * return MEHDG_ESTATE; MEHDG_BATCH_BUDGET_MB in the environment sets another
+ * budget, MEHDG_FORCE_BATCH=1 takes this path for a uniform mesh too).  The
+ * residual VJP is not available for batch contexts.
+ * box: host [nK][6] = x0 y0 z0 x1 y1 z1.
  * face_gid: host [nK][6], global face of each local face, in
  * [0, n_global_faces); a global face used by two elements couples them
  * (interior face), one used once is an unshared face.  Allocates the device
@@ -159,6 +171,50 @@ int mehdg_recover(mehdg_ctx* ctx, const double* dVhat, double* dV, double* dQ, v
 int mehdg_residual_vjp(mehdg_ctx* ctx, const double* lam_V, const double* lam_Vhat, double* g_v,
                        double* g_vhat, void* stream);
 
+/* Adjoint (transposed) condensation of the Newton system of eq. R1, for the
+ * VJP through a Newton step (Euler contexts of one element type; needs a
+ * prior condense, whose LU factors of S = A_vv it reuses).  The transposed
+ * system J^T (lam_V, lam_Vhat) = (g_V, g_Vhat) condenses like eqs. R2-R5
+ * with every block transposed:
+ *   condense_adjoint : bhat_a = g_Vhat - A_v,vhat^T S^-T g_V   (g_Vhat may be NULL = 0)
+ *   apply_..._adjoint: y = A-hat^T x = A_vhat,vhat^T x - A_v,vhat^T S^-T A_vhat,v^T x
+ *   solve_..._adjoint: GMRES on A-hat^T x = bhat_a (arguments and returns as
+ *                      mehdg_solve_condensed)
+ *   recover_adjoint  : lam_V = S^-T (g_V - A_vhat,v^T lam_Vhat)
+ * DEVICE arrays: g_V, lam_V [nK][5][Nn]; g_Vhat, bhat_a, x, y, lam_Vhat
+ * [G][5][n^2].  S^-T is applied with the stored factors (transposed solve)
+ * and refined in FP64 against the exact product S^T x (the residual's VJP),
+ * to refine_tol, like the forward solves; every other transposed block
+ * product is a VJP of the residual at the state.  MEHDG_EINVAL for viscous or
+ * batch contexts, MEHDG_ESTATE before condense. */
+int mehdg_condense_adjoint(mehdg_ctx* ctx, const double* g_V, const double* g_Vhat, double* bhat_a, void* stream);
+int mehdg_apply_condensed_adjoint(mehdg_ctx* ctx, const double* x, double* y, void* stream);
+int mehdg_solve_condensed_adjoint(mehdg_ctx* ctx, const double* bhat_a, double* x, double rtol, int restart,
+                                  int max_iter, int* iters, double* relres, void* stream);
+int mehdg_recover_adjoint(mehdg_ctx* ctx, const double* g_V, const double* lam_Vhat, double* lam_V, void* stream);
+
+/* Vector-Jacobian product through nsteps pseudo-time Newton steps (Sec. 6.1,
+ * eqs. C312, C31223) with a fixed step tau (Euler contexts of one element
+ * type, created with the stage term).  Forward: from the state (v, vhat)
+ * (DEVICE, updated in place to the final iterate), step k solves J(s_k) d_k
+ * = -R(s_k) with v* = v_k by condense, GMRES (lin_rtol, restart, max_iter as
+ * mehdg_solve_condensed) and recover, and s_{k+1} = s_k + d_k.  Reverse:
+ * given the cotangent (gbar_v [nK][5][Nn], gbar_vhat [G][5][n^2] or NULL = 0)
+ * of the final state, for k = nsteps-1 .. 0
+ *   lam = J(s_k)^-T gbar            (mehdg_condense_adjoint, _solve_, _recover_)
+ *   gbar -= J_steady(s_k)^T lam + (d/de J(s_k + e d_k)^T lam)|e=0
+ * where J_steady is the Jacobian without the stage term (the stage term's
+ * derivatives in v and v* = v cancel) and the last term, the transposed
+ * second derivative along the step, is the central difference of the
+ * residual VJP at s_k +- h d_k with v* = v_k fixed, h = fd_step max|s_k| /
+ * max|d_k|.  The result is the cotangent (g_v0, g_vhat0) of the initial state
+ * (DEVICE, same layouts).  Allocates the trajectory (2 nsteps + 8 state
+ * vectors) for the call.  On return the context holds no state (call
+ * set_state before the next residual or condense). */
+int mehdg_pseudo_time_newton_vjp(mehdg_ctx* ctx, double* v, double* vhat, int nsteps, double tau, double lin_rtol,
+                                 int restart, int max_iter, const double* gbar_v, const double* gbar_vhat,
+                                 double* g_v0, double* g_vhat0, double fd_step, void* stream);
+
 /* Global trace solve of Algorithm 1: dVhat with sum_K A-hat^K dVhat = bhat
  * (eq. R5 summed over the elements), by restarted GMRES(restart) without a
  * preconditioner, matrix-free through mehdg_apply_condensed (needs a prior
@@ -174,6 +230,57 @@ int mehdg_residual_vjp(mehdg_ctx* ctx, const double* lam_V, const double* lam_Vh
  * Synchronises the stream at every Arnoldi step. */
 int mehdg_solve_condensed(mehdg_ctx* ctx, const double* bhat, double* dVhat, double rtol, int restart,
                           int max_iter, int* iters, double* relres, void* stream);
+
+/* Step size of the stage term (u(v) - u(v*)) / dt of eq. C242 (and of the
+ * pseudo-time term of Sec. 6.1): dt > 0.  The next condense uses it; a
+ * previous condensation is invalidated (apply/recover return MEHDG_ESTATE
+ * until the next condense). */
+int mehdg_set_dt(mehdg_ctx* ctx, double dt);
+
+/* Inexact Newton with pseudo-transient continuation (Sec. 6.1, eqs.
+ * C31221-C31223), nsteps steps on the state (v [nK][5][Nn], vhat
+ * [G][5][n^2], q [nK][5][3][Nn] or NULL for Euler: DEVICE arrays, updated in
+ * place).  Step k: v* = v_k, stage term (u(v) - u(v*)) / tau_k; condense,
+ * global trace solve (restarted GMRES(restart), relative tolerance lin_rtol,
+ * at most max_iter products, as mehdg_solve_condensed), recover; v += dV,
+ * vhat += dVhat, q += dQ.  tau_0 = tau_init, tau_{k+1} = min(tau_max, tau_k
+ * ||R_k|| / ||R_{k+1}||) with ||R|| the 2-norm of the steady residual (R_V,
+ * R_Vhat and R_Q) at the iterate.  HOST outputs (may be NULL): res_norms
+ * [nsteps+1] (||R|| before the first and after every step), taus [nsteps],
+ * lin_iters [nsteps] (GMRES products).  Needs a context created with
+ * time_term = 1; its dt is restored on return and its state is left at the
+ * final iterate (with v* = v, in a buffer of the context).  Allocates its
+ * workspace on the first call (kept in the context).  Returns the first
+ * failing step's code (MEHDG_ENOCONV from the trace solve, MEHDG_ENONPHYS
+ * for a non-finite residual). */
+int mehdg_pseudo_time_newton(mehdg_ctx* ctx, double* v, double* vhat, double* q, int nsteps, double tau_init,
+                             double tau_max, double lin_rtol, int restart, int max_iter, double* res_norms,
+                             double* taus, int* lin_iters, void* stream);
+
+/* Batch contexts (elements of uneven p, m; see mehdg_set_mesh): the offsets
+ * of the flattened arrays, HOST int64 voff [nK+1] (element K's [5][Nn(K)]
+ * block of v, v*, R_V, dV starts at voff[K]; its [5][3][Nn(K)] block of q,
+ * R_Q, dQ at 3 voff[K]) and toff [n_global_faces+1] (face g's [5][n_g^2]
+ * block of every trace vector starts at toff[g]).  Either may be NULL.
+ * MEHDG_EINVAL for a uniform context.  (No counterpart in the paper, whose
+ * elements share one p and m; it describes the layout of the batch.) */
+int mehdg_batch_layout(mehdg_ctx* ctx, int64_t* voff, int64_t* toff);
+
+/* Autotuner of a batch context (after set_state): for every (p, m) group,
+ * times one condensation of its first min(trial_max, wave) elements for each
+ * candidate LU launch shape (leaf-panel CTAs per SM 1 or 2, then CTAs per
+ * element in the solves 1, 2, 4, 8 with the better leaf; one untimed
+ * warm-up each), keeps the fastest, and records every trial (read with
+ * mehdg_batch_report).  Later condensations use the choices.  Invalidates a
+ * previous condensation. */
+int mehdg_batch_autotune(mehdg_ctx* ctx, int64_t trial_max, void* stream);
+
+/* JSON record of a batch context: resident or streamed, memory budget, and
+ * per group p, m, elements, wave size, cost estimate, bytes per element, the
+ * launch choices and the autotuner's trials.  Writes at most len bytes
+ * (NUL-terminated) into buf (may be NULL) and returns the record's length,
+ * or MEHDG_EINVAL for a uniform context. */
+int mehdg_batch_report(mehdg_ctx* ctx, char* buf, size_t len);
 
 /* Copy the per-element status words (0 or a negative code above) of the
  * last call into the HOST array per_K_status [nK]; synchronises the device.

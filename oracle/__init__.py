@@ -345,9 +345,40 @@ def recover_mesh(prm, mesh, st, dvh_global):
     return dV, dQ
 
 
+def monolithic_system(prm, mesh, st):
+    """The monolithic Newton system of eq. R1 over (Q, V, V-hat global) for all
+    elements: J and R, unknowns ordered Q (viscous) of every element, V of
+    every element, then the global traces."""
+    return _assemble(prm, mesh, st)
+
+
+def adjoint_solve(prm, mesh, st, gV, gVh):
+    """J^T (lam_V, lam_Vhat) = (g_V, g_Vhat) for the monolithic Euler system
+    (the transposed Newton system, solved by the oracle's GEPP; tiny meshes)."""
+    J, _ = _assemble(prm, mesh, st)
+    g = np.concatenate([np.asarray(gV).ravel(), np.asarray(gVh).ravel()])
+    lam = solve(np.ascontiguousarray(J.T), g)
+    nv = mesh.nK * 5 * mesh.Nn
+    return lam[:nv].reshape(mesh.nK, 5, mesh.Nn), lam[nv:].reshape(mesh.n_global_faces, 5, mesh.n2)
+
+
 def brute_force(prm, mesh, st):
     """Monolithic Newton increment: assemble J over (Q, V, V-hat global) for all
     elements and solve J d = -R with the oracle's GEPP (tiny meshes only)."""
+    J, R = _assemble(prm, mesh, st)
+    nK, Nn, n2 = mesh.nK, mesh.Nn, mesh.n2
+    Nv, Nq = 5 * Nn, 15 * Nn
+    vis = bool(prm.viscous)
+    nq_tot = nK * Nq if vis else 0
+    offH = nq_tot + nK * Nv
+    d = solve(J, -R)
+    dQ = d[:nq_tot].reshape(nK, 5, 3, Nn) if vis else None
+    dV = d[nq_tot:offH].reshape(nK, 5, Nn)
+    dH = d[offH:].reshape(mesh.n_global_faces, 5, n2)
+    return dQ, dV, dH
+
+
+def _assemble(prm, mesh, st):
     nK, Nn, n2 = mesh.nK, mesh.Nn, mesh.n2
     Nv, Nq, Ntg = 5 * Nn, 15 * Nn, mesh.n_global_faces * 5 * n2
     vis = bool(prm.viscous)
@@ -372,11 +403,7 @@ def brute_force(prm, mesh, st):
             np.add.at(R, iq, RQ)
             add(iq, iq, B["Aqq"]); add(iq, iv, B["Aqv"]); add(iq, ih, B["Aqh"])
             add(iv, iq, B["Avq"]); add(ih, iq, B["Ahq"])
-    d = solve(J, -R)
-    dQ = d[:nq_tot].reshape(nK, 5, 3, Nn) if vis else None
-    dV = d[nq_tot:offH].reshape(nK, 5, Nn)
-    dH = d[offH:].reshape(mesh.n_global_faces, 5, n2)
-    return dQ, dV, dH
+    return J, R
 
 
 # ---------------------------------------------------------------- element samples in parallel
@@ -419,3 +446,121 @@ def condense_elements(prm, mesh, st, Ks, dvh_global=None, procs=1):
         res.append((bh.reshape(6, 5, n2), None if dV is None else dV.reshape(5, Nn),
                     None if dQ is None else dQ.reshape(5, 3, Nn), t))
     return res
+
+
+def residual_norm(prm, mesh, st):
+    """2-norm of the whole residual (R_Q, R_V, R_V-hat) of eq. s32 at the state"""
+    RV, RQ, RH = residual_mesh(prm, mesh, st)
+    s = float(np.sum(RV * RV) + np.sum(RH * RH))
+    if RQ is not None:
+        s += float(np.sum(RQ * RQ))
+    return float(np.sqrt(s))
+
+
+def pseudo_time_newton(prm_kw, mesh, st, nsteps, tau_init=1.0, tau_max=1e8):
+    """Inexact Newton with pseudo-transient continuation (Sec. 6.1, eqs.
+    C31221-C31223), each linear system solved exactly by the monolithic GEPP
+    of brute_force: at step k the stage term is (u(v) - u(v_k)) / tau_k
+    (v* = v_k), the increment solves J dV = -R (eq. C312) and the state is
+    updated (eq. C31223); tau_0 = tau_init and tau_{k+1} = min(tau_max,
+    tau_k ||R_k|| / ||R_{k+1}||) (residual-based growth), ||R|| the residual
+    at the iterate with v* = v (the steady residual).  Returns (final state,
+    norms [nsteps+1], taus [nsteps]).  Tiny meshes only."""
+    from paper_2507_22195_gb300.inputs import State
+    s = State(v=st.v.copy(), vhat=st.vhat.copy(), q=None if st.q is None else st.q.copy(), vstar=st.v.copy())
+    norms = [residual_norm(params(dt=tau_init, **prm_kw), mesh, s)]
+    taus = []
+    tau = tau_init
+    for _ in range(nsteps):
+        taus.append(tau)
+        prm = params(dt=tau, **prm_kw)
+        s.vstar = s.v.copy()
+        dQ, dV, dH = brute_force(prm, mesh, s)
+        s.v = s.v + dV
+        s.vhat = s.vhat + dH
+        if s.q is not None:
+            s.q = s.q + dQ
+        s.vstar = s.v.copy()
+        r = residual_norm(prm, mesh, s)
+        tau = min(tau_max, tau * norms[-1] / r) if r > 0 else tau_max
+        norms.append(r)
+    return s, norms, taus
+
+
+def condense_uneven(prm, mesh, st, Ks, dvh=None, procs=1):
+    """condense_elements for a batch of uneven p, m (inputs.UnevenMesh with
+    flattened arrays): each element K of Ks as its own one-element problem
+    (Algorithm 1, local parts), with its traces gathered from the flattened
+    trace vectors.  Returns, per element, (b-hat^K [6,5,n2], dV^K [5,Nn] or
+    None, dQ^K or None, seconds)."""
+    from paper_2507_22195_gb300.inputs import State
+    voff, toff = mesh.voff, mesh.toff
+    out = []
+    # one element per call of condense_elements, batched into one pool
+    jobs = []
+    for K in Ks:
+        em = mesh.element_mesh(K)
+        n2, Nn = em.n2, em.Nn
+        vK = st.v[voff[K]:voff[K + 1]].reshape(1, 5, Nn)
+        vsK = st.vstar[voff[K]:voff[K + 1]].reshape(1, 5, Nn)
+        qK = None if st.q is None else st.q[3 * voff[K]:3 * voff[K + 1]].reshape(1, 5, 3, Nn)
+        vh = np.stack([st.vhat[toff[g]:toff[g + 1]].reshape(5, n2) for g in mesh.face_gid[K]])
+        dh = None if dvh is None else np.stack([dvh[toff[g]:toff[g + 1]].reshape(5, n2) for g in mesh.face_gid[K]])
+        jobs.append((em, State(v=vK, vhat=vh, q=qK, vstar=vsK), dh))
+    if procs <= 1:
+        for em, s, dh in jobs:
+            out.append(condense_elements(prm, em, s, [0], dh)[0])
+        return out
+    import multiprocessing as mp
+    build()
+    fields = tuple(getattr(prm, f) for f, _ in Params._fields_)
+    args = []
+    for em, s, dh in jobs:
+        args.append((fields, em.p, em.m, em.boxes[0].copy(), np.ascontiguousarray(s.v[0]),
+                     np.ascontiguousarray(s.vstar[0]), np.ascontiguousarray(s.vhat),
+                     None if s.q is None else np.ascontiguousarray(s.q[0]),
+                     None if dh is None else np.ascontiguousarray(dh).ravel()))
+    with mp.get_context("spawn").Pool(procs) as pool:
+        res = pool.map(_condense_one, args)
+    for (em, _, _), (bh, dV, dQ, t) in zip(jobs, res):
+        out.append((bh.reshape(6, 5, em.n2), None if dV is None else dV.reshape(5, em.Nn),
+                    None if dQ is None else dQ.reshape(5, 3, em.Nn), t))
+    return out
+
+
+def newton_vjp(prm_kw, mesh, st, nsteps, tau, gbar_v, gbar_vh, fd_step=1e-5):
+    """Cotangent of the initial state (v0, vhat0) for the cotangent (gbar_v,
+    gbar_vh) of the state after nsteps Newton steps with the stage term at
+    v* = v_k and a fixed step tau (Sec. 6.1, eqs. C312, C31223; Euler):
+    reverse recursion gbar_k = gbar_{k+1} - J_steady(s_k)^T lam - (d/de
+    J(s_k + e d_k)^T lam)|0 with lam = J(s_k)^-T gbar_{k+1}, every J the
+    monolithic complex-step Jacobian (J_steady without the stage term), the
+    transposed solves by GEPP, the last term by central differences with
+    h = fd_step max|s_k| / max|d_k|.  Returns (g_v0, g_vh0, final State).
+    Tiny meshes only."""
+    from paper_2507_22195_gb300.inputs import State
+    prm = params(dt=tau, **prm_kw)
+    prm_s = params(dt=tau, time_term=0, **prm_kw)
+    v, vh = st.v.copy(), st.vhat.copy()
+    traj = []
+    for _ in range(nsteps):
+        s = State(v=v, vhat=vh, q=None, vstar=v.copy())
+        _, dV, dH = brute_force(prm, mesh, s)
+        traj.append((v.copy(), vh.copy(), dV, dH))
+        v, vh = v + dV, vh + dH
+    g = np.concatenate([np.asarray(gbar_v).ravel(), np.asarray(gbar_vh).ravel()])
+    for v0, vh0, dV, dH in reversed(traj):
+        sk = State(v=v0, vhat=vh0, q=None, vstar=v0.copy())
+        J, _ = _assemble(prm, mesh, sk)
+        lam = solve(np.ascontiguousarray(J.T), g)
+        Js, _ = _assemble(prm_s, mesh, sk)
+        a = Js.T @ lam
+        dm = max(np.abs(dV).max(), np.abs(dH).max())
+        smax = max(np.abs(v0).max(), np.abs(vh0).max())
+        h = fd_step * smax / dm
+        Jp, _ = _assemble(prm, mesh, State(v=v0 + h * dV, vhat=vh0 + h * dH, q=None, vstar=v0.copy()))
+        Jm, _ = _assemble(prm, mesh, State(v=v0 - h * dV, vhat=vh0 - h * dH, q=None, vstar=v0.copy()))
+        g = g - a - (Jp.T @ lam - Jm.T @ lam) / (2 * h)
+    nv = mesh.nK * 5 * mesh.Nn
+    return (g[:nv].reshape(st.v.shape), g[nv:].reshape(st.vhat.shape),
+            State(v=v, vhat=vh, q=None, vstar=v.copy()))

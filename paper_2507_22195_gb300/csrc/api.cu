@@ -45,6 +45,8 @@ void free_mesh(mehdg_ctx* c) {
     dfree(c->d_RQ); dfree(c->d_z); dfree(c->d_dq); dfree(c->d_qt1); dfree(c->d_qt2); dfree(c->d_Minv); dfree(c->d_C1);
     dfree(c->d_pj); dfree(c->d_pjf); dfree(c->d_pq); dfree(c->d_pqf); c->pj_ready = false;
     if (c->d_krylov) { cudaFree(c->d_krylov); c->d_krylov = nullptr; c->krylov_bytes = 0; }
+    if (c->d_newton) { cudaFree(c->d_newton); c->d_newton = nullptr; c->newton_bytes = 0; }
+    if (c->d_adj) { cudaFree(c->d_adj); c->d_adj = nullptr; c->adj_bytes = 0; }
     if (c->lu_graph) { cudaGraphExecDestroy(c->lu_graph); c->lu_graph = nullptr; }
     if (c->lu_ev_in) { cudaEventDestroy(c->lu_ev_in); c->lu_ev_in = nullptr; }
     if (c->lu_ev_out) { cudaEventDestroy(c->lu_ev_out); c->lu_ev_out = nullptr; }
@@ -52,6 +54,7 @@ void free_mesh(mehdg_ctx* c) {
     if (c->zs_ev_out) { cudaEventDestroy(c->zs_ev_out); c->zs_ev_out = nullptr; }
     if (c->lu_stream) { cudaStreamDestroy(c->lu_stream); c->lu_stream = nullptr; }
     if (c->h_cnt) { cudaFreeHost(c->h_cnt); c->h_cnt = nullptr; }
+    batch_free(c);
     c->nK = 0; c->condensed = false; c->lu_graph_failed = false;
 }
 
@@ -137,6 +140,8 @@ LUPlan plan(mehdg_ctx* c) {
     P.S = c->d_S; P.piv = c->d_piv; P.status = c->d_status;
     P.work = c->d_work; P.work_bytes = c->work_bytes;
     P.prof = &c->prof;
+    P.leaf_ctas = c->tune_leaf_ctas;
+    P.solve_ctas = c->tune_solve_ctas;
     return P;
 }
 
@@ -243,8 +248,18 @@ int mehdg_set_mesh(mehdg_ctx* c, int64_t nK, const int32_t* p, const int32_t* m,
     if (!c) return MEHDG_EINVAL;
     if (nK <= 0 || !p || !m || !box || !face_gid || G <= 0) { set_err(c, "set_mesh: bad arguments"); return MEHDG_EINVAL; }
     const int p0 = p[0], m0 = m[0];
+    bool uneven = false;
     for (int64_t K = 0; K < nK; ++K)
-        if (p[K] != p0 || m[K] != m0) { set_err(c, "set_mesh: all elements must share p and m"); return MEHDG_EINVAL; }
+        if (p[K] != p0 || m[K] != m0) uneven = true;
+    // MEHDG_FORCE_BATCH=1 runs a uniform mesh through the batch path as well
+    // (its waves, when the mesh exceeds the memory budget)
+    if (const char* e = std::getenv("MEHDG_FORCE_BATCH")) uneven = uneven || e[0] == '1';
+    if (uneven) {
+        free_mesh(c);
+        const int rc = batch_set_mesh(c, nK, p, m, box, face_gid, G);
+        if (rc) free_mesh(c);
+        return rc;
+    }
     if (p0 < 1 || p0 > MEHDG_MAXP || m0 < 1 || m0 > 16) { set_err(c, "set_mesh: p in 1..4, m in 1..16"); return MEHDG_EINVAL; }
     if (c->prm.viscous && c->prm.prec == MEHDG_FP64 && p0 > 3) {
         set_err(c, "set_mesh: the FP64 viscous Jacobian supports p <= 3"); return MEHDG_EINVAL;
@@ -332,12 +347,13 @@ int mehdg_set_mesh(mehdg_ctx* c, int64_t nK, const int32_t* p, const int32_t* m,
 }
 
 int mehdg_set_state(mehdg_ctx* c, const double* v, const double* vhat, const double* q, const double* vstar,
-                    void*) {
+                    void* stream) {
     if (!c) return MEHDG_EINVAL;
     if (c->nK == 0) { set_err(c, "set_state before set_mesh"); return MEHDG_ESTATE; }
     if (!v || !vhat || (c->prm.viscous && !q) || (c->prm.time_term && !vstar)) {
         set_err(c, "set_state: missing array"); return MEHDG_EINVAL;
     }
+    if (c->batch) return batch_set_state(c, v, vhat, q, vstar, (cudaStream_t)stream);
     c->v = v; c->vh = vhat; c->q = q; c->vs = vstar;
     c->condensed = false;
     c->pj_ready = false;
@@ -347,8 +363,9 @@ int mehdg_set_state(mehdg_ctx* c, const double* v, const double* vhat, const dou
 int mehdg_residual(mehdg_ctx* c, double* R_V, double* R_Q, double* R_Vhat, void* stream) {
     if (!c) return MEHDG_EINVAL;
     if (!c->v) { set_err(c, "residual before set_state"); return MEHDG_ESTATE; }
-    if (!R_V || !R_Vhat) { set_err(c, "residual: null output"); return MEHDG_EINVAL; }
+    if (!R_V || !R_Vhat || (c->batch && c->prm.viscous && !R_Q)) { set_err(c, "residual: null output"); return MEHDG_EINVAL; }
     cudaStream_t st = (cudaStream_t)stream;
+    if (c->batch) return batch_residual(c, R_V, R_Q, R_Vhat, st);
     TRY(cudaMemsetAsync(c->d_status, 0, sizeof(int32_t) * c->nK, st));
     ResidualArgs a = base_args(c);
     a.RV = R_V; a.RQ = viscous(c) ? R_Q : nullptr; a.RH = c->d_RHloc;
@@ -365,6 +382,7 @@ int mehdg_condense(mehdg_ctx* c, double* bhat, double* Ahat_local, void* stream)
     if (!bhat) { set_err(c, "condense: null bhat"); return MEHDG_EINVAL; }
     if (Ahat_local) { set_err(c, "condense: the explicit A-hat^K is not formed; use mehdg_apply_condensed"); return MEHDG_EINVAL; }
     cudaStream_t st = (cudaStream_t)stream;
+    if (c->batch) return batch_condense(c, bhat, st);
     const bool fp64 = c->prm.prec == MEHDG_FP64;
     const bool vis = viscous(c);
     const int64_t nK = c->nK, ld = c->Npad;
@@ -423,9 +441,11 @@ int mehdg_condense(mehdg_ctx* c, double* bhat, double* Ahat_local, void* stream)
 
 int mehdg_apply_condensed(mehdg_ctx* c, const double* x, double* y, void* stream) {
     if (!c) return MEHDG_EINVAL;
-    if (!c->condensed) { set_err(c, "apply_condensed before condense"); return MEHDG_ESTATE; }
+    if (!c->condensed) { set_err(c, c->batch ? "apply_condensed: no condensation kept (before condense, or the batch "
+                                       "streamed in waves)" : "apply_condensed before condense"); return MEHDG_ESTATE; }
     if (!x || !y) return MEHDG_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
+    if (c->batch) return batch_apply(c, x, y, st);
     const bool vis = viscous(c);
     const int64_t nK = c->nK, ld = c->Npad;
     int rc;
@@ -445,9 +465,11 @@ int mehdg_apply_condensed(mehdg_ctx* c, const double* x, double* y, void* stream
 
 int mehdg_recover(mehdg_ctx* c, const double* dVhat, double* dV, double* dQ, void* stream) {
     if (!c) return MEHDG_EINVAL;
-    if (!c->condensed) { set_err(c, "recover before condense"); return MEHDG_ESTATE; }
+    if (!c->condensed) { set_err(c, c->batch ? "recover: no condensation kept (before condense, or the batch "
+                                       "streamed in waves)" : "recover before condense"); return MEHDG_ESTATE; }
     if (!dVhat || !dV || (viscous(c) && !dQ)) return MEHDG_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
+    if (c->batch) return batch_recover(c, dVhat, dV, dQ, st);
     const bool vis = viscous(c);
     const int64_t nK = c->nK, ld = c->Npad;
     int rc;
@@ -483,6 +505,24 @@ int mehdg_status_device(mehdg_ctx* c, int32_t* per_K_status, int32_t* iters, voi
 }
 
 const char* mehdg_last_error(const mehdg_ctx* c) { return c ? c->err : "null context"; }
+
+int mehdg_batch_layout(mehdg_ctx* c, int64_t* voff, int64_t* toff) {
+    if (!c) return MEHDG_EINVAL;
+    if (!c->batch) { set_err(c, "batch_layout: not a batch context"); return MEHDG_EINVAL; }
+    batch_layout(c, voff, toff);
+    return MEHDG_OK;
+}
+
+int mehdg_batch_autotune(mehdg_ctx* c, int64_t trial_max, void* stream) {
+    if (!c) return MEHDG_EINVAL;
+    if (!c->batch) { set_err(c, "batch_autotune: not a batch context"); return MEHDG_EINVAL; }
+    return batch_autotune(c, trial_max, (cudaStream_t)stream);
+}
+
+int mehdg_batch_report(mehdg_ctx* c, char* buf, size_t len) {
+    if (!c || !c->batch) return MEHDG_EINVAL;
+    return batch_report(c, buf, len);
+}
 
 void mehdg_destroy(mehdg_ctx* c) {
     if (!c) return;

@@ -139,6 +139,7 @@ template <> __device__ __forceinline__ Dual<10> cst<Dual<10>>(double x) { return
 
 // ------------------------------------------------------------------ context
 struct DeviceLU;   // defined in lu.cuh
+struct Batch;      // macro-elements of uneven p and m (batch.cu)
 
 struct mehdg_ctx {
     mehdg_params prm;
@@ -194,8 +195,16 @@ struct mehdg_ctx {
     cudaEvent_t zs_ev_in = nullptr, zs_ev_out = nullptr;   // zeroing of S beside the residual
     long long lu_graph_launches = 0;    // kernels in the graph
     bool lu_graph_failed = false;       // capture failed once: the LU is launched directly
+    int tune_leaf_ctas = 0;             // LU launch choices (0 = automatic), set by the batch autotuner
+    int tune_solve_ctas = 0;
     void* d_krylov = nullptr;           // GMRES basis and scratch of the trace solve (first use)
     size_t krylov_bytes = 0;
+    void* d_newton = nullptr;           // pseudo-time Newton loop: v*, residuals, increments (first use)
+    size_t newton_bytes = 0;
+    void* d_adj = nullptr;              // adjoint condensation scratch (first use)
+    size_t adj_bytes = 0;
+    Batch* batch = nullptr;             // set when the elements have uneven p, m (the fields above then
+                                        // describe no single element type)
     Prof prof;
 };
 
@@ -210,3 +219,24 @@ extern std::atomic<long long> g_mehdg_launches;
                                   return MEHDG_ECUDA; } } while (0)
 
 void set_err(mehdg_ctx* ctx, const char* fmt, ...);
+
+// batch contexts (batch.cu)
+int batch_set_mesh(mehdg_ctx* c, int64_t nK, const int32_t* p, const int32_t* m, const double* box,
+                   const int64_t* face_gid, int64_t G);
+int batch_free(mehdg_ctx* c);
+int batch_set_state(mehdg_ctx* c, const double* v, const double* vhat, const double* q, const double* vstar,
+                    cudaStream_t st);
+int batch_residual(mehdg_ctx* c, double* R_V, double* R_Q, double* R_Vhat, cudaStream_t st);
+int batch_condense(mehdg_ctx* c, double* bhat, cudaStream_t st);
+int batch_apply(mehdg_ctx* c, const double* x, double* y, cudaStream_t st);
+int batch_recover(mehdg_ctx* c, const double* dVhat, double* dV, double* dQ, cudaStream_t st);
+int batch_autotune(mehdg_ctx* c, int64_t trial_max, cudaStream_t st);
+int batch_report(const mehdg_ctx* c, char* buf, size_t len);
+void batch_layout(const mehdg_ctx* c, int64_t* voff, int64_t* toff);
+int64_t batch_state_len(const mehdg_ctx* c);
+int64_t batch_trace_len(const mehdg_ctx* c);
+int batch_set_dt(mehdg_ctx* c);
+
+// lengths of the state ([nK][5][Nn] in all) and global trace vectors
+inline int64_t ctx_state_len(const mehdg_ctx* c) { return c->batch ? batch_state_len(c) : c->nK * (int64_t)c->Nv; }
+inline int64_t ctx_trace_len(const mehdg_ctx* c) { return c->batch ? batch_trace_len(c) : c->G * 5 * (int64_t)c->tab.n2; }

@@ -69,12 +69,16 @@ struct LUPlan {
     void* work;               // scratch (operand panels, permutation lists)
     size_t work_bytes;
     Prof* prof;
+    int leaf_ctas = 0;        // leaf panel CTAs per SM: 1, 2, or 0 = chosen from the element count
+    int solve_ctas = 0;       // CTAs per element in the solves: 1, 2, 4, 8, or 0 = chosen from the count
 };
 size_t lu_work_bytes(int64_t nK, int64_t ld, bool fp64, int prec);
 cudaError_t lu_factor(const LUPlan& P, cudaStream_t st);
 // solve S x = r for every element whose conv flag is 0: x (FP64) = LU^-1 r,
 // computed in the factor precision; r, x: [nK][ld] FP64 (padded tail 0).
 cudaError_t lu_solve(const LUPlan& P, const double* r, double* x, const int32_t* skip, cudaStream_t st);
+// the transposed system S^T x = r with the same factors (FP64 accumulation)
+cudaError_t lu_solve_T(const LUPlan& P, const double* r, double* x, const int32_t* skip, cudaStream_t st);
 
 // small vector kernels for the refinement (refine.cu)
 cudaError_t launch_refine_update(int64_t nK, int Nv, int64_t ld, const double* r, const double* Sx,
@@ -85,3 +89,11 @@ cudaError_t launch_set_rhs(int64_t nK, int Nv, int64_t ld, int Nn, const double*
                            const double* b, double sb, double* out, cudaStream_t st);
 cudaError_t launch_copy_unpad(int64_t nK, int Nv, int64_t ld, const double* x, double* out, double s,
                               cudaStream_t st);
+
+// residual VJP passes at the context's state (vjp.cu); Euler only
+cudaError_t launch_vjp(mehdg_ctx* c, const double* lam_V, const double* lam_Vhat, double* g_v, double* g_vhat,
+                       cudaStream_t st);
+// restarted GMRES on a matrix-free trace operator (krylov.cu)
+typedef int (*trace_op_fn)(mehdg_ctx* c, const double* x, double* y, void* stream);
+int gmres_trace(mehdg_ctx* c, trace_op_fn op, const double* b, double* x, double rtol, int restart, int max_iter,
+                int* iters_out, double* relres_out, void* stream);

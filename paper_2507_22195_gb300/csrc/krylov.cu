@@ -81,9 +81,14 @@ extern "C" int mehdg_solve_condensed(mehdg_ctx* c, const double* bhat, double* x
     if (!c) return MEHDG_EINVAL;
     if (!c->condensed) { set_err(c, "solve_condensed before condense"); return MEHDG_ESTATE; }
     if (!bhat || !x || restart < 1 || max_iter < 1 || !(rtol > 0.0)) return MEHDG_EINVAL;
+    return gmres_trace(c, mehdg_apply_condensed, bhat, x, rtol, restart, max_iter, iters_out, relres_out, stream);
+}
+
+int gmres_trace(mehdg_ctx* c, trace_op_fn op, const double* bhat, double* x, double rtol, int restart, int max_iter,
+                int* iters_out, double* relres_out, void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
     const int m = restart;
-    const int64_t n = c->G * 5 * (int64_t)c->tab.n2;
+    const int64_t n = ctx_trace_len(c);
     // workspace: basis V [m+1][n], w [n], partial sums, small device arrays
     const size_t need = sizeof(double) * ((size_t)(m + 2) * n + (size_t)(m + 1) * RED_BLOCKS + 2 * (m + 1));
     if (c->krylov_bytes < need) {
@@ -124,7 +129,7 @@ extern "C" int mehdg_solve_condensed(mehdg_ctx* c, const double* bhat, double* x
     if ((rc = norm(bhat, bn))) return rc;
     if (bn == 0.0) bn = 1.0;
     // r = b - A x into V_0
-    if ((rc = mehdg_apply_condensed(c, x, V, stream))) return rc;
+    if ((rc = op(c, x, V, stream))) return rc;
     axpby_kernel<<<gv, 256, 0, st>>>(1.0, bhat, -1.0, V, n);
     MEHDG_COUNT(1);
     double beta;
@@ -140,7 +145,7 @@ extern "C" int mehdg_solve_condensed(mehdg_ctx* c, const double* bhat, double* x
         int j = 0;
         for (; j < m && it < max_iter; ++j) {
             double* vj1 = V + (size_t)(j + 1) * n;
-            if ((rc = mehdg_apply_condensed(c, V + (size_t)j * n, w, stream))) return rc;
+            if ((rc = op(c, V + (size_t)j * n, w, stream))) return rc;
             ++it;
             // classical Gram-Schmidt, twice
             if ((rc = dots(j + 1, w, h1))) return rc;
@@ -189,7 +194,7 @@ extern "C" int mehdg_solve_condensed(mehdg_ctx* c, const double* bhat, double* x
             MEHDG_COUNT(1);
         }
         // true residual for the restart (and the reported value)
-        if ((rc = mehdg_apply_condensed(c, x, V, stream))) return rc;
+        if ((rc = op(c, x, V, stream))) return rc;
         axpby_kernel<<<gv, 256, 0, st>>>(1.0, bhat, -1.0, V, n);
         MEHDG_COUNT(1);
         if ((rc = norm(V, beta))) return rc;

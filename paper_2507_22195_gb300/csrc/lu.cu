@@ -700,11 +700,18 @@ int pick_ib(int64_t rows, bool two_per_sm) {
 }
 
 template <class TS>
-cudaError_t launch_panel(TS* S, int64_t ld, int c, int32_t* piv, int32_t* status, int64_t nK, cudaStream_t st) {
+cudaError_t launch_panel(TS* S, int64_t ld, int c, int32_t* piv, int32_t* status, int64_t nK, int leaf_ctas,
+                         cudaStream_t st) {
     int dev = 0, nsm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const bool two = nK > nsm;
+    bool two = leaf_ctas == 1 ? false : leaf_ctas == 2 ? true : nK > nsm;
+    // MEHDG_LEAF_CTAS_PER_SM (1 or 2) overrides the choice, e.g. to test or
+    // profile the two-CTA leaves on a mesh with fewer elements than SMs
+    if (const char* f = std::getenv("MEHDG_LEAF_CTAS_PER_SM")) {
+        const int v = std::atoi(f);
+        if (v == 1 || v == 2) two = v == 2;
+    }
     int ib = pick_ib<TS>(ld - c, two);
     size_t sm = (size_t)ib * (ld - c) * sizeof(TS);
     if (sm < 16) sm = 16;
@@ -838,7 +845,7 @@ cudaError_t trailing_update(const LUPlan& P, int r0, int c0, int k0, int M, int 
 template <class TS>
 cudaError_t rec_panel(const LUPlan& P, int c, int w, cudaStream_t st) {
     cudaError_t e;
-    if (w == LEAF) return launch_panel<TS>((TS*)P.S, P.ld, c, P.piv, P.status, P.nK, st);
+    if (w == LEAF) return launch_panel<TS>((TS*)P.S, P.ld, c, P.piv, P.status, P.nK, P.leaf_ctas, st);
     // (every leaf applies its row exchanges to all columns of the outer panel,
     // so the halves need no separate exchange passes)
     int h = w / 2;
@@ -914,6 +921,7 @@ cudaError_t solve_t(const LUPlan& P, const int32_t* perms, const double* r, doub
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     int cl = 1;
     while (cl < 8 && P.nK * cl < 2 * (int64_t)nsm) cl *= 2;
+    if (P.solve_ctas == 1 || P.solve_ctas == 2 || P.solve_ctas == 4 || P.solve_ctas == 8) cl = P.solve_ctas;
     // MEHDG_SOLVE_CTAS (1, 2, 4 or 8) overrides the choice, e.g. to test every variant
     if (const char* f = std::getenv("MEHDG_SOLVE_CTAS")) {
         const int v = std::atoi(f);
@@ -927,6 +935,116 @@ cudaError_t solve_t(const LUPlan& P, const int32_t* perms, const double* r, doub
     }
 }
 }  // namespace
+
+namespace {
+// Transposed solve S^T x = r with the same factors.  The forward solve
+// applies, block column by block column, the panel's row permutation (at the
+// first block of each outer panel) and the elimination with the unit-lower
+// block column, then the backward substitution with U: S^-1 = U^-1 T_last
+// ... T_0.  Hence S^-T = T_0^T ... T_last^T U^-T: a forward substitution
+// with U^T (dot products down U's columns, contiguous in column-major
+// storage), then, from the last block column to the first, the transposed
+// elimination (dots down L's columns below the block, then the unit-upper
+// L_ss^T solve) and the inverse row permutation.  One CTA per element, x in
+// shared memory in FP64 (the factors in their storage precision).
+template <class TS>
+__global__ void __launch_bounds__(512)
+solve_T_kernel(const TS* __restrict__ Sall, int64_t ld, const int32_t* __restrict__ perms, int64_t nK,
+               const double* __restrict__ rall, double* __restrict__ xall, const int32_t* skip) {
+    constexpr int BPP = LU_NB / 32;
+    const int K = blockIdx.x;
+    if (skip && skip[K]) return;
+    const TS* S = Sall + (size_t)K * ld * ld;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* z = reinterpret_cast<double*>(smem_raw);     // [ld]
+    double* tmp = z + ld;                                 // [2 NB]
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    const int nb = (int)(ld / 32);
+    for (int i = tid; i < ld; i += blockDim.x) z[i] = rall[(size_t)K * ld + i];
+    __syncthreads();
+    // z = U^-T z
+    for (int s = 0; s < nb; ++s) {
+        const int r1 = 32 * s;
+        for (int j = wid; j < 32; j += nw) {
+            const TS* col = S + (size_t)(r1 + j) * ld;
+            double acc = 0.0;
+            for (int i = lane; i < r1; i += 32) acc += (double)col[i] * z[i];
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) z[r1 + j] -= acc;
+        }
+        __syncthreads();
+        if (wid == 0) {
+            const TS* col = S + (size_t)(r1 + lane) * ld + r1;    // column lane of U_ss
+            double u[32];
+#pragma unroll
+            for (int k = 0; k < 32; ++k) u[k] = (double)col[k];
+            double y = z[r1 + lane];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                if (lane == i) y = y / u[i];
+                const double yi = __shfl_sync(0xffffffffu, y, i);
+                if (lane > i) y -= u[i] * yi;
+            }
+            z[r1 + lane] = y;
+        }
+        __syncthreads();
+    }
+    // z = T_0^T ... T_last^T z
+    for (int s = nb - 1; s >= 0; --s) {
+        const int r1 = 32 * s, below = r1 + 32;
+        for (int j = wid; j < 32; j += nw) {
+            const TS* col = S + (size_t)(r1 + j) * ld;
+            double acc = 0.0;
+            for (int i = below + lane; i < ld; i += 32) acc += (double)col[i] * z[i];
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) z[r1 + j] -= acc;
+        }
+        __syncthreads();
+        if (wid == 0) {
+            const TS* col = S + (size_t)(r1 + lane) * ld + r1;    // column lane of L_ss (below its diagonal)
+            double l[32];
+#pragma unroll
+            for (int k = 0; k < 32; ++k) l[k] = k > lane ? (double)col[k] : 0.0;
+            double y = z[r1 + lane];
+#pragma unroll
+            for (int i = 31; i >= 0; --i) {
+                const double yi = __shfl_sync(0xffffffffu, y, i);
+                if (lane < i) y -= l[i] * yi;
+            }
+            z[r1 + lane] = y;
+        }
+        __syncthreads();
+        if (s % BPP == 0) {
+            // inverse of the panel's row exchange (new row rows[i] = old row rows[cont[i]])
+            const int32_t* pl = perms + ((size_t)(s / BPP) * nK + K) * LU_PW;
+            const int nr = pl[0];
+            const int32_t* rows = pl + 1;
+            const int32_t* cont = rows + 2 * LU_NB;
+            for (int i = tid; i < nr; i += blockDim.x) tmp[i] = z[rows[i]];
+            __syncthreads();
+            for (int i = tid; i < nr; i += blockDim.x) z[rows[cont[i]]] = tmp[i];
+            __syncthreads();
+        }
+    }
+    for (int i = tid; i < ld; i += blockDim.x) xall[(size_t)K * ld + i] = z[i];
+}
+
+template <class TS>
+cudaError_t solve_T_t(const LUPlan& P, const int32_t* perms, const double* r, double* x, const int32_t* skip,
+                      cudaStream_t st) {
+    const size_t sm = sizeof(double) * ((size_t)P.ld + 2 * LU_NB);
+    cudaFuncSetAttribute(solve_T_kernel<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    solve_T_kernel<TS><<<(unsigned)P.nK, 512, sm, st>>>((const TS*)P.S, P.ld, perms, P.nK, r, x, skip);
+    MEHDG_COUNT(1);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t lu_solve_T(const LUPlan& P, const double* r, double* x, const int32_t* skip, cudaStream_t st) {
+    const int32_t* perms = panel_perm(P, 0);
+    if (P.fp64) return solve_T_t<double>(P, perms, r, x, skip, st);
+    return solve_T_t<float>(P, perms, r, x, skip, st);
+}
 
 cudaError_t lu_solve(const LUPlan& P, const double* r, double* x, const int32_t* skip, cudaStream_t st) {
     const int32_t* perms = panel_perm(P, 0);

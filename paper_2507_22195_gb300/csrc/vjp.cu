@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(128) vjp_volume_kernel(VjpArgs a) {
         for (int k = 0; k < 5; ++k) {
             vl[k * nl + i] = a.v[oV + k * Nn + A];
             vsl[k * nl + i] = a.ph.time_term ? a.vs[oV + k * Nn + A] : 0.0;
-            ll[k * nl + i] = a.lamV[oV + k * Nn + A];
+            ll[k * nl + i] = a.lamV ? a.lamV[oV + k * Nn + A] : 0.0;
         }
     }
     __syncthreads();
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(128) vjp_face_kernel(VjpArgs a) {
         for (int k = 0; k < 5; ++k) {
             fv[k * fl + i] = a.v[oV + k * Nn + A];
             fh[k * fl + i] = a.vh[og + k * n2 + c1 + n * c2];
-            lv[k * fl + i] = a.lamV[oV + k * Nn + A];
+            lv[k * fl + i] = a.lamV ? a.lamV[oV + k * Nn + A] : 0.0;
             lh[k * fl + i] = a.lamH ? a.lamH[og + k * n2 + c1 + n * c2] : 0.0;
         }
     }
@@ -195,24 +195,19 @@ __global__ void __launch_bounds__(128) vjp_face_kernel(VjpArgs a) {
 
 }  // namespace
 
-extern "C" int mehdg_residual_vjp(mehdg_ctx* c, const double* lam_V, const double* lam_Vhat, double* g_v,
-                                  double* g_vhat, void* stream) {
-    if (!c) return MEHDG_EINVAL;
-    if (c->nK == 0 || !c->v || !c->vh) { set_err(c, "residual_vjp before set_mesh/set_state"); return MEHDG_ESTATE; }
-    if (c->ph.viscous) { set_err(c, "residual_vjp: the Euler residual only"); return MEHDG_EINVAL; }
-    if (!lam_V || !g_v || !g_vhat) return MEHDG_EINVAL;
-    if (c->ph.time_term && !c->vs) { set_err(c, "residual_vjp: the time term needs vstar"); return MEHDG_EINVAL; }
-    cudaStream_t st = (cudaStream_t)stream;
+// the two VJP passes at the context's state (no status reset, no checks):
+// g_v, g_vhat overwritten
+cudaError_t launch_vjp(mehdg_ctx* c, const double* lam_V, const double* lam_Vhat, double* g_v, double* g_vhat,
+                       cudaStream_t st) {
     const Tab& t = c->tab;
     VjpArgs a;
     a.tab = t; a.ph = c->ph; a.box = c->d_box; a.gid = c->d_gid;
     a.v = c->v; a.vs = c->vs; a.vh = c->vh; a.lamV = lam_V; a.lamH = lam_Vhat; a.gv = g_v; a.gh = g_vhat;
     a.status = c->d_status;
-    if (cudaMemsetAsync(g_v, 0, sizeof(double) * c->nK * 5 * t.Nn, st) != cudaSuccess ||
-        cudaMemsetAsync(g_vhat, 0, sizeof(double) * c->G * 5 * t.n2, st) != cudaSuccess ||
-        cudaMemsetAsync(c->d_status, 0, sizeof(int32_t) * c->nK, st) != cudaSuccess) {
-        set_err(c, "residual_vjp: memset failed"); return MEHDG_ECUDA;
-    }
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(g_v, 0, sizeof(double) * c->nK * 5 * t.Nn, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(g_vhat, 0, sizeof(double) * c->G * 5 * t.n2, st)) != cudaSuccess)
+        return e;
     const size_t head = sizeof(double) * (2 * MEHDG_MAXG * (MEHDG_MAXP + 1) + 8);
     const size_t sv = head + sizeof(double) * (15 * (size_t)t.nl + 5 * (size_t)t.npt);
     const int fl = (t.p + 1) * (t.p + 1), fpt = t.ng * t.ng;
@@ -222,6 +217,21 @@ extern "C" int mehdg_residual_vjp(mehdg_ctx* c, const double* lam_V, const doubl
     vjp_volume_kernel<<<dim3((unsigned)(t.m * t.m * t.m), (unsigned)c->nK), 128, sv, st>>>(a);
     vjp_face_kernel<<<dim3((unsigned)(6 * t.m * t.m), (unsigned)c->nK), 128, sf, st>>>(a);
     MEHDG_COUNT(2);
-    if (cudaGetLastError() != cudaSuccess) { set_err(c, "residual_vjp: launch failed"); return MEHDG_ECUDA; }
+    return cudaGetLastError();
+}
+
+extern "C" int mehdg_residual_vjp(mehdg_ctx* c, const double* lam_V, const double* lam_Vhat, double* g_v,
+                                  double* g_vhat, void* stream) {
+    if (c && c->batch) { set_err(c, "residual_vjp: not available for elements of uneven p, m"); return MEHDG_EINVAL; }
+    if (!c) return MEHDG_EINVAL;
+    if (c->nK == 0 || !c->v || !c->vh) { set_err(c, "residual_vjp before set_mesh/set_state"); return MEHDG_ESTATE; }
+    if (c->ph.viscous) { set_err(c, "residual_vjp: the Euler residual only"); return MEHDG_EINVAL; }
+    if (!lam_V || !g_v || !g_vhat) return MEHDG_EINVAL;
+    if (c->ph.time_term && !c->vs) { set_err(c, "residual_vjp: the time term needs vstar"); return MEHDG_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(c->d_status, 0, sizeof(int32_t) * c->nK, st) != cudaSuccess) {
+        set_err(c, "residual_vjp: memset failed"); return MEHDG_ECUDA;
+    }
+    if (launch_vjp(c, lam_V, lam_Vhat, g_v, g_vhat, st) != cudaSuccess) { set_err(c, "residual_vjp: launch failed"); return MEHDG_ECUDA; }
     return MEHDG_OK;
 }

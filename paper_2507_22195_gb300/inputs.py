@@ -262,3 +262,114 @@ def make_state(mesh: Mesh, kind: str, amp: float, seed_v: int, seed_vh: int,
 def random_direction(shape, seed: int, amp: float = 1.0) -> np.ndarray:
     r = np.random.Generator(np.random.PCG64(seed))
     return r.uniform(-amp, amp, size=shape)
+
+
+# ---------------------------------------------------------------- uneven batches
+@dataclasses.dataclass
+class UnevenMesh:
+    """Macro-elements of per-element degree p[K] and micro-element count
+    m[K].  Arrays are flattened: element K's [5][Nn(K)] block of v starts at
+    voff[K] (q: [5][3][Nn(K)] at 3 voff[K]), face g's [5][n_g^2] block of a
+    trace vector at toff[g]."""
+    p: np.ndarray
+    m: np.ndarray
+    boxes: np.ndarray
+    face_gid: np.ndarray
+    n_global_faces: int
+
+    @property
+    def nK(self) -> int:
+        return len(self.p)
+
+    def n(self, K) -> int:
+        return int(self.m[K] * self.p[K] + 1)
+
+    @property
+    def voff(self) -> np.ndarray:
+        return np.concatenate([[0], np.cumsum([5 * self.n(K) ** 3 for K in range(self.nK)])]).astype(np.int64)
+
+    @property
+    def toff(self) -> np.ndarray:
+        fn = np.zeros(self.n_global_faces, dtype=np.int64)
+        for K in range(self.nK):
+            fn[self.face_gid[K]] = self.n(K)
+        return np.concatenate([[0], np.cumsum(5 * fn * fn)]).astype(np.int64)
+
+    def element_mesh(self, K) -> Mesh:
+        """element K alone, as a one-element mesh with unshared faces"""
+        return Mesh(int(self.p[K]), int(self.m[K]), self.boxes[K:K + 1].copy(),
+                    np.arange(6, dtype=np.int64).reshape(1, 6), 6)
+
+
+def uneven_batch(nK: int, seed: int, p_choices=(1, 2, 3, 4), m_choices=(2, 3, 4), cells=8,
+                 L=2 * math.pi, specs=None) -> UnevenMesh:
+    """nK independent macro-elements (unshared faces), p and m drawn from the
+    choices with the seed (or given as specs = [(p, m), ...]); each element is
+    a cell of a cells^3 grid of [0, L]^3 at a seeded position, so the fields
+    vary from element to element."""
+    r = np.random.Generator(np.random.PCG64(seed))
+    if specs is not None:
+        nK = len(specs)
+        p = np.array([s[0] for s in specs], dtype=np.int32)
+        m = np.array([s[1] for s in specs], dtype=np.int32)
+    else:
+        p = r.choice(np.asarray(p_choices), size=nK).astype(np.int32)
+        m = r.choice(np.asarray(m_choices), size=nK).astype(np.int32)
+    pos = r.integers(0, cells, size=(nK, 3))
+    h = L / cells
+    boxes = np.concatenate([pos * h, (pos + 1) * h], axis=1).astype(np.float64)
+    gid = np.arange(6 * nK, dtype=np.int64).reshape(nK, 6)
+    return UnevenMesh(p, m, boxes, gid, 6 * nK)
+
+
+def make_uneven_state(mesh: UnevenMesh, amp: float, seed_v: int, seed_vh: int, seed_M: int,
+                      M0_range=(0.1, 0.3), viscous: bool = False) -> State:
+    """TGV-like field per element with its own Mach number M0 ~ U(M0_range)
+    (seed_M), plus U(-amp, amp) on v and, independently, on v-hat; v* = v; q
+    = nodal samples of the analytic grad v of the unperturbed field.  Arrays
+    are flattened with mesh.voff / mesh.toff."""
+    voff, toff = mesh.voff, mesh.toff
+    rM = np.random.Generator(np.random.PCG64(seed_M))
+    M0 = rM.uniform(M0_range[0], M0_range[1], size=mesh.nK)
+    v = np.zeros(voff[-1])
+    q = np.zeros(3 * voff[-1]) if viscous else None
+    vh = np.zeros(toff[-1])
+    for K in range(mesh.nK):
+        em = mesh.element_mesh(K)
+        X, Y, Z = node_coords(em, 0)
+        v[voff[K]:voff[K + 1]] = _field_v("tgv", X, Y, Z, M0=M0[K]).ravel()
+        if viscous:
+            q[3 * voff[K]:3 * voff[K + 1]] = _grad_v("tgv", X, Y, Z, M0=M0[K]).ravel()
+        for f in range(6):
+            g = mesh.face_gid[K, f]
+            pts = face_coords(em, 0, f)
+            vh[toff[g]:toff[g + 1]] = _field_v("tgv", pts[0], pts[1], pts[2], M0=M0[K]).ravel()
+    rv = np.random.Generator(np.random.PCG64(seed_v))
+    rh = np.random.Generator(np.random.PCG64(seed_vh))
+    v = v + rv.uniform(-amp, amp, size=v.shape)
+    vh = vh + rh.uniform(-amp, amp, size=vh.shape)
+    return State(v=v, vhat=vh, q=q, vstar=v.copy())
+
+
+def face_node_index(mesh: Mesh) -> np.ndarray:
+    """[6][n^2] element node A = i + n (j + n k) of every trace node c = i_t1 +
+    n i_t2 of local face f (x-, x+, y-, y+, z-, z+; (t1, t2) the two other
+    axes in increasing order)."""
+    n = mesh.n
+    out = np.zeros((6, n * n), dtype=np.int64)
+    for f in range(6):
+        d, side = f // 2, f % 2
+        t1, t2 = [(1, 2), (0, 2), (0, 1)][d]
+        for b in range(n):
+            for a in range(n):
+                ijk = [0, 0, 0]
+                ijk[d] = n - 1 if side else 0
+                ijk[t1], ijk[t2] = a, b
+                out[f, a + n * b] = ijk[0] + n * (ijk[1] + n * ijk[2])
+    return out
+
+
+def gll_weights(p: int) -> np.ndarray:
+    """Gauss-Lobatto-Legendre weights on [-1, 1] (closed forms, p <= 4)."""
+    return np.array({1: [1.0, 1.0], 2: [1 / 3, 4 / 3, 1 / 3], 3: [1 / 6, 5 / 6, 5 / 6, 1 / 6],
+                     4: [1 / 10, 49 / 90, 32 / 45, 49 / 90, 1 / 10]}[p])

@@ -27,7 +27,10 @@ EXPORTED = ["mehdg_default_params", "mehdg_create", "mehdg_set_mesh", "mehdg_set
             "mehdg_status", "mehdg_last_error", "mehdg_destroy", "mehdg_profile_enable",
             "mehdg_profile_read", "mehdg_launch_count", "mehdg_test_trailing_update",
             "mehdg_test_trailing_work_bytes", "mehdg_residual_static", "mehdg_solve_condensed",
-            "mehdg_residual_vjp", "mehdg_status_device"]
+            "mehdg_residual_vjp", "mehdg_status_device", "mehdg_set_dt", "mehdg_pseudo_time_newton",
+            "mehdg_batch_layout", "mehdg_batch_autotune", "mehdg_batch_report", "mehdg_condense_adjoint",
+            "mehdg_apply_condensed_adjoint", "mehdg_solve_condensed_adjoint", "mehdg_recover_adjoint",
+            "mehdg_pseudo_time_newton_vjp"]
 
 
 class mehdg_params(C.Structure):
@@ -64,6 +67,18 @@ def load(path: str | None = None):
     L.mehdg_recover.argtypes = [_vp, _vp, _vp, _vp, _vp]
     L.mehdg_status.argtypes = [_vp, _vp, _vp]
     L.mehdg_status_device.argtypes = [_vp, _vp, _vp, _vp]
+    L.mehdg_set_dt.argtypes = [_vp, C.c_double]
+    L.mehdg_batch_layout.argtypes = [_vp, _vp, _vp]
+    L.mehdg_condense_adjoint.argtypes = [_vp, _vp, _vp, _vp, _vp]
+    L.mehdg_apply_condensed_adjoint.argtypes = [_vp, _vp, _vp, _vp]
+    L.mehdg_solve_condensed_adjoint.argtypes = [_vp, _vp, _vp, C.c_double, C.c_int, C.c_int, _vp, _vp, _vp]
+    L.mehdg_recover_adjoint.argtypes = [_vp, _vp, _vp, _vp, _vp]
+    L.mehdg_pseudo_time_newton_vjp.argtypes = [_vp, _vp, _vp, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
+                                               _vp, _vp, _vp, _vp, C.c_double, _vp]
+    L.mehdg_batch_autotune.argtypes = [_vp, C.c_int64, _vp]
+    L.mehdg_batch_report.argtypes = [_vp, _vp, C.c_size_t]
+    L.mehdg_pseudo_time_newton.argtypes = [_vp, _vp, _vp, _vp, C.c_int, C.c_double, C.c_double, C.c_double,
+                                           C.c_int, C.c_int, _vp, _vp, _vp, _vp]
     L.mehdg_solve_condensed.argtypes = [_vp, _vp, _vp, C.c_double, C.c_int, C.c_int, _vp, _vp, _vp]
     L.mehdg_residual_vjp.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
     L.mehdg_last_error.argtypes = [_vp]
@@ -183,6 +198,79 @@ def mehdg_status_device(ctx, status, iters=None, stream=None):
         assert t is None or (t.is_cuda and t.dtype == torch.int32 and t.is_contiguous())
     _check(ctx, load().mehdg_status_device(ctx, status.data_ptr(), None if iters is None else iters.data_ptr(),
                                            _stream(stream)), "mehdg_status_device")
+
+
+def mehdg_set_dt(ctx, dt):
+    _check(ctx, load().mehdg_set_dt(ctx, float(dt)), "mehdg_set_dt")
+
+
+def mehdg_pseudo_time_newton(ctx, v, vhat, q, nsteps, tau_init=1.0, tau_max=1e8, lin_rtol=1e-10, restart=30,
+                             max_iter=500, stream=None):
+    """Pseudo-transient Newton steps on the device state (updated in place).
+    Returns (residual norms [nsteps+1], taus [nsteps], GMRES products [nsteps])."""
+    rn = np.zeros(nsteps + 1)
+    ta = np.zeros(max(nsteps, 1))
+    li = np.zeros(max(nsteps, 1), dtype=np.int32)
+    _check(ctx, load().mehdg_pseudo_time_newton(ctx, _ptr(v), _ptr(vhat), _ptr(q), int(nsteps), float(tau_init),
+                                                float(tau_max), float(lin_rtol), int(restart), int(max_iter),
+                                                rn.ctypes.data, ta.ctypes.data, li.ctypes.data, _stream(stream)),
+           "mehdg_pseudo_time_newton")
+    return rn, ta[:nsteps], li[:nsteps]
+
+
+def mehdg_condense_adjoint(ctx, g_V, g_Vhat, bhat_a, stream=None):
+    _check(ctx, load().mehdg_condense_adjoint(ctx, _ptr(g_V), _ptr(g_Vhat), _ptr(bhat_a), _stream(stream)),
+           "mehdg_condense_adjoint")
+
+
+def mehdg_apply_condensed_adjoint(ctx, x, y, stream=None):
+    _check(ctx, load().mehdg_apply_condensed_adjoint(ctx, _ptr(x), _ptr(y), _stream(stream)),
+           "mehdg_apply_condensed_adjoint")
+
+
+def mehdg_solve_condensed_adjoint(ctx, bhat_a, x, rtol=1e-10, restart=30, max_iter=500, stream=None, check=True):
+    it = C.c_int(0)
+    res = C.c_double(0.0)
+    rc = load().mehdg_solve_condensed_adjoint(ctx, _ptr(bhat_a), _ptr(x), float(rtol), int(restart), int(max_iter),
+                                              C.byref(it), C.byref(res), _stream(stream))
+    if check:
+        _check(ctx, rc, "mehdg_solve_condensed_adjoint")
+    return it.value, res.value
+
+
+def mehdg_recover_adjoint(ctx, g_V, lam_Vhat, lam_V, stream=None):
+    _check(ctx, load().mehdg_recover_adjoint(ctx, _ptr(g_V), _ptr(lam_Vhat), _ptr(lam_V), _stream(stream)),
+           "mehdg_recover_adjoint")
+
+
+def mehdg_pseudo_time_newton_vjp(ctx, v, vhat, nsteps, tau, gbar_v, gbar_vhat, g_v0, g_vhat0, lin_rtol=1e-12,
+                                 restart=30, max_iter=1000, fd_step=1e-5, stream=None):
+    _check(ctx, load().mehdg_pseudo_time_newton_vjp(ctx, _ptr(v), _ptr(vhat), int(nsteps), float(tau), float(lin_rtol),
+                                                    int(restart), int(max_iter), _ptr(gbar_v), _ptr(gbar_vhat),
+                                                    _ptr(g_v0), _ptr(g_vhat0), float(fd_step), _stream(stream)),
+           "mehdg_pseudo_time_newton_vjp")
+
+
+def mehdg_batch_layout(ctx, nK, G):
+    """host offsets (voff [nK+1], toff [G+1]) of a batch context's arrays"""
+    voff = np.zeros(nK + 1, dtype=np.int64)
+    toff = np.zeros(G + 1, dtype=np.int64)
+    _check(ctx, load().mehdg_batch_layout(ctx, voff.ctypes.data, toff.ctypes.data), "mehdg_batch_layout")
+    return voff, toff
+
+
+def mehdg_batch_autotune(ctx, trial_max=16, stream=None):
+    _check(ctx, load().mehdg_batch_autotune(ctx, int(trial_max), _stream(stream)), "mehdg_batch_autotune")
+
+
+def mehdg_batch_report(ctx) -> dict:
+    import json
+    n = load().mehdg_batch_report(ctx, None, 0)
+    if n < 0:
+        _check(ctx, n, "mehdg_batch_report")
+    buf = C.create_string_buffer(n + 1)
+    load().mehdg_batch_report(ctx, buf, n + 1)
+    return json.loads(buf.value.decode())
 
 
 def mehdg_last_error(ctx) -> str:
@@ -313,6 +401,61 @@ class Context:
 
     def status(self):
         return mehdg_status(self.ctx, self.mesh.nK)
+
+
+class BatchContext:
+    """Owner of one library context over macro-elements of uneven p and m
+    (inputs.UnevenMesh); arrays are flattened with mesh.voff / mesh.toff."""
+
+    def __init__(self, mesh, **params):
+        self.mesh = mesh
+        self.params = mehdg_default_params(**params)
+        self.ctx = mehdg_create(self.params)
+        mehdg_set_mesh(self.ctx, mesh.p, mesh.m, mesh.boxes, mesh.face_gid, mesh.n_global_faces)
+        self.voff, self.toff = mehdg_batch_layout(self.ctx, mesh.nK, mesh.n_global_faces)
+        assert (self.voff == mesh.voff).all() and (self.toff == mesh.toff).all()
+        self._state = None
+
+    close = Context.close
+    __del__ = Context.__del__
+    status = Context.status
+
+    def set_state(self, v, vhat, q=None, vstar=None):
+        self._state = (v, vhat, q, vstar)
+        mehdg_set_state(self.ctx, v, vhat, q, vstar)
+
+    def _t(self, n):
+        import torch
+        return torch.empty(n, dtype=torch.float64, device=self._state[0].device)
+
+    def residual(self):
+        RV, RH = self._t(self.voff[-1]), self._t(self.toff[-1])
+        RQ = self._t(3 * self.voff[-1]) if self.params.viscous else None
+        mehdg_residual(self.ctx, RV, RQ, RH)
+        return RV, RQ, RH
+
+    def condense(self, bhat=None):
+        bhat = self._t(self.toff[-1]) if bhat is None else bhat
+        mehdg_condense(self.ctx, bhat)
+        return bhat
+
+    def apply(self, x):
+        import torch
+        y = torch.empty_like(x)
+        mehdg_apply_condensed(self.ctx, x, y)
+        return y
+
+    def recover(self, dvh, with_dQ=False):
+        dV = self._t(self.voff[-1])
+        dQ = self._t(3 * self.voff[-1]) if self.params.viscous else None
+        mehdg_recover(self.ctx, dvh, dV, dQ)
+        return (dV, dQ) if with_dQ else dV
+
+    def autotune(self, trial_max=16):
+        mehdg_batch_autotune(self.ctx, trial_max)
+
+    def report(self):
+        return mehdg_batch_report(self.ctx)
 
 
 def residual_function():
