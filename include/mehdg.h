@@ -193,6 +193,29 @@ int mehdg_solve_condensed_adjoint(mehdg_ctx* ctx, const double* bhat_a, double* 
                                   int max_iter, int* iters, double* relres, void* stream);
 int mehdg_recover_adjoint(mehdg_ctx* ctx, const double* g_V, const double* lam_Vhat, double* lam_V, void* stream);
 
+/* A constant added to R_V by residual and condense: src DEVICE [nK][5][Nn]
+ * (caller-owned, kept until the next set_source; NULL removes it).  The
+ * known stages of a DIRK step enter the stage equation this way (eq. C242).
+ * Invalidates a previous condensation.  MEHDG_EINVAL for batch contexts. */
+int mehdg_set_source(mehdg_ctx* ctx, const double* src);
+
+/* One time step of size dt of the three-stage DIRK method of Sec. 5.3 (the
+ * third-order, L-stable, stiffly accurate DIRK(3,3) of Alexander; D = A^-1)
+ * on the state (v, vhat, q: DEVICE, updated in place; q NULL for Euler).
+ * Stage i solves eq. C242,
+ *   (d_ii/dt)(u(v) - u(v^n)) + sum_{j<i} (d_ij/dt)(u(v^{n,j}) - u(v^n)) + spatial terms = 0
+ * (tested against w), by Newton steps (condense, GMRES as
+ * mehdg_solve_condensed, recover) until the 2-norm of its residual is below
+ * newton_tol, at most newton_max steps; its stage term is the context's with
+ * step dt/d_ii and v* = v^n, the known stages a source (mehdg_set_source).
+ * The step's result is the last stage (eq. C241 with e = b^T D = e_3).
+ * HOST outputs (may be NULL): newton_iters [3], res_norms [3] (final stage
+ * residual norms).  Needs a context with the stage term; its dt is
+ * restored; on return it holds no state (call set_state next).  Returns
+ * MEHDG_ENOCONV when a stage does not reach newton_tol. */
+int mehdg_dirk_step(mehdg_ctx* ctx, double* v, double* vhat, double* q, double dt, double newton_tol, int newton_max,
+                    double lin_rtol, int restart, int max_iter, int* newton_iters, double* res_norms, void* stream);
+
 /* Vector-Jacobian product through nsteps pseudo-time Newton steps (Sec. 6.1,
  * eqs. C312, C31223) with a fixed step tau (Euler contexts of one element
  * type, created with the stage term).  Forward: from the state (v, vhat)
@@ -207,7 +230,8 @@ int mehdg_recover_adjoint(mehdg_ctx* ctx, const double* g_V, const double* lam_V
  * derivatives in v and v* = v cancel) and the last term, the transposed
  * second derivative along the step, is the central difference of the
  * residual VJP at s_k +- h d_k with v* = v_k fixed, h = fd_step max|s_k| /
- * max|d_k|.  The result is the cotangent (g_v0, g_vhat0) of the initial state
+ * max|d_k| (fd_step 1e-7 is a good choice: the ES and KEPES dissipations
+ * carry |.| kinks, e.g. |V-hat . n|, that a larger step can straddle).  The result is the cotangent (g_v0, g_vhat0) of the initial state
  * (DEVICE, same layouts).  Allocates the trajectory (2 nsteps + 8 state
  * vectors) for the call.  On return the context holds no state (call
  * set_state before the next residual or condense). */

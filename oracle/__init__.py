@@ -362,10 +362,15 @@ def adjoint_solve(prm, mesh, st, gV, gVh):
     return lam[:nv].reshape(mesh.nK, 5, mesh.Nn), lam[nv:].reshape(mesh.n_global_faces, 5, mesh.n2)
 
 
-def brute_force(prm, mesh, st):
+def brute_force(prm, mesh, st, src_V=None):
     """Monolithic Newton increment: assemble J over (Q, V, V-hat global) for all
-    elements and solve J d = -R with the oracle's GEPP (tiny meshes only)."""
+    elements and solve J d = -R with the oracle's GEPP (tiny meshes only).
+    src_V [K,5,Nn] (optional) is a constant added to R_V."""
     J, R = _assemble(prm, mesh, st)
+    if src_V is not None:
+        nq = mesh.nK * 15 * mesh.Nn if prm.viscous else 0
+        R = R.copy()
+        R[nq:nq + src_V.size] += np.asarray(src_V).ravel()
     nK, Nn, n2 = mesh.nK, mesh.Nn, mesh.n2
     Nv, Nq = 5 * Nn, 15 * Nn
     vis = bool(prm.viscous)
@@ -528,7 +533,7 @@ def condense_uneven(prm, mesh, st, Ks, dvh=None, procs=1):
     return out
 
 
-def newton_vjp(prm_kw, mesh, st, nsteps, tau, gbar_v, gbar_vh, fd_step=1e-5):
+def newton_vjp(prm_kw, mesh, st, nsteps, tau, gbar_v, gbar_vh, fd_step=1e-7):
     """Cotangent of the initial state (v0, vhat0) for the cotangent (gbar_v,
     gbar_vh) of the state after nsteps Newton steps with the stage term at
     v* = v_k and a fixed step tau (Sec. 6.1, eqs. C312, C31223; Euler):
@@ -564,3 +569,77 @@ def newton_vjp(prm_kw, mesh, st, nsteps, tau, gbar_v, gbar_vh, fd_step=1e-5):
     nv = mesh.nK * 5 * mesh.Nn
     return (g[:nv].reshape(st.v.shape), g[nv:].reshape(st.vhat.shape),
             State(v=v, vhat=vh, q=None, vstar=v.copy()))
+
+
+
+# ---------------------------------------------------------------- DIRK stages (Sec. 5.3)
+def dirk33():
+    """Butcher table (A, b, c) of the three-stage, third-order, L-stable,
+    stiffly accurate DIRK method of Alexander (the DIRK(3,3) of Sec. 7):
+    alpha is the root of x^3 - 3 x^2 + 3/2 x - 1/6 in (1/6, 1/2)."""
+    # bisection for the root (no tabulated digits)
+    lo, hi = 1.0 / 6.0, 0.5
+    f = lambda x: x ** 3 - 3 * x ** 2 + 1.5 * x - 1.0 / 6.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if f(lo) * f(mid) <= 0:
+            hi = mid
+        else:
+            lo = mid
+    a = 0.5 * (lo + hi)
+    t2 = (1 + a) / 2
+    b1 = -(6 * a * a - 16 * a + 1) / 4
+    b2 = (6 * a * a - 20 * a + 5) / 4
+    A = np.array([[a, 0, 0], [t2 - a, a, 0], [b1, b2, a]])
+    return A, np.array([b1, b2, a]), np.array([a, t2, 1.0])
+
+
+def stage_difference(prm_kw, mesh, st, va, vb):
+    """(u(va_h) - u(vb_h), w) over the volume quadrature, [K,5,Nn]: the
+    stage term of eq. C242 at dt = 1, as the difference of two residuals whose
+    other terms are identical (v = va, v* = vb against v* = va)."""
+    from paper_2507_22195_gb300.inputs import State
+    prm = params(dt=1.0, time_term=1, **prm_kw)
+    r1, _, _ = residual_mesh(prm, mesh, State(v=va, vhat=st.vhat, q=st.q, vstar=vb))
+    r0, _, _ = residual_mesh(prm, mesh, State(v=va, vhat=st.vhat, q=st.q, vstar=va))
+    return r1 - r0
+
+
+def dirk_step(prm_kw, mesh, st, dt, table=None, newton_tol=1e-11, newton_max=12):
+    """One step of a stiffly accurate DIRK method (eqs. C241, C242) from the
+    state st (v^n, vhat^n, q^n): stage i solves, by monolithic Newton,
+      (d_ii / dt)(u(v) - u(v^n)) + sum_{j<i} (d_ij / dt)(u(v^{n,j}) - u(v^n))
+        + spatial terms = 0       (tested against w; D = A^-1)
+    i.e. the residual with the stage term at v* = v^n and step dt / d_ii plus
+    the known stages as a source; u^{n+1} = u^{n,s} (e = b^T D = e_s for a
+    stiffly accurate table).  Returns (state after the step, [stage states],
+    [Newton iterations per stage])."""
+    from paper_2507_22195_gb300.inputs import State
+    A, b, c = dirk33() if table is None else table
+    D = np.linalg.inv(A)
+    s = A.shape[0]
+    vn = st.v.copy()
+    cur = State(v=st.v.copy(), vhat=st.vhat.copy(), q=None if st.q is None else st.q.copy(), vstar=vn)
+    stages, its = [], []
+    for i in range(s):
+        src = np.zeros_like(vn)
+        for j in range(i):
+            src += D[i, j] / dt * stage_difference(prm_kw, mesh, cur, stages[j].v, vn)
+        prm = params(dt=dt / D[i, i], **prm_kw)
+        k = 0
+        for k in range(newton_max):
+            cur.vstar = vn
+            RV, RQ, RH = residual_mesh(prm, mesh, cur)
+            rn = np.sqrt(np.sum((RV + src) ** 2) + np.sum(RH ** 2) + (0 if RQ is None else np.sum(RQ ** 2)))
+            if rn < newton_tol:
+                break
+            dQ, dV, dH = brute_force(prm, mesh, cur, src_V=src)
+            cur.v = cur.v + dV
+            cur.vhat = cur.vhat + dH
+            if cur.q is not None:
+                cur.q = cur.q + dQ
+        its.append(k)
+        stages.append(State(v=cur.v.copy(), vhat=cur.vhat.copy(), q=None if cur.q is None else cur.q.copy(),
+                            vstar=vn))
+    out = State(v=cur.v.copy(), vhat=cur.vhat.copy(), q=None if cur.q is None else cur.q.copy(), vstar=cur.v.copy())
+    return out, stages, its

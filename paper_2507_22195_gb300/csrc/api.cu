@@ -371,6 +371,7 @@ int mehdg_residual(mehdg_ctx* c, double* R_V, double* R_Q, double* R_Vhat, void*
     a.RV = R_V; a.RQ = viscous(c) ? R_Q : nullptr; a.RH = c->d_RHloc;
     int ev = prof_begin(&c->prof, PH_RESIDUAL, st);
     TRY(launch_residual(a, c->nK, viscous(c), false, st));
+    if (c->src) TRY(launch_add(c->src, R_V, c->nK * (int64_t)c->Nv, st));
     prof_end(&c->prof, ev, st, 0.0);
     TRY(launch_trace_gather(c->d_RHloc, c->d_g2l, c->G, c->tab.n2, R_Vhat, 1.0, nullptr, 0.0, st));
     return MEHDG_OK;
@@ -403,6 +404,7 @@ int mehdg_condense(mehdg_ctx* c, double* bhat, double* Ahat_local, void* stream)
     a.RV = c->d_RV; a.RH = c->d_RHloc; a.RQ = vis ? c->d_RQ : nullptr;
     int ev = prof_begin(&c->prof, PH_RESIDUAL, st);
     TRY(launch_residual(a, nK, vis, false, st));
+    if (c->src) TRY(launch_add(c->src, c->d_RV, nK * (int64_t)c->Nv, st));
     prof_end(&c->prof, ev, st, 0.0);
     // z = A_qq^-1 R_Q
     int rc;

@@ -155,6 +155,7 @@ struct mehdg_ctx {
     int64_t* d_g2l = nullptr;           // [G][2] (K*6+f) or -1
     // state (caller-owned)
     const double *v = nullptr, *vh = nullptr, *q = nullptr, *vs = nullptr;
+    const double* src = nullptr;        // optional constant added to R_V ([nK][5][Nn], caller-owned)
     // workspaces
     double* d_RV = nullptr;             // [nK][5][Nn]      residual at the condensed state
     double* d_RHloc = nullptr;          // [nK][6][5][n2]   per-element trace residual

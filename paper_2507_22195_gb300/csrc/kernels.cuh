@@ -97,3 +97,5 @@ cudaError_t launch_vjp(mehdg_ctx* c, const double* lam_V, const double* lam_Vhat
 typedef int (*trace_op_fn)(mehdg_ctx* c, const double* x, double* y, void* stream);
 int gmres_trace(mehdg_ctx* c, trace_op_fn op, const double* b, double* x, double rtol, int restart, int max_iter,
                 int* iters_out, double* relres_out, void* stream);
+// y += x (n doubles; newton.cu)
+cudaError_t launch_add(const double* x, double* y, int64_t n, cudaStream_t st);

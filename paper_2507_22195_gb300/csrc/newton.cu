@@ -12,6 +12,7 @@
 // the stage term at v* = v.
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <vector>
 #include "common.cuh"
 #include "kernels.cuh"
@@ -49,6 +50,15 @@ __global__ void sum_partials_kernel(const double* __restrict__ partial, int nb, 
 __global__ void add_kernel(const double* __restrict__ x, double* __restrict__ y, int64_t n) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         y[i] += x[i];
+}
+
+__global__ void sub_kernel(const double* __restrict__ x, double* __restrict__ y, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] -= x[i];
+}
+__global__ void axpy_s_kernel(double a, const double* __restrict__ x, double* __restrict__ y, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] += a * x[i];
 }
 
 unsigned grid_n(int64_t n) {
@@ -101,6 +111,150 @@ int residual_norm(mehdg_ctx* c, const NewtonWork& w, double* out, cudaStream_t s
 }
 
 }  // namespace
+
+cudaError_t launch_add(const double* x, double* y, int64_t n, cudaStream_t st) {
+    add_kernel<<<grid_n(n), 256, 0, st>>>(x, y, n);
+    MEHDG_COUNT(1);
+    return cudaGetLastError();
+}
+
+extern "C" int mehdg_set_source(mehdg_ctx* c, const double* src) {
+    if (!c) return MEHDG_EINVAL;
+    if (c->batch) { set_err(c, "set_source: not available for elements of uneven p, m"); return MEHDG_EINVAL; }
+    c->src = src;
+    c->condensed = false;
+    return MEHDG_OK;
+}
+
+namespace {
+
+// out = (u(va_h) - u(vb_h), w): the stage term at dt = 1, as the difference of
+// two residual evaluations whose other terms are identical
+int stage_difference(mehdg_ctx* c, const double* va, const double* vb, double* out, double* tmp, cudaStream_t st) {
+    ResidualArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.tab = c->tab; a.ph = c->ph; a.box = c->d_box; a.gid = c->d_gid;
+    a.ph.inv_dt = 1.0; a.ph.time_term = 1;
+    a.vh = c->vh; a.q = c->q; a.status = c->d_status;
+    a.RH = c->d_tRHloc2;
+    a.v = va; a.vs = vb; a.RV = out;
+    NTRY(launch_residual(a, c->nK, c->prm.viscous != 0, false, st));
+    a.vs = va; a.RV = tmp;
+    NTRY(launch_residual(a, c->nK, c->prm.viscous != 0, false, st));
+    const int64_t nv = c->nK * (int64_t)c->Nv;
+    sub_kernel<<<grid_n(nv), 256, 0, st>>>(tmp, out, nv);
+    MEHDG_COUNT(1);
+    NTRY(cudaGetLastError());
+    return MEHDG_OK;
+}
+
+// Butcher table of the three-stage, third-order, L-stable, stiffly accurate
+// DIRK method of Alexander: alpha is the root of x^3 - 3x^2 + 3/2 x - 1/6 in
+// (1/6, 1/2) (found by bisection); D = A^-1 (lower triangular)
+void dirk33_D(double D[3][3]) {
+    double lo = 1.0 / 6.0, hi = 0.5;
+    auto f = [](double x) { return x * x * x - 3.0 * x * x + 1.5 * x - 1.0 / 6.0; };
+    for (int i = 0; i < 200; ++i) {
+        const double mid = 0.5 * (lo + hi);
+        if (f(lo) * f(mid) <= 0.0) hi = mid; else lo = mid;
+    }
+    const double al = 0.5 * (lo + hi), t2 = 0.5 * (1.0 + al);
+    const double b1 = -(6.0 * al * al - 16.0 * al + 1.0) / 4.0, b2 = (6.0 * al * al - 20.0 * al + 5.0) / 4.0;
+    const double A[3][3] = {{al, 0, 0}, {t2 - al, al, 0}, {b1, b2, al}};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) D[i][j] = 0.0;
+    for (int j = 0; j < 3; ++j) {         // column j of A^-1 by forward substitution
+        for (int i = 0; i < 3; ++i) {
+            double s = i == j ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) s -= A[i][k] * D[k][j];
+            D[i][j] = s / A[i][i];
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" int mehdg_dirk_step(mehdg_ctx* c, double* v, double* vhat, double* q, double dt, double newton_tol,
+                               int newton_max, double lin_rtol, int restart, int max_iter, int* newton_iters,
+                               double* res_norms, void* stream) {
+    if (!c) return MEHDG_EINVAL;
+    if (c->nK == 0) { set_err(c, "dirk_step before set_mesh"); return MEHDG_ESTATE; }
+    if (c->batch || !c->prm.time_term) { set_err(c, "dirk_step: one element type, with the stage term"); return MEHDG_EINVAL; }
+    if (!v || !vhat || (c->prm.viscous && !q) || !(dt > 0.0) || !(newton_tol > 0.0) || newton_max < 1 ||
+        !(lin_rtol > 0.0) || restart < 1 || max_iter < 1) {
+        set_err(c, "dirk_step: bad arguments");
+        return MEHDG_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    NewtonWork w;
+    const size_t need = newton_layout(c, &w, nullptr);
+    if (c->newton_bytes < need) {
+        if (c->d_newton) cudaFree(c->d_newton);
+        c->d_newton = nullptr; c->newton_bytes = 0;
+        if (cudaMalloc(&c->d_newton, need) != cudaSuccess) { set_err(c, "dirk_step: out of memory"); return MEHDG_ENOMEM; }
+        c->newton_bytes = need;
+    }
+    newton_layout(c, &w, reinterpret_cast<unsigned char*>(c->d_newton));
+    const int64_t nv = c->nK * (int64_t)c->Nv, nt = c->G * 5 * (int64_t)c->tab.n2, nq = 3 * nv;
+    // v^n, the stages, the source and a difference buffer
+    double* buf = nullptr;
+    if (cudaMalloc((void**)&buf, sizeof(double) * 7 * (size_t)nv) != cudaSuccess) {
+        set_err(c, "dirk_step: out of memory"); return MEHDG_ENOMEM;
+    }
+    double *vn = buf, *stg = buf + nv, *src = buf + 4 * nv, *dif = buf + 5 * nv, *tmp = buf + 6 * nv;
+    const double dt0 = c->prm.dt;
+    double D[3][3];
+    dirk33_D(D);
+    auto done = [&](int rc) {
+        c->src = nullptr;
+        mehdg_set_dt(c, dt0);
+        cudaFree(buf);
+        // the context's v* and source pointed into the freed buffer
+        c->v = nullptr; c->vh = nullptr; c->vs = nullptr; c->q = nullptr; c->condensed = false;
+        return rc;
+    };
+#define DTRY(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { set_err(c, "%s: %s", #x, cudaGetErrorString(e_)); return done(MEHDG_ECUDA); } } while (0)
+#define DRC(x) do { int r_ = (x); if (r_) return done(r_); } while (0)
+    DTRY(cudaMemcpyAsync(vn, v, sizeof(double) * nv, cudaMemcpyDeviceToDevice, st));
+    DRC(mehdg_set_state(c, v, vhat, q, vn, stream));
+    for (int i = 0; i < 3; ++i) {
+        // known stages: src = sum_{j<i} (d_ij / dt) (u(v^{n,j}) - u(v^n), w)
+        DTRY(cudaMemsetAsync(src, 0, sizeof(double) * nv, st));
+        for (int j = 0; j < i; ++j) {
+            DRC(stage_difference(c, stg + (size_t)j * nv, vn, dif, tmp, st));
+            axpy_s_kernel<<<grid_n(nv), 256, 0, st>>>(D[i][j] / dt, dif, src, nv);
+            MEHDG_COUNT(1);
+        }
+        DRC(mehdg_set_dt(c, dt / D[i][i]));
+        DRC(mehdg_set_source(c, i > 0 ? src : nullptr));
+        int it = 0;
+        double rn = 0.0;
+        for (;; ++it) {
+            DRC(mehdg_set_state(c, v, vhat, q, vn, stream));
+            DRC(residual_norm(c, w, &rn, st));
+            if (!std::isfinite(rn)) { set_err(c, "dirk_step: non-finite residual in stage %d", i); return done(MEHDG_ENONPHYS); }
+            if (rn <= newton_tol || it == newton_max) break;
+            DRC(mehdg_condense(c, w.bhat, nullptr, stream));
+            DTRY(cudaMemsetAsync(w.dvh, 0, sizeof(double) * nt, st));
+            DRC(mehdg_solve_condensed(c, w.bhat, w.dvh, lin_rtol, restart, max_iter, nullptr, nullptr, stream));
+            DRC(mehdg_recover(c, w.dvh, w.dV, c->prm.viscous ? w.dQ : nullptr, stream));
+            add_kernel<<<grid_n(nv), 256, 0, st>>>(w.dV, v, nv);
+            add_kernel<<<grid_n(nt), 256, 0, st>>>(w.dvh, vhat, nt);
+            MEHDG_COUNT(2);
+            if (c->prm.viscous) { add_kernel<<<grid_n(nq), 256, 0, st>>>(w.dQ, q, nq); MEHDG_COUNT(1); }
+            DTRY(cudaGetLastError());
+        }
+        if (newton_iters) newton_iters[i] = it;
+        if (res_norms) res_norms[i] = rn;
+        if (rn > newton_tol) { set_err(c, "dirk_step: stage %d residual %.3e after %d Newton steps", i, rn, it); return done(MEHDG_ENOCONV); }
+        DTRY(cudaMemcpyAsync(stg + (size_t)i * nv, v, sizeof(double) * nv, cudaMemcpyDeviceToDevice, st));
+    }
+    DTRY(cudaStreamSynchronize(st));
+    // stiffly accurate: u^{n+1} = u^{n,3}, already in (v, vhat, q)
+    return done(MEHDG_OK);
+#undef DTRY
+#undef DRC
+}
 
 extern "C" int mehdg_set_dt(mehdg_ctx* c, double dt) {
     if (!c) return MEHDG_EINVAL;

@@ -30,7 +30,7 @@ EXPORTED = ["mehdg_default_params", "mehdg_create", "mehdg_set_mesh", "mehdg_set
             "mehdg_residual_vjp", "mehdg_status_device", "mehdg_set_dt", "mehdg_pseudo_time_newton",
             "mehdg_batch_layout", "mehdg_batch_autotune", "mehdg_batch_report", "mehdg_condense_adjoint",
             "mehdg_apply_condensed_adjoint", "mehdg_solve_condensed_adjoint", "mehdg_recover_adjoint",
-            "mehdg_pseudo_time_newton_vjp"]
+            "mehdg_pseudo_time_newton_vjp", "mehdg_set_source", "mehdg_dirk_step"]
 
 
 class mehdg_params(C.Structure):
@@ -73,6 +73,9 @@ def load(path: str | None = None):
     L.mehdg_apply_condensed_adjoint.argtypes = [_vp, _vp, _vp, _vp]
     L.mehdg_solve_condensed_adjoint.argtypes = [_vp, _vp, _vp, C.c_double, C.c_int, C.c_int, _vp, _vp, _vp]
     L.mehdg_recover_adjoint.argtypes = [_vp, _vp, _vp, _vp, _vp]
+    L.mehdg_set_source.argtypes = [_vp, _vp]
+    L.mehdg_dirk_step.argtypes = [_vp, _vp, _vp, _vp, C.c_double, C.c_double, C.c_int, C.c_double, C.c_int, C.c_int,
+                                  _vp, _vp, _vp]
     L.mehdg_pseudo_time_newton_vjp.argtypes = [_vp, _vp, _vp, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
                                                _vp, _vp, _vp, _vp, C.c_double, _vp]
     L.mehdg_batch_autotune.argtypes = [_vp, C.c_int64, _vp]
@@ -244,11 +247,27 @@ def mehdg_recover_adjoint(ctx, g_V, lam_Vhat, lam_V, stream=None):
 
 
 def mehdg_pseudo_time_newton_vjp(ctx, v, vhat, nsteps, tau, gbar_v, gbar_vhat, g_v0, g_vhat0, lin_rtol=1e-12,
-                                 restart=30, max_iter=1000, fd_step=1e-5, stream=None):
+                                 restart=30, max_iter=1000, fd_step=1e-7, stream=None):
     _check(ctx, load().mehdg_pseudo_time_newton_vjp(ctx, _ptr(v), _ptr(vhat), int(nsteps), float(tau), float(lin_rtol),
                                                     int(restart), int(max_iter), _ptr(gbar_v), _ptr(gbar_vhat),
                                                     _ptr(g_v0), _ptr(g_vhat0), float(fd_step), _stream(stream)),
            "mehdg_pseudo_time_newton_vjp")
+
+
+def mehdg_set_source(ctx, src):
+    _check(ctx, load().mehdg_set_source(ctx, _ptr(src)), "mehdg_set_source")
+
+
+def mehdg_dirk_step(ctx, v, vhat, q, dt, newton_tol=1e-11, newton_max=12, lin_rtol=1e-12, restart=30, max_iter=2000,
+                    stream=None):
+    """One DIRK(3,3) step on the device state (in place); returns (Newton
+    steps per stage, final residual norm per stage)."""
+    its = np.zeros(3, dtype=np.int32)
+    rn = np.zeros(3)
+    _check(ctx, load().mehdg_dirk_step(ctx, _ptr(v), _ptr(vhat), _ptr(q), float(dt), float(newton_tol),
+                                       int(newton_max), float(lin_rtol), int(restart), int(max_iter),
+                                       its.ctypes.data, rn.ctypes.data, _stream(stream)), "mehdg_dirk_step")
+    return its, rn
 
 
 def mehdg_batch_layout(ctx, nK, G):

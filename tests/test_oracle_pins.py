@@ -662,3 +662,28 @@ def test_oracle_residual_vjp_against_central_differences():
     fd = (vals[0] - vals[1]) / (2 * eps)
     ad = (gv * dv).sum() + (gh * dh).sum()
     assert abs(fd - ad) < 1e-7 * abs(ad), (fd, ad)
+
+
+def test_dirk33_table_and_third_order_in_time():
+    """DIRK(3,3) (Sec. 5.3): the table satisfies the order conditions up to
+    order 3 (b.1 = 1, b.c = 1/2, b.c^2 = 1/3, b.A c = 1/6, c = A 1) and is
+    stiffly accurate; on a perturbed TGV the oracle's steps show third order in
+    time: with errors against the finest of dt, dt/2, dt/4, the ratio
+    |u_dt - u_dt/4| / |u_dt/2 - u_dt/4| is 2^p + 1 = 9 for order p = 3
+    asymptotically (5 for p = 2)."""
+    A, b, c = oracle.dirk33()
+    assert abs(b.sum() - 1) < 1e-14 and abs(b @ c - 0.5) < 1e-14
+    assert abs(b @ c ** 2 - 1 / 3) < 1e-14 and abs(b @ A @ c - 1 / 6) < 1e-14
+    assert np.allclose(A.sum(1), c, atol=1e-14) and np.allclose(A[-1], b, atol=1e-15)
+    mesh = I.periodic_mesh(2, 1, 1)
+    st0 = I.make_state(mesh, "tgv", 2e-2, 5, 6, M0=0.3)
+    kw = dict(flux=1, Mach=0.3)
+    T, res = 0.4, {}
+    for n in (2, 4, 8):
+        st = st0
+        for _ in range(n):
+            st, _, its = oracle.dirk_step(kw, mesh, st, T / n)
+            assert max(its) < 12
+        res[n] = st.v
+    ratio = np.linalg.norm(res[2] - res[8]) / np.linalg.norm(res[4] - res[8])
+    assert 7.0 < ratio < 10.0, ratio
