@@ -138,7 +138,7 @@ def oracle_sample(mesh, st, prm_kw, Ks, dvh, procs):
     t = time.time()
     res = oracle.condense_elements(prm, mesh, st, Ks, dvh, procs=procs)
     dt = time.time() - t
-    return len(Ks) / dt, [r[3] for r in res], {K: r[1] for K, r in zip(Ks, res)}
+    return len(Ks) / dt, [r[3] for r in res], {K: (r[1], r[0]) for K, r in zip(Ks, res)}
 
 
 def _oracle_prm(kw):
@@ -357,7 +357,7 @@ def uneven_batch(nK, dev, barrier, M, sample_per_group=2):
     ctx = M.BatchContext(mesh, prec=PREC["bf16x3"], **kw)
     ctx.set_state(*w)
     t0 = time.perf_counter()
-    ctx.autotune(trial_max=16)
+    ctx.autotune(trial_max=8)
     torch.cuda.synchronize()
     tune_s = time.perf_counter() - t0
     bh = torch.empty(int(mesh.toff[-1]), dtype=torch.float64, device=d)
@@ -552,11 +552,28 @@ def main():
     bh_mixed = bh.clone()
     err_or = None
     if ref_dV:
-        e = {K: float(np.linalg.norm(dV_np[K] - d) / np.linalg.norm(d)) for K, d in ref_dV.items()}
-        err_or = {"value": max(e.values()), "median": float(statistics.median(e.values())),
-                  "what": "max over the oracle's sample elements of ||dV^K_gpu - dV^K_oracle|| / ||dV^K_oracle||, "
-                          "dV recovered for the seeded dVhat after this condensation",
-                  "per_element": {str(K): float("%.3g" % x) for K, x in sorted(e.items())}}
+        e = {K: float(np.linalg.norm(dV_np[K] - d[0]) / np.linalg.norm(d[0])) for K, d in ref_dV.items()}
+        # b-hat^K of the sample elements: the same elements in a context of their own with unshared
+        # faces (each face one element side), the same state and precision
+        Ks = sorted(ref_dV)
+        sub = I.unshared(mesh, Ks)
+        gsel = mesh.face_gid[Ks].ravel()
+        s_sub = I.State(v=st.v[Ks].copy(), vhat=st.vhat[gsel].copy(), q=None, vstar=st.vstar[Ks].copy())
+        csub = M.Context(sub, prec=PREC[a.prec], **kw)
+        csub.set_state(*_to_dev(s_sub, dev))
+        bsub = csub.condense().cpu().numpy()
+        csub.close()
+        eb = {K: float(np.linalg.norm(bsub[6 * i:6 * i + 6] - ref_dV[K][1]) / np.linalg.norm(ref_dV[K][1]))
+              for i, K in enumerate(Ks)}
+        err_or = {"value": max(max(e.values()), max(eb.values())),
+                  "what": "max over the oracle's sample elements of the relative errors of b-hat^K and of dV^K "
+                          "(recovered for the seeded dVhat after this condensation)",
+                  "bhat_max": max(eb.values()), "bhat_median": float(statistics.median(eb.values())),
+                  "dV_max": max(e.values()), "dV_median": float(statistics.median(e.values())),
+                  "dV_per_element": {str(K): float("%.3g" % x) for K, x in sorted(e.items())},
+                  "note": "KEPES: at a face point with P close to P-hat the hybrid's theta = sqrt(|P - P-hat| / "
+                          "(P + P-hat)) has an unbounded derivative, and dV^K of such an element moves by up to "
+                          "1e-8 under a one-ulp change of the inputs in the oracle itself"}
 
     # roofline of the dominant kernel: the outer trailing update of the LU
     pk = peaks()
@@ -605,13 +622,22 @@ def main():
         ctx.close()
     del v, vh, q, vs
     torch.cuda.empty_cache()
+    def side(fn, *args):
+        """a measurement beside the headline: its failure is reported in its key"""
+        try:
+            return fn(*args)
+        except Exception as ex:                       # noqa: BLE001
+            torch.cuda.synchronize()
+            return {"error": f"{type(ex).__name__}: {ex}"[:400]}
+        finally:
+            torch.cuda.empty_cache()
+
     visc = None
     if a.workload == "tgv_inviscid" and a.viscous_block > 0 and world == 1:
-        visc = viscous_wave(a.viscous_block, dev, barrier, M)
-    torch.cuda.empty_cache()
+        visc = side(viscous_wave, a.viscous_block, dev, barrier, M)
     unev = None
     if a.workload == "tgv_inviscid" and a.uneven > 0 and world == 1:
-        unev = uneven_batch(a.uneven, dev, barrier, M)
+        unev = side(uneven_batch, a.uneven, dev, barrier, M)
 
     if rank == 0:
         out = {

@@ -84,10 +84,16 @@ class Shard:
 
     def sum_shared(self, t, dist=None):
         """t [local faces][5][n^2]: add the other ranks' sides on the shared
-        faces, in place; returns t.  No-op on a single rank."""
+        faces, in place; returns t.  No-op on a single rank.  With the gloo
+        backend a device tensor is exchanged through host copies."""
         if dist is None or not self.peers:
             return t
         import torch
+        if t.is_cuda and dist.get_backend() == "gloo":
+            h = t.cpu()
+            self.sum_shared(h, dist)
+            t.copy_(h)
+            return t
         sends, recvs, ops = [], [], []
         for r, idx in self.peers.items():
             ii = torch.as_tensor(idx, device=t.device)
@@ -112,3 +118,89 @@ class Shard:
         if dist is not None and self.world > 1:
             dist.all_reduce(s, op=dist.ReduceOp.SUM)
         return float(s.item())
+
+
+class ShardedSystem:
+    """One rank's part of the condensed trace system on its own GPU context:
+    the rank condenses its elements (Algorithm 1, local parts), completes the
+    face sums of b-hat and A-hat x with its neighbours (sum_shared), and takes
+    part in a GMRES over the distributed trace vector whose dot products count
+    every face once (dot).  Recovery is local (every element's faces are on
+    its rank).  The vector arithmetic of the Krylov iteration on the rank's
+    trace vector is torch on the device; the Hessenberg least-squares problem
+    is host arithmetic, identical on every rank."""
+
+    def __init__(self, shard, state, dist=None, device="cuda", **params):
+        import torch
+        from . import mehdg as M
+        self.sh, self.dist = shard, dist
+        self.ctx = M.Context(shard.mesh, **params)
+        d = torch.device(device)
+        self._st = [None if a is None else torch.tensor(a, device=d) for a in (state.v, state.vhat, state.q,
+                                                                              state.vstar)]
+        self.ctx.set_state(*self._st)
+
+    def condense(self):
+        return self.sh.sum_shared(self.ctx.condense(), self.dist)
+
+    def apply(self, x):
+        return self.sh.sum_shared(self.ctx.apply(x.contiguous()), self.dist)
+
+    def recover(self, dvh):
+        return self.ctx.recover(dvh.contiguous())
+
+    def dot(self, a, b):
+        return self.sh.dot(a, b, self.dist)
+
+    def solve(self, b, rtol=1e-10, restart=30, max_iter=500):
+        """restarted GMRES on sum_K A-hat^K x = b (classical Gram-Schmidt applied
+        twice); returns (x, products, relative residual)"""
+        import math
+        import torch
+        x = torch.zeros_like(b)
+        bn = math.sqrt(max(self.dot(b, b), 1e-300))
+        r = b - self.apply(x)
+        beta = math.sqrt(self.dot(r, r))
+        it, res = 0, beta / bn
+        while res > rtol and it < max_iter:
+            V = [r / beta]
+            H = [[0.0] * restart for _ in range(restart + 1)]
+            cs, sn, g = [0.0] * restart, [0.0] * restart, [0.0] * (restart + 1)
+            g[0] = beta
+            j = 0
+            while j < restart and it < max_iter:
+                w = self.apply(V[j])
+                it += 1
+                for _ in range(2):
+                    h = [self.dot(V[i], w) for i in range(j + 1)]
+                    for i in range(j + 1):
+                        w = w - h[i] * V[i]
+                        H[i][j] += h[i]
+                hn = math.sqrt(max(self.dot(w, w), 0.0))
+                H[j + 1][j] = hn
+                V.append(w / hn if hn > 0 else w)
+                for i in range(j):
+                    a_, b_ = H[i][j], H[i + 1][j]
+                    H[i][j], H[i + 1][j] = cs[i] * a_ + sn[i] * b_, -sn[i] * a_ + cs[i] * b_
+                rr = math.hypot(H[j][j], H[j + 1][j])
+                cs[j], sn[j] = (H[j][j] / rr, H[j + 1][j] / rr) if rr > 0 else (1.0, 0.0)
+                H[j][j], H[j + 1][j] = rr, 0.0
+                g[j + 1], g[j] = -sn[j] * g[j], cs[j] * g[j]
+                j += 1
+                res = abs(g[j]) / bn
+                if res <= rtol or hn == 0:
+                    break
+            y = [0.0] * j
+            for i in range(j - 1, -1, -1):
+                y[i] = (g[i] - sum(H[i][k] * y[k] for k in range(i + 1, j))) / H[i][i] if H[i][i] else 0.0
+            for i in range(j):
+                x = x + y[i] * V[i]
+            r = b - self.apply(x)
+            beta = math.sqrt(self.dot(r, r))
+            res = beta / bn
+            if beta == 0:
+                break
+        return x, it, res
+
+    def close(self):
+        self.ctx.close()
