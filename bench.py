@@ -412,6 +412,50 @@ def uneven_batch(nK, dev, barrier, M, sample_per_group=2):
                          "status_ok": outs["fp64"][2] and outs["bf16x3"][2]}}
 
 
+def graph_condense(dev, barrier, M, steps=20):
+    """direct calls against the condensation replayed from one CUDA graph, on
+    two launch-bound cases: the 2^3 x 2^3, p = 2 vortex (configs[0], 8
+    elements) and a resident batch of 2048 elements with p in {1, 2, 3} and
+    m in {2, 3} (seed 22204; inviscid TGV-like fields, ES, split BF16)"""
+    import torch
+    from paper_2507_22195_gb300 import inputs as I
+    out = {}
+    cases = []
+    mesh, st, kw = workload("vortex")
+    cases.append(("vortex_8", lambda: M.Context(mesh, prec=PREC["bf16x3"], **kw), mesh.nK,
+                  (st.v, st.vhat, None, st.vstar), (mesh.n_global_faces, 5, mesh.n2)))
+    um = I.uneven_batch(2048, 22204, p_choices=(1, 2, 3), m_choices=(2, 3))
+    us = I.make_uneven_state(um, 1e-2, 22205, 22206, 22207)
+    cases.append(("uneven_2048", lambda: M.BatchContext(um, prec=PREC["bf16x3"], flux=1, Mach=0.1), um.nK,
+                  (us.v, us.vhat, None, us.vstar), (int(um.toff[-1]),)))
+    for name, make, nK, state, bshape in cases:
+        c = make()
+        w = [None if a is None else torch.tensor(a, device=dev) for a in state]
+        c.set_state(*w)
+        bh = torch.empty(bshape, dtype=torch.float64, device=dev)
+        for _ in range(3):
+            c.condense(bh)
+        ms_d = timed_condense(c, bh, steps, barrier)
+        M.mehdg_condense_graph(c.ctx, bh)
+        for _ in range(2):
+            M.mehdg_condense_graph(c.ctx, bh)
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        for _ in range(steps):
+            M.mehdg_condense_graph(c.ctx, bh)
+        e1.record(stream)
+        barrier()
+        ms_g = e0.elapsed_time(e1)
+        stt, _ = c.status()
+        out[name] = {"elements": nK, "direct": nK * steps / (ms_d / 1e3), "graph": nK * steps / (ms_g / 1e3),
+                     "unit": UNIT, "steps": steps, "status_ok": bool((stt == 0).all())}
+        c.close()
+        del w
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -638,6 +682,7 @@ def main():
     unev = None
     if a.workload == "tgv_inviscid" and a.uneven > 0 and world == 1:
         unev = side(uneven_batch, a.uneven, dev, barrier, M)
+    graph = side(graph_condense, dev, barrier, M) if a.workload == "tgv_inviscid" and world == 1 else None
 
     if rank == 0:
         out = {
@@ -663,6 +708,7 @@ def main():
             "fp64_gpu": fp,
             "viscous_tgv": visc,
             "uneven_batch": unev,
+            "graph_condense": graph,
             "recover": rec,
         }
         print(json.dumps(out))

@@ -151,6 +151,20 @@ int mehdg_residual(mehdg_ctx* ctx, double* R_V, double* R_Q, double* R_Vhat, voi
  * Ahat_local must be NULL (the explicit A-hat^K is not formed; use apply). */
 int mehdg_condense(mehdg_ctx* ctx, double* bhat, double* Ahat_local, void* stream);
 
+/* The same condensation as mehdg_condense (Ahat_local NULL), replayed from
+ * one CUDA graph: the first call (and any call after set_state, set_source or
+ * a batch's state changed pointers, or with another bhat) condenses once
+ * directly, then records the whole condensation -- residual, Jacobian,
+ * Q-elimination, LU, refinement, b-hat; for a batch context every (p, m)
+ * group in order -- and later calls launch that graph.  For the recording
+ * the refinement runs all refine_max_iter sweeps without synchronising the
+ * stream; elements that have converged skip the remaining sweeps on the
+ * device, so the result equals mehdg_condense's.  The graph reads the state
+ * through the pointers given to set_state: new values in the same arrays
+ * need no new recording (a batch context gathers them in set_state).
+ * MEHDG_EINVAL for a batch streamed in waves or with phase profiling on. */
+int mehdg_condense_graph(mehdg_ctx* ctx, double* bhat, void* stream);
+
 /* y = A-hat x for a global trace vector x (the four stages y1..y4 of
  * Sec. 6.3 summed over elements).  Needs a prior condense.  Device. */
 int mehdg_apply_condensed(mehdg_ctx* ctx, const double* x, double* y, void* stream);

@@ -48,6 +48,11 @@ void free_mesh(mehdg_ctx* c) {
     if (c->d_newton) { cudaFree(c->d_newton); c->d_newton = nullptr; c->newton_bytes = 0; }
     if (c->d_adj) { cudaFree(c->d_adj); c->d_adj = nullptr; c->adj_bytes = 0; }
     if (c->lu_graph) { cudaGraphExecDestroy(c->lu_graph); c->lu_graph = nullptr; }
+    if (c->cond_graph) { cudaGraphExecDestroy(c->cond_graph); c->cond_graph = nullptr; }
+    if (c->cap_in) { cudaEventDestroy(c->cap_in); c->cap_in = nullptr; }
+    if (c->cap_out) { cudaEventDestroy(c->cap_out); c->cap_out = nullptr; }
+    if (c->cap_stream) { cudaStreamDestroy(c->cap_stream); c->cap_stream = nullptr; }
+    for (auto& k : c->cap_key) k = nullptr;
     if (c->lu_ev_in) { cudaEventDestroy(c->lu_ev_in); c->lu_ev_in = nullptr; }
     if (c->lu_ev_out) { cudaEventDestroy(c->lu_ev_out); c->lu_ev_out = nullptr; }
     if (c->zs_ev_in) { cudaEventDestroy(c->zs_ev_in); c->zs_ev_in = nullptr; }
@@ -83,7 +88,9 @@ cudaError_t factor_all(mehdg_ctx* c, const LUPlan& P, cudaStream_t st) {
     // MEHDG_NO_GRAPH=1: direct launches (e.g. under a kernel profiler that
     // replays launches one by one)
     static const bool no_graph = [] { const char* e = std::getenv("MEHDG_NO_GRAPH"); return e && e[0] == '1'; }();
-    if (c->prof.on || no_graph || c->lu_graph_failed) return lu_factor(P, st);
+    // (while the whole condensation is being recorded, its LU kernels go into that graph directly:
+    // a graph launch cannot be part of a stream capture)
+    if (c->prof.on || no_graph || c->lu_graph_failed || c->graph_refine) return lu_factor(P, st);
     cudaError_t e;
     if (!c->lu_graph) {
         if (!c->lu_stream && (e = cudaStreamCreateWithFlags(&c->lu_stream, cudaStreamNonBlocking)) != cudaSuccess) return e;
@@ -201,6 +208,8 @@ int refine_solve(mehdg_ctx* c, const double* r, double* x, cudaStream_t st) {
         TRY(launch_refine_update(nK, c->Nv, ld, r, c->d_tRV, c->d_res, c->d_nrm, c->d_conv, c->d_iters,
                                  c->d_status, c->prm.refine_tol, it, it == maxit - 1, nullptr, nullptr,
                                  c->d_cnt, st));
+        // graph capture: every sweep is recorded; converged elements skip their work on the device
+        if (c->graph_refine) continue;
         TRY(cudaMemcpyAsync(c->h_cnt, c->d_cnt, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         TRY(cudaStreamSynchronize(st));
         if (*c->h_cnt == 0) break;
@@ -409,15 +418,17 @@ int mehdg_condense(mehdg_ctx* c, double* bhat, double* Ahat_local, void* stream)
     // z = A_qq^-1 R_Q
     int rc;
     if (vis && (rc = qproj(c, 1.0, nullptr, 0.0, nullptr, 0.0, c->d_z, nullptr, st))) return rc;
-    // S^K = A_vv - A_vq C (dense), padded identity
-    TRY(cudaStreamWaitEvent(st, c->zs_ev_out, 0));
-    ev = prof_begin(&c->prof, PH_JACOBIAN, st);
-    TRY(launch_pad_identity(c->d_S, nK, ld, c->Nv, fp64, st));
+    // S^K = A_vv - A_vq C (dense), padded identity: the point passes (FP64-bound, S untouched) also
+    // run beside the zeroing of S; the passes that add into S wait for it
     JacobianArgs ja;
     ja.tab = c->tab; ja.ph = c->ph; ja.box = c->d_box; ja.v = c->v; ja.vs = c->vs; ja.vh = c->vh; ja.q = c->q;
     ja.gid = c->d_gid; ja.S = c->d_S; ja.ld = ld; ja.status = c->d_status; ja.C1 = c->d_C1;
     ja.pj = c->d_pj; ja.pjf = c->d_pjf; ja.pq = c->d_pq; ja.pqf = c->d_pqf;
-    TRY(launch_jacobian(ja, nK, fp64, st));
+    ev = prof_begin(&c->prof, PH_JACOBIAN, st);
+    TRY(launch_jacobian(ja, nK, fp64, st, 1));
+    TRY(cudaStreamWaitEvent(st, c->zs_ev_out, 0));
+    TRY(launch_pad_identity(c->d_S, nK, ld, c->Nv, fp64, st));
+    TRY(launch_jacobian(ja, nK, fp64, st, 2));
     c->pj_ready = c->d_pj != nullptr;
     prof_end(&c->prof, ev, st, 0.0);
     // LU

@@ -602,3 +602,20 @@ void batch_layout(const mehdg_ctx* c, int64_t* voff, int64_t* toff) {
     if (voff) std::memcpy(voff, B.voff.data(), sizeof(int64_t) * B.voff.size());
     if (toff) std::memcpy(toff, B.toff.data(), sizeof(int64_t) * B.toff.size());
 }
+
+bool batch_resident(const mehdg_ctx* c) { return c->batch && c->batch->resident; }
+
+void batch_set_graph_refine(mehdg_ctx* c, bool on) {
+    for (auto& g : c->batch->groups)
+        if (g.sub) g.sub->graph_refine = on;
+}
+
+void batch_mark_condensed(mehdg_ctx* c) {
+    for (auto& g : c->batch->groups)
+        if (g.sub) g.sub->condensed = true;
+}
+
+void batch_end_captures(mehdg_ctx* c) {
+    for (auto& g : c->batch->groups)
+        if (g.sub) end_captures(g.sub);
+}

@@ -196,6 +196,12 @@ struct mehdg_ctx {
     cudaEvent_t zs_ev_in = nullptr, zs_ev_out = nullptr;   // zeroing of S beside the residual
     long long lu_graph_launches = 0;    // kernels in the graph
     bool lu_graph_failed = false;       // capture failed once: the LU is launched directly
+    bool graph_refine = false;          // refinement without host synchronisation (graph capture)
+    cudaGraphExec_t cond_graph = nullptr; // the whole condensation, captured (mehdg_condense_graph)
+    cudaStream_t cap_stream = nullptr;
+    cudaEvent_t cap_in = nullptr, cap_out = nullptr;
+    const void* cap_key[7] = {};        // pointers the captured graph was recorded with
+    long long cond_graph_launches = 0;
     int tune_leaf_ctas = 0;             // LU launch choices (0 = automatic), set by the batch autotuner
     int tune_solve_ctas = 0;
     void* d_krylov = nullptr;           // GMRES basis and scratch of the trace solve (first use)
@@ -237,6 +243,11 @@ void batch_layout(const mehdg_ctx* c, int64_t* voff, int64_t* toff);
 int64_t batch_state_len(const mehdg_ctx* c);
 int64_t batch_trace_len(const mehdg_ctx* c);
 int batch_set_dt(mehdg_ctx* c);
+bool batch_resident(const mehdg_ctx* c);
+void batch_set_graph_refine(mehdg_ctx* c, bool on);
+void batch_mark_condensed(mehdg_ctx* c);
+void batch_end_captures(mehdg_ctx* c);
+void end_captures(mehdg_ctx* c);        // graph.cu
 
 // lengths of the state ([nK][5][Nn] in all) and global trace vectors
 inline int64_t ctx_state_len(const mehdg_ctx* c) { return c->batch ? batch_state_len(c) : c->nK * (int64_t)c->Nv; }

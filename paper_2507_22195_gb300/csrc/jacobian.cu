@@ -718,7 +718,7 @@ size_t sf_smem_bytes(const Tab& t, bool visc, size_t ts) {
 
 }  // namespace
 
-cudaError_t launch_jacobian(const JacobianArgs& a, int64_t nK, bool fp64, cudaStream_t st) {
+cudaError_t launch_jacobian(const JacobianArgs& a, int64_t nK, bool fp64, cudaStream_t st, int phase) {
     const Tab& t = a.tab;
     bool visc = a.ph.viscous != 0;
     size_t ts = fp64 ? 8 : 4;
@@ -731,27 +731,39 @@ cudaError_t launch_jacobian(const JacobianArgs& a, int64_t nK, bool fp64, cudaSt
     size_t sf = sizeof(double) * (MEHDG_MAXG * (MEHDG_MAXP + 1) + 8 + 25 * (size_t)fl + (fl + 1) / 2 + 1)
               + ts * 25 * (size_t)fpt + 64;
     dim3 gv(t.m * t.m * t.m, (unsigned)nK), gf(6 * t.m * t.m, (unsigned)nK), b(256);
+    // phase 1: the point passes (they write the stored point Jacobians, not S);
+    // phase 2: everything that adds into S
 #define LJ(TS, V)                                                                                        \
     do { if (use_sf && !V && a.pj) {                                                                     \
-             const size_t sp = sizeof(double) * (HEAD_DOUBLES + 10 * (size_t)t.nl) + 16;                 \
-             cudaFuncSetAttribute(jac_points_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp); \
-             jac_points_kernel<<<gv, 128, sp, st>>>(a);                                                  \
-             cudaFuncSetAttribute(jac_volume_sf_kernel<TS, V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sv); \
-             jac_volume_sf_kernel<TS, V, true><<<gv, b, sv, st>>>(a);                                    \
+             if (phase & 1) {                                                                            \
+                 const size_t sp = sizeof(double) * (HEAD_DOUBLES + 10 * (size_t)t.nl) + 16;             \
+                 cudaFuncSetAttribute(jac_points_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp); \
+                 jac_points_kernel<<<gv, 128, sp, st>>>(a);                                              \
+                 MEHDG_COUNT(1);                                                                         \
+             }                                                                                           \
+             if (phase & 2) {                                                                            \
+                 cudaFuncSetAttribute(jac_volume_sf_kernel<TS, V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sv); \
+                 jac_volume_sf_kernel<TS, V, true><<<gv, b, sv, st>>>(a);                                \
+                 MEHDG_COUNT(1);                                                                         \
+             }                                                                                           \
+         } else if (phase & 2) {                                                                         \
+             if (use_sf) {                                                                               \
+                 cudaFuncSetAttribute(jac_volume_sf_kernel<TS, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sv); \
+                 jac_volume_sf_kernel<TS, V><<<gv, b, sv, st>>>(a);                                      \
+             } else {                                                                                    \
+                 cudaFuncSetAttribute(jac_volume_kernel<TS, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sv); \
+                 jac_volume_kernel<TS, V><<<gv, b, sv, st>>>(a);                                         \
+             }                                                                                           \
              MEHDG_COUNT(1);                                                                             \
-         } else if (use_sf) {                                                                            \
-             cudaFuncSetAttribute(jac_volume_sf_kernel<TS, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sv); \
-             jac_volume_sf_kernel<TS, V><<<gv, b, sv, st>>>(a);                                          \
-         } else {                                                                                        \
-             cudaFuncSetAttribute(jac_volume_kernel<TS, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sv); \
-             jac_volume_kernel<TS, V><<<gv, b, sv, st>>>(a);                                             \
          }                                                                                               \
-         cudaFuncSetAttribute(jac_face_kernel<TS, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf); \
-         jac_face_kernel<TS, V><<<gf, b, sf, st>>>(a); } while (0)
+         if (phase & 2) {                                                                                \
+             cudaFuncSetAttribute(jac_face_kernel<TS, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf); \
+             jac_face_kernel<TS, V><<<gf, b, sf, st>>>(a);                                               \
+             MEHDG_COUNT(1);                                                                             \
+         } } while (0)
     if (fp64) { if (visc) LJ(double, true); else LJ(double, false); }
     else { if (visc) LJ(float, true); else LJ(float, false); }
 #undef LJ
-    MEHDG_COUNT(2);
     if (visc) {
         const size_t G2 = (size_t)t.ng * t.ng, TW = (size_t)(t.p + 1) * t.n;
         const size_t base = sizeof(double) * (HEAD_DOUBLES + (size_t)t.n * t.n + 5 * (size_t)t.nl + 5 * (size_t)t.npt)
@@ -770,20 +782,28 @@ cudaError_t launch_jacobian(const JacobianArgs& a, int64_t nK, bool fp64, cudaSt
         if (sq > 227 * 1024) return cudaErrorInvalidValue;      // FP64 at p = 4: not supported
 #define LQ(TS)                                                                                          \
         do { if (pre) {                                                                                 \
-                 const size_t sp = sizeof(double) * (HEAD_DOUBLES + 5 * (size_t)t.nl) + 16;             \
-                 jac_visc_q_points_kernel<<<gv, 128, sp, st>>>(a);                                      \
-                 cudaFuncSetAttribute(jac_visc_q_volume_kernel<TS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sq); \
-                 jac_visc_q_volume_kernel<TS, true><<<gv, b, sq, st>>>(a, a.C1, kg);                    \
-                 MEHDG_COUNT(1);                                                                        \
-             } else {                                                                                   \
+                 if (phase & 1) {                                                                       \
+                     const size_t sp = sizeof(double) * (HEAD_DOUBLES + 5 * (size_t)t.nl) + 16;         \
+                     jac_visc_q_points_kernel<<<gv, 128, sp, st>>>(a);                                  \
+                     MEHDG_COUNT(1);                                                                    \
+                 }                                                                                      \
+                 if (phase & 2) {                                                                       \
+                     cudaFuncSetAttribute(jac_visc_q_volume_kernel<TS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sq); \
+                     jac_visc_q_volume_kernel<TS, true><<<gv, b, sq, st>>>(a, a.C1, kg);                \
+                     MEHDG_COUNT(1);                                                                    \
+                 }                                                                                      \
+             } else if (phase & 2) {                                                                    \
                  cudaFuncSetAttribute(jac_visc_q_volume_kernel<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sq); \
                  jac_visc_q_volume_kernel<TS><<<gv, b, sq, st>>>(a, a.C1, kg);                          \
+                 MEHDG_COUNT(1);                                                                        \
              }                                                                                          \
-             cudaFuncSetAttribute(jac_visc_q_face_kernel<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sqf); \
-             jac_visc_q_face_kernel<TS><<<gf, b, sqf, st>>>(a, a.C1); } while (0)
+             if (phase & 2) {                                                                           \
+                 cudaFuncSetAttribute(jac_visc_q_face_kernel<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sqf); \
+                 jac_visc_q_face_kernel<TS><<<gf, b, sqf, st>>>(a, a.C1);                               \
+                 MEHDG_COUNT(1);                                                                        \
+             } } while (0)
         if (fp64) LQ(double); else LQ(float);
 #undef LQ
-        MEHDG_COUNT(2);
     }
     return cudaGetLastError();
 }

@@ -55,7 +55,9 @@ struct JacobianArgs {
     double* pq;               // if set: scratch for the viscous point blocks dG/dq [nK][m^3][225][npt]
     double* pqf;              // if set: the weighted FP64 viscous face blocks dGhat/dq [nK][6 m^2][75][fpt]
 };
-cudaError_t launch_jacobian(const JacobianArgs& a, int64_t nK, bool fp64, cudaStream_t st);
+// phase: 1 = the point passes (stored point Jacobians only, S untouched), 2 = the passes that add
+// into S (they read what phase 1 wrote), 3 = both
+cudaError_t launch_jacobian(const JacobianArgs& a, int64_t nK, bool fp64, cudaStream_t st, int phase = 3);
 cudaError_t launch_pad_identity(void* S, int64_t nK, int64_t ld, int Nv, bool fp64, cudaStream_t st);
 
 // batched dense LU with partial pivoting and solves (lu.cu)

@@ -30,7 +30,7 @@ EXPORTED = ["mehdg_default_params", "mehdg_create", "mehdg_set_mesh", "mehdg_set
             "mehdg_residual_vjp", "mehdg_status_device", "mehdg_set_dt", "mehdg_pseudo_time_newton",
             "mehdg_batch_layout", "mehdg_batch_autotune", "mehdg_batch_report", "mehdg_condense_adjoint",
             "mehdg_apply_condensed_adjoint", "mehdg_solve_condensed_adjoint", "mehdg_recover_adjoint",
-            "mehdg_pseudo_time_newton_vjp", "mehdg_set_source", "mehdg_dirk_step"]
+            "mehdg_pseudo_time_newton_vjp", "mehdg_set_source", "mehdg_dirk_step", "mehdg_condense_graph"]
 
 
 class mehdg_params(C.Structure):
@@ -74,6 +74,7 @@ def load(path: str | None = None):
     L.mehdg_solve_condensed_adjoint.argtypes = [_vp, _vp, _vp, C.c_double, C.c_int, C.c_int, _vp, _vp, _vp]
     L.mehdg_recover_adjoint.argtypes = [_vp, _vp, _vp, _vp, _vp]
     L.mehdg_set_source.argtypes = [_vp, _vp]
+    L.mehdg_condense_graph.argtypes = [_vp, _vp, _vp]
     L.mehdg_dirk_step.argtypes = [_vp, _vp, _vp, _vp, C.c_double, C.c_double, C.c_int, C.c_double, C.c_int, C.c_int,
                                   _vp, _vp, _vp]
     L.mehdg_pseudo_time_newton_vjp.argtypes = [_vp, _vp, _vp, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
@@ -177,6 +178,10 @@ def mehdg_residual_vjp(ctx, lam_V, lam_Vhat, g_v, g_vhat, stream=None):
 
 def mehdg_condense(ctx, bhat, Ahat_local=None, stream=None):
     _check(ctx, load().mehdg_condense(ctx, _ptr(bhat), _ptr(Ahat_local), _stream(stream)), "mehdg_condense")
+
+
+def mehdg_condense_graph(ctx, bhat, stream=None):
+    _check(ctx, load().mehdg_condense_graph(ctx, _ptr(bhat), _stream(stream)), "mehdg_condense_graph")
 
 
 def mehdg_apply_condensed(ctx, x, y, stream=None):
