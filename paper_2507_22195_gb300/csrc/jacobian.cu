@@ -360,6 +360,113 @@ jac_face_kernel(JacobianArgs a) {
     }
 }
 
+// Face point pass alone (with a.pjf): the dual-number two-point flux at every
+// Gauss point of one macro-face (all its micro-faces, one thread per point),
+// written as the weighted FP64 blocks W d(Fhat+Ghat)/dv (the layout of the
+// fused kernel above).  It adds nothing into S, so it can run beside the
+// zeroing of S; jac_face_contract_kernel then reads the blocks.
+template <bool VISC>
+__global__ void __launch_bounds__(256)
+jac_face_points_kernel(JacobianArgs a) {
+    const Tab& tb = a.tab;
+    const int K = blockIdx.y, f = blockIdx.x;
+    const int p = tb.p, m = tb.m, n = tb.n, ng = tb.ng, Nn = tb.Nn, n2 = tb.n2, p1 = p + 1;
+    const int d = f / 2, t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+    const double sgn = (f & 1) ? 1.0 : -1.0;
+    const int fl = p1 * p1, fpt = ng * ng, mm = m * m;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* sL = reinterpret_cast<double*>(smem_raw);
+    double* sW = sL + MEHDG_MAXG * (MEHDG_MAXP + 1);
+    double* fv = sW + 8;              // [5][n2] element values on the face
+    double* fh = fv + 5 * n2;         // [5][n2] trace values
+    double* fq = fh + 5 * n2;         // [15][n2] (viscous)
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (int i = tid; i < ng * p1; i += nth) sL[i] = tb.L[i / p1][i % p1];
+    if (tid < ng) sW[tid] = tb.w[tid];
+    const double* box = a.box + 6 * K;
+    const double hw1 = 0.5 * (box[3 + t1] - box[t1]) / m, hw2 = 0.5 * (box[3 + t2] - box[t2]) / m;
+    const int64_t oV = (int64_t)K * 5 * Nn, oQ = (int64_t)K * 15 * Nn, og = a.gid[6 * K + f] * 5 * n2;
+    for (int c = tid; c < n2; c += nth) {
+        const int c1 = c % n, c2 = c / n;
+        int idx[3]; idx[d] = (f & 1) ? n - 1 : 0; idx[t1] = c1; idx[t2] = c2;
+        const int A = idx[0] + n * (idx[1] + n * idx[2]);
+        for (int k = 0; k < 5; ++k) {
+            fv[k * n2 + c] = a.v[oV + k * Nn + A];
+            fh[k * n2 + c] = a.vh[og + k * n2 + c];
+        }
+        if (VISC) for (int q = 0; q < 15; ++q) fq[q * n2 + c] = a.q[oQ + q * Nn + A];
+    }
+    __syncthreads();
+    for (int t = tid; t < mm * fpt; t += nth) {
+        const int e = t / fpt, x = t % fpt;
+        const int e1 = e % m, e2 = e / m, g1 = x % ng, g2 = x / ng;
+        double vx[5] = {0, 0, 0, 0, 0}, hx[5] = {0, 0, 0, 0, 0}, qx[15];
+        for (int q = 0; q < 15; ++q) qx[q] = 0.0;
+        for (int i = 0; i < fl; ++i) {
+            const double mu = sL[g1 * p1 + i % p1] * sL[g2 * p1 + i / p1];
+            const int c = (e1 * p + i % p1) + n * (e2 * p + i / p1);
+            for (int k = 0; k < 5; ++k) { vx[k] += mu * fv[k * n2 + c]; hx[k] += mu * fh[k * n2 + c]; }
+            if (VISC) for (int q = 0; q < 15; ++q) qx[q] += mu * fq[q * n2 + c];
+        }
+        Dual<5> dv[5], dh[5], dq[15];
+        for (int k = 0; k < 5; ++k) { dv[k] = mkdual<5>(vx[k]); dv[k].d[k] = 1.0; dh[k] = mkdual<5>(hx[k]); }
+        for (int q = 0; q < 15; ++q) dq[q] = mkdual<5>(qx[q]);
+        Dual<5> Fh[5];
+        face_integrand(a.ph, dv, dh, dq, d, sgn, Fh);
+        const double W = sW[g1] * hw1 * sW[g2] * hw2;
+        double* out = a.pjf + (((size_t)K * 6 * mm + (size_t)f * mm + e) * 25) * fpt + x;
+        for (int k = 0; k < 5; ++k)
+            for (int l = 0; l < 5; ++l) out[(size_t)(k * 5 + l) * fpt] = W * Fh[k].d[l];
+    }
+}
+
+// Contraction of the stored face blocks into S, one CTA per (micro-face,
+// element): the pair loop of the fused kernel, at several CTAs per SM.
+template <class TS>
+__global__ void __launch_bounds__(256)
+jac_face_contract_kernel(JacobianArgs a) {
+    const Tab& tb = a.tab;
+    const int K = blockIdx.y;
+    const int p = tb.p, m = tb.m, n = tb.n, ng = tb.ng, p1 = p + 1;
+    const int f = blockIdx.x / (m * m), e = blockIdx.x % (m * m);
+    const int e1 = e % m, e2 = e / m;
+    const int d = f / 2, t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+    const int fl = p1 * p1, fpt = ng * ng;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* sL = reinterpret_cast<double*>(smem_raw);
+    int* nodeA = reinterpret_cast<int*>(sL + MEHDG_MAXG * (MEHDG_MAXP + 1));       // [fl]
+    TS* P = reinterpret_cast<TS*>(sL + MEHDG_MAXG * (MEHDG_MAXP + 1) + (fl + 1) / 2 + 1);   // [fpt][25]
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (int i = tid; i < ng * p1; i += nth) sL[i] = tb.L[i / p1][i % p1];
+    for (int i = tid; i < fl; i += nth) {
+        const int c1 = e1 * p + i % p1, c2 = e2 * p + i / p1;
+        int idx[3]; idx[d] = (f & 1) ? n - 1 : 0; idx[t1] = c1; idx[t2] = c2;
+        nodeA[i] = idx[0] + n * (idx[1] + n * idx[2]);
+    }
+    const double* blk = a.pjf + (((size_t)K * 6 * m * m + blockIdx.x) * 25) * fpt;
+    for (int i = tid; i < 25 * fpt; i += nth) {
+        const int kl = i / fpt, x = i % fpt;          // reads run over the points (coalesced)
+        P[x * 25 + kl] = (TS)blk[i];
+    }
+    __syncthreads();
+    TS* S = reinterpret_cast<TS*>(a.S) + (size_t)K * a.ld * a.ld;
+    for (int r = tid; r < fl * fl; r += nth) {
+        const int ia = r % fl, ib = r / fl;
+        TS acc[25];
+        for (int i = 0; i < 25; ++i) acc[i] = 0;
+        for (int x = 0; x < fpt; ++x) {
+            const int g1 = x % ng, g2 = x / ng;
+            const TS c = (TS)(sL[g1 * p1 + ia % p1] * sL[g2 * p1 + ia / p1] * sL[g1 * p1 + ib % p1] *
+                              sL[g2 * p1 + ib / p1]);
+            for (int kl = 0; kl < 25; ++kl) acc[kl] += c * P[x * 25 + kl];
+        }
+        const int A = nodeA[ia], B = nodeA[ib];
+        for (int k = 0; k < 5; ++k)
+            for (int l = 0; l < 5; ++l)
+                atomic_add_t(&S[(size_t)(A * 5 + k) + (size_t)(B * 5 + l) * a.ld], (double)acc[k * 5 + l]);
+    }
+}
+
 // ---------------------------------------------------------------- viscous: -A_vq C
 // Q-elimination term of S = A_vv - A_vq A_qq^-1 A_qv (eq. R3).  A_qq = I x M
 // with M a tensor product of 1-D mass matrices, so C = A_qq^-1 A_qv acts on
@@ -731,6 +838,9 @@ cudaError_t launch_jacobian(const JacobianArgs& a, int64_t nK, bool fp64, cudaSt
     size_t sf = sizeof(double) * (MEHDG_MAXG * (MEHDG_MAXP + 1) + 8 + 25 * (size_t)fl + (fl + 1) / 2 + 1)
               + ts * 25 * (size_t)fpt + 64;
     dim3 gv(t.m * t.m * t.m, (unsigned)nK), gf(6 * t.m * t.m, (unsigned)nK), b(256);
+    // split face pass: the point pass stages the macro-face's nodal values, the contraction its blocks
+    const size_t sfp = sizeof(double) * (MEHDG_MAXG * (MEHDG_MAXP + 1) + 8 + (size_t)(10 + (visc ? 15 : 0)) * t.n2);
+    const size_t sfc = sizeof(double) * (MEHDG_MAXG * (MEHDG_MAXP + 1) + (fl + 1) / 2 + 1) + ts * 25 * (size_t)fpt + 64;
     // phase 1: the point passes (they write the stored point Jacobians, not S);
     // phase 2: everything that adds into S
 #define LJ(TS, V)                                                                                        \
@@ -756,7 +866,18 @@ cudaError_t launch_jacobian(const JacobianArgs& a, int64_t nK, bool fp64, cudaSt
              }                                                                                           \
              MEHDG_COUNT(1);                                                                             \
          }                                                                                               \
-         if (phase & 2) {                                                                                \
+         if (a.pjf) {                                                                                    \
+             if (phase & 1) {                                                                            \
+                 cudaFuncSetAttribute(jac_face_points_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sfp); \
+                 jac_face_points_kernel<V><<<dim3(6, (unsigned)nK), b, sfp, st>>>(a);                    \
+                 MEHDG_COUNT(1);                                                                         \
+             }                                                                                           \
+             if (phase & 2) {                                                                            \
+                 cudaFuncSetAttribute(jac_face_contract_kernel<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sfc); \
+                 jac_face_contract_kernel<TS><<<gf, b, sfc, st>>>(a);                                    \
+                 MEHDG_COUNT(1);                                                                         \
+             }                                                                                           \
+         } else if (phase & 2) {                                                                         \
              cudaFuncSetAttribute(jac_face_kernel<TS, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf); \
              jac_face_kernel<TS, V><<<gf, b, sf, st>>>(a);                                               \
              MEHDG_COUNT(1);                                                                             \
