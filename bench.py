@@ -226,23 +226,56 @@ def once_main(a):
     return 0
 
 
-# DRAM bytes / algorithmic bytes of the outer trailing update (split BF16),
-# measured with ncu on one launch of a 27-element case of the same kernel
-# (3^3 elements of the p = 3, m = 3 TGV, 2.8 GB of S): C is streamed once per
-# launch, so the ratio carries over to the full workload.  Other precisions
-# were not captured and report null.
-TRAFFIC_RATIO = {"bf16x3": 0.987}
+# DRAM bytes / algorithmic bytes of the outer trailing updates (split BF16),
+# measured with ncu on one launch of each kind on a 27-element case of the
+# same kernels (3^3 elements of the p = 3, m = 3 TGV, 2.8 GB of S): C is
+# streamed once per launch, so the ratios carry over to the full workload.
+# "one": the depth-256 update of the one-panel form; with merged pairs,
+# "merged": the depth-512 update, "narrow": the depth-256 updates of 256 rows
+# or 256 columns.  Other precisions were not captured and report null.
+TRAFFIC_RATIO = {"bf16x3": {"one": 0.987, "merged": 0.988, "narrow": 0.88}}
+# tensor rate of a precision mode relative to BF16 (nominal dense GB300 rates:
+# TF32 1.1, BF16 2.25 PFLOP/s) and the tensor products per method flop
+TENSOR_RATE = {"bf16": 1.0, "bf16x3": 1.0, "tf32": 1.1 / 2.25, "tf32x3": 1.1 / 2.25}
+PRODUCTS = {"bf16": 1, "bf16x3": 3, "tf32": 1, "tf32x3": 3}
 
 
-def trailing_bytes(ld, nK):
-    """algorithmic bytes of all outer trailing updates of one condensation:
-    C read and written (FP32) and the two operand panels (rest x 256, FP32)"""
-    byt = 0
-    for c0 in range(0, ld, 256):
-        rest = ld - c0 - 256
-        if rest > 0:
-            byt += 8 * rest * rest + 2 * 4 * rest * 256
-    return byt * nK
+def lu_pairs(prec):
+    """whether the library merges the outer updates of two panels (split BF16,
+    unless MEHDG_LU_PAIRS=0)"""
+    return prec == "bf16x3" and os.environ.get("MEHDG_LU_PAIRS", "1") != "0"
+
+
+def outer_updates(ld, pairs):
+    """(kind, M, N, Kd) of every outer trailing update of one factorisation"""
+    ups = []
+    if not pairs:
+        for c0 in range(0, ld, 256):
+            r = ld - c0 - 256
+            if r > 0:
+                ups.append(("one", r, r, 256))
+        return ups
+    for ca in range(0, ld, 512):
+        cb, jr = ca + 256, ca + 512
+        if cb >= ld:
+            break
+        ups.append(("narrow", ld - cb, 256, 256))
+        nr = ld - jr
+        if nr <= 0:
+            break
+        ups += [("narrow", 256, nr, 256), ("merged", nr, nr, 512)]
+    return ups
+
+
+def update_bytes(M, N, Kd):
+    """algorithmic bytes of one update: C read and written (FP32) and the two
+    operand panels (M x Kd and Kd x N, counted in FP32)"""
+    return 8 * M * N + 4 * (M + N) * Kd
+
+
+def trailing_bytes(ld, nK, pairs=False):
+    """algorithmic bytes of all outer trailing updates of one condensation"""
+    return sum(update_bytes(M, N, Kd) for _, M, N, Kd in outer_updates(ld, pairs)) * nK
 
 
 def rel_per_element(a, b):
@@ -619,11 +652,10 @@ def main():
                           "(P + P-hat)) has an unbounded derivative, and dV^K of such an element moves by up to "
                           "1e-8 under a one-ulp change of the inputs in the oracle itself"}
 
-    # roofline of the dominant kernel: the outer trailing update of the LU
+    # roofline of the dominant kernel: the outer trailing updates of the LU
     pk = peaks()
     gem = prof["lu_trailing_update"]
     ld = (5 * mesh.Nn + 255) // 256 * 256
-    byt = trailing_bytes(ld, mesh.nK) * a.steps
     roof_t = None
     if a.prec == "fp64":
         fl = gem["flops"]
@@ -632,27 +664,43 @@ def main():
                 "traffic": None, "peak_source": "nominal FP64 rate of GB300 (no measured FP64 peak)",
                 "kernel": "lu_trailing_update (FP64 SIMT, depth 256)", "launches": gem["launches"], "ms": gem["ms"]}
     else:
-        ach = byt / (gem["ms"] / 1e3) / 1e9
+        pairs = lu_pairs(a.prec)
+        ups = outer_updates(ld, pairs)
+        byt = trailing_bytes(ld, mesh.nK, pairs) * a.steps
+        sec = gem["ms"] / 1e3
         hbm = pk.get("hbm_gbs", 6800.0)
-        ratio = TRAFFIC_RATIO.get(a.prec) if a.workload == "tgv_inviscid" else None
-        tr = ratio * byt / max(gem["launches"], 1) if ratio else None
-        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": tr, "traffic_unit": "bytes per launch (27-element ncu capture, scaled)" if tr else None,
-                "algorithmic_per_launch": byt / max(gem["launches"], 1),
-                "peak_source": "measured" if "hbm_gbs" in pk else "fallback",
-                "kernel": "lu_trailing_update (tcgen05, depth 256)", "launches": gem["launches"],
-                "ms": gem["ms"]}
-        # the same kernel on the method's work: 2 rest^2 256 flop per outer
-        # update (the LU's 2/3 N^3 less the panels), against the sustained
-        # BF16 rate; the split modes issue three products per flop counted here
-        sus = pk.get("bf16_tflops_sustained", 1700.0)
-        tfl = gem["flops"] / (gem["ms"] / 1e3) / 1e12
+        ratios = TRAFFIC_RATIO.get(a.prec) if a.workload == "tgv_inviscid" else None
+        tr = (sum(ratios[k] * update_bytes(M, N, Kd) for k, M, N, Kd in ups) * mesh.nK / len(ups)
+              if ratios and ups else None)
+        kernel = ("lu_trailing_update (tcgen05; per pair of outer panels one depth-512 update and two "
+                  "depth-256 updates of 256 rows or columns)" if pairs else "lu_trailing_update (tcgen05, depth 256)")
+        roof_h = {"bound": "hbm", "achieved": byt / sec / 1e9, "peak": hbm, "unit": "GB/s",
+                  "frac": byt / sec / 1e9 / hbm, "traffic": tr,
+                  "traffic_unit": "bytes per launch (27-element ncu captures, scaled)" if tr else None,
+                  "algorithmic_per_launch": byt / max(gem["launches"], 1),
+                  "peak_source": "measured" if "hbm_gbs" in pk else "fallback",
+                  "kernel": kernel, "launches": gem["launches"],
+                  "launches_expected": len(ups) * a.steps, "ms": gem["ms"]}
+        # the same launches on the tensor pipe: 2 M N Kd method flops per
+        # update, and the split modes issue three products per method flop;
+        # the peak is the measured sustained BF16 rate (TF32: x 1.1/2.25)
+        sus = pk.get("bf16_tflops_sustained", 1700.0) * TENSOR_RATE[a.prec]
+        mfl = gem["flops"] / sec / 1e12
+        tfl = PRODUCTS[a.prec] * mfl
         roof_t = {"bound": "tensor", "achieved": tfl, "peak": sus, "unit": "TFLOP/s", "frac": tfl / sus,
-                  "peak_source": "measured sustained bf16" if "bf16_tflops_sustained" in pk else "fallback",
+                  "traffic": tr,
+                  "achieved_counts": "tensor-core products: %d per method flop" % PRODUCTS[a.prec],
+                  "method_flops_achieved": mfl, "method_frac": mfl / sus,
+                  "peak_source": ("measured sustained bf16" if "bf16_tflops_sustained" in pk else "fallback")
+                  + ("" if TENSOR_RATE[a.prec] == 1.0 else " x nominal tf32/bf16 ratio"),
+                  "kernel": kernel, "launches": gem["launches"], "ms": gem["ms"],
                   "flops_per_step": gem["flops"] / a.steps,
                   "lu_method_flops_per_step": 2.0 / 3.0 * (5 * mesh.Nn) ** 3 * mesh.nK,
-                  "tensor_products_per_flop": 3 if a.prec.endswith("x3") else 1,
                   "traffic_vs_compulsory": byt / a.steps / (2 * 4 * ld * ld * mesh.nK)}
+        # the binding roofline: the larger of the two floors (time at peak)
+        floor_h, floor_t = byt / (hbm * 1e9), PRODUCTS[a.prec] * gem["flops"] / (sus * 1e12)
+        roof_h["floor_ms"], roof_t["floor_ms"] = floor_h * 1e3, floor_t * 1e3
+        roof, roof_t = (roof_t, roof_h) if floor_t > floor_h else (roof_h, roof_t)
     fp = None
     if a.prec != "fp64" and a.fp64_sample > 0:
         ctx.close()
@@ -695,7 +743,7 @@ def main():
                        "l2": "inputs larger than L2 (dense S^K of all elements: %.1f GB)" % (
                            mesh.nK * ld * ld * (8 if a.prec == "fp64" else 4) / 1e9)},
             "roofline": roof,
-            "roofline_tensor": roof_t,
+            "roofline_other": roof_t,
             "cpu_baseline": cpu,
             "err_vs_oracle": err_or,
             "e2e": {"value": job_rate(world, mesh.nK, a.steps, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,

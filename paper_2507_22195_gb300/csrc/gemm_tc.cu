@@ -136,13 +136,13 @@ constexpr int n_stages() { return RING_BYTES / stage_bytes<BN, SPLIT>() < 6 ? RI
 template <int BN, bool SPLIT>
 constexpr size_t stream_smem_bytes() { return (size_t)n_stages<BN, SPLIT>() * stage_bytes<BN, SPLIT>() + 1024; }
 
-// SPLIT: the panels hold [hi | lo] (segment length kp); each chunk is loaded
-// once per part and takes the three products hi hi, hi lo, lo hi.
+// SPLIT: the panels hold [hi | lo] (lo at K offset kpa in A, kpb in B); each
+// chunk is loaded once per part and takes the three products hi hi, hi lo, lo hi.
 template <int BN, bool BF16, bool STORE, bool SPLIT>
 __global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
 tc_stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                 float* __restrict__ Sall, int64_t ld, int r0, int c0, int M, int N, int nchunk, int kp,
-                 int tiles_m, int tiles_n, int64_t ntiles, int32_t* status, __nv_bfloat16* bq, int bq_kp) {
+                 float* __restrict__ Sall, int64_t ld, int r0, int c0, int M, int N, int nchunk, int kpa, int kpb,
+                 int tiles_m, int tiles_n, int64_t ntiles, int32_t* status, BqOut bo) {
     constexpr int A_BYTES = TM * CHUNK_BYTES;
     constexpr int B_BYTES = BN * CHUNK_BYTES;
     constexpr int NP = SPLIT ? 2 : 1;
@@ -190,8 +190,8 @@ tc_stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
                     tma_load_3d(slot, &mapA, &full[s], c * CHUNK_K, tm * TM, K);
                     tma_load_3d(slot + NP * A_BYTES, &mapB, &full[s], c * CHUNK_K, tn * BN, K);
                     if (SPLIT) {
-                        tma_load_3d(slot + A_BYTES, &mapA, &full[s], kp + c * CHUNK_K, tm * TM, K);
-                        tma_load_3d(slot + NP * A_BYTES + B_BYTES, &mapB, &full[s], kp + c * CHUNK_K, tn * BN, K);
+                        tma_load_3d(slot + A_BYTES, &mapA, &full[s], kpa + c * CHUNK_K, tm * TM, K);
+                        tma_load_3d(slot + NP * A_BYTES + B_BYTES, &mapB, &full[s], kpb + c * CHUNK_K, tn * BN, K);
                     }
                 }
                 if (!ok) { if (status) status[K] = MEHDG_ETIMEOUT; break; }
@@ -262,19 +262,20 @@ tc_stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
                     if (j < nc) __stcs(p, STORE ? __uint_as_float(r[j]) : cv[j] - __uint_as_float(r[j]));
                     p += ld;
                 }
-                if (STORE && bq) {
+                if (STORE && bo.p) {
                     // the same product as the next update's split-BF16 B operand
                     // (row = its K index, column = its N index): [hi | lo] rows
-                    __nv_bfloat16* qb = bq + ((size_t)K * N + col0) * (size_t)(2 * bq_kp) + row;
+                    __nv_bfloat16* qb = reinterpret_cast<__nv_bfloat16*>(bo.p) +
+                                        ((size_t)K * bo.nc + bo.c0 + col0) * (size_t)(2 * bo.kp) + bo.k0 + row;
 #pragma unroll
                     for (int j = 0; j < W; ++j) {
                         if (j < nc) {
                             const float v = __uint_as_float(r[j]);
                             const __nv_bfloat16 hi = __float2bfloat16_rn(v);
                             qb[0] = hi;
-                            qb[bq_kp] = __float2bfloat16_rn(v - __bfloat162float(hi));
+                            qb[bo.kp] = __float2bfloat16_rn(v - __bfloat162float(hi));
                         }
-                        qb += 2 * bq_kp;
+                        qb += 2 * bo.kp;
                     }
                 }
             }
@@ -404,6 +405,29 @@ pack_B_kernel(const float* __restrict__ Sall, int64_t ld, int k0, int c0, int N,
     }
 }
 
+// Gathered rows of an A panel (split BF16): slot i in [i0, min(i1, nr)) of
+// the net permutation perm with cont[i] != i gives packed row rows[i] - r0
+// the values S[rows[cont[i]]][k0 + k] for k < kn (the rest of the row stays
+// as packed).  One warp per slot; the source row is read along its columns.
+__global__ void __launch_bounds__(256)
+pack_A_gather_kernel(const float* __restrict__ Sall, int64_t ld, const int32_t* __restrict__ perm, int i0, int i1,
+                     int r0, int M, int k0, int kn, int Kp, void* __restrict__ out) {
+    const int K = blockIdx.y;
+    const float* S = Sall + (size_t)K * ld * ld;
+    const int32_t* pl = perm + (size_t)K * LU_PW;
+    const int nr = pl[0];
+    const int32_t* rows = pl + 1;
+    const int32_t* cont = rows + 2 * LU_NB;
+    const int i = i0 + blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (i >= i1 || i >= nr) return;
+    const int ci = cont[i];
+    if (ci == i) return;
+    const int m = rows[i] - r0, src = rows[ci];
+    if (m < 0 || m >= M || src < 0 || src >= ld) return;
+    const size_t base = ((size_t)K * M + m) * (size_t)(2 * Kp);
+    for (int k = lane; k < kn; k += 32) op_put<true>(out, base, Kp, k, 2, S[(size_t)src + (size_t)(k0 + k) * ld]);
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 bool encoder() {
@@ -417,14 +441,18 @@ bool encoder() {
     return true;
 }
 
-// 3-D map over packed panels [nK][rows][Kp], box = 128 bytes of K x box_rows
-bool make_map(CUtensorMap* map, void* base, bool bf16, int Kp, int rows, int64_t nK, int box_rows) {
+// 3-D map over packed panels [nK][rows][Kp] (elements elem_rows rows apart,
+// default rows), box = 128 bytes of K x box_rows
+bool make_map(CUtensorMap* map, const void* base, bool bf16, int Kp, int rows, int64_t nK, int box_rows,
+              int elem_rows = 0) {
     const int es = bf16 ? 2 : 4;
+    if (elem_rows <= 0) elem_rows = rows;
     cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)nK};
-    cuuint64_t strides[2] = {(cuuint64_t)Kp * es, (cuuint64_t)Kp * es * rows};
+    cuuint64_t strides[2] = {(cuuint64_t)Kp * es, (cuuint64_t)Kp * es * elem_rows};
     cuuint32_t box[3] = {(cuuint32_t)(CHUNK_BYTES / es), (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = g_encode(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base,
+    CUresult r = g_encode(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                          const_cast<void*>(base),
                           dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
@@ -449,16 +477,15 @@ size_t panel_bytes(int64_t nK, int64_t ld) {
 
 template <int BN, bool BF16, bool STORE, bool SPLIT>
 cudaError_t launch_stream(const CUtensorMap& a, const CUtensorMap& b, const LUPlan& P, int r0, int c0, int M, int N,
-                          int nchunk, int kp, cudaStream_t st, void* bq = nullptr, int bq_kp = 0) {
+                          int nchunk, int kpa, int kpb, cudaStream_t st, BqOut bo = BqOut()) {
     const int tiles_m = (M + TM - 1) / TM, tiles_n = (N + BN - 1) / BN;
     const int64_t ntiles = (int64_t)tiles_m * tiles_n * P.nK;
     constexpr size_t sm = stream_smem_bytes<BN, SPLIT>();
     auto kern = tc_stream_kernel<BN, BF16, STORE, SPLIT>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sm_count());
-    kern<<<(unsigned)grid, 64 + 32 * EPI_WARPS, sm, st>>>(a, b, (float*)P.S, P.ld, r0, c0, M, N, nchunk, kp, tiles_m,
-                                                         tiles_n, ntiles, P.status,
-                                                         reinterpret_cast<__nv_bfloat16*>(bq), bq_kp);
+    kern<<<(unsigned)grid, 64 + 32 * EPI_WARPS, sm, st>>>(a, b, (float*)P.S, P.ld, r0, c0, M, N, nchunk, kpa, kpb,
+                                                         tiles_m, tiles_n, ntiles, P.status, bo);
     MEHDG_COUNT(1);
     return cudaGetLastError();
 }
@@ -466,10 +493,10 @@ cudaError_t launch_stream(const CUtensorMap& a, const CUtensorMap& b, const LUPl
 // one update / solve product with the operand panels already packed
 template <bool BF16, bool STORE, bool SPLIT>
 cudaError_t launch_stream_bn(int BN, const CUtensorMap& a, const CUtensorMap& b, const LUPlan& P, int r0, int c0,
-                             int M, int N, int nchunk, int kp, cudaStream_t st, void* bq = nullptr, int bq_kp = 0) {
-    if (BN == 128) return launch_stream<128, BF16, STORE, SPLIT>(a, b, P, r0, c0, M, N, nchunk, kp, st, bq, bq_kp);
-    if (BN == 64) return launch_stream<64, BF16, STORE, SPLIT>(a, b, P, r0, c0, M, N, nchunk, kp, st, bq, bq_kp);
-    return launch_stream<32, BF16, STORE, SPLIT>(a, b, P, r0, c0, M, N, nchunk, kp, st, bq, bq_kp);
+                             int M, int N, int nchunk, int kpa, int kpb, cudaStream_t st, BqOut bo = BqOut()) {
+    if (BN == 128) return launch_stream<128, BF16, STORE, SPLIT>(a, b, P, r0, c0, M, N, nchunk, kpa, kpb, st, bo);
+    if (BN == 64) return launch_stream<64, BF16, STORE, SPLIT>(a, b, P, r0, c0, M, N, nchunk, kpa, kpb, st, bo);
+    return launch_stream<32, BF16, STORE, SPLIT>(a, b, P, r0, c0, M, N, nchunk, kpa, kpb, st, bo);
 }
 
 
@@ -555,16 +582,17 @@ trtri256_kernel(const float* __restrict__ Sall, int64_t ld, int c0, int nseg, vo
 // the net permutation (the 256 block rows and the rows below that take
 // part), writes the rows below that change, and writes the new block rows
 // as the split-TF32 panel Bp[K][n][hi 256 | lo 256].  The block rows of S are
-// not written back: the TRSM product overwrites them.
+// not written back: the TRSM product overwrites them.  Without a permutation
+// (perm null) the block rows c0.. are packed as they are.
 __global__ void __launch_bounds__(256)
-laswp_pack_kernel(float* __restrict__ Sall, int64_t ld, const int32_t* __restrict__ perm, int j0, int N,
+laswp_pack_kernel(float* __restrict__ Sall, int64_t ld, const int32_t* __restrict__ perm, int c0, int j0, int N,
                   float* __restrict__ Bp) {
     const int K = blockIdx.y;
     float* S = Sall + (size_t)K * ld * ld;
-    const int32_t* pl = perm + (size_t)K * LU_PW;
-    const int nr = pl[0];
-    const int32_t* rows = pl + 1;
-    const int32_t* cont = rows + 2 * LU_NB;
+    const int32_t* pl = perm ? perm + (size_t)K * LU_PW : nullptr;
+    const int nr = pl ? pl[0] : LU_NB;
+    const int32_t* rows = pl ? pl + 1 : nullptr;
+    const int32_t* cont = pl ? rows + 2 * LU_NB : nullptr;
     __shared__ float buf[8][2 * LU_NB];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = blockIdx.x * 8 + warp;
@@ -575,14 +603,17 @@ laswp_pack_kernel(float* __restrict__ Sall, int64_t ld, const int32_t* __restric
     for (int i0 = lane; i0 < nr; i0 += 128) {
         float v[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) { const int i = i0 + 32 * u; v[u] = i < nr ? Sc[rows[i]] : 0.f; }
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + 32 * u;
+            v[u] = i < nr ? Sc[rows ? rows[i] : c0 + i] : 0.f;
+        }
 #pragma unroll
         for (int u = 0; u < 4; ++u) { const int i = i0 + 32 * u; if (i < nr) b[i] = v[u]; }
     }
     __syncwarp();
     float* out = Bp + ((size_t)K * N + n) * (size_t)(2 * LU_NB);
     for (int i = lane; i < nr; i += 32) {
-        const int ci = cont[i];
+        const int ci = cont ? cont[i] : i;
         const float v = b[ci];
         if (i < LU_NB) {
             const float hi = tf32_rn(v);
@@ -600,7 +631,8 @@ laswp_pack_kernel(float* __restrict__ Sall, int64_t ld, const int32_t* __restric
 // cores, through the explicit inverse of the unit-lower block L11.
 namespace {
 // the TRSM product with B = rows [c0, c0+256) of the columns [j0, j0+N), packed in Bp
-cudaError_t trsm256_product(const LUPlan& P, int c0, int j0, int N, void* Ap, void* Bp, void* bq, cudaStream_t st) {
+cudaError_t trsm256_product(const LUPlan& P, int c0, int j0, int N, void* Ap, void* Bp, const BqOut* bq,
+                            cudaStream_t st) {
     const int Kd = LU_NB, nseg = 2, nchunk = Kd / (CHUNK_BYTES / 4);
     {
         dim3 gt(LU_NB / 32, (unsigned)P.nK);
@@ -611,9 +643,17 @@ cudaError_t trsm256_product(const LUPlan& P, int c0, int j0, int N, void* Ap, vo
     CUtensorMap ma, mb;
     if (!make_map(&ma, Ap, false, nseg * Kd, 256, P.nK, TM) || !make_map(&mb, Bp, false, nseg * Kd, N, P.nK, BN))
         return cudaErrorInvalidValue;
-    return launch_stream_bn<false, true, true>(BN, ma, mb, P, c0, j0, 256, N, nchunk, Kd, st, bq, LU_NB);
+    return launch_stream_bn<false, true, true>(BN, ma, mb, P, c0, j0, 256, N, nchunk, Kd, Kd, st,
+                                               bq ? *bq : BqOut());
+}
+
+// the three operand panels of the workspace: A, B, and the next update's B (split BF16)
+unsigned char* panel_base(const LUPlan& P) {
+    return reinterpret_cast<unsigned char*>(P.work) + lu_perm_bytes(P.nK, P.ld);
 }
 }  // namespace
+
+void* gemm_tc_bq_panel(const LUPlan& P) { return panel_base(P) + 2 * panel_bytes(P.nK, P.ld); }
 
 // The outer step right of panel c0: row exchanges of the columns [c0+256, ld)
 // by the panel's net permutation, fused with the packing of B, then the TRSM
@@ -621,57 +661,61 @@ cudaError_t trsm256_product(const LUPlan& P, int c0, int j0, int N, void* Ap, vo
 // TF32 (every mixed mode: the explicit inverse of L11 amplifies operand
 // rounding, and one-pass TF32 or BF16 here leaves the factors too inexact for
 // the FP64 refinement).
-cudaError_t gemm_tc_swap_trsm256(const LUPlan& P, const int32_t* perm, int c0, cudaStream_t st,
-                                 const void** update_b) {
-    if (update_b) *update_b = nullptr;
+cudaError_t gemm_tc_swap_trsm256(const LUPlan& P, const int32_t* perm, int c0, cudaStream_t st, const BqOut* bq) {
     const int j0 = c0 + LU_NB, N = (int)P.ld - j0;
     if (N <= 0) return cudaSuccess;
     if (!encoder()) return cudaErrorNotSupported;
-    unsigned char* w = reinterpret_cast<unsigned char*>(P.work) + lu_perm_bytes(P.nK, P.ld);
+    unsigned char* w = panel_base(P);
     const size_t pan = panel_bytes(P.nK, P.ld);
     void* Ap = w;
     float* Bp = reinterpret_cast<float*>(w + pan);
-    // split BF16: the product also writes the next update's B panel (third panel)
-    void* bq = P.prec == MEHDG_MIXED_BF16X3 ? (void*)(w + 2 * pan) : nullptr;
     dim3 gb((unsigned)((N + 7) / 8), (unsigned)P.nK);
-    laswp_pack_kernel<<<gb, 256, 0, st>>>((float*)P.S, P.ld, perm, j0, N, Bp);
+    laswp_pack_kernel<<<gb, 256, 0, st>>>((float*)P.S, P.ld, perm, c0, j0, N, Bp);
     MEHDG_COUNT(1);
-    cudaError_t e = trsm256_product(P, c0, j0, N, Ap, Bp, bq, st);
-    if (e == cudaSuccess && update_b) *update_b = bq;
-    return e;
+    return trsm256_product(P, c0, j0, N, Ap, Bp, bq, st);
 }
 
 size_t gemm_tc_work_bytes(int64_t nK, int64_t ld, int prec) {
     (void)prec;
-    // three panels of at most ld x (2 x 256) FP32 per element (split precision):
-    // A, B, and the next update's B written by the TRSM product
+    // three panels of ld rows x 2 KB per element: split FP32/TF32 operands of
+    // depth 256 or split BF16 of depth 512 (A, B, and the next update's B
+    // written by the TRSM products)
     return 3 * panel_bytes(nK, ld);
 }
 
 cudaError_t gemm_tc_update(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st,
-                           int ph_pack, int ph_gemm, double flops, const void* b_packed) {
+                           int ph_pack, int ph_gemm, double flops, const PackedB* b, const AGather* g) {
     if (M <= 0 || N <= 0) return cudaSuccess;
-    if (M < TM) return gemm_simt_update_f32(P, r0, c0, k0, M, N, Kd, st);   // a few tiny inner updates
-    if (!encoder()) return cudaErrorNotSupported;
     const bool bf16 = P.prec == MEHDG_MIXED_BF16 || P.prec == MEHDG_MIXED_BF16X3;
     const bool split = P.prec == MEHDG_MIXED_TF32X3 || P.prec == MEHDG_MIXED_BF16X3;
+    if ((b || g) && (!(bf16 && split) || M < TM)) return cudaErrorInvalidValue;   // split BF16, whole row tiles
+    if (M < TM) return gemm_simt_update_f32(P, r0, c0, k0, M, N, Kd, st);   // a few tiny inner updates
+    if (!encoder()) return cudaErrorNotSupported;
     const int nseg = split ? 2 : 1;
     const int es = bf16 ? 2 : 4;
     const int chunk_k = CHUNK_BYTES / es;
     const int Kp = (Kd + chunk_k - 1) / chunk_k * chunk_k;
     const int nchunk = Kp / chunk_k;
-    unsigned char* w = reinterpret_cast<unsigned char*>(P.work) + lu_perm_bytes(P.nK, P.ld);
+    // each operand panel holds ld rows x 2 KB per element
+    if ((size_t)std::max(M, N) * nseg * Kp * es > (size_t)P.ld * 2 * LU_NB * 4) return cudaErrorInvalidValue;
+    unsigned char* w = panel_base(P);
     const size_t pan = panel_bytes(P.nK, P.ld);
     void* Ap = w;
-    void* Bp = b_packed ? const_cast<void*>(b_packed) : (void*)(w + pan);
+    void* Bp = w + pan;
     // pack
     {
         const int ev = ph_pack >= 0 ? prof_begin(P.prof, ph_pack, st) : -1;
-        dim3 g((unsigned)((M + 63) / 64), (unsigned)(Kp / 32), (unsigned)P.nK);
-        if (bf16) pack_A_kernel<true><<<g, 256, 0, st>>>((const float*)P.S, P.ld, r0, k0, M, Kd, Kp, nseg, Ap);
-        else pack_A_kernel<false><<<g, 256, 0, st>>>((const float*)P.S, P.ld, r0, k0, M, Kd, Kp, nseg, Ap);
+        dim3 g3((unsigned)((M + 63) / 64), (unsigned)(Kp / 32), (unsigned)P.nK);
+        if (bf16) pack_A_kernel<true><<<g3, 256, 0, st>>>((const float*)P.S, P.ld, r0, k0, M, Kd, Kp, nseg, Ap);
+        else pack_A_kernel<false><<<g3, 256, 0, st>>>((const float*)P.S, P.ld, r0, k0, M, Kd, Kp, nseg, Ap);
         MEHDG_COUNT(1);
-        if (!b_packed) {
+        if (g && g->i1 > g->i0) {
+            dim3 gg((unsigned)((g->i1 - g->i0 + 7) / 8), (unsigned)P.nK);
+            pack_A_gather_kernel<<<gg, 256, 0, st>>>((const float*)P.S, P.ld, g->perm, g->i0, g->i1, r0, M, k0,
+                                                     std::min(g->kn, Kd), Kp, Ap);
+            MEHDG_COUNT(1);
+        }
+        if (!b) {
             dim3 gb((unsigned)((N + 7) / 8), 1, (unsigned)P.nK);
             if (bf16) pack_B_kernel<true><<<gb, 256, 0, st>>>((const float*)P.S, P.ld, k0, c0, N, Kd, Kp, nseg, Bp);
             else pack_B_kernel<false><<<gb, 256, 0, st>>>((const float*)P.S, P.ld, k0, c0, N, Kd, Kp, nseg, Bp);
@@ -681,14 +725,24 @@ cudaError_t gemm_tc_update(const LUPlan& P, int r0, int c0, int k0, int M, int N
     }
     const int BN = N >= 128 ? 128 : (N >= 64 ? 64 : 32);
     CUtensorMap ma, mb;
-    if (!make_map(&ma, Ap, bf16, nseg * Kp, M, P.nK, TM) || !make_map(&mb, Bp, bf16, nseg * Kp, N, P.nK, BN))
-        return cudaErrorInvalidValue;
+    bool ok = make_map(&ma, Ap, bf16, nseg * Kp, M, P.nK, TM);
+    int kpb = Kp;
+    if (b) {
+        // rows c0.. of the packed panel; a K chunk of this update never reaches the lo segment
+        if (b->kp < Kp || b->c0 < 0 || b->c0 + N > b->nc) return cudaErrorInvalidValue;
+        const void* base = reinterpret_cast<const __nv_bfloat16*>(b->p) + (size_t)b->c0 * 2 * b->kp;
+        ok = ok && make_map(&mb, base, true, 2 * b->kp, N, P.nK, BN, b->nc);
+        kpb = b->kp;
+    } else {
+        ok = ok && make_map(&mb, Bp, bf16, nseg * Kp, N, P.nK, BN);
+    }
+    if (!ok) return cudaErrorInvalidValue;
     const int ev = ph_gemm >= 0 ? prof_begin(P.prof, ph_gemm, st) : -1;
     cudaError_t e;
-    if (bf16) e = split ? launch_stream_bn<true, false, true>(BN, ma, mb, P, r0, c0, M, N, nchunk, Kp, st)
-                        : launch_stream_bn<true, false, false>(BN, ma, mb, P, r0, c0, M, N, nchunk, Kp, st);
-    else e = split ? launch_stream_bn<false, false, true>(BN, ma, mb, P, r0, c0, M, N, nchunk, Kp, st)
-                   : launch_stream_bn<false, false, false>(BN, ma, mb, P, r0, c0, M, N, nchunk, Kp, st);
+    if (bf16) e = split ? launch_stream_bn<true, false, true>(BN, ma, mb, P, r0, c0, M, N, nchunk, Kp, kpb, st)
+                        : launch_stream_bn<true, false, false>(BN, ma, mb, P, r0, c0, M, N, nchunk, Kp, kpb, st);
+    else e = split ? launch_stream_bn<false, false, true>(BN, ma, mb, P, r0, c0, M, N, nchunk, Kp, kpb, st)
+                   : launch_stream_bn<false, false, false>(BN, ma, mb, P, r0, c0, M, N, nchunk, Kp, kpb, st);
     if (ev >= 0) prof_end(P.prof, ev, st, flops);
     return e;
 }

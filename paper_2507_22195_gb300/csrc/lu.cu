@@ -830,15 +830,16 @@ cudaError_t launch_update32(const LUPlan& P, int r0, int c0, int k0, int M, cuda
 
 template <class TS>
 cudaError_t trailing_update(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st,
-                            int ph_pack = -1, int ph_gemm = -1, double flops = 0.0, const void* b_packed = nullptr) {
+                            int ph_pack = -1, int ph_gemm = -1, double flops = 0.0, const PackedB* b = nullptr,
+                            const AGather* g = nullptr) {
     if constexpr (std::is_same<TS, double>::value) {
         const int ev = ph_gemm >= 0 ? prof_begin(P.prof, ph_gemm, st) : -1;
         cudaError_t e = launch_gemm_simt<double>(P, r0, c0, k0, M, N, Kd, st);
         if (ev >= 0) prof_end(P.prof, ev, st, flops);
         return e;
     } else {
-        if (N == 32 && Kd == 32 && !b_packed) return launch_update32(P, r0, c0, k0, M, st);
-        return gemm_tc_update(P, r0, c0, k0, M, N, Kd, st, ph_pack, ph_gemm, flops, b_packed);
+        if (N == 32 && Kd == 32 && !b && !g) return launch_update32(P, r0, c0, k0, M, st);
+        return gemm_tc_update(P, r0, c0, k0, M, N, Kd, st, ph_pack, ph_gemm, flops, b, g);
     }
 }
 
@@ -855,35 +856,121 @@ cudaError_t rec_panel(const LUPlan& P, int c, int w, cudaStream_t st) {
     return rec_panel<TS>(P, c + h, h, st);
 }
 
+// outer panel c0 factored, and its net permutation built (kept for the solves)
+template <class TS>
+cudaError_t outer_panel(const LUPlan& P, int c0, cudaStream_t st, int32_t** pp) {
+    cudaError_t e;
+    if ((e = rec_panel<TS>(P, c0, LU_NB, st)) != cudaSuccess) return e;
+    *pp = panel_perm(P, c0);
+    return launch_perm_build(P, c0, LU_NB, *pp, st);
+}
+
+inline double upd_flops(const LUPlan& P, int M, int N, int Kd) { return 2.0 * M * (double)N * Kd * (double)P.nK; }
+
 template <class TS>
 cudaError_t factor_t(const LUPlan& P, cudaStream_t st) {
     cudaError_t e;
     const int ld = (int)P.ld;
     for (int c0 = 0; c0 < ld; c0 += LU_NB) {
         int ev = prof_begin(P.prof, PH_LU_PANELS, st);
-        if ((e = rec_panel<TS>(P, c0, LU_NB, st)) != cudaSuccess) return e;
-        int32_t* pp = panel_perm(P, c0);
-        const void* upd_b = nullptr;
-        if ((e = launch_perm_build(P, c0, LU_NB, pp, st)) != cudaSuccess) return e;
-        if (c0 + LU_NB < ld) {
+        int32_t* pp = nullptr;
+        if ((e = outer_panel<TS>(P, c0, st, &pp)) != cudaSuccess) return e;
+        const int j0 = c0 + LU_NB, rest = ld - j0;
+        BqOut bo;
+        if (rest > 0) {
             if constexpr (std::is_same<TS, double>::value) {
-                if ((e = launch_laswp_perm<TS>(P, pp, LU_NB, c0 + LU_NB, ld, st)) != cudaSuccess) return e;
-                e = launch_trsm<TS>(P, c0, LU_NB, c0 + LU_NB, ld, st);
+                if ((e = launch_laswp_perm<TS>(P, pp, LU_NB, j0, ld, st)) != cudaSuccess) return e;
+                e = launch_trsm<TS>(P, c0, LU_NB, j0, ld, st);
             } else {
-                e = gemm_tc_swap_trsm256(P, pp, c0, st, &upd_b);
+                // split BF16: the product also writes the update's B panel
+                if (P.prec == MEHDG_MIXED_BF16X3) bo = BqOut{gemm_tc_bq_panel(P), rest, 0, 0, LU_NB};
+                e = gemm_tc_swap_trsm256(P, pp, c0, st, bo.p ? &bo : nullptr);
             }
             if (e != cudaSuccess) return e;
         }
         prof_end(P.prof, ev, st, 0.0);
-        if (c0 + LU_NB < ld) {
-            int rest = ld - (c0 + LU_NB);
-            if ((e = trailing_update<TS>(P, c0 + LU_NB, c0 + LU_NB, c0, rest, rest, LU_NB, st, PH_PACK_OUTER,
-                                         PH_GEMM_OUTER, 2.0 * rest * (double)rest * LU_NB * (double)P.nK,
-                                         upd_b)) != cudaSuccess)
+        if (rest > 0) {
+            const PackedB pb{bo.p, bo.nc, 0, bo.kp};
+            if ((e = trailing_update<TS>(P, j0, j0, c0, rest, rest, LU_NB, st, PH_PACK_OUTER, PH_GEMM_OUTER,
+                                         upd_flops(P, rest, rest, LU_NB), bo.p ? &pb : nullptr)) != cudaSuccess)
                 return e;
         }
     }
     return cudaSuccess;
+}
+
+// Split BF16 with the outer updates of two panels merged.  For the pair of
+// outer panels a = [c0, c0+256) and b = [c0+256, c0+512), with R the columns
+// right of b:
+//   1. factor a; exchange the rows of all columns right of a by a's
+//      permutation P_a and take U_a = L_aa^-1 A of their rows in a (TRSM
+//      product, which also writes U_a as the B operand, K entries 0..255);
+//   2. update only b's 256 columns by a (depth 256), and factor b;
+//   3. on R: exchange rows by P_b (block rows written back); the block rows
+//      of b then hold rows of A not yet updated by a: subtract their part
+//      L_a(src) U_a, with the multipliers L_a of the rows they came from (a's
+//      columns are not exchanged by P_b);
+//   4. U_b = L_bb^-1 (those rows) by the TRSM product (K entries 256..511 of
+//      the same B operand);
+//   5. one update of R's rows below b with depth 512: [L_a | L_b] [U_a; U_b],
+//      L_a gathered through P_b for the rows that P_b moved.
+// The factors and the permutations kept for the solves are those of the
+// one-panel form (rows left of a panel are never exchanged again); only the
+// order of the roundings in the trailing matrix differs, and its C is
+// streamed once per pair instead of twice.
+cudaError_t factor_pairs(const LUPlan& P, cudaStream_t st) {
+    cudaError_t e;
+    const int ld = (int)P.ld;
+    void* bq = gemm_tc_bq_panel(P);
+    for (int ca = 0; ca < ld; ca += 2 * LU_NB) {
+        const int cb = ca + LU_NB, jr = cb + LU_NB;
+        int ev = prof_begin(P.prof, PH_LU_PANELS, st);
+        int32_t *pa = nullptr, *pb = nullptr;
+        if ((e = outer_panel<float>(P, ca, st, &pa)) != cudaSuccess) return e;
+        if (cb >= ld) { prof_end(P.prof, ev, st, 0.0); break; }
+        const int n1 = ld - cb;                       // columns right of a (b's and R's)
+        const BqOut ba{bq, n1, 0, 0, 2 * LU_NB};
+        if ((e = gemm_tc_swap_trsm256(P, pa, ca, st, &ba)) != cudaSuccess) return e;
+        prof_end(P.prof, ev, st, 0.0);
+        {
+            const PackedB b{bq, n1, 0, 2 * LU_NB};
+            if ((e = trailing_update<float>(P, cb, cb, ca, n1, LU_NB, LU_NB, st, PH_PACK_OUTER, PH_GEMM_OUTER,
+                                            upd_flops(P, n1, LU_NB, LU_NB), &b)) != cudaSuccess)
+                return e;
+        }
+        ev = prof_begin(P.prof, PH_LU_PANELS, st);
+        if ((e = outer_panel<float>(P, cb, st, &pb)) != cudaSuccess) return e;
+        const int nr = ld - jr;                       // columns of R
+        if (nr <= 0) { prof_end(P.prof, ev, st, 0.0); break; }
+        if ((e = launch_laswp_perm<float>(P, pb, LU_NB, jr, ld, st)) != cudaSuccess) return e;
+        prof_end(P.prof, ev, st, 0.0);
+        const PackedB b{bq, n1, LU_NB, 2 * LU_NB};
+        {
+            const AGather g{pb, LU_NB, 0, LU_NB};     // the block rows of b
+            if ((e = trailing_update<float>(P, cb, jr, ca, LU_NB, nr, LU_NB, st, PH_PACK_OUTER, PH_GEMM_OUTER,
+                                            upd_flops(P, LU_NB, nr, LU_NB), &b, &g)) != cudaSuccess)
+                return e;
+        }
+        ev = prof_begin(P.prof, PH_LU_PANELS, st);
+        const BqOut bb{bq, n1, LU_NB, LU_NB, 2 * LU_NB};
+        if ((e = gemm_tc_swap_trsm256(P, nullptr, cb, st, &bb)) != cudaSuccess) return e;
+        prof_end(P.prof, ev, st, 0.0);
+        {
+            const AGather g{pb, LU_NB, LU_NB, 2 * LU_NB};   // the rows below b that P_b moved
+            if ((e = trailing_update<float>(P, jr, jr, ca, nr, nr, 2 * LU_NB, st, PH_PACK_OUTER, PH_GEMM_OUTER,
+                                            upd_flops(P, nr, nr, 2 * LU_NB), &b, &g)) != cudaSuccess)
+                return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+// merged pairs of outer updates: split BF16 only (the mode whose TRSM product
+// writes the B operand); MEHDG_LU_PAIRS=0 selects the one-panel form
+bool use_pairs(const LUPlan& P) {
+    if (P.fp64 || P.prec != MEHDG_MIXED_BF16X3) return false;
+    if (const char* f = std::getenv("MEHDG_LU_PAIRS")) return std::atoi(f) != 0;
+    return true;
 }
 
 }  // namespace
@@ -898,6 +985,7 @@ size_t lu_work_bytes(int64_t nK, int64_t ld, bool fp64, int prec) {
 
 cudaError_t lu_factor(const LUPlan& P, cudaStream_t st) {
     if (P.fp64) return factor_t<double>(P, st);
+    if (use_pairs(P)) return factor_pairs(P, st);
     return factor_t<float>(P, st);
 }
 

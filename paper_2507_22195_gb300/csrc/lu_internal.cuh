@@ -13,18 +13,45 @@ inline size_t lu_perm_panels_bytes(int64_t nK, int64_t ld) {
 }
 inline size_t lu_perm_bytes(int64_t nK, int64_t ld) { return lu_perm_scratch_bytes(nK) + lu_perm_panels_bytes(nK, ld); }
 
+// A B panel already packed in split BF16 by a TRSM product: per element nc
+// rows (one per column of the trailing matrix), each [hi (kp) | lo (kp)];
+// this update's first column is row c0 of it.
+struct PackedB {
+    const void* p = nullptr;
+    int nc = 0, c0 = 0, kp = 0;
+};
+// Rows of the A operand taken from other rows of S for their first kn K
+// entries: slot i in [i0, i1) of a net permutation (rows[i] takes the old
+// content of rows[cont[i]]) with cont[i] != i gives operand row rows[i] the
+// values of row rows[cont[i]] (the deferred update's first-half multipliers,
+// which the second half's exchanges did not move).
+struct AGather {
+    const int32_t* perm = nullptr;   // [nK][LU_PW]
+    int kn = 0, i0 = 0, i1 = 0;
+};
+// The TRSM product's copy of U12 as the next update's B operand (split BF16):
+// per element nc rows of [hi (kp) | lo (kp)]; product column n goes to row
+// c0 + n, its K index k (the row inside the 256 block) to entry k0 + k.
+struct BqOut {
+    void* p = nullptr;
+    int nc = 0, c0 = 0, k0 = 0, kp = 0;
+};
+
 // C[r0.., c0..] -= L[r0.., k0..k0+Kd) * U[k0..k0+Kd, c0..] on the tensor cores
 // (TF32 or BF16 operands, FP32 accumulation), S^K column-major FP32.
 // With ph_gemm >= 0 the update kernel alone is timed under that phase (flops
 // recorded with it) and the operand packing under ph_pack.
-// b_packed: the B panel already packed (split BF16) by the TRSM product, or null
+// b: the B panel already packed (split BF16) by a TRSM product, or null;
+// g: A rows gathered through a net permutation, or null
 cudaError_t gemm_tc_update(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st,
-                           int ph_pack = -1, int ph_gemm = -1, double flops = 0.0, const void* b_packed = nullptr);
+                           int ph_pack = -1, int ph_gemm = -1, double flops = 0.0, const PackedB* b = nullptr,
+                           const AGather* g = nullptr);
 size_t gemm_tc_work_bytes(int64_t nK, int64_t ld, int prec);
-// row exchanges of the columns right of outer panel c0 by its net permutation
-// (perm: [nK][LU_PW]) and the TRSM of their rows [c0, c0+256), fused
-// (update_b, if not null, receives the next update's packed B panel, or null
-// when the precision mode does not fuse it)
-cudaError_t gemm_tc_swap_trsm256(const LUPlan& P, const int32_t* perm, int c0, cudaStream_t st,
-                                 const void** update_b);
+// The next update's B panel of the split-BF16 mode (written by the TRSM products)
+void* gemm_tc_bq_panel(const LUPlan& P);
+// Row exchanges of the columns right of outer panel c0 by its net permutation
+// (perm: [nK][LU_PW]; null: the rows are already in place) and the TRSM of
+// their rows [c0, c0+256), fused.  bq: where the product also writes U12 as
+// split-BF16 B operand (null: not written; only the split-BF16 mode has it).
+cudaError_t gemm_tc_swap_trsm256(const LUPlan& P, const int32_t* perm, int c0, cudaStream_t st, const BqOut* bq);
 cudaError_t gemm_simt_update_f32(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st);

@@ -210,6 +210,30 @@ def test_condense_at_bench_lu_configuration_matches_oracle(bench_lu_case, prec):
     ctx.close()
 
 
+@pytest.mark.parametrize("pairs", [1, 0])
+@pytest.mark.parametrize("name", ["vortex_p2m2", "tgv_p3m2"])
+def test_lu_pair_and_one_panel_forms_match_oracle(name, pairs, monkeypatch):
+    """split BF16 merges the outer updates of two panels into one of depth 512
+    (MEHDG_LU_PAIRS=0 selects one update per panel): 3 outer panels (one pair
+    and a single panel) and 7 (three pairs and a single panel) per element"""
+    monkeypatch.setenv("MEHDG_LU_PAIRS", str(pairs))
+    mesh, st, kw = case(name)
+    ctx = M().Context(mesh, flux=2, prec=M().MEHDG_MIXED_BF16X3, **kw)
+    ctx.set_state(*to_dev(st))
+    bh = ctx.condense()
+    dvh_np = I.random_direction(st.vhat.shape, 78, 1e-3)
+    dV = ctx.recover(torch.tensor(dvh_np, device="cuda:0"))
+    torch.cuda.synchronize()
+    stat, iters = ctx.status()
+    assert (stat == 0).all(), (stat, iters)
+    prm = oracle.params(flux=2, **kw)
+    bh_o, _ = oracle.condense_mesh(prm, mesh, st)
+    dV_o, _ = oracle.recover_mesh(prm, mesh, st, dvh_np)
+    e = (rel(bh, bh_o), rel(dV, dV_o))
+    assert max(e) < 1e-8, (e, iters)
+    ctx.close()
+
+
 @pytest.mark.parametrize("ctas", [1, 2, 4, 8])
 def test_solve_cluster_sizes_match_oracle(ctas, monkeypatch):
     """the solve with 1, 2, 4 and 8 CTAs per element (normally chosen from the

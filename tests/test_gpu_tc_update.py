@@ -39,7 +39,9 @@ def _product(L, U, prec):
                                    # ragged tiles inside the matrix (per-thread epilogue)
                                    (768, 260, 256, 0, 300, 200, 64),
                                    # several tiles per persistent CTA (both C and TMEM buffers reused)
-                                   (2048, 256, 256, 0, 1792, 1792, 256)])
+                                   (2048, 256, 256, 0, 1792, 1792, 256),
+                                   # depth 512 (the merged outer updates of two panels)
+                                   (1024, 512, 512, 0, 512, 512, 512)])
 def test_trailing_update_matches_torch(prec, shape):
     from paper_2507_22195_gb300 import mehdg
     ld, r0, c0, k0, M, N, Kd = shape
