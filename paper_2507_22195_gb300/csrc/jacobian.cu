@@ -98,13 +98,99 @@ __device__ __forceinline__ void load_tables(const Tab& tb, double* sL, double* s
     if (threadIdx.x < tb.ng) sW[threadIdx.x] = tb.w[threadIdx.x];
 }
 
+// The contraction of the stored point blocks P into S for one micro-element,
+// with p + 1 = P1 known at compile time (ng = p + 2 = P1 + 1): every index
+// division is by a constant, the loops over the quadrature points unroll, and
+// stage 3 keeps the P1 sums of a row a3 of an item as independent
+// accumulators, reading that row of the z-table once per (alpha, g3) (as a
+// float4 when P1 = 4).
+// Every sum runs over its quadrature index in increasing order.  Mt:
+// [3 dir][2 tau][NG][PP] pair tables, P: [NG^3][100],
+// H1: [4 alpha][G2][P1 b1][P1 a1][5 k], O: the node index of the
+// micro-element's first node in the macro-element.
+template <int P1, class TS>
+__device__ __forceinline__ void vol_contract(const TS* __restrict__ Mt, const TS* __restrict__ P, TS* __restrict__ H1,
+                                             TS* S, int64_t ld, int n, int O) {
+    constexpr int NG = P1 + 1, PP = P1 * P1, G2 = NG * NG, NH = 5 * 4 * PP * G2;
+    const TS* M1 = Mt;
+    const TS* M2 = Mt + 2 * NG * PP;
+    const TS* M3 = Mt + 4 * NG * PP;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const size_t sa = (size_t)5 * n * n, sb = sa * (size_t)ld;
+    for (int l = 0; l < 5; ++l) {
+        // stage 1: contract g1 (alpha = 1 takes the x derivative of the test function)
+        for (int i = tid; i < NH; i += nth) {
+            const int k = i % 5, a1 = (i / 5) % P1, b1 = (i / (5 * P1)) % P1;
+            const int g23 = (i / (5 * PP)) % G2, al = i / (5 * PP * G2);
+            const TS* Mx = M1 + (al == 1 ? NG * PP : 0) + a1 * P1 + b1;
+            const TS* Pc = P + (size_t)NG * g23 * 100 + 25 * al + 5 * k + l;
+            TS s = 0;
+#pragma unroll
+            for (int g1 = 0; g1 < NG; ++g1) s += Mx[g1 * PP] * Pc[g1 * 100];
+            H1[i] = s;
+        }
+        __syncthreads();
+        // stages 2 and 3 per item (k, a1, a2, b1, b2)
+        for (int it = tid; it < 5 * PP * PP; it += nth) {
+            int r = it;
+            const int k = r % 5; r /= 5;
+            const int a1 = r % P1; r /= P1;
+            const int a2 = r % P1; r /= P1;
+            const int b1 = r % P1; const int b2 = r / P1;
+            TS h2[4][NG];
+#pragma unroll
+            for (int al = 0; al < 4; ++al) {
+                const TS* My = M2 + (al == 2 ? NG * PP : 0) + a2 * P1 + b2;
+                const TS* h = H1 + al * G2 * 5 * PP + (b1 * P1 + a1) * 5 + k;
+#pragma unroll
+                for (int g3 = 0; g3 < NG; ++g3) {
+                    TS s = 0;
+#pragma unroll
+                    for (int g2 = 0; g2 < NG; ++g2) s += My[g2 * PP] * h[(g2 + NG * g3) * 5 * PP];
+                    h2[al][g3] = s;
+                }
+            }
+            TS* Sb = S + (size_t)((O + a1 + n * a2) * 5 + k) + (size_t)((O + b1 + n * b2) * 5 + l) * ld;
+#pragma unroll 1
+            for (int a3 = 0; a3 < P1; ++a3) {
+                TS acc[P1];
+#pragma unroll
+                for (int q = 0; q < P1; ++q) acc[q] = 0;
+#pragma unroll
+                for (int al = 0; al < 4; ++al) {
+                    const TS* Mz = M3 + (al == 3 ? NG * PP : 0) + a3 * P1;
+#pragma unroll
+                    for (int g3 = 0; g3 < NG; ++g3) {
+                        const TS hv = h2[al][g3];
+                        const TS* row = Mz + g3 * PP;
+                        if constexpr (P1 == 4 && sizeof(TS) == 4) {
+                            const float4 v = *reinterpret_cast<const float4*>(row);
+                            acc[0] += v.x * hv;
+                            acc[1] += v.y * hv;
+                            acc[2] += v.z * hv;
+                            acc[3] += v.w * hv;
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < P1; ++q) acc[q] += row[q] * hv;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int b3 = 0; b3 < P1; ++b3) atomic_add_t(Sb + a3 * sa + b3 * sb, (double)acc[b3]);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------- sum factorised
 // Per trial component l: stage 1 contracts g1 for all five test components k
-// into H1[k][alpha][a1 b1][g2 g3]; then every thread takes items
+// into H1[alpha][g2 g3][b1][a1][k]; then every thread takes items
 // (k, a1, a2, b1, b2), contracts g2 into registers (4 x ng values) and g3 for
 // all (a3, b3), and adds the p1^2 results into S.  Items are ordered k
 // fastest, then a1, so a warp's atomics fall on runs of 5 p1 consecutive rows
-// 5 A + k of one column.
+// 5 A + k of one column, and its reads of H1 on consecutive words (with k or
+// a1 slowest in H1, the 20 lanes would read one shared-memory bank).
 // Point pass alone (inviscid, with a.pj): the dual-number physics at the
 // Gauss points of one micro-element, written to a.pj.  Its 255 registers no
 // longer hold the contraction below to one CTA per SM.
@@ -136,7 +222,7 @@ jac_volume_sf_kernel(JacobianArgs a) {
     const Tab& tb = a.tab;
     const int K = blockIdx.y, e = blockIdx.x;
     const int p = tb.p, m = tb.m, n = tb.n, ng = tb.ng, nl = tb.nl, npt = tb.npt, p1 = p + 1;
-    const int PP = p1 * p1, G2 = ng * ng;
+    const int PP = p1 * p1;
     const int e1 = e % m, e2 = (e / m) % m, e3 = e / (m * m);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* sL = reinterpret_cast<double*>(smem_raw);
@@ -148,7 +234,9 @@ jac_volume_sf_kernel(JacobianArgs a) {
     double* vl = reinterpret_cast<double*>(uni);            // phase 1: nodal state
     double* vsl = vl + 5 * nl;
     double* ql = vsl + 5 * nl;
-    TS* H1 = reinterpret_cast<TS*>(uni);                     // phase 2: [5][4][PP][G2]
+    // phase 2: H1[al][g23][b1][a1][k], so that the lanes of a warp (k fastest,
+    // then a1) read consecutive words in stage 2
+    TS* H1 = reinterpret_cast<TS*>(uni);
     const int tid = threadIdx.x, nth = blockDim.x;
     load_tables(tb, sL, sD, sW);
     double sc[3], hw[3];
@@ -172,60 +260,12 @@ jac_volume_sf_kernel(JacobianArgs a) {
         volume_point_jacobians<TS, VISC>(a, K, e1, e2, e3, sL, sW, hw, vl, vsl, ql, P);
     }
     TS* S = reinterpret_cast<TS*>(a.S) + (size_t)K * a.ld * a.ld;
-    const TS* M1 = Mt;                       // direction x: tau=0 at [0], tau=1 at [ng*PP]
-    const TS* M2 = Mt + 2 * ng * PP;
-    const TS* M3 = Mt + 4 * ng * PP;
-    const int nh1 = 4 * PP * G2;
-    for (int l = 0; l < 5; ++l) {
-        // stage 1: contract g1 (alpha = 1 takes the x derivative of the test function)
-        for (int i = tid; i < 5 * nh1; i += nth) {
-            const int g23 = i % G2, ab1 = (i / G2) % PP, al = (i / (G2 * PP)) & 3, k = i / nh1;
-            const TS* Mx = M1 + (al == 1 ? ng * PP : 0);
-            const TS* Pc = P + (size_t)ng * g23 * 100 + 25 * al + 5 * k + l;
-            TS s = 0;
-            for (int g1 = 0; g1 < ng; ++g1) s += Mx[g1 * PP + ab1] * Pc[(size_t)g1 * 100];
-            H1[i] = s;
-        }
-        __syncthreads();
-        // stages 2 and 3 per item
-        for (int it = tid; it < 5 * PP * PP; it += nth) {
-            int r = it;
-            const int k = r % 5; r /= 5;
-            const int a1 = r % p1; r /= p1;
-            const int a2 = r % p1; r /= p1;
-            const int b1 = r % p1; const int b2 = r / p1;
-            const int ab1 = a1 * p1 + b1, ab2 = a2 * p1 + b2;
-            TS h2[4][MEHDG_MAXG];
-#pragma unroll
-            for (int al = 0; al < 4; ++al) {
-                const TS* My = M2 + (al == 2 ? ng * PP : 0) + ab2;
-                const TS* h = H1 + (size_t)k * nh1 + ((size_t)al * PP + ab1) * G2;
-#pragma unroll
-                for (int g3 = 0; g3 < MEHDG_MAXG; ++g3) {
-                    TS s = 0;
-                    if (g3 < ng)
-                        for (int g2 = 0; g2 < ng; ++g2) s += My[g2 * PP] * h[g2 + ng * g3];
-                    h2[al][g3] = s;
-                }
-            }
-            const int Arow = (e1 * p + a1) + n * ((e2 * p + a2) + n * (e3 * p));
-            const int Bcol = (e1 * p + b1) + n * ((e2 * p + b2) + n * (e3 * p));
-            for (int a3 = 0; a3 < p1; ++a3)
-                for (int b3 = 0; b3 < p1; ++b3) {
-                    const int ab3 = a3 * p1 + b3;
-                    TS s = 0;
-#pragma unroll
-                    for (int al = 0; al < 4; ++al) {
-                        const TS* Mz = M3 + (al == 3 ? ng * PP : 0) + ab3;
-#pragma unroll
-                        for (int g3 = 0; g3 < MEHDG_MAXG; ++g3)
-                            if (g3 < ng) s += Mz[g3 * PP] * h2[al][g3];
-                    }
-                    const int A = Arow + n * n * a3, B = Bcol + n * n * b3;
-                    atomic_add_t(&S[(size_t)(A * 5 + k) + (size_t)(B * 5 + l) * a.ld], (double)s);
-                }
-        }
-        __syncthreads();
+    const int O = e1 * p + n * (e2 * p + n * e3 * p);
+    switch (p1) {
+    case 2: vol_contract<2, TS>(Mt, P, H1, S, a.ld, n, O); break;
+    case 3: vol_contract<3, TS>(Mt, P, H1, S, a.ld, n, O); break;
+    case 4: vol_contract<4, TS>(Mt, P, H1, S, a.ld, n, O); break;
+    default: vol_contract<5, TS>(Mt, P, H1, S, a.ld, n, O); break;    // p = MEHDG_MAXP
     }
 }
 
@@ -478,9 +518,10 @@ jac_face_contract_kernel(JacobianArgs a) {
 // for every node b of the macro-element's d-line (n of them).  So
 //   S[(a,k),(b,l)] += sum_x W sum_j dG_kj/dq_ld d_j phi_a  psi_{b,d}
 // is sum-factorised like A_vv, with n instead of p+1 trial functions along d:
-// stage 1 contracts g1 into H1[k][j][a1 b1][g2 g3]; items (k, a1, a2, b1, b2)
+// stage 1 contracts g1 into H1[j][g2 g3][b1][a1][k]; items (k, a1, a2, b1, b2)
 // contract g2 into registers and g3 for every (a3, b3).  Items run k fastest,
-// then a1, so a warp's atomics fall on runs of consecutive rows 5 A + k.
+// then a1, so a warp's atomics fall on runs of consecutive rows 5 A + k and its
+// reads of H1 on consecutive words.
 // The five test components k are processed kg at a time (kg = 5 unless the
 // stage-1 buffer would not fit in shared memory).
 // Point pass of the Q-elimination term: dG/dq at every Gauss point of one
@@ -548,7 +589,9 @@ jac_visc_q_volume_kernel(JacobianArgs a, const double* __restrict__ C1, int kg) 
     double* vx = vl + 5 * nl;                                // [npt][5]
     TS* T = reinterpret_cast<TS*>(vx + 5 * npt);             // [3 dir][2 tau][ng][TW]
     TS* P = T + 6 * ng * TW;                                 // [npt][3 j][25 kl]
-    TS* H1 = P + (size_t)npt * 75;                           // [kg][3 j][TW][G2]
+    // H1[j][g23][b1][a1][kk] (kk < kn <= kg), so that the lanes of a warp (kk
+    // fastest, then a1) read consecutive words in stage 2
+    TS* H1 = P + (size_t)npt * 75;
     const int tid = threadIdx.x, nth = blockDim.x;
     load_tables(tb, sL, sD, sW);
     double sc[3], hw[3];
@@ -623,19 +666,20 @@ jac_visc_q_volume_kernel(JacobianArgs a, const double* __restrict__ C1, int kg) 
         const TS* T1 = T + (0 * 2) * ng * TW;         // direction x (tau at + ng * TW)
         const TS* T2 = T + (1 * 2) * ng * TW;
         const TS* T3 = T + (2 * 2) * ng * TW;
-        const int nh1 = 3 * TW * G2;
+        const int PB = p1 * nb[0];                   // (a1, b1) pairs
         for (int l = 0; l < 5; ++l)
             for (int k0 = 0; k0 < 5; k0 += kg) {
                 const int kn = 5 - k0 < kg ? 5 - k0 : kg;
-                // stage 1: H1[kk][j][a1 * nb0 + b1][g23] = sum_g1 T1_(j==0)[g1][a1 b1] P[x][j][k l]
-                for (int i = tid; i < kn * 3 * p1 * nb[0] * G2; i += nth) {
-                    const int g23 = i % G2, ab1 = (i / G2) % (p1 * nb[0]);
-                    const int j = (i / (G2 * p1 * nb[0])) % 3, kk = i / (G2 * p1 * nb[0] * 3);
+                // stage 1: H1[j][g23][b1][a1][kk] = sum_g1 T1_(j==0)[g1][a1 b1] P[x][j][k l]
+                for (int i = tid; i < kn * 3 * PB * G2; i += nth) {
+                    const int kk = i % kn, a1 = (i / kn) % p1, b1 = (i / (kn * p1)) % nb[0];
+                    const int g23 = (i / (kn * PB)) % G2, j = i / (kn * PB * G2);
+                    const int ab1 = a1 * nb[0] + b1;
                     const TS* Tx = T1 + (j == 0 ? ng * TW : 0) + ab1;
                     const TS* Pc = P + (size_t)ng * g23 * 75 + 25 * j + 5 * (k0 + kk) + l;
                     TS s = 0;
                     for (int g1 = 0; g1 < ng; ++g1) s += Tx[g1 * TW] * Pc[(size_t)g1 * 75];
-                    H1[(size_t)kk * nh1 + ((size_t)j * TW + ab1) * G2 + g23] = s;
+                    H1[i] = s;
                 }
                 __syncthreads();
                 const int nitem = kn * p1 * p1 * nb[0] * nb[1];
@@ -645,17 +689,17 @@ jac_visc_q_volume_kernel(JacobianArgs a, const double* __restrict__ C1, int kg) 
                     const int a1 = r % p1; r /= p1;
                     const int a2 = r % p1; r /= p1;
                     const int b1 = r % nb[0]; const int b2 = r / nb[0];
-                    const int ab1 = a1 * nb[0] + b1, ab2 = a2 * nb[1] + b2;
+                    const int ab2 = a2 * nb[1] + b2;
                     TS h2[3][MEHDG_MAXG];
 #pragma unroll
                     for (int j = 0; j < 3; ++j) {
                         const TS* Ty = T2 + (j == 1 ? ng * TW : 0) + ab2;
-                        const TS* h = H1 + (size_t)kk * nh1 + ((size_t)j * TW + ab1) * G2;
+                        const TS* h = H1 + (size_t)j * G2 * kn * PB + (b1 * p1 + a1) * kn + kk;
 #pragma unroll
                         for (int g3 = 0; g3 < MEHDG_MAXG; ++g3) {
                             TS s = 0;
                             if (g3 < ng)
-                                for (int g2 = 0; g2 < ng; ++g2) s += Ty[g2 * TW] * h[g2 + ng * g3];
+                                for (int g2 = 0; g2 < ng; ++g2) s += Ty[g2 * TW] * h[(size_t)(g2 + ng * g3) * kn * PB];
                             h2[j][g3] = s;
                         }
                     }
@@ -688,8 +732,9 @@ jac_visc_q_volume_kernel(JacobianArgs a, const double* __restrict__ C1, int kg) 
 // the normal direction (d = face direction) chi_b at the face end is the
 // constant (2/h) C1_ref[end][b]; along a tangential direction it is chi_b of
 // that direction.  Per face and q-direction d: stage 1 contracts g1 into
-// H1[k][a1 b1][g2], items (k, a1, a2, b1, b2) contract g2 and add the result
-// (times the normal factor for every b on the normal line when d is normal).
+// H1[g2][b1][a1][k] (a warp's lanes, k fastest and then a1, read consecutive
+// words), items (k, a1, a2, b1, b2) contract g2 and add the result (times the
+// normal factor for every b on the normal line when d is normal).
 template <class TS>
 __global__ void __launch_bounds__(256)
 jac_visc_q_face_kernel(JacobianArgs a, const double* __restrict__ C1) {
@@ -709,7 +754,7 @@ jac_visc_q_face_kernel(JacobianArgs a, const double* __restrict__ C1) {
     double* fh = C1s + n * n;         // [5][fl]
     TS* PF = reinterpret_cast<TS*>(fh + 5 * fl);   // [fpt][3 d][25 kl]
     TS* T = PF + (size_t)fpt * 75;                  // [2 tangential][ng][TW]
-    TS* H1 = T + 2 * ng * TW;                       // [5][TW][ng]
+    TS* H1 = T + 2 * ng * TW;                       // [ng][nb1][p1][5] (at most 5 TW ng)
     TS* cn = H1 + 5 * TW * ng;                      // [n] normal factors
     const int tid = threadIdx.x, nth = blockDim.x;
     for (int i = tid; i < ng * p1; i += nth) sL[i] = tb.L[i / p1][i % p1];
@@ -773,11 +818,12 @@ jac_visc_q_face_kernel(JacobianArgs a, const double* __restrict__ C1) {
         __syncthreads();
         for (int l = 0; l < 5; ++l) {
             for (int i = tid; i < 5 * p1 * nb1 * ng; i += nth) {
-                const int g2 = i % ng, ab1 = (i / ng) % (p1 * nb1), k = i / (ng * p1 * nb1);
+                const int k = i % 5, a1 = (i / 5) % p1, b1 = (i / (5 * p1)) % nb1, g2 = i / (5 * p1 * nb1);
+                const int ab1 = a1 * nb1 + b1;
                 TS s = 0;
                 for (int g1 = 0; g1 < ng; ++g1)
                     s += T[g1 * TW + ab1] * PF[(size_t)(g1 + ng * g2) * 75 + d * 25 + k * 5 + l];
-                H1[((size_t)k * TW + ab1) * ng + g2] = s;
+                H1[i] = s;
             }
             __syncthreads();
             const int nitem = 5 * p1 * p1 * nb1 * nb2;
@@ -787,10 +833,10 @@ jac_visc_q_face_kernel(JacobianArgs a, const double* __restrict__ C1) {
                 const int a1 = r % p1; r /= p1;
                 const int a2 = r % p1; r /= p1;
                 const int b1 = r % nb1; const int b2 = r / nb1;
-                const TS* hk = H1 + ((size_t)k * TW + a1 * nb1 + b1) * ng;
+                const TS* hk = H1 + (b1 * p1 + a1) * 5 + k;
                 const TS* Ty = T + ng * TW + a2 * nb2 + b2;
                 TS s = 0;
-                for (int g2 = 0; g2 < ng; ++g2) s += Ty[g2 * TW] * hk[g2];
+                for (int g2 = 0; g2 < ng; ++g2) s += Ty[g2 * TW] * hk[(size_t)g2 * 5 * p1 * nb1];
                 int ca[3], cb[3];
                 ca[df] = iface; ca[t1] = eo1 + a1; ca[t2] = eo2 + a2;
                 cb[df] = iface; cb[t1] = d == t1 ? b1 : eo1 + b1; cb[t2] = d == t2 ? b2 : eo2 + b2;
