@@ -508,6 +508,99 @@ jac_face_contract_kernel(JacobianArgs a) {
 }
 
 // ---------------------------------------------------------------- viscous: -A_vq C
+// The contraction of the point blocks P (direction d of q) into S for one
+// micro-element, with p + 1 = P1 known at compile time (ng = P1 + 1): the
+// quadrature loops unroll and the index divisions are by constants, except
+// those by n (the line direction's trial count) and by kn.  Stage 1 gives a
+// thread one (a1, g23, j, b1) and all kn components (the T1 values loaded
+// once); stage 3 keeps four b3 sums of a row a3 as independent accumulators.
+// Every sum runs over its quadrature index in increasing order, as in the
+// formulas of the comment below.  T: [3 dir][2 tau][NG][TW] line tables
+// (TW = P1 n), P: [NG^3][3 j][25 kl], H1: [3 j][G2][nb0 b1][P1 a1][kn kk].
+template <int P1, class TS>
+__device__ __forceinline__ void q_contract(const TS* __restrict__ T, const TS* __restrict__ P, TS* __restrict__ H1,
+                                           TS* S, int64_t ld, int n, const int (&eo)[3], int d, int kg) {
+    constexpr int NG = P1 + 1, G2 = NG * NG, PP = P1 * P1;
+    const int TW = P1 * n;
+    const int nb0 = d == 0 ? n : P1, nb1 = d == 1 ? n : P1, nb2 = d == 2 ? n : P1;
+    const int PB = P1 * nb0;                        // (a1, b1) pairs
+    const TS* T1 = T;                               // direction x (tau at + NG * TW)
+    const TS* T2 = T + 2 * NG * TW;
+    const TS* T3 = T + 4 * NG * TW;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const size_t sa = (size_t)5 * n * n, sb = sa * (size_t)ld;
+    for (int l = 0; l < 5; ++l)
+        for (int k0 = 0; k0 < 5; k0 += kg) {
+            const int kn = 5 - k0 < kg ? 5 - k0 : kg;
+            // stage 1: H1[j][g23][b1][a1][kk] = sum_g1 T1_(j==0)[g1][a1 b1] P[x][j][k l]
+            for (int i = tid; i < P1 * G2 * 3 * nb0; i += nth) {
+                const int a1 = i % P1, g23 = (i / P1) % G2, j = (i / (P1 * G2)) % 3, b1 = i / (3 * P1 * G2);
+                const TS* Tx = T1 + (j == 0 ? NG * TW : 0) + a1 * nb0 + b1;
+                const TS* Pc = P + (size_t)NG * g23 * 75 + 25 * j + 5 * k0 + l;
+                TS tx[NG];
+#pragma unroll
+                for (int g1 = 0; g1 < NG; ++g1) tx[g1] = Tx[g1 * TW];
+                TS* out = H1 + ((size_t)(j * G2 + g23) * PB + b1 * P1 + a1) * kn;
+                for (int kk = 0; kk < kn; ++kk) {
+                    TS s = 0;
+#pragma unroll
+                    for (int g1 = 0; g1 < NG; ++g1) s += tx[g1] * Pc[g1 * 75 + 5 * kk];
+                    out[kk] = s;
+                }
+            }
+            __syncthreads();
+            // stages 2 and 3 per item (kk, a1, a2, b1, b2), kk fastest
+            const int nitem = kn * PP * nb0 * nb1;
+            for (int it = tid; it < nitem; it += nth) {
+                int r = it;
+                const int kk = r % kn; r /= kn;
+                const int a1 = r % P1; r /= P1;
+                const int a2 = r % P1; r /= P1;
+                const int b1 = r % nb0; const int b2 = r / nb0;
+                TS h2[3][NG];
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const TS* Ty = T2 + (j == 1 ? NG * TW : 0) + a2 * nb1 + b2;
+                    const TS* h = H1 + (size_t)j * G2 * PB * kn + (b1 * P1 + a1) * kn + kk;
+#pragma unroll
+                    for (int g3 = 0; g3 < NG; ++g3) {
+                        TS s = 0;
+#pragma unroll
+                        for (int g2 = 0; g2 < NG; ++g2) s += Ty[g2 * TW] * h[(size_t)(g2 + NG * g3) * PB * kn];
+                        h2[j][g3] = s;
+                    }
+                }
+                const int k = k0 + kk;
+                // S row (A, k) with A = (eo0 + a1) + n (eo1 + a2) + n^2 (eo2 + a3); column (B, l) with
+                // B = B1 + n B2 + n^2 B3, B3 = b3 on the line direction d = 2, else eo2 + b3
+                const int B1 = d == 0 ? b1 : eo[0] + b1, B2 = d == 1 ? b2 : eo[1] + b2;
+                TS* Sb = S + (size_t)(((eo[0] + a1) + n * (eo[1] + a2) + n * n * eo[2]) * 5 + k) +
+                         (size_t)((B1 + n * (B2 + n * (d == 2 ? 0 : eo[2]))) * 5 + l) * ld;
+#pragma unroll 1
+                for (int a3 = 0; a3 < P1; ++a3)
+                    for (int b30 = 0; b30 < nb2; b30 += 4) {
+                        TS acc[4] = {0, 0, 0, 0};
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) {
+                            const TS* Tz = T3 + (j == 2 ? NG * TW : 0) + a3 * nb2 + b30;
+#pragma unroll
+                            for (int g3 = 0; g3 < NG; ++g3) {
+                                const TS hv = h2[j][g3];
+                                const TS* row = Tz + g3 * TW;
+#pragma unroll
+                                for (int q = 0; q < 4; ++q)
+                                    if (b30 + q < nb2) acc[q] += row[q] * hv;
+                            }
+                        }
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (b30 + q < nb2) atomic_add_t(Sb + a3 * sa + (b30 + q) * sb, (double)acc[q]);
+                    }
+            }
+            __syncthreads();
+        }
+}
+
 // Q-elimination term of S = A_vv - A_vq A_qq^-1 A_qv (eq. R3).  A_qq = I x M
 // with M a tensor product of 1-D mass matrices, so C = A_qq^-1 A_qv acts on
 // the q-component (l, d) along the d-lines only: C = (2/h_d) C1_ref (x) I.
@@ -578,7 +671,7 @@ jac_visc_q_volume_kernel(JacobianArgs a, const double* __restrict__ C1, int kg) 
     const Tab& tb = a.tab;
     const int K = blockIdx.y, e = blockIdx.x;
     const int p = tb.p, m = tb.m, n = tb.n, ng = tb.ng, Nn = tb.Nn, nl = tb.nl, npt = tb.npt, p1 = p + 1;
-    const int G2 = ng * ng, TW = p1 * n;
+    const int TW = p1 * n;
     const int eo[3] = {(e % m) * p, ((e / m) % m) * p, (e / (m * m)) * p};
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* sL = reinterpret_cast<double*>(smem_raw);
@@ -663,67 +756,12 @@ jac_visc_q_volume_kernel(JacobianArgs a, const double* __restrict__ C1, int kg) 
                     }
         }
         __syncthreads();
-        const TS* T1 = T + (0 * 2) * ng * TW;         // direction x (tau at + ng * TW)
-        const TS* T2 = T + (1 * 2) * ng * TW;
-        const TS* T3 = T + (2 * 2) * ng * TW;
-        const int PB = p1 * nb[0];                   // (a1, b1) pairs
-        for (int l = 0; l < 5; ++l)
-            for (int k0 = 0; k0 < 5; k0 += kg) {
-                const int kn = 5 - k0 < kg ? 5 - k0 : kg;
-                // stage 1: H1[j][g23][b1][a1][kk] = sum_g1 T1_(j==0)[g1][a1 b1] P[x][j][k l]
-                for (int i = tid; i < kn * 3 * PB * G2; i += nth) {
-                    const int kk = i % kn, a1 = (i / kn) % p1, b1 = (i / (kn * p1)) % nb[0];
-                    const int g23 = (i / (kn * PB)) % G2, j = i / (kn * PB * G2);
-                    const int ab1 = a1 * nb[0] + b1;
-                    const TS* Tx = T1 + (j == 0 ? ng * TW : 0) + ab1;
-                    const TS* Pc = P + (size_t)ng * g23 * 75 + 25 * j + 5 * (k0 + kk) + l;
-                    TS s = 0;
-                    for (int g1 = 0; g1 < ng; ++g1) s += Tx[g1 * TW] * Pc[(size_t)g1 * 75];
-                    H1[i] = s;
-                }
-                __syncthreads();
-                const int nitem = kn * p1 * p1 * nb[0] * nb[1];
-                for (int it = tid; it < nitem; it += nth) {
-                    int r = it;
-                    const int kk = r % kn; r /= kn;
-                    const int a1 = r % p1; r /= p1;
-                    const int a2 = r % p1; r /= p1;
-                    const int b1 = r % nb[0]; const int b2 = r / nb[0];
-                    const int ab2 = a2 * nb[1] + b2;
-                    TS h2[3][MEHDG_MAXG];
-#pragma unroll
-                    for (int j = 0; j < 3; ++j) {
-                        const TS* Ty = T2 + (j == 1 ? ng * TW : 0) + ab2;
-                        const TS* h = H1 + (size_t)j * G2 * kn * PB + (b1 * p1 + a1) * kn + kk;
-#pragma unroll
-                        for (int g3 = 0; g3 < MEHDG_MAXG; ++g3) {
-                            TS s = 0;
-                            if (g3 < ng)
-                                for (int g2 = 0; g2 < ng; ++g2) s += Ty[g2 * TW] * h[(size_t)(g2 + ng * g3) * kn * PB];
-                            h2[j][g3] = s;
-                        }
-                    }
-                    const int k = k0 + kk;
-                    const int A12 = (eo[0] + a1) + n * (eo[1] + a2);
-                    const int B1 = d == 0 ? b1 : eo[0] + b1, B2 = d == 1 ? b2 : eo[1] + b2;
-                    for (int a3 = 0; a3 < p1; ++a3)
-                        for (int b3 = 0; b3 < nb[2]; ++b3) {
-                            const int ab3 = a3 * nb[2] + b3;
-                            TS s = 0;
-#pragma unroll
-                            for (int j = 0; j < 3; ++j) {
-                                const TS* Tz = T3 + (j == 2 ? ng * TW : 0) + ab3;
-#pragma unroll
-                                for (int g3 = 0; g3 < MEHDG_MAXG; ++g3)
-                                    if (g3 < ng) s += Tz[g3 * TW] * h2[j][g3];
-                            }
-                            const int A = A12 + n * n * (eo[2] + a3);
-                            const int B = B1 + n * (B2 + n * (d == 2 ? b3 : eo[2] + b3));
-                            atomic_add_t(&S[(size_t)(A * 5 + k) + (size_t)(B * 5 + l) * a.ld], (double)s);
-                        }
-                }
-                __syncthreads();
-            }
+        switch (p1) {
+        case 2: q_contract<2, TS>(T, P, H1, S, a.ld, n, eo, d, kg); break;
+        case 3: q_contract<3, TS>(T, P, H1, S, a.ld, n, eo, d, kg); break;
+        case 4: q_contract<4, TS>(T, P, H1, S, a.ld, n, eo, d, kg); break;
+        default: q_contract<5, TS>(T, P, H1, S, a.ld, n, eo, d, kg); break;   // p = MEHDG_MAXP
+        }
     }
 }
 
