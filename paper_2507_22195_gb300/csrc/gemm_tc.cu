@@ -24,6 +24,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include "lu_internal.cuh"
 #include "prof.cuh"
@@ -230,16 +231,20 @@ tc_stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
             }
         }
     } else {
-        const int ew = warp - 2, q = warp & 3, h = ew >> 2;   // lane quarter q, column group h
-        const bool active = h < NH;
+        // lane quarter q, column group h (and h + 4 when BN = 256: the second
+        // group's C is read after the first group's stores, which keeps the
+        // registers of one group)
+        const int ew = warp - 2, q = warp & 3, h = ew >> 2;
+        constexpr int GPW = BN > 128 ? BN / 128 : 1;      // column groups per warp
         float* S0 = Sall;
         int i = 0;
         for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
             const int K = (int)(t / tiles_e), rem = (int)(t % tiles_e);
             const int tm = rem % tiles_m, tn = rem / tiles_m, b = i & 1;
-            const int row = tm * TM + 32 * q + lane, col0 = tn * BN + h * W;
+            const int row = tm * TM + 32 * q + lane;
+            int hh = h, col0 = tn * BN + hh * W;
             // columns of this warp's slice inside the update (0 for rows past M)
-            const int nc = (active && row < M) ? min(W, N - col0) : 0;
+            int nc = (hh < NH && row < M) ? min(W, N - col0) : 0;
             float* Cp = S0 + (size_t)K * ld * ld + (size_t)(r0 + row) + (size_t)(c0 + col0) * ld;
             float cv[W];
             if (!STORE) {
@@ -250,32 +255,46 @@ tc_stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
             const bool ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[b], (i >> 1) & 1));
             if (!ok) { if (lane == 0 && status) status[K] = MEHDG_ETIMEOUT; break; }
             tc_fence_after();
-            if (active) {
-                uint32_t r[32];
-                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + h * W), r);
-                // a fresh copy of the base pointer, so that the 32 store addresses are
-                // recomputed instead of being kept live from the loads
-                float* p;
-                asm volatile("mov.b64 %0, %1;" : "=l"(p) : "l"(Cp));
+#pragma unroll 1
+            for (int gs = 0; gs < GPW; ++gs) {
+                if (gs > 0) {
+                    hh = h + 4 * gs;
+                    col0 = tn * BN + hh * W;
+                    nc = (hh < NH && row < M) ? min(W, N - col0) : 0;
+                    Cp = S0 + (size_t)K * ld * ld + (size_t)(r0 + row) + (size_t)(c0 + col0) * ld;
+                    if (!STORE) {
+                        const float* p = Cp;
 #pragma unroll
-                for (int j = 0; j < W; ++j) {
-                    if (j < nc) __stcs(p, STORE ? __uint_as_float(r[j]) : cv[j] - __uint_as_float(r[j]));
-                    p += ld;
+                        for (int j = 0; j < W; ++j) { cv[j] = j < nc ? __ldcs(p) : 0.f; p += ld; }
+                    }
                 }
-                if (STORE && bo.p) {
-                    // the same product as the next update's split-BF16 B operand
-                    // (row = its K index, column = its N index): [hi | lo] rows
-                    __nv_bfloat16* qb = reinterpret_cast<__nv_bfloat16*>(bo.p) +
-                                        ((size_t)K * bo.nc + bo.c0 + col0) * (size_t)(2 * bo.kp) + bo.k0 + row;
+                if (hh < NH) {
+                    uint32_t r[32];
+                    tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + hh * W), r);
+                    // a fresh copy of the base pointer, so that the 32 store addresses are
+                    // recomputed instead of being kept live from the loads
+                    float* p;
+                    asm volatile("mov.b64 %0, %1;" : "=l"(p) : "l"(Cp));
 #pragma unroll
                     for (int j = 0; j < W; ++j) {
-                        if (j < nc) {
-                            const float v = __uint_as_float(r[j]);
-                            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-                            qb[0] = hi;
-                            qb[bo.kp] = __float2bfloat16_rn(v - __bfloat162float(hi));
+                        if (j < nc) __stcs(p, STORE ? __uint_as_float(r[j]) : cv[j] - __uint_as_float(r[j]));
+                        p += ld;
+                    }
+                    if (STORE && bo.p) {
+                        // the same product as the next update's split-BF16 B operand
+                        // (row = its K index, column = its N index): [hi | lo] rows
+                        __nv_bfloat16* qb = reinterpret_cast<__nv_bfloat16*>(bo.p) +
+                                            ((size_t)K * bo.nc + bo.c0 + col0) * (size_t)(2 * bo.kp) + bo.k0 + row;
+#pragma unroll
+                        for (int j = 0; j < W; ++j) {
+                            if (j < nc) {
+                                const float v = __uint_as_float(r[j]);
+                                const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+                                qb[0] = hi;
+                                qb[bo.kp] = __float2bfloat16_rn(v - __bfloat162float(hi));
+                            }
+                            qb += 2 * bo.kp;
                         }
-                        qb += 2 * bo.kp;
                     }
                 }
             }
@@ -458,6 +477,11 @@ bool make_map(CUtensorMap* map, const void* base, bool bf16, int Kp, int rows, i
     return r == CUDA_SUCCESS;
 }
 
+bool wide_tiles() {
+    const char* f = std::getenv("MEHDG_TC_BN");
+    return !(f && std::atoi(f) == 128);
+}
+
 int sm_count() {
     static int n = 0;
     if (n == 0) {
@@ -494,6 +518,8 @@ cudaError_t launch_stream(const CUtensorMap& a, const CUtensorMap& b, const LUPl
 template <bool BF16, bool STORE, bool SPLIT>
 cudaError_t launch_stream_bn(int BN, const CUtensorMap& a, const CUtensorMap& b, const LUPlan& P, int r0, int c0,
                              int M, int N, int nchunk, int kpa, int kpb, cudaStream_t st, BqOut bo = BqOut()) {
+    if constexpr (BF16 && !STORE && SPLIT)
+        if (BN == 256) return launch_stream<256, BF16, STORE, SPLIT>(a, b, P, r0, c0, M, N, nchunk, kpa, kpb, st, bo);
     if (BN == 128) return launch_stream<128, BF16, STORE, SPLIT>(a, b, P, r0, c0, M, N, nchunk, kpa, kpb, st, bo);
     if (BN == 64) return launch_stream<64, BF16, STORE, SPLIT>(a, b, P, r0, c0, M, N, nchunk, kpa, kpb, st, bo);
     return launch_stream<32, BF16, STORE, SPLIT>(a, b, P, r0, c0, M, N, nchunk, kpa, kpb, st, bo);
@@ -723,7 +749,11 @@ cudaError_t gemm_tc_update(const LUPlan& P, int r0, int c0, int k0, int M, int N
         }
         if (ev >= 0) prof_end(P.prof, ev, st, 0.0);
     }
-    const int BN = N >= 128 ? 128 : (N >= 64 ? 64 : 32);
+    // split BF16 updates at least 256 wide take 128 x 256 tiles: their MMAs read
+    // a quarter fewer shared-memory bytes per flop (MEHDG_TC_BN=128 keeps
+    // 128 x 128 tiles)
+    int BN = N >= 128 ? 128 : (N >= 64 ? 64 : 32);
+    if (bf16 && split && N >= 256 && wide_tiles()) BN = 256;
     CUtensorMap ma, mb;
     bool ok = make_map(&ma, Ap, bf16, nseg * Kp, M, P.nK, TM);
     int kpb = Kp;
