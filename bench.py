@@ -231,9 +231,11 @@ def once_main(a):
 # same kernels (3^3 elements of the p = 3, m = 3 TGV, 2.8 GB of S): C is
 # streamed once per launch, so the ratios carry over to the full workload.
 # "one": the depth-256 update of the one-panel form; with merged pairs,
-# "merged": the depth-512 update, "narrow": the depth-256 updates of 256 rows
-# or 256 columns.  Other precisions were not captured and report null.
-TRAFFIC_RATIO = {"bf16x3": {"one": 0.987, "merged": 0.988, "narrow": 0.88}}
+# "merged": the depth-512 update, "cols": the depth-256 update of the second
+# panel's 256 columns, "rows": the depth-256 correction of its 256 block rows.
+# A kind not captured since its kernel last changed has no entry, and the
+# traffic is then reported as null.
+TRAFFIC_RATIO = {"bf16x3": {"one": 0.987}}
 # tensor rate of a precision mode relative to BF16 (nominal dense GB300 rates:
 # TF32 1.1, BF16 2.25 PFLOP/s) and the tensor products per method flop
 TENSOR_RATE = {"bf16": 1.0, "bf16x3": 1.0, "tf32": 1.1 / 2.25, "tf32x3": 1.1 / 2.25}
@@ -259,23 +261,24 @@ def outer_updates(ld, pairs):
         cb, jr = ca + 256, ca + 512
         if cb >= ld:
             break
-        ups.append(("narrow", ld - cb, 256, 256))
+        ups.append(("cols", ld - cb, 256, 256))
         nr = ld - jr
         if nr <= 0:
             break
-        ups += [("narrow", 256, nr, 256), ("merged", nr, nr, 512)]
+        ups += [("rows", 256, nr, 256), ("merged", nr, nr, 512)]
     return ups
 
 
-def update_bytes(M, N, Kd):
-    """algorithmic bytes of one update: C read and written (FP32) and the two
-    operand panels (M x Kd and Kd x N, counted in FP32)"""
-    return 8 * M * N + 4 * (M + N) * Kd
+def update_bytes(M, N, Kd, kind=""):
+    """algorithmic bytes of one update: C read and written (FP32; the block-row
+    correction writes its result as split TF32, 8 bytes) and the two operand
+    panels (M x Kd and Kd x N, counted in FP32)"""
+    return (12 if kind == "rows" else 8) * M * N + 4 * (M + N) * Kd
 
 
 def trailing_bytes(ld, nK, pairs=False):
     """algorithmic bytes of all outer trailing updates of one condensation"""
-    return sum(update_bytes(M, N, Kd) for _, M, N, Kd in outer_updates(ld, pairs)) * nK
+    return sum(update_bytes(M, N, Kd, k) for k, M, N, Kd in outer_updates(ld, pairs)) * nK
 
 
 def rel_per_element(a, b):
@@ -670,10 +673,11 @@ def main():
         sec = gem["ms"] / 1e3
         hbm = pk.get("hbm_gbs", 6800.0)
         ratios = TRAFFIC_RATIO.get(a.prec) if a.workload == "tgv_inviscid" else None
-        tr = (sum(ratios[k] * update_bytes(M, N, Kd) for k, M, N, Kd in ups) * mesh.nK / len(ups)
-              if ratios and ups else None)
-        kernel = ("lu_trailing_update (tcgen05; per pair of outer panels one depth-512 update and two "
-                  "depth-256 updates of 256 rows or columns)" if pairs else "lu_trailing_update (tcgen05, depth 256)")
+        tr = (sum(ratios[k] * update_bytes(M, N, Kd, k) for k, M, N, Kd in ups) * mesh.nK / len(ups)
+              if ratios and ups and all(k in ratios for k, _, _, _ in ups) else None)
+        kernel = ("lu_trailing_update (tcgen05, 128 x 256 tiles; per pair of outer panels one depth-512 update "
+                  "and two depth-256 updates of 256 rows or columns)" if pairs
+                  else "lu_trailing_update (tcgen05, depth 256)")
         roof_h = {"bound": "hbm", "achieved": byt / sec / 1e9, "peak": hbm, "unit": "GB/s",
                   "frac": byt / sec / 1e9 / hbm, "traffic": tr,
                   "traffic_unit": "bytes per launch (27-element ncu captures, scaled)" if tr else None,

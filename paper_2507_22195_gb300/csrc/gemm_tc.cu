@@ -95,6 +95,13 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// round to TF32 (nearest, ties away), kept in FP32 storage
+__device__ __forceinline__ float tf32_rn(float x) {
+    uint32_t y;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
+    return __uint_as_float(y);
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -268,7 +275,24 @@ tc_stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
                         for (int j = 0; j < W; ++j) { cv[j] = j < nc ? __ldcs(p) : 0.f; p += ld; }
                     }
                 }
-                if (hh < NH) {
+                if (hh < NH && !STORE && bo.p) {
+                    // an update whose result is the next TRSM's B operand: C - D as split
+                    // TF32 [hi | lo] rows (row = its K index), S left as it is
+                    uint32_t r[32];
+                    tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + hh * W), r);
+                    float* qf = reinterpret_cast<float*>(bo.p) +
+                                ((size_t)K * bo.nc + bo.c0 + col0) * (size_t)(2 * bo.kp) + bo.k0 + row;
+#pragma unroll
+                    for (int j = 0; j < W; ++j) {
+                        if (j < nc) {
+                            const float v = cv[j] - __uint_as_float(r[j]);
+                            const float hi = tf32_rn(v);
+                            qf[0] = hi;
+                            qf[bo.kp] = tf32_rn(v - hi);
+                        }
+                        qf += 2 * bo.kp;
+                    }
+                } else if (hh < NH) {
                     uint32_t r[32];
                     tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + hh * W), r);
                     // a fresh copy of the base pointer, so that the 32 store addresses are
@@ -318,11 +342,6 @@ tc_stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
 // a_hi b_hi + a_hi b_lo + a_lo b_hi (hi = round(x), lo = round(x - hi)): both
 // panels hold the two K-segments [hi | lo] and the MMA issuer takes the three
 // products from one ring slot.
-__device__ __forceinline__ float tf32_rn(float x) {
-    uint32_t y;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
-    return __uint_as_float(y);
-}
 template <bool BF16>
 __device__ __forceinline__ float op_round(float x) {
     if constexpr (BF16) return __bfloat162float(__float2bfloat16_rn(x));
@@ -608,17 +627,16 @@ trtri256_kernel(const float* __restrict__ Sall, int64_t ld, int c0, int nseg, vo
 // the net permutation (the 256 block rows and the rows below that take
 // part), writes the rows below that change, and writes the new block rows
 // as the split-TF32 panel Bp[K][n][hi 256 | lo 256].  The block rows of S are
-// not written back: the TRSM product overwrites them.  Without a permutation
-// (perm null) the block rows c0.. are packed as they are.
+// not written back: the TRSM product overwrites them.
 __global__ void __launch_bounds__(256)
-laswp_pack_kernel(float* __restrict__ Sall, int64_t ld, const int32_t* __restrict__ perm, int c0, int j0, int N,
+laswp_pack_kernel(float* __restrict__ Sall, int64_t ld, const int32_t* __restrict__ perm, int j0, int N,
                   float* __restrict__ Bp) {
     const int K = blockIdx.y;
     float* S = Sall + (size_t)K * ld * ld;
-    const int32_t* pl = perm ? perm + (size_t)K * LU_PW : nullptr;
-    const int nr = pl ? pl[0] : LU_NB;
-    const int32_t* rows = pl ? pl + 1 : nullptr;
-    const int32_t* cont = pl ? rows + 2 * LU_NB : nullptr;
+    const int32_t* pl = perm + (size_t)K * LU_PW;
+    const int nr = pl[0];
+    const int32_t* rows = pl + 1;
+    const int32_t* cont = rows + 2 * LU_NB;
     __shared__ float buf[8][2 * LU_NB];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = blockIdx.x * 8 + warp;
@@ -631,7 +649,7 @@ laswp_pack_kernel(float* __restrict__ Sall, int64_t ld, const int32_t* __restric
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int i = i0 + 32 * u;
-            v[u] = i < nr ? Sc[rows ? rows[i] : c0 + i] : 0.f;
+            v[u] = i < nr ? Sc[rows[i]] : 0.f;
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) { const int i = i0 + 32 * u; if (i < nr) b[i] = v[u]; }
@@ -639,7 +657,7 @@ laswp_pack_kernel(float* __restrict__ Sall, int64_t ld, const int32_t* __restric
     __syncwarp();
     float* out = Bp + ((size_t)K * N + n) * (size_t)(2 * LU_NB);
     for (int i = lane; i < nr; i += 32) {
-        const int ci = cont ? cont[i] : i;
+        const int ci = cont[i];
         const float v = b[ci];
         if (i < LU_NB) {
             const float hi = tf32_rn(v);
@@ -680,6 +698,7 @@ unsigned char* panel_base(const LUPlan& P) {
 }  // namespace
 
 void* gemm_tc_bq_panel(const LUPlan& P) { return panel_base(P) + 2 * panel_bytes(P.nK, P.ld); }
+void* gemm_tc_bp_panel(const LUPlan& P) { return panel_base(P) + panel_bytes(P.nK, P.ld); }
 
 // The outer step right of panel c0: row exchanges of the columns [c0+256, ld)
 // by the panel's net permutation, fused with the packing of B, then the TRSM
@@ -696,9 +715,18 @@ cudaError_t gemm_tc_swap_trsm256(const LUPlan& P, const int32_t* perm, int c0, c
     void* Ap = w;
     float* Bp = reinterpret_cast<float*>(w + pan);
     dim3 gb((unsigned)((N + 7) / 8), (unsigned)P.nK);
-    laswp_pack_kernel<<<gb, 256, 0, st>>>((float*)P.S, P.ld, perm, c0, j0, N, Bp);
+    laswp_pack_kernel<<<gb, 256, 0, st>>>((float*)P.S, P.ld, perm, j0, N, Bp);
     MEHDG_COUNT(1);
     return trsm256_product(P, c0, j0, N, Ap, Bp, bq, st);
+}
+
+// The TRSM product alone, with its B operand (rows [c0, c0+256) of the
+// columns right of them) already in the split-TF32 panel
+cudaError_t gemm_tc_trsm256(const LUPlan& P, int c0, cudaStream_t st, const BqOut* bq) {
+    const int j0 = c0 + LU_NB, N = (int)P.ld - j0;
+    if (N <= 0) return cudaSuccess;
+    if (!encoder()) return cudaErrorNotSupported;
+    return trsm256_product(P, c0, j0, N, panel_base(P), gemm_tc_bp_panel(P), bq, st);
 }
 
 size_t gemm_tc_work_bytes(int64_t nK, int64_t ld, int prec) {
@@ -710,11 +738,12 @@ size_t gemm_tc_work_bytes(int64_t nK, int64_t ld, int prec) {
 }
 
 cudaError_t gemm_tc_update(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st,
-                           int ph_pack, int ph_gemm, double flops, const PackedB* b, const AGather* g) {
+                           int ph_pack, int ph_gemm, double flops, const PackedB* b, const AGather* g,
+                           const BqOut* out) {
     if (M <= 0 || N <= 0) return cudaSuccess;
     const bool bf16 = P.prec == MEHDG_MIXED_BF16 || P.prec == MEHDG_MIXED_BF16X3;
     const bool split = P.prec == MEHDG_MIXED_TF32X3 || P.prec == MEHDG_MIXED_BF16X3;
-    if ((b || g) && (!(bf16 && split) || M < TM)) return cudaErrorInvalidValue;   // split BF16, whole row tiles
+    if ((b || g || out) && (!(bf16 && split) || M < TM)) return cudaErrorInvalidValue;   // split BF16, whole row tiles
     if (M < TM) return gemm_simt_update_f32(P, r0, c0, k0, M, N, Kd, st);   // a few tiny inner updates
     if (!encoder()) return cudaErrorNotSupported;
     const int nseg = split ? 2 : 1;
@@ -769,7 +798,8 @@ cudaError_t gemm_tc_update(const LUPlan& P, int r0, int c0, int k0, int M, int N
     if (!ok) return cudaErrorInvalidValue;
     const int ev = ph_gemm >= 0 ? prof_begin(P.prof, ph_gemm, st) : -1;
     cudaError_t e;
-    if (bf16) e = split ? launch_stream_bn<true, false, true>(BN, ma, mb, P, r0, c0, M, N, nchunk, Kp, kpb, st)
+    if (bf16) e = split ? launch_stream_bn<true, false, true>(BN, ma, mb, P, r0, c0, M, N, nchunk, Kp, kpb, st,
+                                                              out ? *out : BqOut())
                         : launch_stream_bn<true, false, false>(BN, ma, mb, P, r0, c0, M, N, nchunk, Kp, kpb, st);
     else e = split ? launch_stream_bn<false, false, true>(BN, ma, mb, P, r0, c0, M, N, nchunk, Kp, kpb, st)
                    : launch_stream_bn<false, false, false>(BN, ma, mb, P, r0, c0, M, N, nchunk, Kp, kpb, st);

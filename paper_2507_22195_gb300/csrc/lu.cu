@@ -831,15 +831,15 @@ cudaError_t launch_update32(const LUPlan& P, int r0, int c0, int k0, int M, cuda
 template <class TS>
 cudaError_t trailing_update(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st,
                             int ph_pack = -1, int ph_gemm = -1, double flops = 0.0, const PackedB* b = nullptr,
-                            const AGather* g = nullptr) {
+                            const AGather* g = nullptr, const BqOut* out = nullptr) {
     if constexpr (std::is_same<TS, double>::value) {
         const int ev = ph_gemm >= 0 ? prof_begin(P.prof, ph_gemm, st) : -1;
         cudaError_t e = launch_gemm_simt<double>(P, r0, c0, k0, M, N, Kd, st);
         if (ev >= 0) prof_end(P.prof, ev, st, flops);
         return e;
     } else {
-        if (N == 32 && Kd == 32 && !b && !g) return launch_update32(P, r0, c0, k0, M, st);
-        return gemm_tc_update(P, r0, c0, k0, M, N, Kd, st, ph_pack, ph_gemm, flops, b, g);
+        if (N == 32 && Kd == 32 && !b && !g && !out) return launch_update32(P, r0, c0, k0, M, st);
+        return gemm_tc_update(P, r0, c0, k0, M, N, Kd, st, ph_pack, ph_gemm, flops, b, g, out);
     }
 }
 
@@ -909,7 +909,8 @@ cudaError_t factor_t(const LUPlan& P, cudaStream_t st) {
 //   3. on R: exchange rows by P_b (block rows written back); the block rows
 //      of b then hold rows of A not yet updated by a: subtract their part
 //      L_a(src) U_a, with the multipliers L_a of the rows they came from (a's
-//      columns are not exchanged by P_b);
+//      columns are not exchanged by P_b), the result going straight to the
+//      TRSM's split-TF32 B operand;
 //   4. U_b = L_bb^-1 (those rows) by the TRSM product (K entries 256..511 of
 //      the same B operand);
 //   5. one update of R's rows below b with depth 512: [L_a | L_b] [U_a; U_b],
@@ -946,14 +947,16 @@ cudaError_t factor_pairs(const LUPlan& P, cudaStream_t st) {
         prof_end(P.prof, ev, st, 0.0);
         const PackedB b{bq, n1, LU_NB, 2 * LU_NB};
         {
-            const AGather g{pb, LU_NB, 0, LU_NB};     // the block rows of b
+            // the block rows of b, corrected and written as the TRSM's split-TF32 B operand
+            const AGather g{pb, LU_NB, 0, LU_NB};
+            const BqOut bp{gemm_tc_bp_panel(P), nr, 0, 0, LU_NB};
             if ((e = trailing_update<float>(P, cb, jr, ca, LU_NB, nr, LU_NB, st, PH_PACK_OUTER, PH_GEMM_OUTER,
-                                            upd_flops(P, LU_NB, nr, LU_NB), &b, &g)) != cudaSuccess)
+                                            upd_flops(P, LU_NB, nr, LU_NB), &b, &g, &bp)) != cudaSuccess)
                 return e;
         }
         ev = prof_begin(P.prof, PH_LU_PANELS, st);
         const BqOut bb{bq, n1, LU_NB, LU_NB, 2 * LU_NB};
-        if ((e = gemm_tc_swap_trsm256(P, nullptr, cb, st, &bb)) != cudaSuccess) return e;
+        if ((e = gemm_tc_trsm256(P, cb, st, &bb)) != cudaSuccess) return e;
         prof_end(P.prof, ev, st, 0.0);
         {
             const AGather g{pb, LU_NB, LU_NB, 2 * LU_NB};   // the rows below b that P_b moved

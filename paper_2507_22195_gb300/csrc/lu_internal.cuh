@@ -31,7 +31,9 @@ struct AGather {
 };
 // The TRSM product's copy of U12 as the next update's B operand (split BF16):
 // per element nc rows of [hi (kp) | lo (kp)]; product column n goes to row
-// c0 + n, its K index k (the row inside the 256 block) to entry k0 + k.
+// c0 + n, its K index k (the row inside the 256 block) to entry k0 + k.  Given
+// to an update (split BF16), the same layout receives C - D in split TF32 (a
+// float panel: the next TRSM product's B operand) and S is not written.
 struct BqOut {
     void* p = nullptr;
     int nc = 0, c0 = 0, k0 = 0, kp = 0;
@@ -43,15 +45,21 @@ struct BqOut {
 // recorded with it) and the operand packing under ph_pack.
 // b: the B panel already packed (split BF16) by a TRSM product, or null;
 // g: A rows gathered through a net permutation, or null
+// out: the result as the next TRSM's split-TF32 B operand instead of into S, or null
 cudaError_t gemm_tc_update(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st,
                            int ph_pack = -1, int ph_gemm = -1, double flops = 0.0, const PackedB* b = nullptr,
-                           const AGather* g = nullptr);
+                           const AGather* g = nullptr, const BqOut* out = nullptr);
 size_t gemm_tc_work_bytes(int64_t nK, int64_t ld, int prec);
 // The next update's B panel of the split-BF16 mode (written by the TRSM products)
 void* gemm_tc_bq_panel(const LUPlan& P);
+// The TRSM's split-TF32 B panel ([nK][columns][hi 256 | lo 256] floats)
+void* gemm_tc_bp_panel(const LUPlan& P);
 // Row exchanges of the columns right of outer panel c0 by its net permutation
-// (perm: [nK][LU_PW]; null: the rows are already in place) and the TRSM of
-// their rows [c0, c0+256), fused.  bq: where the product also writes U12 as
-// split-BF16 B operand (null: not written; only the split-BF16 mode has it).
+// (perm: [nK][LU_PW]) and the TRSM of their rows [c0, c0+256), fused.  bq:
+// where the product also writes U12 as split-BF16 B operand (null: not
+// written; only the split-BF16 mode has it).
 cudaError_t gemm_tc_swap_trsm256(const LUPlan& P, const int32_t* perm, int c0, cudaStream_t st, const BqOut* bq);
+// The TRSM of rows [c0, c0+256) of the columns right of them, with its B
+// operand already in the split-TF32 panel (written by an update with out set)
+cudaError_t gemm_tc_trsm256(const LUPlan& P, int c0, cudaStream_t st, const BqOut* bq);
 cudaError_t gemm_simt_update_f32(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st);
