@@ -388,13 +388,14 @@ __device__ __forceinline__ void op_put8(void* out, size_t row_base, int Kp, int 
     if (nseg == 2) op_store8<BF16>(out, row_base + Kp + k, lo);
 }
 
-// A panel: Ap[K][m][seg*Kp + k] = L[r0+m][k0+k] (k < Kd, else 0).  A 64 (m) x 32 (k)
-// tile is transposed through shared memory; each thread then writes 8
-// consecutive k of one row per segment.  Kp is a multiple of 32.
+// A panel: Ap[K][m][seg*Kp + kout + k] = L[r0+m][k0+k] (k < Kd, else 0), elements
+// erows rows apart.  A 64 (m) x 32 (k) tile is transposed through shared
+// memory; each thread then writes 8 consecutive k of one row per segment.
+// Kp and kout are multiples of 32; grid.y covers the k blocks written.
 template <bool BF16>
 __global__ void __launch_bounds__(256)
 pack_A_kernel(const float* __restrict__ Sall, int64_t ld, int r0, int k0, int M, int Kd, int Kp,
-              int nseg, void* __restrict__ out) {
+              int nseg, int erows, int kout, void* __restrict__ out) {
     const int K = blockIdx.z;
     const float* S = Sall + (size_t)K * ld * ld;
     __shared__ float t[32][65];
@@ -415,7 +416,7 @@ pack_A_kernel(const float* __restrict__ Sall, int64_t ld, int r0, int k0, int M,
     float x[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) x[j] = t[kq + j][ml];
-    op_put8<BF16>(out, ((size_t)K * M + m) * (size_t)(nseg * Kp), Kp, kk0 + kq, nseg, x);
+    op_put8<BF16>(out, ((size_t)K * erows + m) * (size_t)(nseg * Kp), Kp, kout + kk0 + kq, nseg, x);
 }
 // B panel: Bp[K][n][seg*Kp + k] = U[k0+k][c0+n] (contiguous in k on both sides);
 // one warp per column n, 8 consecutive k per lane.  k0 is a multiple of 4 and
@@ -730,20 +731,47 @@ cudaError_t gemm_tc_trsm256(const LUPlan& P, int c0, cudaStream_t st, const BqOu
 }
 
 size_t gemm_tc_work_bytes(int64_t nK, int64_t ld, int prec) {
-    (void)prec;
-    // three panels of ld rows x 2 KB per element: split FP32/TF32 operands of
-    // depth 256 or split BF16 of depth 512 (A, B, and the next update's B
-    // written by the TRSM products)
-    return 3 * panel_bytes(nK, ld);
+    // panels of ld rows x 2 KB per element: split FP32/TF32 operands of depth
+    // 256 or split BF16 of depth 512 (A, B, and the next update's B written by
+    // the TRSM products); split BF16 adds the multipliers of a pair of outer
+    // panels, kept from one update to the next
+    return (prec == MEHDG_MIXED_BF16X3 ? 4 : 3) * panel_bytes(nK, ld);
+}
+
+void* gemm_tc_a2_panel(const LUPlan& P) { return panel_base(P) + 3 * panel_bytes(P.nK, P.ld); }
+
+cudaError_t gemm_tc_pack_a2(const LUPlan& P, int erows, int row0, int kp, int kout, int r0, int k0, int M, int Kd,
+                            cudaStream_t st) {
+    if (M <= 0) return cudaSuccess;
+    if (P.prec != MEHDG_MIXED_BF16X3 || Kd % 32 || kout % 32 || kout + Kd > kp || row0 < 0 || row0 + M > erows ||
+        (size_t)erows * 4 * kp > (size_t)P.ld * 2 * LU_NB * 4)
+        return cudaErrorInvalidValue;
+    __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(gemm_tc_a2_panel(P)) + (size_t)row0 * 2 * kp;
+    dim3 g3((unsigned)((M + 63) / 64), (unsigned)(Kd / 32), (unsigned)P.nK);
+    pack_A_kernel<true><<<g3, 256, 0, st>>>((const float*)P.S, P.ld, r0, k0, M, Kd, kp, 2, erows, kout, out);
+    MEHDG_COUNT(1);
+    return cudaGetLastError();
+}
+
+cudaError_t gemm_tc_gather_a2(const LUPlan& P, int erows, int kp, int r0, int k0, const AGather& g, cudaStream_t st) {
+    if (g.i1 <= g.i0) return cudaSuccess;
+    if (P.prec != MEHDG_MIXED_BF16X3 || g.kn > kp || (size_t)erows * 4 * kp > (size_t)P.ld * 2 * LU_NB * 4)
+        return cudaErrorInvalidValue;
+    dim3 gg((unsigned)((g.i1 - g.i0 + 7) / 8), (unsigned)P.nK);
+    pack_A_gather_kernel<<<gg, 256, 0, st>>>((const float*)P.S, P.ld, g.perm, g.i0, g.i1, r0, erows, k0, g.kn, kp,
+                                             gemm_tc_a2_panel(P));
+    MEHDG_COUNT(1);
+    return cudaGetLastError();
 }
 
 cudaError_t gemm_tc_update(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st,
                            int ph_pack, int ph_gemm, double flops, const PackedB* b, const AGather* g,
-                           const BqOut* out) {
+                           const BqOut* out, const PackedA* a) {
     if (M <= 0 || N <= 0) return cudaSuccess;
     const bool bf16 = P.prec == MEHDG_MIXED_BF16 || P.prec == MEHDG_MIXED_BF16X3;
     const bool split = P.prec == MEHDG_MIXED_TF32X3 || P.prec == MEHDG_MIXED_BF16X3;
-    if ((b || g || out) && (!(bf16 && split) || M < TM)) return cudaErrorInvalidValue;   // split BF16, whole row tiles
+    // split BF16 only, whole row tiles; a packed A takes no gathers here
+    if ((b || g || out || a) && (!(bf16 && split) || M < TM || (a && g))) return cudaErrorInvalidValue;
     if (M < TM) return gemm_simt_update_f32(P, r0, c0, k0, M, N, Kd, st);   // a few tiny inner updates
     if (!encoder()) return cudaErrorNotSupported;
     const int nseg = split ? 2 : 1;
@@ -761,10 +789,12 @@ cudaError_t gemm_tc_update(const LUPlan& P, int r0, int c0, int k0, int M, int N
     {
         const int ev = ph_pack >= 0 ? prof_begin(P.prof, ph_pack, st) : -1;
         dim3 g3((unsigned)((M + 63) / 64), (unsigned)(Kp / 32), (unsigned)P.nK);
-        if (bf16) pack_A_kernel<true><<<g3, 256, 0, st>>>((const float*)P.S, P.ld, r0, k0, M, Kd, Kp, nseg, Ap);
-        else pack_A_kernel<false><<<g3, 256, 0, st>>>((const float*)P.S, P.ld, r0, k0, M, Kd, Kp, nseg, Ap);
-        MEHDG_COUNT(1);
-        if (g && g->i1 > g->i0) {
+        if (!a) {
+            if (bf16) pack_A_kernel<true><<<g3, 256, 0, st>>>((const float*)P.S, P.ld, r0, k0, M, Kd, Kp, nseg, M, 0, Ap);
+            else pack_A_kernel<false><<<g3, 256, 0, st>>>((const float*)P.S, P.ld, r0, k0, M, Kd, Kp, nseg, M, 0, Ap);
+            MEHDG_COUNT(1);
+        }
+        if (!a && g && g->i1 > g->i0) {
             dim3 gg((unsigned)((g->i1 - g->i0 + 7) / 8), (unsigned)P.nK);
             pack_A_gather_kernel<<<gg, 256, 0, st>>>((const float*)P.S, P.ld, g->perm, g->i0, g->i1, r0, M, k0,
                                                      std::min(g->kn, Kd), Kp, Ap);
@@ -784,8 +814,17 @@ cudaError_t gemm_tc_update(const LUPlan& P, int r0, int c0, int k0, int M, int N
     int BN = N >= 128 ? 128 : (N >= 64 ? 64 : 32);
     if (bf16 && split && N >= 256 && wide_tiles()) BN = 256;
     CUtensorMap ma, mb;
-    bool ok = make_map(&ma, Ap, bf16, nseg * Kp, M, P.nK, TM);
-    int kpb = Kp;
+    bool ok;
+    int kpa = Kp, kpb = Kp;
+    if (a) {
+        // rows row0.. of the packed A panel
+        if (a->kp < Kp || a->row0 < 0 || a->row0 + M > a->erows) return cudaErrorInvalidValue;
+        const void* base = reinterpret_cast<const __nv_bfloat16*>(a->p) + (size_t)a->row0 * 2 * a->kp;
+        ok = make_map(&ma, base, true, 2 * a->kp, M, P.nK, TM, a->erows);
+        kpa = a->kp;
+    } else {
+        ok = make_map(&ma, Ap, bf16, nseg * Kp, M, P.nK, TM);
+    }
     if (b) {
         // rows c0.. of the packed panel; a K chunk of this update never reaches the lo segment
         if (b->kp < Kp || b->c0 < 0 || b->c0 + N > b->nc) return cudaErrorInvalidValue;
@@ -798,7 +837,7 @@ cudaError_t gemm_tc_update(const LUPlan& P, int r0, int c0, int k0, int M, int N
     if (!ok) return cudaErrorInvalidValue;
     const int ev = ph_gemm >= 0 ? prof_begin(P.prof, ph_gemm, st) : -1;
     cudaError_t e;
-    if (bf16) e = split ? launch_stream_bn<true, false, true>(BN, ma, mb, P, r0, c0, M, N, nchunk, Kp, kpb, st,
+    if (bf16) e = split ? launch_stream_bn<true, false, true>(BN, ma, mb, P, r0, c0, M, N, nchunk, kpa, kpb, st,
                                                               out ? *out : BqOut())
                         : launch_stream_bn<true, false, false>(BN, ma, mb, P, r0, c0, M, N, nchunk, Kp, kpb, st);
     else e = split ? launch_stream_bn<false, false, true>(BN, ma, mb, P, r0, c0, M, N, nchunk, Kp, kpb, st)

@@ -831,15 +831,15 @@ cudaError_t launch_update32(const LUPlan& P, int r0, int c0, int k0, int M, cuda
 template <class TS>
 cudaError_t trailing_update(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st,
                             int ph_pack = -1, int ph_gemm = -1, double flops = 0.0, const PackedB* b = nullptr,
-                            const AGather* g = nullptr, const BqOut* out = nullptr) {
+                            const AGather* g = nullptr, const BqOut* out = nullptr, const PackedA* a = nullptr) {
     if constexpr (std::is_same<TS, double>::value) {
         const int ev = ph_gemm >= 0 ? prof_begin(P.prof, ph_gemm, st) : -1;
         cudaError_t e = launch_gemm_simt<double>(P, r0, c0, k0, M, N, Kd, st);
         if (ev >= 0) prof_end(P.prof, ev, st, flops);
         return e;
     } else {
-        if (N == 32 && Kd == 32 && !b && !g && !out) return launch_update32(P, r0, c0, k0, M, st);
-        return gemm_tc_update(P, r0, c0, k0, M, N, Kd, st, ph_pack, ph_gemm, flops, b, g, out);
+        if (N == 32 && Kd == 32 && !b && !g && !out && !a) return launch_update32(P, r0, c0, k0, M, st);
+        return gemm_tc_update(P, r0, c0, k0, M, N, Kd, st, ph_pack, ph_gemm, flops, b, g, out, a);
     }
 }
 
@@ -915,6 +915,8 @@ cudaError_t factor_t(const LUPlan& P, cudaStream_t st) {
 //      the same B operand);
 //   5. one update of R's rows below b with depth 512: [L_a | L_b] [U_a; U_b],
 //      L_a gathered through P_b for the rows that P_b moved.
+// L_a of the rows below a is packed once, into a fourth operand panel that
+// the three updates of the pair share (b's multipliers join it for step 5).
 // The factors and the permutations kept for the solves are those of the
 // one-panel form (rows left of a panel are never exchanged again); only the
 // order of the roundings in the trailing matrix differs, and its C is
@@ -933,10 +935,17 @@ cudaError_t factor_pairs(const LUPlan& P, cudaStream_t st) {
         const BqOut ba{bq, n1, 0, 0, 2 * LU_NB};
         if ((e = gemm_tc_swap_trsm256(P, pa, ca, st, &ba)) != cudaSuccess) return e;
         prof_end(P.prof, ev, st, 0.0);
+        // a's multipliers of every row below a, packed once into the pair's A
+        // panel (rows cb.., segment 512) for the three updates of the pair
+        constexpr int KP2 = 2 * LU_NB;
         {
-            const PackedB b{bq, n1, 0, 2 * LU_NB};
+            const int evp = prof_begin(P.prof, PH_PACK_OUTER, st);
+            if ((e = gemm_tc_pack_a2(P, n1, 0, KP2, 0, cb, ca, n1, LU_NB, st)) != cudaSuccess) return e;
+            prof_end(P.prof, evp, st, 0.0);
+            const PackedB b{bq, n1, 0, KP2};
+            const PackedA a2{gemm_tc_a2_panel(P), n1, 0, KP2};
             if ((e = trailing_update<float>(P, cb, cb, ca, n1, LU_NB, LU_NB, st, PH_PACK_OUTER, PH_GEMM_OUTER,
-                                            upd_flops(P, n1, LU_NB, LU_NB), &b)) != cudaSuccess)
+                                            upd_flops(P, n1, LU_NB, LU_NB), &b, nullptr, nullptr, &a2)) != cudaSuccess)
                 return e;
         }
         ev = prof_begin(P.prof, PH_LU_PANELS, st);
@@ -945,13 +954,18 @@ cudaError_t factor_pairs(const LUPlan& P, cudaStream_t st) {
         if (nr <= 0) { prof_end(P.prof, ev, st, 0.0); break; }
         if ((e = launch_laswp_perm<float>(P, pb, LU_NB, jr, ld, st)) != cudaSuccess) return e;
         prof_end(P.prof, ev, st, 0.0);
-        const PackedB b{bq, n1, LU_NB, 2 * LU_NB};
+        const PackedB b{bq, n1, LU_NB, KP2};
         {
-            // the block rows of b, corrected and written as the TRSM's split-TF32 B operand
-            const AGather g{pb, LU_NB, 0, LU_NB};
+            // the block rows of b (a's multipliers of the rows they came from),
+            // corrected and written as the TRSM's split-TF32 B operand
+            const int evp = prof_begin(P.prof, PH_PACK_OUTER, st);
+            if ((e = gemm_tc_gather_a2(P, n1, KP2, cb, ca, AGather{pb, LU_NB, 0, LU_NB}, st)) != cudaSuccess)
+                return e;
+            prof_end(P.prof, evp, st, 0.0);
+            const PackedA a2{gemm_tc_a2_panel(P), n1, 0, KP2};
             const BqOut bp{gemm_tc_bp_panel(P), nr, 0, 0, LU_NB};
             if ((e = trailing_update<float>(P, cb, jr, ca, LU_NB, nr, LU_NB, st, PH_PACK_OUTER, PH_GEMM_OUTER,
-                                            upd_flops(P, LU_NB, nr, LU_NB), &b, &g, &bp)) != cudaSuccess)
+                                            upd_flops(P, LU_NB, nr, LU_NB), &b, nullptr, &bp, &a2)) != cudaSuccess)
                 return e;
         }
         ev = prof_begin(P.prof, PH_LU_PANELS, st);
@@ -959,9 +973,16 @@ cudaError_t factor_pairs(const LUPlan& P, cudaStream_t st) {
         if ((e = gemm_tc_trsm256(P, cb, st, &bb)) != cudaSuccess) return e;
         prof_end(P.prof, ev, st, 0.0);
         {
-            const AGather g{pb, LU_NB, LU_NB, 2 * LU_NB};   // the rows below b that P_b moved
+            // rows below b: b's multipliers beside a's (K entries 256..511), and a's
+            // multipliers of the rows that P_b moved taken from their source rows
+            const int evp = prof_begin(P.prof, PH_PACK_OUTER, st);
+            if ((e = gemm_tc_pack_a2(P, n1, LU_NB, KP2, LU_NB, jr, cb, nr, LU_NB, st)) != cudaSuccess) return e;
+            if ((e = gemm_tc_gather_a2(P, n1, KP2, cb, ca, AGather{pb, LU_NB, LU_NB, 2 * LU_NB}, st)) != cudaSuccess)
+                return e;
+            prof_end(P.prof, evp, st, 0.0);
+            const PackedA a2{gemm_tc_a2_panel(P), n1, LU_NB, KP2};
             if ((e = trailing_update<float>(P, jr, jr, ca, nr, nr, 2 * LU_NB, st, PH_PACK_OUTER, PH_GEMM_OUTER,
-                                            upd_flops(P, nr, nr, 2 * LU_NB), &b, &g)) != cudaSuccess)
+                                            upd_flops(P, nr, nr, 2 * LU_NB), &b, nullptr, nullptr, &a2)) != cudaSuccess)
                 return e;
         }
     }

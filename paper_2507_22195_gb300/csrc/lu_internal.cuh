@@ -29,6 +29,13 @@ struct AGather {
     const int32_t* perm = nullptr;   // [nK][LU_PW]
     int kn = 0, i0 = 0, i1 = 0;
 };
+// An A operand already packed in split BF16 (the fourth operand panel): per
+// element erows rows of [hi (kp) | lo (kp)]; this update's first row is row
+// row0 of it.
+struct PackedA {
+    const void* p = nullptr;
+    int erows = 0, row0 = 0, kp = 0;
+};
 // The TRSM product's copy of U12 as the next update's B operand (split BF16):
 // per element nc rows of [hi (kp) | lo (kp)]; product column n goes to row
 // c0 + n, its K index k (the row inside the 256 block) to entry k0 + k.  Given
@@ -45,10 +52,22 @@ struct BqOut {
 // recorded with it) and the operand packing under ph_pack.
 // b: the B panel already packed (split BF16) by a TRSM product, or null;
 // g: A rows gathered through a net permutation, or null
-// out: the result as the next TRSM's split-TF32 B operand instead of into S, or null
+// out: the result as the next TRSM's split-TF32 B operand instead of into S, or null;
+// a: the A operand already packed (then g must be null), or null
 cudaError_t gemm_tc_update(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st,
                            int ph_pack = -1, int ph_gemm = -1, double flops = 0.0, const PackedB* b = nullptr,
-                           const AGather* g = nullptr, const BqOut* out = nullptr);
+                           const AGather* g = nullptr, const BqOut* out = nullptr, const PackedA* a = nullptr);
+// The fourth operand panel (split BF16 only): the multipliers of a pair of
+// outer panels, packed once for the three updates of the pair
+void* gemm_tc_a2_panel(const LUPlan& P);
+// Rows [r0, r0+M) of S's columns [k0, k0+Kd) (Kd a multiple of 32) into it: per
+// element erows rows of [hi (kp) | lo (kp)], S row r0 + m at row row0 + m, K
+// entries kout.. kout+Kd
+cudaError_t gemm_tc_pack_a2(const LUPlan& P, int erows, int row0, int kp, int kout, int r0, int k0, int M, int Kd,
+                            cudaStream_t st);
+// Its rows re-packed through a net permutation (row 0 = S row r0; K entries
+// 0..g.kn from S's columns k0..)
+cudaError_t gemm_tc_gather_a2(const LUPlan& P, int erows, int kp, int r0, int k0, const AGather& g, cudaStream_t st);
 size_t gemm_tc_work_bytes(int64_t nK, int64_t ld, int prec);
 // The next update's B panel of the split-BF16 mode (written by the TRSM products)
 void* gemm_tc_bq_panel(const LUPlan& P);
