@@ -306,7 +306,7 @@ int mehdg_batch_layout(mehdg_ctx* ctx, int64_t* voff, int64_t* toff);
 
 /* Autotuner of a batch context (after set_state): for every (p, m) group,
  * times one condensation of its first min(trial_max, wave) elements for each
- * candidate LU launch shape (leaf-panel CTAs per SM 1 or 2, then CTAs per
+ * candidate LU launch shape (leaf-panel CTAs per SM 1, 2 or 4, then CTAs per
  * element in the solves 1, 2, 4, 8 with the better leaf; one untimed
  * warm-up each), keeps the fastest, and records every trial (read with
  * mehdg_batch_report).  Later condensations use the choices.  Invalidates a

@@ -544,7 +544,7 @@ int batch_autotune(mehdg_ctx* c, int64_t trial_max, cudaStream_t st) {
         // greedy: leaf CTAs per SM first (solves automatic), then the solve's CTAs per element
         float best = 1e30f;
         int bl = 0, bs = 0;
-        for (int leaf : {1, 2}) {
+        for (int leaf : {1, 2, 4}) {
             set_choice(g, leaf, 0);
             float ms = 0.f;
             BRC(time_trial(c, g, n, st, &ms));

@@ -39,10 +39,11 @@ __device__ __forceinline__ double tabs(double x) { return fabs(x); }
 // pivot column costs two barriers: one to publish the per-warp maxima, one
 // after every thread has read the old pivot row and row cc.  The search for
 // the next pivot runs on the values the update has just produced.
-// one FP32 CTA per SM (fewer elements than SMs): 1024 threads; otherwise 512
-// (FP64 keeps 512 so that its registers do not spill)
+// one FP32 CTA per SM (fewer elements than SMs): 1024 threads; four per SM
+// (small leaves of many elements): 256; otherwise 512 (FP64 keeps 512 so that
+// its registers do not spill)
 template <class TS, int MINB> constexpr int panel_threads() {
-    return (MINB == 1 && sizeof(TS) == 4) ? 2 * PANEL_THREADS : PANEL_THREADS;
+    return (MINB == 1 && sizeof(TS) == 4) ? 2 * PANEL_THREADS : MINB == 4 ? PANEL_THREADS / 2 : PANEL_THREADS;
 }
 
 template <class TS, int IB, int MINB>
@@ -684,14 +685,17 @@ solve_kernel(const TS* __restrict__ Sall, int64_t ld, const int32_t* __restrict_
 }
 
 // sub-panel width: the whole leaf when its (ld - c) x 32 block fits in the
-// shared-memory budget, else the widest of 8, 4, 2, 1 that fits (16 would
-// need more registers than the left-looking step can hold)
+// shared-memory budget of one CTA (ctas per SM: 1, 2 or 4), else the widest
+// of 8, 4, 2, 1 that fits (16 would need more registers than the left-looking
+// step can hold)
 template <class TS>
-int pick_ib(int64_t rows, bool two_per_sm) {
+int pick_ib(int64_t rows, int ctas) {
     // with more elements than SMs, two CTAs per SM (the leaf is latency-bound:
     // a second element's leaf hides the barriers of the first) as long as the
     // sub-panel stays >= 4 wide; otherwise the widest sub-panel that fits
-    const size_t budget1 = 200 * 1024, budget = two_per_sm ? 100 * 1024 : budget1;
+    // (four per SM: 47 KB, so that four CTAs with their up to 8.4 KB of static
+    // shared memory and the 1 KB each that the driver keeps fit in 228 KB)
+    const size_t budget1 = 200 * 1024, budget = ctas == 4 ? 47 * 1024 : ctas == 2 ? 100 * 1024 : budget1;
     if ((size_t)LEAF * rows * sizeof(TS) <= budget) return LEAF;
     int ib = 8;
     while (ib > 4 && (size_t)ib * rows * sizeof(TS) > budget) ib >>= 1;
@@ -699,32 +703,52 @@ int pick_ib(int64_t rows, bool two_per_sm) {
     return ib;
 }
 
+// Leaf CTAs per SM: 1 (1024 threads, up to 200 KB), 2 (512 threads, 100 KB)
+// or 4 (256 threads, 47 KB: with more than two elements per SM a leaf launch
+// then runs in one wave instead of two, for the FP32 leaves whose sub-panel of
+// at least 8 columns fits -- at most 1504 rows; taller ones take 2, since
+// 4-column sub-panels there measured slower than two CTAs with 8).  leaf_ctas
+// 0 chooses from the element count; MEHDG_LEAF_CTAS_PER_SM (1, 2 or 4)
+// overrides it.
 template <class TS>
 cudaError_t launch_panel(TS* S, int64_t ld, int c, int32_t* piv, int32_t* status, int64_t nK, int leaf_ctas,
                          cudaStream_t st) {
     int dev = 0, nsm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    bool two = leaf_ctas == 1 ? false : leaf_ctas == 2 ? true : nK > nsm;
-    // MEHDG_LEAF_CTAS_PER_SM (1 or 2) overrides the choice, e.g. to test or
-    // profile the two-CTA leaves on a mesh with fewer elements than SMs
+    int ctas = (leaf_ctas == 1 || leaf_ctas == 2 || leaf_ctas == 4) ? leaf_ctas
+             : nK > 2 * nsm ? 4 : nK > nsm ? 2 : 1;
     if (const char* f = std::getenv("MEHDG_LEAF_CTAS_PER_SM")) {
         const int v = std::atoi(f);
-        if (v == 1 || v == 2) two = v == 2;
+        if (v == 1 || v == 2 || v == 4) ctas = v;
     }
-    int ib = pick_ib<TS>(ld - c, two);
+    if (ctas == 4 && (sizeof(TS) != 4 || pick_ib<TS>(ld - c, 4) < 8)) ctas = 2;
+    const int ib = pick_ib<TS>(ld - c, ctas);
     size_t sm = (size_t)ib * (ld - c) * sizeof(TS);
     if (sm < 16) sm = 16;
-    // two CTAs per SM: registers capped at 64 per thread; one: up to 128
+    // registers: 64 per thread with two or four CTAs per SM, up to 128 with one
 #define LP2(IB, MB) do { cudaFuncSetAttribute(panel_kernel<TS, IB, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
                          panel_kernel<TS, IB, MB><<<(unsigned)nK, panel_threads<TS, MB>(), sm, st>>>(S, ld, c, piv, status); } while (0)
-#define LP(IB) do { if (two) LP2(IB, 2); else LP2(IB, 1); } while (0)
-    switch (ib) {
-    case 32: LP(32); break;
-    case 8: LP(8); break;
-    case 4: LP(4); break;
-    case 2: LP(2); break;
-    default: LP(1); break;
+#define LP(IB) do { if (ctas == 2) LP2(IB, 2); else LP2(IB, 1); } while (0)
+    if constexpr (sizeof(TS) == 4) {
+        if (ctas == 4) {
+            switch (ib) {
+            case 32: LP2(32, 4); break;
+            case 8: LP2(8, 4); break;
+            default: LP2(4, 4); break;
+            }
+            MEHDG_COUNT(1);
+            return cudaGetLastError();
+        }
+    }
+    {
+        switch (ib) {
+        case 32: LP(32); break;
+        case 8: LP(8); break;
+        case 4: LP(4); break;
+        case 2: LP(2); break;
+        default: LP(1); break;
+        }
     }
 #undef LP
 #undef LP2

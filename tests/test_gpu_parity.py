@@ -184,13 +184,17 @@ def bench_lu_case():
     return mesh, st, dvh, ref
 
 
-@pytest.mark.parametrize("prec", [4, 3])
-def test_condense_at_bench_lu_configuration_matches_oracle(bench_lu_case, prec):
+@pytest.mark.parametrize("prec,leaf", [(4, 0), (3, 0), (4, 4)])
+def test_condense_at_bench_lu_configuration_matches_oracle(bench_lu_case, prec, leaf, monkeypatch):
     """p = 3, m = 3 (N_v = 5000, ld = 5120) with more elements than SMs: the
     LU runs the leaf variants the benchmark runs (two 512-thread CTAs per SM,
-    4-, 8- and 32-column sub-panels) and the one-CTA-per-element solve.
-    b-hat^K (its faces are unshared, so the global b-hat on them is b-hat^K)
-    and the recovered dV^K are compared element by element."""
+    4-, 8- and 32-column sub-panels; with leaf = 4 also the four 256-thread
+    CTAs per SM that the leaves of at most 1504 rows take with more than two
+    elements per SM) and the one-CTA-per-element solve.  b-hat^K (its faces
+    are unshared, so the global b-hat on them is b-hat^K) and the recovered
+    dV^K are compared element by element."""
+    if leaf:
+        monkeypatch.setenv("MEHDG_LEAF_CTAS_PER_SM", str(leaf))
     mesh, st, dvh_np, ref = bench_lu_case
     ctx = M().Context(mesh, flux=2, prec=prec, Mach=0.1)
     ctx.set_state(*to_dev(st))
