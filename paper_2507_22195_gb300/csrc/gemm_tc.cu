@@ -146,8 +146,13 @@ constexpr size_t stream_smem_bytes() { return (size_t)n_stages<BN, SPLIT>() * st
 
 // SPLIT: the panels hold [hi | lo] (lo at K offset kpa in A, kpb in B); each
 // chunk is loaded once per part and takes the three products hi hi, hi lo, lo hi.
+// STORE (the TRSM product, split TF32): B arrives as plain FP32 rows and two
+// more warps split each chunk in shared memory (hi in place, lo beside it)
+// before the MMAs take it.
+constexpr int CONV_WARPS = 2;
+template <bool STORE> constexpr int stream_threads() { return 64 + 32 * EPI_WARPS + (STORE ? 32 * CONV_WARPS : 0); }
 template <int BN, bool BF16, bool STORE, bool SPLIT>
-__global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
+__global__ void __launch_bounds__(stream_threads<STORE>(), 1)
 tc_stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                  float* __restrict__ Sall, int64_t ld, int r0, int c0, int M, int N, int nchunk, int kpa, int kpb,
                  int tiles_m, int tiles_n, int64_t ntiles, int32_t* status, BqOut bo) {
@@ -160,16 +165,18 @@ tc_stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
     constexpr uint32_t ID = idesc(TM, BN, BF16 ? 1u : 2u);
     constexpr int NH = BN / 32;                    // column groups per lane quarter
     constexpr int W = 32;                          // columns per epilogue warp
+    constexpr bool CONVB = STORE;                  // B split in shared memory
+    static_assert(!CONVB || (SPLIT && !BF16), "the TRSM product is split TF32");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     // slot s: [A hi | A lo | B hi | B lo] (lo parts only when split)
-    __shared__ uint64_t full[SSTAGES], empty[SSTAGES], acc_full[2], acc_empty[2];
+    __shared__ uint64_t full[SSTAGES], empty[SSTAGES], conv[SSTAGES], acc_full[2], acc_empty[2];
     __shared__ uint32_t tmem_slot;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tiles_e = tiles_m * tiles_n;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < SSTAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        for (int s = 0; s < SSTAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); mbar_init(&conv[s], CONV_WARPS); }
         for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], EPI_WARPS); }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -194,12 +201,13 @@ tc_stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
                     const int s = (int)(g % SSTAGES);
                     if (g >= SSTAGES && !mbar_wait(&empty[s], ((g / SSTAGES) - 1) & 1)) { ok = false; break; }
                     unsigned char* slot = smem + (size_t)s * STG;
-                    mbar_expect_tx(&full[s], STG);
+                    mbar_expect_tx(&full[s], CONVB ? STG - B_BYTES : STG);
                     tma_load_3d(slot, &mapA, &full[s], c * CHUNK_K, tm * TM, K);
                     tma_load_3d(slot + NP * A_BYTES, &mapB, &full[s], c * CHUNK_K, tn * BN, K);
                     if (SPLIT) {
                         tma_load_3d(slot + A_BYTES, &mapA, &full[s], kpa + c * CHUNK_K, tm * TM, K);
-                        tma_load_3d(slot + NP * A_BYTES + B_BYTES, &mapB, &full[s], kpb + c * CHUNK_K, tn * BN, K);
+                        if (!CONVB)
+                            tma_load_3d(slot + NP * A_BYTES + B_BYTES, &mapB, &full[s], kpb + c * CHUNK_K, tn * BN, K);
                     }
                 }
                 if (!ok) { if (status) status[K] = MEHDG_ETIMEOUT; break; }
@@ -216,7 +224,7 @@ tc_stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
                 const uint32_t d = tmem + (uint32_t)(b * BN);
                 for (int c = 0; ok && c < nchunk; ++c, ++g) {
                     const int s = (int)(g % SSTAGES);
-                    if (!mbar_wait(&full[s], (g / SSTAGES) & 1)) { ok = false; break; }
+                    if (!mbar_wait(CONVB ? &conv[s] : &full[s], (g / SSTAGES) & 1)) { ok = false; break; }
                     tc_fence_after();
                     unsigned char* slot = smem + (size_t)s * STG;
                     const uint64_t da = sdesc(s_addr(slot));
@@ -236,6 +244,37 @@ tc_stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
                 if (!ok) { if (status) status[K] = MEHDG_ETIMEOUT; break; }
                 umma_commit(&acc_full[b]);
             }
+        }
+    } else if (CONVB && warp >= 2 + EPI_WARPS) {
+        // the B chunk of each slot, FP32 as loaded, into hi (in place) and lo
+        // (the next B_BYTES): the same offsets, so the swizzled layout carries over
+        const int ct = (warp - 2 - EPI_WARPS) * 32 + lane;
+        uint32_t g = 0;
+        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            const int K = (int)(t / tiles_e);
+            bool ok = true;
+            for (int c = 0; c < nchunk; ++c, ++g) {
+                const int s = (int)(g % SSTAGES);
+                if (!mbar_wait(&full[s], (g / SSTAGES) & 1)) { ok = false; break; }
+                float4* hb = reinterpret_cast<float4*>(smem + (size_t)s * STG + NP * A_BYTES);
+                float4* lb = reinterpret_cast<float4*>(smem + (size_t)s * STG + NP * A_BYTES + B_BYTES);
+#pragma unroll 4
+                for (int i = ct; i < B_BYTES / 16; i += 32 * CONV_WARPS) {
+                    const float4 v = hb[i];
+                    float4 h, l;
+                    h.x = tf32_rn(v.x); l.x = tf32_rn(v.x - h.x);
+                    h.y = tf32_rn(v.y); l.y = tf32_rn(v.y - h.y);
+                    h.z = tf32_rn(v.z); l.z = tf32_rn(v.z - h.z);
+                    h.w = tf32_rn(v.w); l.w = tf32_rn(v.w - h.w);
+                    hb[i] = h;
+                    lb[i] = l;
+                }
+                // the tensor cores read shared memory through the async proxy
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&conv[s]);
+            }
+            if (!ok) { if (lane == 0 && status) status[K] = MEHDG_ETIMEOUT; break; }
         }
     } else {
         // lane quarter q, column group h (and h + 4 when BN = 256: the second
@@ -276,21 +315,16 @@ tc_stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
                     }
                 }
                 if (hh < NH && !STORE && bo.p) {
-                    // an update whose result is the next TRSM's B operand: C - D as split
-                    // TF32 [hi | lo] rows (row = its K index), S left as it is
+                    // an update whose result is the next TRSM's B operand: C - D as FP32
+                    // rows of kp entries (row = its K index), S left as it is
                     uint32_t r[32];
                     tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + hh * W), r);
                     float* qf = reinterpret_cast<float*>(bo.p) +
-                                ((size_t)K * bo.nc + bo.c0 + col0) * (size_t)(2 * bo.kp) + bo.k0 + row;
+                                ((size_t)K * bo.nc + bo.c0 + col0) * (size_t)bo.kp + bo.k0 + row;
 #pragma unroll
                     for (int j = 0; j < W; ++j) {
-                        if (j < nc) {
-                            const float v = cv[j] - __uint_as_float(r[j]);
-                            const float hi = tf32_rn(v);
-                            qf[0] = hi;
-                            qf[bo.kp] = tf32_rn(v - hi);
-                        }
-                        qf += 2 * bo.kp;
+                        if (j < nc) qf[0] = cv[j] - __uint_as_float(r[j]);
+                        qf += bo.kp;
                     }
                 } else if (hh < NH) {
                     uint32_t r[32];
@@ -528,7 +562,7 @@ cudaError_t launch_stream(const CUtensorMap& a, const CUtensorMap& b, const LUPl
     auto kern = tc_stream_kernel<BN, BF16, STORE, SPLIT>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sm_count());
-    kern<<<(unsigned)grid, 64 + 32 * EPI_WARPS, sm, st>>>(a, b, (float*)P.S, P.ld, r0, c0, M, N, nchunk, kpa, kpb,
+    kern<<<(unsigned)grid, stream_threads<STORE>(), sm, st>>>(a, b, (float*)P.S, P.ld, r0, c0, M, N, nchunk, kpa, kpb,
                                                          tiles_m, tiles_n, ntiles, P.status, bo);
     MEHDG_COUNT(1);
     return cudaGetLastError();
@@ -627,8 +661,9 @@ trtri256_kernel(const float* __restrict__ Sall, int64_t ld, int c0, int nseg, vo
 // packing of the TRSM's B operand: one warp per column gathers the rows of
 // the net permutation (the 256 block rows and the rows below that take
 // part), writes the rows below that change, and writes the new block rows
-// as the split-TF32 panel Bp[K][n][hi 256 | lo 256].  The block rows of S are
-// not written back: the TRSM product overwrites them.
+// to the FP32 panel Bp[K][n][256] (the TRSM product splits them in shared
+// memory).  The block rows of S are not written back: the TRSM product
+// overwrites them.
 __global__ void __launch_bounds__(256)
 laswp_pack_kernel(float* __restrict__ Sall, int64_t ld, const int32_t* __restrict__ perm, int j0, int N,
                   float* __restrict__ Bp) {
@@ -656,17 +691,12 @@ laswp_pack_kernel(float* __restrict__ Sall, int64_t ld, const int32_t* __restric
         for (int u = 0; u < 4; ++u) { const int i = i0 + 32 * u; if (i < nr) b[i] = v[u]; }
     }
     __syncwarp();
-    float* out = Bp + ((size_t)K * N + n) * (size_t)(2 * LU_NB);
+    float* out = Bp + ((size_t)K * N + n) * (size_t)LU_NB;
     for (int i = lane; i < nr; i += 32) {
         const int ci = cont[i];
         const float v = b[ci];
-        if (i < LU_NB) {
-            const float hi = tf32_rn(v);
-            out[i] = hi;
-            out[LU_NB + i] = tf32_rn(v - hi);
-        } else if (ci != i) {
-            Sc[rows[i]] = v;
-        }
+        if (i < LU_NB) out[i] = v;
+        else if (ci != i) Sc[rows[i]] = v;
     }
 }
 
@@ -675,7 +705,7 @@ laswp_pack_kernel(float* __restrict__ Sall, int64_t ld, const int32_t* __restric
 // Rows [c0, c0+256) of the columns [j0, j1): U12 = L11^-1 A12 on the tensor
 // cores, through the explicit inverse of the unit-lower block L11.
 namespace {
-// the TRSM product with B = rows [c0, c0+256) of the columns [j0, j0+N), packed in Bp
+// the TRSM product with B = rows [c0, c0+256) of the columns [j0, j0+N), FP32 in Bp
 cudaError_t trsm256_product(const LUPlan& P, int c0, int j0, int N, void* Ap, void* Bp, const BqOut* bq,
                             cudaStream_t st) {
     const int Kd = LU_NB, nseg = 2, nchunk = Kd / (CHUNK_BYTES / 4);
@@ -686,7 +716,8 @@ cudaError_t trsm256_product(const LUPlan& P, int c0, int j0, int N, void* Ap, vo
     }
     const int BN = N >= 128 ? 128 : (N >= 64 ? 64 : 32);
     CUtensorMap ma, mb;
-    if (!make_map(&ma, Ap, false, nseg * Kd, 256, P.nK, TM) || !make_map(&mb, Bp, false, nseg * Kd, N, P.nK, BN))
+    // B: plain FP32 rows of 256 (split by the kernel's converter warps)
+    if (!make_map(&ma, Ap, false, nseg * Kd, 256, P.nK, TM) || !make_map(&mb, Bp, false, Kd, N, P.nK, BN))
         return cudaErrorInvalidValue;
     return launch_stream_bn<false, true, true>(BN, ma, mb, P, c0, j0, 256, N, nchunk, Kd, Kd, st,
                                                bq ? *bq : BqOut());

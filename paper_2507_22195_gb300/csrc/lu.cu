@@ -934,7 +934,7 @@ cudaError_t factor_t(const LUPlan& P, cudaStream_t st) {
 //      of b then hold rows of A not yet updated by a: subtract their part
 //      L_a(src) U_a, with the multipliers L_a of the rows they came from (a's
 //      columns are not exchanged by P_b), the result going straight to the
-//      TRSM's split-TF32 B operand;
+//      TRSM's B operand;
 //   4. U_b = L_bb^-1 (those rows) by the TRSM product (K entries 256..511 of
 //      the same B operand);
 //   5. one update of R's rows below b with depth 512: [L_a | L_b] [U_a; U_b],
@@ -981,7 +981,7 @@ cudaError_t factor_pairs(const LUPlan& P, cudaStream_t st) {
         const PackedB b{bq, n1, LU_NB, KP2};
         {
             // the block rows of b (a's multipliers of the rows they came from),
-            // corrected and written as the TRSM's split-TF32 B operand
+            // corrected and written as the TRSM's FP32 B operand
             const int evp = prof_begin(P.prof, PH_PACK_OUTER, st);
             if ((e = gemm_tc_gather_a2(P, n1, KP2, cb, ca, AGather{pb, LU_NB, 0, LU_NB}, st)) != cudaSuccess)
                 return e;

@@ -39,8 +39,9 @@ struct PackedA {
 // The TRSM product's copy of U12 as the next update's B operand (split BF16):
 // per element nc rows of [hi (kp) | lo (kp)]; product column n goes to row
 // c0 + n, its K index k (the row inside the 256 block) to entry k0 + k.  Given
-// to an update (split BF16), the same layout receives C - D in split TF32 (a
-// float panel: the next TRSM product's B operand) and S is not written.
+// to an update (split BF16), C - D goes instead to FP32 rows of kp entries
+// (row c0 + n, entry k0 + k: the next TRSM product's B operand) and S is not
+// written.
 struct BqOut {
     void* p = nullptr;
     int nc = 0, c0 = 0, k0 = 0, kp = 0;
@@ -52,7 +53,7 @@ struct BqOut {
 // recorded with it) and the operand packing under ph_pack.
 // b: the B panel already packed (split BF16) by a TRSM product, or null;
 // g: A rows gathered through a net permutation, or null
-// out: the result as the next TRSM's split-TF32 B operand instead of into S, or null;
+// out: the result as the next TRSM's FP32 B operand instead of into S, or null;
 // a: the A operand already packed (then g must be null), or null
 cudaError_t gemm_tc_update(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st,
                            int ph_pack = -1, int ph_gemm = -1, double flops = 0.0, const PackedB* b = nullptr,
@@ -71,7 +72,7 @@ cudaError_t gemm_tc_gather_a2(const LUPlan& P, int erows, int kp, int r0, int k0
 size_t gemm_tc_work_bytes(int64_t nK, int64_t ld, int prec);
 // The next update's B panel of the split-BF16 mode (written by the TRSM products)
 void* gemm_tc_bq_panel(const LUPlan& P);
-// The TRSM's split-TF32 B panel ([nK][columns][hi 256 | lo 256] floats)
+// The TRSM's FP32 B panel ([nK][columns][256] floats; the product splits it)
 void* gemm_tc_bp_panel(const LUPlan& P);
 // Row exchanges of the columns right of outer panel c0 by its net permutation
 // (perm: [nK][LU_PW]) and the TRSM of their rows [c0, c0+256), fused.  bq:
@@ -79,6 +80,6 @@ void* gemm_tc_bp_panel(const LUPlan& P);
 // written; only the split-BF16 mode has it).
 cudaError_t gemm_tc_swap_trsm256(const LUPlan& P, const int32_t* perm, int c0, cudaStream_t st, const BqOut* bq);
 // The TRSM of rows [c0, c0+256) of the columns right of them, with its B
-// operand already in the split-TF32 panel (written by an update with out set)
+// operand already in the FP32 B panel (written by an update with out set)
 cudaError_t gemm_tc_trsm256(const LUPlan& P, int c0, cudaStream_t st, const BqOut* bq);
 cudaError_t gemm_simt_update_f32(const LUPlan& P, int r0, int c0, int k0, int M, int N, int Kd, cudaStream_t st);
