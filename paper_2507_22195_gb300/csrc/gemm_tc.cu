@@ -753,7 +753,7 @@ cudaError_t gemm_tc_swap_trsm256(const LUPlan& P, const int32_t* perm, int c0, c
 }
 
 // The TRSM product alone, with its B operand (rows [c0, c0+256) of the
-// columns right of them) already in the split-TF32 panel
+// columns right of them) already in the FP32 B panel
 cudaError_t gemm_tc_trsm256(const LUPlan& P, int c0, cudaStream_t st, const BqOut* bq) {
     const int j0 = c0 + LU_NB, N = (int)P.ld - j0;
     if (N <= 0) return cudaSuccess;
