@@ -406,22 +406,31 @@ laswp_kernel(TS* __restrict__ Sall, int64_t ld, const int32_t* __restrict__ perm
 // ---------------------------------------------------------------- TRSM
 // X = L^-1 X for X = rows [c0, c0+t) of columns [j0, j1), L = unit-lower
 // S[c0:c0+t, c0:c0+t].  One CTA per 32 columns; 256 threads = 32 cols x 8.
+// Loads and stores of X and of the diagonal blocks run with consecutive
+// threads on consecutive rows of a column (coalesced in column-major S); X
+// and the blocks are padded to 33 columns in shared memory.
+constexpr int TRSM_XS = 33;
 template <class TS>
 __global__ void __launch_bounds__(256)
 trsm_kernel(TS* __restrict__ Sall, int64_t ld, int c0, int t, int j0, int j1) {
     const int K = blockIdx.y;
     TS* S = Sall + (size_t)K * ld * ld;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    TS* X = reinterpret_cast<TS*>(smem_raw);        // [t][32]
-    TS* Lo = X + (size_t)t * 32;                     // [t - 32][33]: L below the diagonal block
+    TS* X = reinterpret_cast<TS*>(smem_raw);        // [t][33]
+    TS* Lo = X + (size_t)t * TRSM_XS;                // [t - 32][33]: L below the diagonal block
     __shared__ TS Lb[32][33];
     const int tc = threadIdx.x & 31, tr = threadIdx.x >> 5;
-    const int col = j0 + blockIdx.x * 32 + tc;
-    const bool act = col < j1;
-    for (int i = tr; i < t; i += 8) X[i * 32 + tc] = act ? S[(size_t)(c0 + i) + (size_t)col * ld] : (TS)0;
+    const int cb = j0 + blockIdx.x * 32;             // first column of this CTA
+    for (int e = threadIdx.x; e < t * 32; e += 256) {
+        const int i = e % t, cc = e / t;
+        X[i * TRSM_XS + cc] = cb + cc < j1 ? S[(size_t)(c0 + i) + (size_t)(cb + cc) * ld] : (TS)0;
+    }
     __syncthreads();
     for (int rb = 0; rb < t; rb += 32) {
-        for (int i = tr; i < 32; i += 8) Lb[i][tc] = S[(size_t)(c0 + rb + i) + (size_t)(c0 + rb + tc) * ld];
+        for (int e = threadIdx.x; e < 32 * 32; e += 256) {
+            const int i = e & 31, q = e >> 5;
+            Lb[i][q] = S[(size_t)(c0 + rb + i) + (size_t)(c0 + rb + q) * ld];
+        }
         // the L rows below the block, staged with coalesced loads (lane = row)
         for (int i0 = rb + 32; i0 < t; i0 += 32)
             for (int q = tr; q < 32; q += 8)
@@ -434,26 +443,28 @@ trsm_kernel(TS* __restrict__ Sall, int64_t ld, int c0, int t, int j0, int j1) {
             // independent updates per step instead of one dependent chain)
             TS x[32];
 #pragma unroll
-            for (int i = 0; i < 32; ++i) x[i] = X[(rb + i) * 32 + tc];
+            for (int i = 0; i < 32; ++i) x[i] = X[(rb + i) * TRSM_XS + tc];
 #pragma unroll
             for (int q = 0; q < 31; ++q)
 #pragma unroll
                 for (int i = q + 1; i < 32; ++i) x[i] -= Lb[i][q] * x[q];
 #pragma unroll
-            for (int i = 1; i < 32; ++i) X[(rb + i) * 32 + tc] = x[i];
+            for (int i = 1; i < 32; ++i) X[(rb + i) * TRSM_XS + tc] = x[i];
         }
         __syncthreads();
         for (int i = rb + 32 + tr; i < t; i += 8) {
-            TS s = X[i * 32 + tc];
+            TS s = X[i * TRSM_XS + tc];
             const TS* Lr = Lo + (i - 32) * 33;
 #pragma unroll 8
-            for (int q = 0; q < 32; ++q) s -= Lr[q] * X[(rb + q) * 32 + tc];
-            X[i * 32 + tc] = s;
+            for (int q = 0; q < 32; ++q) s -= Lr[q] * X[(rb + q) * TRSM_XS + tc];
+            X[i * TRSM_XS + tc] = s;
         }
         __syncthreads();
     }
-    if (act)
-        for (int i = tr; i < t; i += 8) S[(size_t)(c0 + i) + (size_t)col * ld] = X[i * 32 + tc];
+    for (int e = threadIdx.x; e < t * 32; e += 256) {
+        const int i = e % t, cc = e / t;
+        if (cb + cc < j1) S[(size_t)(c0 + i) + (size_t)(cb + cc) * ld] = X[i * TRSM_XS + cc];
+    }
 }
 
 // ---------------------------------------------------------------- SIMT GEMM
@@ -786,7 +797,7 @@ cudaError_t launch_laswp_perm(const LUPlan& P, const int32_t* perm, int w, int j
 template <class TS>
 cudaError_t launch_trsm(const LUPlan& P, int c0, int t, int j0, int j1, cudaStream_t st) {
     if (j1 <= j0) return cudaSuccess;
-    size_t sm = ((size_t)t * 32 + (size_t)(t > 32 ? t - 32 : 0) * 33) * sizeof(TS);
+    size_t sm = ((size_t)t * TRSM_XS + (size_t)(t > 32 ? t - 32 : 0) * 33) * sizeof(TS);
     cudaFuncSetAttribute(trsm_kernel<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     dim3 g((unsigned)((j1 - j0 + 31) / 32), (unsigned)P.nK);
     trsm_kernel<TS><<<g, 256, sm, st>>>((TS*)P.S, P.ld, c0, t, j0, j1);
