@@ -235,7 +235,7 @@ def once_main(a):
 # panel's 256 columns, "rows": the depth-256 correction of its 256 block rows.
 # A kind not captured since its kernel last changed has no entry, and the
 # traffic is then reported as null.
-TRAFFIC_RATIO = {"bf16x3": {"merged": 0.988, "cols": 0.867}}
+TRAFFIC_RATIO = {"bf16x3": {"merged": 0.988, "cols": 0.867, "rows": 0.870}}
 # tensor rate of a precision mode relative to BF16 (nominal dense GB300 rates:
 # TF32 1.1, BF16 2.25 PFLOP/s) and the tensor products per method flop
 TENSOR_RATE = {"bf16": 1.0, "bf16x3": 1.0, "tf32": 1.1 / 2.25, "tf32x3": 1.1 / 2.25}
