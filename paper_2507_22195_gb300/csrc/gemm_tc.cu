@@ -5,19 +5,22 @@
 //
 // 1. pack: L (M x Kd) and U (Kd x N) are copied into K-major operand panels
 //    in the operand type (TF32 rounded to nearest, or BF16), zero-padded in K
-//    to whole 128-byte rows;
+//    to whole 128-byte rows (or taken from panels that earlier kernels wrote:
+//    the TRSM product's copy of U12, a merged pair's multipliers);
 // 2. MMA: a persistent kernel, one CTA per SM, walks the 128 x BN tiles of C
-//    (BN = 128, or 32/64 for narrow updates) of all elements.  Warp 0 (one
-//    lane) streams 128-byte K-chunks of both panels into a 6-slot
-//    shared-memory ring with TMA (128B swizzle, mbarrier transaction counts);
-//    warp 1 (one lane) issues tcgen05.mma (kind::tf32 or kind::f16) into one
-//    of two TMEM accumulators and releases each ring slot with
-//    tcgen05.commit;
+//    (BN = 256 for split-BF16 updates at least 256 wide, else 128, or 32/64
+//    for narrow updates) of all elements.  Warp 0 (one lane) streams 128-byte
+//    K-chunks of both panels into a shared-memory ring with TMA (128B
+//    swizzle, mbarrier transaction counts); warp 1 (one lane) issues
+//    tcgen05.mma (kind::tf32 or kind::f16) into one of two TMEM accumulators
+//    and releases each ring slot with tcgen05.commit;
 // 3. epilogue: sixteen warps, four per TMEM lane quarter (32 rows), each on
-//    32 columns: C is read before the accumulator is ready, then C - D is
-//    written in place (32 consecutive rows per warp and column: coalesced
-//    128-byte accesses).  The epilogue of one tile runs while the MMAs of the
-//    next tile fill the other accumulator.
+//    32 columns (two such groups at BN = 256): C is read before the
+//    accumulator is ready, then C - D is written in place (32 consecutive rows
+//    per warp and column: coalesced 128-byte accesses).  The epilogue of one
+//    tile runs while the MMAs of the next tile fill the other accumulator.
+// The TRSM product (store mode) writes the product instead of C - D, and two
+// more warps split its FP32 B operand into TF32 hi and lo in shared memory.
 // Every mbarrier wait is bounded; on timeout the element's status becomes
 // MEHDG_ETIMEOUT, the loops end and TMEM is still released.
 #include <cuda.h>
@@ -116,16 +119,20 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
 
 // ---------------------------------------------------------------- streaming kernel
 // Persistent form of the update: one CTA per SM walks the tiles
-// (element-major, then column tiles, then row tiles) with ten warps:
-//   warp 0 (one lane)  TMA: operand chunks into a 6-slot ring;
+// (element-major, then column tiles, then row tiles) with eighteen warps
+// (twenty in store mode):
+//   warp 0 (one lane)  TMA: operand chunks into the ring (up to 6 slots; 3 in
+//                      the split modes, 2 at BN = 256);
 //   warp 1 (one lane)  tcgen05.mma into one of two TMEM accumulators (2 x BN
 //                      columns); the whole warp owns the TMEM allocation;
 //   warps 2-17         epilogue: four warps per TMEM lane quarter, each on
-//                      32 of the tile's columns (BN / 32 of them active).  A
-//                      warp fetches its C values for the next tile before it
-//                      waits for that tile's accumulator, so the C reads (32
-//                      per thread in flight) overlap the MMAs, and the stores
-//                      of one tile overlap the MMAs of the next.
+//                      32 of the tile's columns (BN / 32 groups; a warp takes
+//                      two at BN = 256).  A warp fetches its C values for the
+//                      next tile before it waits for that tile's accumulator,
+//                      so the C reads (32 per thread in flight) overlap the
+//                      MMAs, and the stores of one tile overlap the MMAs of
+//                      the next;
+//   warps 18-19        store mode only: split each B chunk in shared memory.
 // Every mbarrier wait is bounded; a warp that times out records
 // MEHDG_ETIMEOUT and leaves its loop, the others time out in turn, and TMEM
 // is released after the final barrier.
