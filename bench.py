@@ -351,9 +351,10 @@ def subset_compare(mesh, st, kw, dev, n_s, prec, barrier, M):
 
 
 def viscous_wave(block, dev, barrier, M, steps=2):
-    """configs[2]: one wave of the viscous TGV (a block^3 block of the 16^3 x
-    4^3 mesh, p = 3; block 7 holds 166 GB of FP32 S, under 60 % of HBM) in
-    split BF16 and split TF32, and the FP64 GPU path on its first 8 elements"""
+    """one wave of the viscous TGV workload (Re 1600, 16^3 macro-elements of
+    4^3, p = 3): a block^3 block of it (block 7 holds 166 GB of FP32 S, under
+    60 % of HBM) in split BF16 and split TF32, and the FP64 GPU path on its
+    first 8 elements"""
     mesh, st, kw = workload("tgv_viscous", block=block)
     out = {"workload": f"viscous TGV Re=1600, {block}^3 block of the 16^3 x 4^3 mesh, p=3, ES",
            "nK": mesh.nK, "N_v": 5 * mesh.Nn, "steps": steps, "warmup": 1}
@@ -376,7 +377,7 @@ def viscous_wave(block, dev, barrier, M, steps=2):
 
 
 def uneven_batch(nK, dev, barrier, M, sample_per_group=2):
-    """configs[4]: nK macro-elements with p in {1..4} and m in {2, 3, 4}
+    """the uneven batch workload: nK macro-elements with p in {1..4} and m in {2, 3, 4}
     drawn with seed 22199, each a TGV-like field with its own Mach number
     M0 ~ U(0.1, 0.3) plus U(-1e-2, 1e-2), viscous (Re 1600, Pr 0.71), ES flux,
     split BF16 with FP64 refinement: autotuned, then one timed condensation of
@@ -451,7 +452,7 @@ def uneven_batch(nK, dev, barrier, M, sample_per_group=2):
 
 def graph_condense(dev, barrier, M, steps=20):
     """direct calls against the condensation replayed from one CUDA graph, on
-    two launch-bound cases: the 2^3 x 2^3, p = 2 vortex (configs[0], 8
+    two launch-bound cases: the 2^3 x 2^3, p = 2 isentropic vortex (8
     elements) and a resident batch of 2048 elements with p in {1, 2, 3} and
     m in {2, 3} (seed 22204; inviscid TGV-like fields, ES, split BF16)"""
     import torch
@@ -545,9 +546,9 @@ def main():
                          f"b-hat, dV), one per spawned process, {dt:.1f} s wall",
                "single_core": {"value": 1.0 / statistics.mean(per), "unit": UNIT,
                                "what": "1 / mean seconds per element of one process while all cores are busy"},
-               "configs0_vortex": {"value": vval, "single_core": 1.0 / statistics.mean(vper), "unit": UNIT,
+               "vortex_2x2x2_p2": {"value": vval, "single_core": 1.0 / statistics.mean(vper), "unit": UNIT,
                                    "sample": f"all {vmesh.nK} elements of the 2^3 x 2^3, p = 2 vortex (ES)"},
-               "configs2_viscous": "not timed: the oracle's dense A_qq of a p = 3, m = 4 element is 8.7 GB and "
+               "viscous_tgv_p3m4": "not timed: the oracle's dense A_qq of a p = 3, m = 4 element is 8.7 GB and "
                                    "its GEPP alone is 2.4e13 flop (hours on one core)"}
 
     import numpy as np

@@ -111,7 +111,7 @@ def _oracle_condensed(prm, mesh, st, dvh, key=None):
 
 
 CONDENSE_CASES = [(nm, 2, pr) for nm in ("vortex_p2m1", "vortex_p2m2", "tgv_p3m2") for pr in (0, 1, 2, 3, 4)]
-# the other fluxes of configs[0] (EC, ES on the vortex) and configs[1] (EC on the TGV)
+# the other fluxes of the vortex workload (EC, ES) and of the inviscid TGV workload (EC)
 CONDENSE_CASES += [(nm, fl, pr) for nm, fl in (("vortex_p2m2", 0), ("vortex_p2m2", 1), ("tgv_p3m2", 0))
                    for pr in (0, 3, 4)]
 
